@@ -1,0 +1,188 @@
+/*
+ * pm.h - C ABI of the GB300 particle-mesh step with quantum pressure.
+ *
+ * Method: Veltmaat & Niemeyer, "Cosmological particle-in-cell simulations with
+ * ultralight axion dark matter", arXiv:1608.00802, Sec. II.A and Sec. III.
+ * Each step (i) deposits the particle density on a periodic mesh with a
+ * kernel estimate (Eq. rhodis; here the cloud-in-cell kernel), (ii) solves
+ * the gravity potential and evaluates the quantum pressure
+ * Q = -(hbar^2/2m^2) lap(sqrt rho)/sqrt rho (Eq. quantumpressure, comoving
+ * form Eq. comquantumpressure) with a seven-point Laplacian, (iii) turns both
+ * potentials into particle forces (central mesh gradient or the kernel-gradient
+ * form of Eq. equationofmotion) inside a kick-drift-kick leapfrog.
+ *
+ * Units: length Mpc/h, time 1/H0 (H0 = 1), mean comoving density 1 (so
+ * 4 pi G rho_bar = 3/2 Omega_m and a particle weighs box^3/n_part), momentum
+ * p = a^2 dx/dt.  Mesh node n sits at n*box/n_mesh; mesh arrays are
+ * row-major [z][y][x] with x fastest.  Static (non-cosmological) runs use
+ * a = 1 and take the time t where a cosmological run takes the scale factor.
+ *
+ * Memory and threads: the caller owns one device buffer (the arena, sized by
+ * pm_arena_bytes) and one CUDA stream; the library sub-allocates the arena and
+ * enqueues all work on that stream.  cuFFT keeps its plan tables in its own
+ * device memory; everything else lives in the arena.  Host arrays stay owned
+ * by the caller and are copied.  A pm_sim is used from one host thread at a
+ * time.  Entry points return a pm_status and never abort; pm_last_error gives
+ * the message of the last failure.  Calls marked "async" return once the
+ * work is enqueued; calls marked "sync" wait for the stream.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_ABI_VERSION 1
+
+typedef enum {
+  PM_OK = 0,
+  PM_ERR_INVALID_ARG = 1, /* a pointer, size or configuration value is out of range */
+  PM_ERR_NO_MEMORY = 2,   /* the arena passed to pm_create is smaller than pm_arena_bytes */
+  PM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in pm_last_error) */
+  PM_ERR_CUFFT = 4,       /* a cuFFT call failed */
+  PM_ERR_NONFINITE = 5,   /* a NaN/Inf reached a particle or a diagnostic */
+  PM_ERR_STATE = 6        /* call out of order (e.g. no particles set yet) */
+} pm_status;
+
+/* how a mesh potential becomes a particle force (Sec. II.A, step (iii)) */
+enum {
+  PM_FORCE_MESHGRAD = 0,   /* gravity and Q: central-difference mesh gradient, CIC-interpolated */
+  PM_FORCE_HYBRID = 1,     /* gravity as MESHGRAD; Q by Eq. equationofmotion (sum_n Q_n grad W) */
+  PM_FORCE_LAGRANGIAN = 2  /* gravity and Q by the kernel gradient: conserves the discrete energies */
+};
+/* seven-point Laplacian in Q (the operator named after Eq. equationofmotion) */
+enum {
+  PM_LAP_COMPACT = 0,      /* neighbours at +-dx; pairs with forward differences in K_rho */
+  PM_LAP_WIDE = 1          /* neighbours at +-2dx; pairs with the central differences of Eq. diskpoten */
+};
+enum { PM_FP32 = 0, PM_FP64 = 1 };
+enum { PM_FIELD_RHO = 0, PM_FIELD_PHI = 1, PM_FIELD_Q = 2 };
+
+typedef struct {
+  int64_t n_part;      /* number of particles, 1 .. 2^31-1 */
+  int32_t n_mesh;      /* N: the mesh has N^3 nodes; even, 8 .. 1024 */
+  int32_t precision;   /* PM_FP32: int32 cell + fp32 offset positions, fp32 mesh and FFT;
+                          PM_FP64: fp64 offsets, momenta, mesh and FFT */
+  double box;          /* periodic box side L [Mpc/h] */
+  double omega_m;      /* matter density today; 4 pi G rho_bar = 3/2 omega_m */
+  double omega_l;      /* cosmological constant today */
+  double h;            /* H0 / (100 km/s/Mpc), sets hbar/m in code units */
+  double m22;          /* axion mass / 1e-22 eV (Sec. II.A uses 2.5) */
+  int32_t quantum;     /* 0: quantum pressure off (CDM), 1: on */
+  int32_t force_mode;  /* PM_FORCE_* */
+  int32_t lap;         /* PM_LAP_* */
+  int32_t cosmological;/* 1: comoving equations with a(t); 0: static, a = 1 */
+  double rho_floor;    /* sqrt(rho) uses max(rho, rho_floor) (units of the mean); Q is
+                          undefined where rho = 0 (Sec. II.A) */
+  double rho_fp64;     /* PM_FP32 only: nodes with rho below this evaluate sqrt(rho) and Q
+                          in fp64 (ill-conditioned ratio); 0 disables */
+} pm_config;
+
+typedef struct pm_sim pm_sim;
+
+/* Fills a configuration with defaults (fp32, MESHGRAD, compact, quantum on,
+ * cosmological, Omega_m 0.3, Omega_L 0.7, h 0.7, m22 2.5, floor 1e-6,
+ * fp64 branch below 1e-2).  n_part, n_mesh and box are left 0. */
+void pm_config_default(pm_config* cfg);
+
+/* hbar/m in code units (Mpc/h)^2 H0 for the configuration's m22 and h. */
+double pm_hbar_over_m(const pm_config* cfg);
+
+/* Device bytes the arena must hold for this configuration (includes the cuFFT
+ * work area; needs a current CUDA device).  0 if the configuration is invalid. */
+size_t pm_arena_bytes(const pm_config* cfg);
+
+/* Creates a simulation in the caller's arena (>= pm_arena_bytes bytes,
+ * 256-byte aligned device memory) bound to the caller's cudaStream_t `stream`
+ * (NULL = legacy default stream).  Builds the cuFFT plans.  Sync. */
+pm_status pm_create(const pm_config* cfg, void* dev_arena, size_t arena_bytes,
+                    void* stream, pm_sim** out);
+
+/* Destroys the cuFFT plans and the handle; the arena stays the caller's. Sync. */
+pm_status pm_destroy(pm_sim* sim);
+
+/* Loads n_part particles from host arrays x[n][3] (positions in [0, box),
+ * wrapped periodically otherwise) and p[n][3] (momenta a^2 dx/dt).  The input
+ * index is the particle's id.  Converts positions to an integer cell plus an
+ * offset in [0,1) and sorts by cell.  Sync. */
+pm_status pm_set_particles(pm_sim* sim, const double* x, const double* p);
+
+/* Copies positions and momenta back in id order (x = (cell + offset) dx). Sync. */
+pm_status pm_get_particles(pm_sim* sim, double* x, double* p);
+
+/* Step (i): sorts the particles by cell and deposits the cloud-in-cell
+ * density rho_n = sum_i m_i W(x_n - q_i)/dx^3 (Eq. rhodis) by a deterministic
+ * gather.  rho_host (nullable) receives the N^3 densities (sync); otherwise
+ * async. */
+pm_status pm_deposit(pm_sim* sim, double* rho_host);
+
+/* Steps (i)-(iii) at scale factor a: acc_host[n][3] (id order) receives
+ * dp/dt = -grad(phi)/a - grad(Q~)/a^2 with lap7 phi = 3/2 Omega_m (rho - 1)
+ * and Q~ = -(hbar/m)^2/2 lap7(sqrt rho)/sqrt rho.  Sync. */
+pm_status pm_forces(pm_sim* sim, double a, double* acc_host);
+
+/* One kick-drift-kick step from a0 to a1 (the leapfrog of Sec. II.A; half
+ * point sqrt(a0 a1), or (t0+t1)/2 in static runs).  Forces at a0 are reused
+ * from the previous step when valid.  Async. */
+pm_status pm_step(pm_sim* sim, double a0, double a1);
+
+/* nsteps leapfrog steps from a_start to a_end, uniform in ln a (in t for static
+ * runs), with the closing half kick of each step merged into the opening half
+ * kick of the next; momenta are synchronised at a_end.  Async. */
+pm_status pm_run(pm_sim* sim, int32_t nsteps, double a_start, double a_end);
+
+/* Energies at scale factor a for the current particles (momenta synchronised):
+ * out = {K_v (Eq. diskkinen), W_g = (1/2a) sum (rho-1) phi dx^3,
+ *        K_rho (Eq. diskpoten; forward differences for the compact Laplacian,
+ *        the printed central differences for the wide one), P_x, P_y, P_z}.
+ * Reductions in fp64.  Sync. */
+pm_status pm_energy(pm_sim* sim, double a, double out[6]);
+
+/* Power spectrum of delta = rho - 1 on the CIC mesh, deconvolved by the CIC
+ * window: P = (L^3/N^6) |delta_k|^2 / prod_d sinc^4(k_d dx/2), shells
+ * i = 1..nbins (nbins <= N/2) of width k_f = 2 pi/L centred on i k_f, over
+ * the full grid.  k[i], P[i]: shell means; nmodes[i]: mode count.  Sync. */
+pm_status pm_power_spectrum(pm_sim* sim, int32_t nbins, double* k, double* P,
+                            int64_t* nmodes);
+
+/* Copies a mesh field (PM_FIELD_RHO, PM_FIELD_PHI = phi~, PM_FIELD_Q = Q~) of
+ * the last force evaluation to host memory as N^3 doubles.  Sync. */
+pm_status pm_get_field(pm_sim* sim, int32_t which, double* host_out);
+
+/* Replaces the density by host values (N^3 doubles) and evaluates phi~ and Q~
+ * from it, so mesh stages can be checked on prescribed fields.  Sync. */
+pm_status pm_set_density(pm_sim* sim, const double* rho_host);
+
+/* Current storage order: cell key (iz*N+iy)*N+ix and id of each slot. Sync. */
+pm_status pm_get_order(pm_sim* sim, uint32_t* cell, uint32_t* id);
+
+/* Stages timed by the profiler (one CUDA-event pair per launch, recorded on
+ * the simulation's stream).  The cuFFT stages cover one cufftExec call each. */
+enum {
+  PM_STAGE_SORT_UPSWEEP = 0, PM_STAGE_SORT_SCAN = 1, PM_STAGE_SORT_DOWNSWEEP = 2,
+  PM_STAGE_CELL_START = 3, PM_STAGE_DEPOSIT = 4, PM_STAGE_FFT_R2C = 5, PM_STAGE_GREEN = 6,
+  PM_STAGE_FFT_C2R = 7, PM_STAGE_STENCIL = 8, PM_STAGE_KICK = 9, PM_STAGE_OTHER = 10,
+  PM_NSTAGES = 11
+};
+
+/* Starts recording a CUDA-event pair around every launch of this handle, for
+ * up to `capacity` launches (events are created here, before any timed work).
+ * Async. */
+pm_status pm_profile_begin(pm_sim* sim, int32_t capacity);
+
+/* Stops recording, waits for the stream and returns per stage the summed
+ * device time in ms and the number of launches (arrays of PM_NSTAGES).  Sync. */
+pm_status pm_profile_end(pm_sim* sim, double* ms, int64_t* launches);
+
+/* Message of the last failure on this handle (or of the last pm_create
+ * failure when sim is NULL). */
+const char* pm_last_error(const pm_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

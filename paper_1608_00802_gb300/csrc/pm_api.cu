@@ -1,0 +1,829 @@
+// Host side of the C ABI declared in include/pm.h: arena layout, cuFFT plans,
+// leapfrog weights and the order of the stages of one step
+// (Veltmaat & Niemeyer, arXiv:1608.00802, Sec. II.A: (i) density, (ii) Q on
+// the grid, (iii) force on each particle, inside a kick-drift-kick leapfrog).
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pm.h"
+#include "pm_internal.h"
+
+using namespace pm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------- units
+// hbar/m in (Mpc/h)^2 H0: (hbar c) c / (m c^2), with one code unit of
+// length^2/time = (100/h) Mpc km/s.  CODATA 2018 hbar*c, IAU parsec.
+double hbar_over_m(double m22, double h) {
+  const double hbarc_ev_m = 1.973269804e-7, c = 299792458.0, mpc = 3.0856775814913673e22;
+  double si = hbarc_ev_m * c / (m22 * 1e-22);  // m^2/s
+  return si / (mpc * 1e3) / (100.0 / h);
+}
+
+// ---------------------------------------------------------------- quadrature
+// Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n.
+struct GaussLegendre {
+  static const int N = 32;
+  double x[N], w[N];
+  GaussLegendre() {
+    for (int i = 0; i < (N + 1) / 2; ++i) {
+      double z = cos(M_PI * (i + 0.75) / (N + 0.5)), pp = 1.0;
+      for (int it = 0; it < 100; ++it) {
+        double p1 = 1.0, p2 = 0.0;
+        for (int j = 1; j <= N; ++j) {
+          double p3 = p2;
+          p2 = p1;
+          p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+        }
+        pp = N * (z * p1 - p2) / (z * z - 1.0);
+        double dz = p1 / pp;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+      }
+      x[i] = -z;
+      x[N - 1 - i] = z;
+      w[i] = w[N - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+  }
+};
+const GaussLegendre& gl() {
+  static GaussLegendre g;
+  return g;
+}
+
+struct Weights {
+  double kg;  // int da / (a^2 H): kick weight of -grad(phi~)  (comoving dp/dt = -grad phi~ / a)
+  double kq;  // int da / (a^3 H): kick weight of -grad(Q~) and drift weight (dx/dt = p / a^2)
+};
+
+Weights time_weights(const pm_config& c, double a0, double a1) {
+  if (!c.cosmological) return {a1 - a0, a1 - a0};
+  const GaussLegendre& g = gl();
+  double mid = 0.5 * (a0 + a1), half = 0.5 * (a1 - a0), kg = 0.0, kq = 0.0;
+  for (int i = 0; i < GaussLegendre::N; ++i) {
+    double a = mid + half * g.x[i];
+    double hub = sqrt(c.omega_m / (a * a * a) + c.omega_l);
+    kg += g.w[i] / (a * a * hub);
+    kq += g.w[i] / (a * a * a * hub);
+  }
+  return {kg * half, kq * half};
+}
+
+double half_point(const pm_config& c, double a0, double a1) {
+  return c.cosmological ? sqrt(a0 * a1) : 0.5 * (a0 + a1);
+}
+
+// ---------------------------------------------------------------- layout
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t pos[2], mom[2], keys[3], vals[2], cell_start, rho, phi, q, spec, work, staging, hist, digit_total, part,
+      part_aux, red, err, total;
+  int key_bits, passes, digit_bits, ntiles;
+};
+
+bool valid_config(const pm_config* c, std::string* why) {
+  if (!c) {
+    *why = "null configuration";
+    return false;
+  }
+  if (c->n_part < 1 || c->n_part > 0x7fffffffLL) {
+    *why = "n_part must be in [1, 2^31-1]";
+    return false;
+  }
+  if (c->n_mesh < 8 || c->n_mesh > 1024 || (c->n_mesh & 1)) {
+    *why = "n_mesh must be even and in [8, 1024]";
+    return false;
+  }
+  if (c->precision != PM_FP32 && c->precision != PM_FP64) {
+    *why = "precision must be PM_FP32 or PM_FP64";
+    return false;
+  }
+  if (!(c->box > 0) || !isfinite(c->box)) {
+    *why = "box must be positive";
+    return false;
+  }
+  if (c->force_mode < 0 || c->force_mode > 2 || (c->lap != 0 && c->lap != 1)) {
+    *why = "force_mode or lap out of range";
+    return false;
+  }
+  if (c->quantum && (!(c->m22 > 0) || !(c->h > 0))) {
+    *why = "m22 and h must be positive with quantum pressure on";
+    return false;
+  }
+  if (c->cosmological && (!(c->omega_m >= 0) || !(c->omega_m + c->omega_l > 0))) {
+    *why = "cosmological run needs omega_m >= 0 and omega_m + omega_l > 0";
+    return false;
+  }
+  if (!(c->rho_floor > 0)) {
+    *why = "rho_floor must be positive";
+    return false;
+  }
+  return true;
+}
+
+Layout make_layout(const pm_config& c, size_t work_bytes) {
+  Layout L;
+  const size_t n = size_t(c.n_part), N = size_t(c.n_mesh), n3 = N * N * N;
+  const size_t rsz = c.precision == PM_FP64 ? 8 : 4;
+  const size_t recsz = 4 * rsz;
+  int bits = 0;
+  while ((size_t(1) << bits) < n3) ++bits;
+  L.key_bits = bits;
+  L.passes = (bits + RS_MAX_BITS - 1) / RS_MAX_BITS;
+  if (L.passes < 1) L.passes = 1;
+  L.digit_bits = (bits + L.passes - 1) / L.passes;
+  L.ntiles = int((n + RS_TILE - 1) / RS_TILE);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  for (int k = 0; k < 2; ++k) L.pos[k] = take(n * recsz);
+  for (int k = 0; k < 2; ++k) L.mom[k] = take(n * recsz);
+  for (int k = 0; k < 3; ++k) L.keys[k] = take(n * 4);
+  for (int k = 0; k < 2; ++k) L.vals[k] = take(n * 4);
+  L.cell_start = take((n3 + 1) * 4);
+  L.rho = take(n3 * rsz);
+  L.phi = take(n3 * rsz);
+  L.q = take(n3 * rsz);
+  L.spec = take(N * N * (N / 2 + 1) * 2 * rsz);
+  L.work = take(work_bytes);
+  size_t stage = 6 * n * 8;
+  if (n3 * 8 > stage) stage = n3 * 8;
+  L.staging = take(stage);
+  L.hist = take((size_t(1) << L.digit_bits) * size_t(L.ntiles) * 4);
+  L.digit_total = take((size_t(1) << L.digit_bits) * 4);
+  size_t nkb = size_t(kick_blocks(int64_t(n)));
+  size_t npart = 4 * nkb;
+  if (size_t(RED_GRID) * 3 * PK_MAX_BINS > npart) npart = size_t(RED_GRID) * 3 * PK_MAX_BINS;
+  L.part = take(npart * 8);
+  L.part_aux = take(2 * RED_GRID * 8);
+  L.red = take(3 * PK_MAX_BINS * 8 + 64);
+  L.err = take(256);
+  L.total = off;
+  return L;
+}
+
+bool fft_work_bytes(const pm_config& c, size_t* out, std::string* why) {
+  cufftType fwd = c.precision == PM_FP64 ? CUFFT_D2Z : CUFFT_R2C;
+  cufftType inv = c.precision == PM_FP64 ? CUFFT_Z2D : CUFFT_C2R;
+  size_t ws[2] = {0, 0};
+  cufftType types[2] = {fwd, inv};
+  for (int k = 0; k < 2; ++k) {
+    cufftHandle h;
+    if (cufftCreate(&h) != CUFFT_SUCCESS) {
+      *why = "cufftCreate failed";
+      return false;
+    }
+    cufftSetAutoAllocation(h, 0);
+    cufftResult r = cufftMakePlan3d(h, c.n_mesh, c.n_mesh, c.n_mesh, types[k], &ws[k]);
+    cufftDestroy(h);
+    if (r != CUFFT_SUCCESS) {
+      *why = "cufftMakePlan3d failed (" + std::to_string(int(r)) + ")";
+      return false;
+    }
+  }
+  *out = ws[0] > ws[1] ? ws[0] : ws[1];
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the handle
+struct pm_sim {
+  pm_config cfg;
+  cudaStream_t stream;
+  char* arena;
+  Layout L;
+  Mesh mesh;
+  double dx, hbm, norm;
+  int cur;  // which of pos[2]/mom[2] holds the state
+  uint32_t* keys;  // sorted (current) keys
+  uint32_t* keys_tmp[2];
+  cufftHandle plan_fwd, plan_inv;
+  bool have_particles, sorted, fields_valid;
+  std::string err;
+  // profiler: event pairs around launches while enabled
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_stage;
+  size_t prof_used = 0;
+
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(arena + off);
+  }
+  void* pos() const { return arena + L.pos[cur]; }
+  void* mom() const { return arena + L.mom[cur]; }
+  bool fp64() const { return cfg.precision == PM_FP64; }
+  int64_t n() const { return cfg.n_part; }
+  uint32_t* errword() const { return at<uint32_t>(L.err); }
+  double* part() const { return at<double>(L.part); }
+  double* red() const { return at<double>(L.red); }
+  double* staging() const { return at<double>(L.staging); }
+};
+
+namespace {
+
+pm_status fail(pm_sim* s, pm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s)
+    s->err = buf;
+  else
+    g_create_error = buf;
+  return st;
+}
+
+// Records an event pair around one launch when the profiler is on.
+struct ProfScope {
+  pm_sim* s;
+  size_t slot;
+  ProfScope(pm_sim* sim, int stage) : s(sim), slot(size_t(-1)) {
+    if (s->prof_on && 2 * (s->prof_used + 1) <= s->prof_ev.size()) {
+      slot = s->prof_used++;
+      s->prof_stage[slot] = stage;
+      cudaEventRecord(s->prof_ev[2 * slot], s->stream);
+    }
+  }
+  ~ProfScope() {
+    if (slot != size_t(-1)) cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
+  }
+};
+#define PROF(sim, stage) ProfScope prof_scope_##__LINE__(sim, stage)
+
+#define CU(sim, expr)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess) return fail(sim, PM_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+#define CF(sim, expr)                                                                      \
+  do {                                                                                     \
+    cufftResult r_ = (expr);                                                               \
+    if (r_ != CUFFT_SUCCESS) return fail(sim, PM_ERR_CUFFT, "%s: cufft error %d", #expr, int(r_)); \
+  } while (0)
+
+// Partials: the kick diagnostics and the power spectrum use `part`; the
+// gravity-energy and K_rho sums of the last force evaluation live in
+// `part_aux` (one RED_GRID-long row each) until the next evaluation.
+double* wg_part(pm_sim* s) { return s->at<double>(s->L.part_aux); }
+double* kr_part(pm_sim* s) { return wg_part(s) + RED_GRID; }
+
+template <typename R>
+pm_status sort_particles(pm_sim* s) {
+  const Layout& L = s->L;
+  const int64_t n = s->n();
+  uint32_t* hist = s->at<uint32_t>(L.hist);
+  uint32_t* dtot = s->at<uint32_t>(L.digit_total);
+  uint32_t* vals[2] = {s->at<uint32_t>(L.vals[0]), s->at<uint32_t>(L.vals[1])};
+  const uint32_t* kin = s->keys;
+  const uint32_t* vin = nullptr;
+  int tmp = 0;
+  for (int p = 0; p < L.passes; ++p) {
+    const int shift = p * L.digit_bits;
+    const int bits = (shift + L.digit_bits <= L.key_bits) ? L.digit_bits : (L.key_bits - shift);
+    const bool last = p == L.passes - 1;
+    {
+      PROF(s, PM_STAGE_SORT_UPSWEEP);
+      CU(s, launch_radix_upsweep(kin, n, shift, bits, hist, L.ntiles, s->stream));
+    }
+    {
+      PROF(s, PM_STAGE_SORT_SCAN);
+      CU(s, launch_radix_scan(hist, L.ntiles, bits, dtot, s->stream));
+    }
+    if (!last) {
+      uint32_t* kout = s->keys_tmp[tmp];
+      uint32_t* vout = vals[tmp];
+      PROF(s, PM_STAGE_SORT_DOWNSWEEP);
+      CU(s, launch_radix_downsweep<R>(false, kin, vin, n, shift, bits, hist, dtot, L.ntiles, kout, vout, nullptr,
+                                      nullptr, nullptr, nullptr, s->stream));
+      kin = kout;
+      vin = vout;
+      tmp ^= 1;
+    } else {
+      // the sorted keys go to a buffer that is not the input
+      uint32_t* kout = (kin == s->keys) ? s->keys_tmp[tmp] : s->keys;
+      const int nxt = s->cur ^ 1;
+      {
+        PROF(s, PM_STAGE_SORT_DOWNSWEEP);
+        CU(s, launch_radix_downsweep<R>(true, kin, vin, n, shift, bits, hist, dtot, L.ntiles, kout, nullptr,
+                                      s->pos(), s->mom(), s->arena + L.pos[nxt], s->arena + L.mom[nxt],
+                                        s->stream));
+      }
+      if (kout != s->keys) {  // swap roles so that s->keys holds the sorted keys
+        for (int k = 0; k < 2; ++k)
+          if (s->keys_tmp[k] == kout) s->keys_tmp[k] = s->keys;
+        s->keys = kout;
+      }
+      s->cur = nxt;
+    }
+  }
+  {
+    PROF(s, PM_STAGE_CELL_START);
+    CU(s, launch_cell_start(s->keys, n, s->mesh.n3, s->at<uint32_t>(L.cell_start), s->stream));
+  }
+  s->sorted = true;
+  return PM_OK;
+}
+
+template <typename R>
+pm_status mesh_from_density(pm_sim* s) {
+  const Layout& L = s->L;
+  R* rho = s->at<R>(L.rho);
+  {
+    PROF(s, PM_STAGE_FFT_R2C);
+    if (s->fp64()) {
+      CF(s, cufftExecD2Z(s->plan_fwd, (cufftDoubleReal*)rho, (cufftDoubleComplex*)(s->arena + L.spec)));
+    } else {
+      CF(s, cufftExecR2C(s->plan_fwd, (cufftReal*)rho, (cufftComplex*)(s->arena + L.spec)));
+    }
+  }
+  const double N = s->cfg.n_mesh;
+  const double coef = -1.5 * s->cfg.omega_m * s->dx * s->dx / (4.0 * N * N * N);
+  {
+    PROF(s, PM_STAGE_GREEN);
+    CU(s, launch_green<R>(s->arena + L.spec, s->mesh, coef, wg_part(s), s->stream));
+  }
+  {
+    PROF(s, PM_STAGE_FFT_C2R);
+    if (s->fp64()) {
+      CF(s, cufftExecZ2D(s->plan_inv, (cufftDoubleComplex*)(s->arena + L.spec), (cufftDoubleReal*)(s->arena + L.phi)));
+    } else {
+      CF(s, cufftExecC2R(s->plan_inv, (cufftComplex*)(s->arena + L.spec), (cufftReal*)(s->arena + L.phi)));
+    }
+  }
+  if (s->cfg.quantum) {
+    StencilParams sp;
+    sp.step = s->cfg.lap == PM_LAP_WIDE ? 2 : 1;
+    sp.rho_floor = s->cfg.rho_floor;
+    sp.rho_fp64 = s->cfg.rho_fp64;
+    sp.qcoef = -0.5 * s->hbm * s->hbm / ((sp.step * s->dx) * (sp.step * s->dx));
+    PROF(s, PM_STAGE_STENCIL);
+    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->stream));
+  }
+  s->fields_valid = true;
+  return PM_OK;
+}
+
+template <typename R>
+pm_status deposit(pm_sim* s) {
+  if (!s->sorted) {
+    pm_status st = sort_particles<R>(s);
+    if (st != PM_OK) return st;
+  }
+  PROF(s, PM_STAGE_DEPOSIT);
+  CU(s, launch_deposit<R>(s->pos(), s->at<uint32_t>(s->L.cell_start), s->n(), s->mesh, s->norm, s->at<R>(s->L.rho),
+                          s->stream));
+  return PM_OK;
+}
+
+template <typename R>
+pm_status compute_fields(pm_sim* s) {
+  pm_status st = deposit<R>(s);
+  if (st != PM_OK) return st;
+  return mesh_from_density<R>(s);
+}
+
+KickParams base_kick(const pm_sim* s) {
+  KickParams kp;
+  memset(&kp, 0, sizeof kp);
+  kp.inv_dx = 1.0 / s->dx;
+  kp.grav_kernel = s->cfg.force_mode == PM_FORCE_LAGRANGIAN;
+  kp.q_kernel = s->cfg.force_mode != PM_FORCE_MESHGRAD;
+  kp.quantum = s->cfg.quantum != 0;
+  return kp;
+}
+
+template <typename R>
+pm_status kick(pm_sim* s, const KickParams& kp, double* acc) {
+  const Layout& L = s->L;
+  {
+    PROF(s, PM_STAGE_KICK);
+    CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, s->part(),
+                         acc, s->errword(), s->stream));
+  }
+  if (kp.drift != 0.0) {
+    s->sorted = false;
+    s->fields_valid = false;
+  }
+  return PM_OK;
+}
+
+#define DISPATCH(s, fn, ...) ((s)->fp64() ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+pm_status check(pm_sim* s) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (!s->have_particles) return fail(s, PM_ERR_STATE, "no particles set");
+  return PM_OK;
+}
+
+pm_status ensure_fields(pm_sim* s) {
+  if (s->fields_valid) return PM_OK;
+  return DISPATCH(s, compute_fields, s);
+}
+
+// one leapfrog pass: kick by (w1, w2) and drift by d (0 = none); diag = K_v of p_sync
+pm_status pass(pm_sim* s, Weights w1, Weights w2, double d, bool diag) {
+  KickParams kp = base_kick(s);
+  kp.cg1 = w1.kg;
+  kp.cq1 = w1.kq;
+  kp.cg2 = w2.kg;
+  kp.cq2 = w2.kq;
+  kp.drift = d / s->dx;
+  kp.diag = diag;
+  return DISPATCH(s, kick, s, kp, nullptr);
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+void pm_config_default(pm_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof *c);
+  c->precision = PM_FP32;
+  c->omega_m = 0.3;
+  c->omega_l = 0.7;
+  c->h = 0.7;
+  c->m22 = 2.5;
+  c->quantum = 1;
+  c->force_mode = PM_FORCE_MESHGRAD;
+  c->lap = PM_LAP_COMPACT;
+  c->cosmological = 1;
+  c->rho_floor = 1e-6;
+  c->rho_fp64 = 1e-2;
+}
+
+double pm_hbar_over_m(const pm_config* c) { return c ? hbar_over_m(c->m22, c->h) : 0.0; }
+
+size_t pm_arena_bytes(const pm_config* c) {
+  std::string why;
+  if (!valid_config(c, &why)) {
+    g_create_error = why;
+    return 0;
+  }
+  size_t ws = 0;
+  if (!fft_work_bytes(*c, &ws, &why)) {
+    g_create_error = why;
+    return 0;
+  }
+  return make_layout(*c, ws).total;
+}
+
+pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* stream, pm_sim** out) {
+  if (!out) return fail(nullptr, PM_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  std::string why;
+  if (!valid_config(c, &why)) return fail(nullptr, PM_ERR_INVALID_ARG, "%s", why.c_str());
+  if (!dev_arena || (reinterpret_cast<uintptr_t>(dev_arena) & 255))
+    return fail(nullptr, PM_ERR_INVALID_ARG, "arena must be a 256-byte aligned device pointer");
+  size_t ws = 0;
+  if (!fft_work_bytes(*c, &ws, &why)) return fail(nullptr, PM_ERR_CUFFT, "%s", why.c_str());
+  Layout L = make_layout(*c, ws);
+  if (bytes < L.total) return fail(nullptr, PM_ERR_NO_MEMORY, "arena has %zu bytes, needs %zu", bytes, L.total);
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, dev_arena) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(nullptr, PM_ERR_INVALID_ARG, "arena is not device memory");
+  }
+  pm_sim* s = new pm_sim();
+  s->cfg = *c;
+  s->stream = reinterpret_cast<cudaStream_t>(stream);
+  s->arena = reinterpret_cast<char*>(dev_arena);
+  s->L = L;
+  const int N = c->n_mesh;
+  s->mesh.n = N;
+  s->mesh.log2n = (N & (N - 1)) == 0 ? __builtin_ctz(unsigned(N)) : -1;
+  s->mesh.n2 = uint32_t(N) * uint32_t(N);
+  s->mesh.n3 = s->mesh.n2 * uint32_t(N);
+  s->dx = c->box / N;
+  s->hbm = hbar_over_m(c->m22, c->h);
+  s->norm = double(s->mesh.n3) / double(c->n_part);  // m_p / dx^3 with m_p = L^3 / n_part
+  s->cur = 0;
+  s->keys = s->at<uint32_t>(L.keys[0]);
+  s->keys_tmp[0] = s->at<uint32_t>(L.keys[1]);
+  s->keys_tmp[1] = s->at<uint32_t>(L.keys[2]);
+  s->have_particles = s->sorted = s->fields_valid = false;
+  cufftType fwd = c->precision == PM_FP64 ? CUFFT_D2Z : CUFFT_R2C;
+  cufftType inv = c->precision == PM_FP64 ? CUFFT_Z2D : CUFFT_C2R;
+  cufftHandle* plans[2] = {&s->plan_fwd, &s->plan_inv};
+  cufftType types[2] = {fwd, inv};
+  for (int k = 0; k < 2; ++k) {
+    size_t w = 0;
+    cufftResult r = cufftCreate(plans[k]);
+    if (r == CUFFT_SUCCESS) r = cufftSetAutoAllocation(*plans[k], 0);
+    if (r == CUFFT_SUCCESS) r = cufftMakePlan3d(*plans[k], N, N, N, types[k], &w);
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(*plans[k], s->arena + L.work);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(*plans[k], s->stream);
+    if (r != CUFFT_SUCCESS) {
+      if (k == 1) cufftDestroy(s->plan_fwd);
+      delete s;
+      return fail(nullptr, PM_ERR_CUFFT, "cuFFT plan setup failed (%d)", int(r));
+    }
+  }
+  if (cudaMemsetAsync(s->errword(), 0, 4, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    cufftDestroy(s->plan_fwd);
+    cufftDestroy(s->plan_inv);
+    delete s;
+    return fail(nullptr, PM_ERR_CUDA, "stream setup failed");
+  }
+  *out = s;
+  return PM_OK;
+}
+
+pm_status pm_destroy(pm_sim* s) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  cudaStreamSynchronize(s->stream);
+  for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  cufftDestroy(s->plan_fwd);
+  cufftDestroy(s->plan_inv);
+  delete s;
+  return PM_OK;
+}
+
+pm_status pm_set_particles(pm_sim* s, const double* x, const double* p) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (!x || !p) return fail(s, PM_ERR_INVALID_ARG, "x and p must be non-null host arrays");
+  const size_t bytes = size_t(s->n()) * 3 * sizeof(double);
+  double* dx = s->staging();
+  double* dp = dx + 3 * size_t(s->n());
+  CU(s, cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s->stream));
+  CU(s, cudaMemcpyAsync(dp, p, bytes, cudaMemcpyHostToDevice, s->stream));
+  s->cur = 0;
+  CU(s, DISPATCH(s, launch_init_particles, dx, dp, s->n(), s->mesh, 1.0 / s->dx, s->pos(), s->mom(), s->keys,
+                 s->errword(), s->stream));
+  s->have_particles = true;
+  s->sorted = s->fields_valid = false;
+  pm_status st = DISPATCH(s, sort_particles, s);
+  if (st != PM_OK) return st;
+  CU(s, cudaStreamSynchronize(s->stream));
+  uint32_t e = 0;
+  CU(s, cudaMemcpy(&e, s->errword(), 4, cudaMemcpyDeviceToHost));
+  if (e & ERR_NONFINITE) {
+    cudaMemset(s->errword(), 0, 4);
+    return fail(s, PM_ERR_NONFINITE, "non-finite input position");
+  }
+  return PM_OK;
+}
+
+pm_status pm_get_particles(pm_sim* s, double* x, double* p) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (!x || !p) return fail(s, PM_ERR_INVALID_ARG, "x and p must be non-null");
+  double* dx = s->staging();
+  double* dp = dx + 3 * size_t(s->n());
+  CU(s, DISPATCH(s, launch_get_particles, s->pos(), s->mom(), s->n(), s->mesh, s->dx, dx, dp, s->stream));
+  const size_t bytes = size_t(s->n()) * 3 * sizeof(double);
+  CU(s, cudaMemcpyAsync(x, dx, bytes, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  return PM_OK;
+}
+
+pm_status pm_deposit(pm_sim* s, double* rho_host) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  st = DISPATCH(s, deposit, s);
+  if (st != PM_OK) return st;
+  s->fields_valid = false;  // phi and Q no longer match rho until the mesh stages run
+  if (rho_host) return pm_get_field(s, PM_FIELD_RHO, rho_host);
+  return PM_OK;
+}
+
+pm_status pm_forces(pm_sim* s, double a, double* acc_host) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (!acc_host) return fail(s, PM_ERR_INVALID_ARG, "acc must be non-null");
+  if (s->cfg.cosmological && !(a > 0)) return fail(s, PM_ERR_INVALID_ARG, "a must be positive");
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  const double aa = s->cfg.cosmological ? a : 1.0;
+  KickParams kp = base_kick(s);
+  kp.cg1 = 1.0 / aa;
+  kp.cq1 = 1.0 / (aa * aa);
+  kp.accel_out = 1;
+  double* dacc = s->staging();
+  st = DISPATCH(s, kick, s, kp, dacc);
+  if (st != PM_OK) return st;
+  CU(s, cudaMemcpyAsync(acc_host, dacc, size_t(s->n()) * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  return PM_OK;
+}
+
+pm_status pm_step(pm_sim* s, double a0, double a1) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (s->cfg.cosmological && !(a0 > 0 && a1 > 0)) return fail(s, PM_ERR_INVALID_ARG, "a0, a1 must be positive");
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  const double ah = half_point(s->cfg, a0, a1);
+  const Weights zero = {0.0, 0.0};
+  const Weights d = time_weights(s->cfg, a0, a1);
+  st = pass(s, zero, time_weights(s->cfg, a0, ah), d.kq, false);
+  if (st != PM_OK) return st;
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  return pass(s, time_weights(s->cfg, ah, a1), zero, 0.0, true);
+}
+
+pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (nsteps < 1) return fail(s, PM_ERR_INVALID_ARG, "nsteps must be >= 1");
+  if (s->cfg.cosmological && !(a_start > 0 && a_end > 0)) return fail(s, PM_ERR_INVALID_ARG, "a must be positive");
+  auto a_at = [&](int i) {
+    if (i == nsteps) return a_end;
+    double t = double(i) / nsteps;
+    return s->cfg.cosmological ? a_start * pow(a_end / a_start, t) : a_start + (a_end - a_start) * t;
+  };
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  const Weights zero = {0.0, 0.0};
+  Weights pending = zero;  // closing half kick of the previous step
+  for (int i = 0; i < nsteps; ++i) {
+    const double a0 = a_at(i), a1 = a_at(i + 1), ah = half_point(s->cfg, a0, a1);
+    st = pass(s, pending, time_weights(s->cfg, a0, ah), time_weights(s->cfg, a0, a1).kq, false);
+    if (st != PM_OK) return st;
+    st = ensure_fields(s);
+    if (st != PM_OK) return st;
+    pending = time_weights(s->cfg, ah, a1);
+  }
+  return pass(s, pending, zero, 0.0, true);
+}
+
+pm_status pm_energy(pm_sim* s, double a, double out[6]) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (!out) return fail(s, PM_ERR_INVALID_ARG, "out must be non-null");
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  // K_v and momentum of the current (synchronised) momenta
+  st = pass(s, Weights{0.0, 0.0}, Weights{0.0, 0.0}, 0.0, true);
+  if (st != PM_OK) return st;
+  const int nkb = kick_blocks(s->n());
+  double* red = s->red();
+  CU(s, launch_reduce(s->part(), nkb, 4, red, s->stream));
+  CU(s, launch_reduce(wg_part(s), RED_GRID, s->cfg.quantum ? 2 : 1, red + 4, s->stream));
+  double h[6];
+  CU(s, cudaMemcpyAsync(h, red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  uint32_t e = 0;
+  CU(s, cudaMemcpyAsync(&e, s->errword(), 4, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  const double aa = s->cfg.cosmological ? a : 1.0;
+  const double box = s->cfg.box;
+  const double mp = box * box * box / double(s->n());
+  const double dx3 = s->dx * s->dx * s->dx;
+  out[0] = 0.5 * mp * h[0] / (aa * aa);
+  out[1] = 0.5 / aa * h[4] * dx3;
+  out[2] = s->cfg.quantum ? 0.5 * s->hbm * s->hbm / (aa * aa) * s->dx * h[5] : 0.0;
+  out[3] = mp * h[1];
+  out[4] = mp * h[2];
+  out[5] = mp * h[3];
+  bool bad = (e & ERR_NONFINITE) != 0;
+  for (int k = 0; k < 6; ++k) bad |= !isfinite(out[k]);
+  if (bad) return fail(s, PM_ERR_NONFINITE, "non-finite momentum or energy");
+  return PM_OK;
+}
+
+pm_status pm_power_spectrum(pm_sim* s, int32_t nbins, double* k, double* P, int64_t* nmodes) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (nbins < 1 || nbins > s->cfg.n_mesh / 2 || nbins > PK_MAX_BINS || !k || !P || !nmodes)
+    return fail(s, PM_ERR_INVALID_ARG, "nbins must be in [1, N/2] with non-null outputs");
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  const Layout& L = s->L;
+  if (s->fp64()) {
+    CF(s, cufftExecD2Z(s->plan_fwd, s->at<cufftDoubleReal>(L.rho), (cufftDoubleComplex*)(s->arena + L.spec)));
+  } else {
+    CF(s, cufftExecR2C(s->plan_fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
+  }
+  double* part = s->part();
+  CU(s, DISPATCH(s, launch_power, s->arena + L.spec, s->mesh, nbins, part, s->stream));
+  double* red = s->red();
+  CU(s, launch_reduce(part, RED_GRID, 3 * nbins, red, s->stream));
+  double* h = new double[3 * nbins];
+  cudaError_t e1 = cudaMemcpyAsync(h, red, 3 * nbins * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e2 = cudaStreamSynchronize(s->stream);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    delete[] h;
+    return fail(s, PM_ERR_CUDA, "power spectrum copy failed");
+  }
+  const double N = s->cfg.n_mesh, box = s->cfg.box;
+  const double kf = 2.0 * M_PI / box;
+  const double norm = box * box * box / (N * N * N * N * N * N);
+  for (int b = 0; b < nbins; ++b) {
+    double cnt = h[b];
+    nmodes[b] = int64_t(llround(cnt));
+    k[b] = cnt > 0 ? kf * h[nbins + b] / cnt : NAN;
+    P[b] = cnt > 0 ? norm * h[2 * nbins + b] / cnt : NAN;
+  }
+  delete[] h;
+  return PM_OK;
+}
+
+pm_status pm_get_field(pm_sim* s, int32_t which, double* host_out) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (!host_out || which < 0 || which > 2) return fail(s, PM_ERR_INVALID_ARG, "bad field or output");
+  if (which == PM_FIELD_Q && !s->cfg.quantum) return fail(s, PM_ERR_STATE, "quantum pressure is off");
+  const Layout& L = s->L;
+  const size_t offs[3] = {L.rho, L.phi, L.q};
+  const int64_t n3 = s->mesh.n3;
+  double* d = s->staging();
+  if (s->fp64()) {
+    CU(s, cudaMemcpyAsync(d, s->arena + offs[which], n3 * 8, cudaMemcpyDeviceToDevice, s->stream));
+  } else {
+    CU(s, launch_to_double<float>(s->at<float>(offs[which]), n3, d, s->stream));
+  }
+  CU(s, cudaMemcpyAsync(host_out, d, n3 * 8, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  return PM_OK;
+}
+
+pm_status pm_set_density(pm_sim* s, const double* rho_host) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (!rho_host) return fail(s, PM_ERR_INVALID_ARG, "rho must be non-null");
+  const int64_t n3 = s->mesh.n3;
+  double* d = s->staging();
+  CU(s, cudaMemcpyAsync(d, rho_host, n3 * 8, cudaMemcpyHostToDevice, s->stream));
+  if (s->fp64()) {
+    CU(s, cudaMemcpyAsync(s->arena + s->L.rho, d, n3 * 8, cudaMemcpyDeviceToDevice, s->stream));
+  } else {
+    CU(s, launch_from_double<float>(d, n3, s->at<float>(s->L.rho), s->stream));
+  }
+  pm_status st = DISPATCH(s, mesh_from_density, s);
+  if (st != PM_OK) return st;
+  CU(s, cudaStreamSynchronize(s->stream));
+  return PM_OK;
+}
+
+pm_status pm_get_order(pm_sim* s, uint32_t* cell, uint32_t* id) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (!cell || !id) return fail(s, PM_ERR_INVALID_ARG, "outputs must be non-null");
+  if (!s->sorted) {
+    st = DISPATCH(s, sort_particles, s);
+    if (st != PM_OK) return st;
+  }
+  uint32_t* d = reinterpret_cast<uint32_t*>(s->staging());
+  CU(s, DISPATCH(s, launch_get_order, s->pos(), s->mom(), s->n(), d, d + s->n(), s->stream));
+  CU(s, cudaMemcpyAsync(cell, d, size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaMemcpyAsync(id, d + s->n(), size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  return PM_OK;
+}
+
+pm_status pm_profile_begin(pm_sim* s, int32_t capacity) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (capacity < 1) return fail(s, PM_ERR_INVALID_ARG, "capacity must be >= 1");
+  for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  s->prof_ev.assign(2 * size_t(capacity), nullptr);
+  s->prof_stage.assign(size_t(capacity), PM_STAGE_OTHER);
+  for (auto& e : s->prof_ev) CU(s, cudaEventCreate(&e));
+  s->prof_used = 0;
+  s->prof_on = true;
+  return PM_OK;
+}
+
+pm_status pm_profile_end(pm_sim* s, double* ms, int64_t* launches) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (!ms || !launches) return fail(s, PM_ERR_INVALID_ARG, "outputs must be non-null");
+  s->prof_on = false;
+  CU(s, cudaStreamSynchronize(s->stream));
+  for (int k = 0; k < PM_NSTAGES; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < s->prof_used; ++i) {
+    float t = 0.f;
+    CU(s, cudaEventElapsedTime(&t, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]));
+    ms[s->prof_stage[i]] += t;
+    launches[s->prof_stage[i]] += 1;
+  }
+  for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  s->prof_ev.clear();
+  s->prof_stage.clear();
+  s->prof_used = 0;
+  return PM_OK;
+}
+
+const char* pm_last_error(const pm_sim* s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Internal declarations shared by the host C-ABI (pm_api.cu) and the kernel
+// translation units (pm_kernels_f32.cu, pm_kernels_f64.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+namespace pm {
+
+// 32-byte record for the fp64 path (CUDA 13 deprecates the plain double4).
+struct __align__(32) D4 {
+  double x, y, z, w;
+};
+
+template <typename R> struct VT;
+template <> struct VT<float> {
+  using v4 = float4;
+  using cplx = cufftComplex;
+};
+template <> struct VT<double> {
+  using v4 = D4;
+  using cplx = cufftDoubleComplex;
+};
+
+// Mesh geometry: N^3 nodes, node (x,y,z) at linear index (z*N + y)*N + x.
+struct Mesh {
+  int n;        // N
+  int log2n;    // log2(N) when N is a power of two, else -1
+  uint32_t n2;  // N^2
+  uint32_t n3;  // N^3
+};
+
+// Leapfrog weights for one pass over the particles.  The momentum update is
+//   p_sync = p - (cg1 grad phi + cq1 grad Q),  p_new = p_sync - (cg2 grad phi + cq2 grad Q)
+// and the offsets (cell units) move by p_new * drift.
+struct KickParams {
+  double cg1, cq1, cg2, cq2;
+  double drift;       // D/dx, 0 = no drift
+  double inv_dx;      // 1/dx
+  int grav_kernel;    // 1: gravity by the kernel gradient, 0: central mesh gradient
+  int q_kernel;       // 1: Q by the kernel gradient (Eq. equationofmotion), 0: central
+  int quantum;        // Q force on/off
+  int diag;           // accumulate sum p_sync^2 and sum p_sync per block
+  int accel_out;      // write -(cg1 grad phi + cq1 grad Q) to acc[id] and leave the state
+};
+
+struct StencilParams {
+  int step;           // 1 = compact Laplacian, 2 = wide
+  double rho_floor;   // s = sqrt(max(rho, rho_floor))
+  double rho_fp64;    // nodes below take the fp64 branch (fp32 path)
+  double qcoef;       // -(hbar/m)^2 / 2 / (step*dx)^2
+};
+
+// error bits of the device error word
+enum : uint32_t { ERR_NONFINITE = 1u };
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_MAX_BITS = 10;
+
+constexpr int KICK_THREADS = 256;
+constexpr int MESH_THREADS = 256;
+constexpr int RED_GRID = 608;   // 4 blocks per SM on 152 SMs, fixed for deterministic reductions
+constexpr int PK_MAX_BINS = 512;
+
+inline size_t radix_smem_bytes(int bits) {
+  size_t radix = size_t(1) << bits;
+  return (RS_WARPS * radix + 2 * radix + 2 * RS_TILE + 64) * sizeof(uint32_t);
+}
+
+template <typename R>
+cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, Mesh m, double inv_dx,
+                                  void* pos, void* mom, uint32_t* keys, uint32_t* err, cudaStream_t s);
+cudaError_t launch_radix_upsweep(const uint32_t* keys, int64_t n, int shift, int bits, uint32_t* hist,
+                                 int ntiles, cudaStream_t s);
+cudaError_t launch_radix_scan(uint32_t* hist, int ntiles, int bits, uint32_t* digit_total, cudaStream_t s);
+template <typename R>
+cudaError_t launch_radix_downsweep(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
+                                   int shift, int bits, const uint32_t* hist, const uint32_t* digit_total,
+                                   int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
+                                   const void* mom_in, void* pos_out, void* mom_out, cudaStream_t s);
+cudaError_t launch_cell_start(const uint32_t* keys, int64_t n, uint32_t ncell, uint32_t* cell_start,
+                              cudaStream_t s);
+template <typename R>
+cudaError_t launch_deposit(const void* pos, const uint32_t* cell_start, int64_t n, Mesh m, double norm, R* rho,
+                           cudaStream_t s);
+template <typename R>
+cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
+template <typename R>
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s);
+template <typename R>
+cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
+                        KickParams kp, double* part, double* acc, uint32_t* err, cudaStream_t s);
+template <typename R>
+cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s);
+cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);
+template <typename R>
+cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Mesh m, double dx, double* x,
+                                 double* p, cudaStream_t s);
+template <typename R>
+cudaError_t launch_get_order(const void* pos, const void* mom, int64_t n, uint32_t* cell, uint32_t* id,
+                             cudaStream_t s);
+template <typename R>
+cudaError_t launch_to_double(const R* f, int64_t n, double* out, cudaStream_t s);
+template <typename R>
+cudaError_t launch_from_double(const double* f, int64_t n, R* out, cudaStream_t s);
+
+inline int kick_blocks(int64_t n) { return int((n + KICK_THREADS - 1) / KICK_THREADS); }
+
+}  // namespace pm

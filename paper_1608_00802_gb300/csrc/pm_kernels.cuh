@@ -1,0 +1,644 @@
+// Device kernels of the particle-mesh step with quantum pressure
+// (Veltmaat & Niemeyer, arXiv:1608.00802, Sec. II.A), templated on the real
+// type R (float: int32 cell + fp32 offset positions and fp32 mesh; double:
+// the plain fp64 path).  Included by pm_kernels_f32.cu / pm_kernels_f64.cu.
+//
+// Particle storage (sorted by cell between steps):
+//   pos[i] = {cell (bits), fx, fy, fz}   offsets in cell units, in [0,1)
+//   mom[i] = {px, py, pz, id (bits)}     p = a^2 dx/dt
+// None of these kernels use floating-point atomics on the step's data, so a
+// step is bitwise reproducible for a fixed launch configuration.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pm_internal.h"
+
+namespace pm {
+
+// ---------------------------------------------------------------- record access
+__device__ __forceinline__ uint32_t rec_cell(const float4& r) { return __float_as_uint(r.x); }
+__device__ __forceinline__ uint32_t rec_cell(const D4& r) { return (uint32_t)__double_as_longlong(r.x); }
+__device__ __forceinline__ uint32_t rec_id(const float4& r) { return __float_as_uint(r.w); }
+__device__ __forceinline__ uint32_t rec_id(const D4& r) { return (uint32_t)__double_as_longlong(r.w); }
+__device__ __forceinline__ float4 make_pos(uint32_t c, float fx, float fy, float fz) {
+  return make_float4(__uint_as_float(c), fx, fy, fz);
+}
+__device__ __forceinline__ D4 make_pos(uint32_t c, double fx, double fy, double fz) {
+  D4 r;
+  r.x = __longlong_as_double((long long)c);
+  r.y = fx;
+  r.z = fy;
+  r.w = fz;
+  return r;
+}
+__device__ __forceinline__ float4 make_mom(float px, float py, float pz, uint32_t id) {
+  return make_float4(px, py, pz, __uint_as_float(id));
+}
+__device__ __forceinline__ D4 make_mom(double px, double py, double pz, uint32_t id) {
+  D4 r;
+  r.x = px;
+  r.y = py;
+  r.z = pz;
+  r.w = __longlong_as_double((long long)id);
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ D4 ldg<D4>(const D4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  D4 r;
+  r.x = a.x;
+  r.y = a.y;
+  r.z = b.x;
+  r.w = b.y;
+  return r;
+}
+
+__device__ __forceinline__ void split_cell(uint32_t c, const Mesh& m, int& x, int& y, int& z) {
+  if (m.log2n >= 0) {
+    uint32_t mask = uint32_t(m.n) - 1u;
+    x = int(c & mask);
+    y = int((c >> m.log2n) & mask);
+    z = int(c >> (2 * m.log2n));
+  } else {
+    uint32_t q = c / uint32_t(m.n);
+    x = int(c - q * uint32_t(m.n));
+    z = int(q / uint32_t(m.n));
+    y = int(q - uint32_t(z) * uint32_t(m.n));
+  }
+}
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of NV doubles (fixed order); thread 0 gets the totals.
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, int nblocks) {
+  __shared__ double sh[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[w][k];
+      part[k * nblocks + blockIdx.x] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- S0: load + keys
+template <typename R>
+__global__ void k_init_particles(const double* __restrict__ x, const double* __restrict__ p, int64_t n, Mesh m,
+                                 double inv_dx, typename VT<R>::v4* pos, typename VT<R>::v4* mom,
+                                 uint32_t* keys, uint32_t* err) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3];
+  R f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double u = x[3 * i + d] * inv_dx;
+    if (!isfinite(u)) {
+      atomicOr(err, ERR_NONFINITE);
+      u = 0.0;
+    }
+    double fl = floor(u);
+    double fr = u - fl;
+    int64_t ci = (int64_t)fl;
+    R o = R(fr);
+    if (o >= R(1)) {  // rounding of the offset to R reached 1: carry into the cell
+      o = R(0);
+      ci += 1;
+    }
+    ci %= m.n;
+    if (ci < 0) ci += m.n;
+    c[d] = int(ci);
+    f[d] = o;
+  }
+  uint32_t cell = (uint32_t(c[2]) * uint32_t(m.n) + uint32_t(c[1])) * uint32_t(m.n) + uint32_t(c[0]);
+  pos[i] = make_pos(cell, f[0], f[1], f[2]);
+  mom[i] = make_mom(R(p[3 * i]), R(p[3 * i + 1]), R(p[3 * i + 2]), uint32_t(i));
+  keys[i] = cell;
+}
+
+// ---------------------------------------------------------------- S1: deposit (gather)
+// rho_n = norm * sum over the particles of the eight cells n - {0,1}^3 of the
+// cloud-in-cell weight prod_d (1 - f_d or f_d), i.e. Eq. (rhodis) with the
+// tent kernel.  One thread per node, fixed summation order: (dz, dy) in
+// lexicographic order, cell x-1 before cell x, particles in storage order.
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_deposit(const typename VT<R>::v4* __restrict__ pos,
+                                                          const uint32_t* __restrict__ cs, uint32_t np, Mesh m,
+                                                          R norm, R* __restrict__ rho) {
+  using V4 = typename VT<R>::v4;
+  uint32_t node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= m.n3) return;
+  int x, y, z;
+  split_cell(node, m, x, y, z);
+  const int n = m.n;
+  R acc = R(0);
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    const int zc = wrap(z - dz, n);
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int yc = wrap(y - dy, n);
+      const uint32_t row = (uint32_t(zc) * n + uint32_t(yc)) * n;
+      const uint32_t own = row + uint32_t(x);  // the cell whose lower x-corner is this node
+      uint32_t b0, e0, b1, e1;
+      if (x > 0) {
+        b0 = __ldg(cs + own - 1);
+        e0 = __ldg(cs + own + 1);
+        b1 = e1 = 0;
+      } else {
+        b0 = __ldg(cs + row + n - 1);
+        e0 = __ldg(cs + row + n);
+        b1 = __ldg(cs + row);
+        e1 = __ldg(cs + row + 1);
+      }
+      // cell starts are clamped to the particle count so that no read leaves pos[]
+      e0 = min(e0, np);
+      e1 = min(e1, np);
+      R part = R(0);
+      for (uint32_t j = b0; j < e0; ++j) {
+        V4 r = ldg(pos + j);
+        R wx = (rec_cell(r) == own) ? R(1) - r.y : r.y;
+        R wy = dy ? r.z : R(1) - r.z;
+        R wz = dz ? r.w : R(1) - r.w;
+        part += wx * wy * wz;
+      }
+      for (uint32_t j = b1; j < e1; ++j) {
+        V4 r = ldg(pos + j);
+        R wx = R(1) - r.y;  // cell 0 == own
+        R wy = dy ? r.z : R(1) - r.z;
+        R wz = dz ? r.w : R(1) - r.w;
+        part += wx * wy * wz;
+      }
+      acc += part;
+    }
+  }
+  rho[node] = acc * norm;
+}
+
+// ---------------------------------------------------------------- S3: Green's function
+__device__ __forceinline__ float sinpi_sq(float t) {
+  float s = sinpif(t);
+  return s * s;
+}
+__device__ __forceinline__ double sinpi_sq(double t) {
+  double s = sinpi(t);
+  return s * s;
+}
+
+// phi^_k = coef * rho^_k / sum_d sin^2(pi j_d / N), coef = -(3/2) Om dx^2 / (4 N^3):
+// the exact periodic inverse of the compact seven-point Laplacian with the
+// inverse-FFT normalisation folded in; k = 0 set to zero.  Also accumulates
+// sum_n rho_n phi_n = sum_k w_k G_k |rho^_k|^2 (Parseval over the half spectrum,
+// w = 1 on the x = 0 and x = N/2 planes, 2 elsewhere) for W_g.
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef,
+                                                        double* part) {
+  const int n = m.n, nh = m.n / 2 + 1;
+  const int64_t total = int64_t(n) * n * nh;
+  const R inv_n = R(1) / R(n);
+  R wsum = R(0);
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    int jx = int(e % nh);
+    int64_t r = e / nh;
+    int jy = int(r % n);
+    int jz = int(r / n);
+    R s = sinpi_sq(R(jx) * inv_n) + sinpi_sq(R(jy) * inv_n) + sinpi_sq(R(jz) * inv_n);
+    auto v = spec[e];
+    R g = (e == 0) ? R(0) : coef / s;
+    R re = v.x, im = v.y;
+    R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
+    wsum += w * g * (re * re + im * im);
+    v.x = re * g;
+    v.y = im * g;
+    spec[e] = v;
+  }
+  double acc[1] = {double(wsum)};
+  block_sum_store<1>(acc, part, gridDim.x);
+}
+
+// ---------------------------------------------------------------- S5: quantum stencil
+// Q~_n = qcoef * sum_d [(s_{n+e_d} - s_n) + (s_{n-e_d} - s_n)] / s_n with
+// s = sqrt(max(rho, floor)) and neighbours at +-step (Eq. quantumpressure with
+// the seven-point Laplacian; comoving 1/a^2 applied by the kick weights).
+// Also accumulates the K_rho sum of Eq. (diskpoten): compact -> sum_d
+// (s_{n+e_d} - s_n)^2, wide -> (1/4) sum_d (s_{n+2e_d}... written here as
+// (s_{n+step e_d} - s_{n-step e_d})^2 / 4 with step = 1 for the printed form.
+template <typename R>
+__device__ __forceinline__ R sfloor(R rho, R fl) {
+  return sqrt(rho > fl ? rho : fl);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ rho, Mesh m, StencilParams sp,
+                                                          R* __restrict__ q, double* part) {
+  const int n = m.n;
+  R ksum = R(0);
+  const R fl = R(sp.rho_floor);
+  const R qc = R(sp.qcoef);
+  for (uint32_t node = blockIdx.x * blockDim.x + threadIdx.x; node < m.n3; node += gridDim.x * blockDim.x) {
+    int x, y, z;
+    split_cell(node, m, x, y, z);
+    const int st = sp.step;
+    const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
+    const uint32_t xp = wrap(x + st, n), xm = wrap(x - st, n);
+    const uint32_t yp = uint32_t(wrap(y + st, n)) * n, ym = uint32_t(wrap(y - st, n)) * n;
+    const uint32_t zp = uint32_t(wrap(z + st, n)) * m.n2, zm = uint32_t(wrap(z - st, n)) * m.n2;
+    const R r0 = __ldg(rho + node);
+    const R rxp = __ldg(rho + zn + yn + xp), rxm = __ldg(rho + zn + yn + xm);
+    const R ryp = __ldg(rho + zn + yp + x), rym = __ldg(rho + zn + ym + x);
+    const R rzp = __ldg(rho + zp + yn + x), rzm = __ldg(rho + zm + yn + x);
+    R s0 = sfloor(r0, fl);
+    R sxp = sfloor(rxp, fl), sxm = sfloor(rxm, fl);
+    R syp = sfloor(ryp, fl), sym = sfloor(rym, fl);
+    R szp = sfloor(rzp, fl), szm = sfloor(rzm, fl);
+    R lap = ((sxp - s0) + (sxm - s0)) + ((syp - s0) + (sym - s0)) + ((szp - s0) + (szm - s0));
+    R qv = qc * lap / s0;
+    if (sizeof(R) == 4 && double(r0) < sp.rho_fp64) {
+      // near-empty node: the ratio lap(s)/s is ill-conditioned, evaluate in fp64
+      const double fd = sp.rho_floor;
+      double t0 = sfloor(double(r0), fd);
+      double l = ((sfloor(double(rxp), fd) - t0) + (sfloor(double(rxm), fd) - t0)) +
+                 ((sfloor(double(ryp), fd) - t0) + (sfloor(double(rym), fd) - t0)) +
+                 ((sfloor(double(rzp), fd) - t0) + (sfloor(double(rzm), fd) - t0));
+      qv = R(sp.qcoef * l / t0);
+    }
+    q[node] = qv;
+    if (st == 1) {
+      R a = sxp - s0, b = syp - s0, c = szp - s0;
+      ksum += a * a + b * b + c * c;
+    } else {
+      // printed form of Eq. (diskpoten): central differences over +-dx
+      const R cxp = sfloor(__ldg(rho + zn + yn + wrap(x + 1, n)), fl);
+      const R cxm = sfloor(__ldg(rho + zn + yn + wrap(x - 1, n)), fl);
+      const R cyp = sfloor(__ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x), fl);
+      const R cym = sfloor(__ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x), fl);
+      const R czp = sfloor(__ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x), fl);
+      const R czm = sfloor(__ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x), fl);
+      R a = cxp - cxm, b = cyp - cym, c = czp - czm;
+      ksum += R(0.25) * (a * a + b * b + c * c);
+    }
+  }
+  double acc[1] = {double(ksum)};
+  block_sum_store<1>(acc, part, gridDim.x);
+}
+
+// ---------------------------------------------------------------- S6: interpolate + kick + drift
+// Gradient of a mesh potential at the particle, in one of two forms:
+//   central : sum_c w_c (f[c+e] - f[c-e]) / 2dx over the 8 cloud-in-cell corners c
+//   kernel  : grad_q sum_c f_c w_c  (Eq. equationofmotion; 8 corner values)
+struct Stencil {
+  uint32_t xi[4];  // x - 1, x, x + 1, x + 2 (wrapped)
+  uint32_t yi[4];  // rows times N
+  uint32_t zi[4];  // planes times N^2
+};
+
+template <typename R>
+__device__ __forceinline__ void grad_kernel(const R* __restrict__ f, const Stencil& s, const R (&wx)[2],
+                                            const R (&wy)[2], const R (&wz)[2], R inv_dx, R (&g)[3]) {
+  R c[2][2][2];
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) c[dz][dy][dx] = __ldg(f + s.zi[dz + 1] + s.yi[dy + 1] + s.xi[dx + 1]);
+  R gx = 0, gy = 0, gz = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      gx += wz[a] * wy[b] * (c[a][b][1] - c[a][b][0]);
+      gy += wz[a] * wx[b] * (c[a][1][b] - c[a][0][b]);
+      gz += wy[a] * wx[b] * (c[1][a][b] - c[0][a][b]);
+    }
+  g[0] = gx * inv_dx;
+  g[1] = gy * inv_dx;
+  g[2] = gz * inv_dx;
+}
+
+template <typename R>
+__device__ __forceinline__ void grad_central(const R* __restrict__ f, const Stencil& s, const R (&wx)[2],
+                                             const R (&wy)[2], const R (&wz)[2], R inv_dx, R (&g)[3]) {
+  R gx = 0, gy = 0, gz = 0;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const R* row = f + s.zi[dz + 1] + s.yi[dy + 1];
+      R u0 = __ldg(row + s.xi[0]), u1 = __ldg(row + s.xi[1]), u2 = __ldg(row + s.xi[2]), u3 = __ldg(row + s.xi[3]);
+      gx += wz[dz] * wy[dy] * (wx[0] * (u2 - u0) + wx[1] * (u3 - u1));
+    }
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const R* col = f + s.zi[dz + 1] + s.xi[dx + 1];
+      R u0 = __ldg(col + s.yi[0]), u1 = __ldg(col + s.yi[1]), u2 = __ldg(col + s.yi[2]), u3 = __ldg(col + s.yi[3]);
+      gy += wz[dz] * wx[dx] * (wy[0] * (u2 - u0) + wy[1] * (u3 - u1));
+    }
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const R* pil = f + s.yi[dy + 1] + s.xi[dx + 1];
+      R u0 = __ldg(pil + s.zi[0]), u1 = __ldg(pil + s.zi[1]), u2 = __ldg(pil + s.zi[2]), u3 = __ldg(pil + s.zi[3]);
+      gz += wy[dy] * wx[dx] * (wz[0] * (u2 - u0) + wz[1] * (u3 - u1));
+    }
+  const R h = R(0.5) * inv_dx;
+  g[0] = gx * h;
+  g[1] = gy * h;
+  g[2] = gz * h;
+}
+
+template <typename R>
+__device__ __forceinline__ bool finite3(R a, R b, R c) {
+  return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// Moves an offset o (cell units) into [0,1) and returns the integer carry.
+template <typename R>
+__device__ __forceinline__ int carry(R& o) {
+  R fl = floor(o);
+  fl = fl > R(1 << 29) ? R(1 << 29) : (fl < R(-(1 << 29)) ? R(-(1 << 29)) : fl);
+  int c = int(fl);
+  o -= fl;
+  if (o >= R(1)) {  // o was a tiny negative number: o - floor(o) rounded to 1
+    o = R(0);
+    c += 1;
+  }
+  if (o < R(0)) o = R(0);
+  return c;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
+                                                       uint32_t* keys, int64_t n, const R* __restrict__ phi,
+                                                       const R* __restrict__ qf, Mesh m, KickParams kp,
+                                                       double* part, double* acc_out, uint32_t* err) {
+  using V4 = typename VT<R>::v4;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double dg[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    V4 ps = pos[i];
+    V4 mo = mom[i];
+    const uint32_t cell = rec_cell(ps);
+    int cx, cy, cz;
+    split_cell(cell, m, cx, cy, cz);
+    const int nn = m.n;
+    Stencil s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      s.xi[k] = uint32_t(wrap(cx + k - 1, nn));
+      s.yi[k] = uint32_t(wrap(cy + k - 1, nn)) * uint32_t(nn);
+      s.zi[k] = uint32_t(wrap(cz + k - 1, nn)) * m.n2;
+    }
+    const R wx[2] = {R(1) - ps.y, ps.y}, wy[2] = {R(1) - ps.z, ps.z}, wz[2] = {R(1) - ps.w, ps.w};
+    const R inv_dx = R(kp.inv_dx);
+    R gp[3], gq[3] = {R(0), R(0), R(0)};
+    if (kp.grav_kernel)
+      grad_kernel(phi, s, wx, wy, wz, inv_dx, gp);
+    else
+      grad_central(phi, s, wx, wy, wz, inv_dx, gp);
+    if (kp.quantum) {
+      if (kp.q_kernel)
+        grad_kernel(qf, s, wx, wy, wz, inv_dx, gq);
+      else
+        grad_central(qf, s, wx, wy, wz, inv_dx, gq);
+    }
+    const R cg1 = R(kp.cg1), cq1 = R(kp.cq1);
+    R d1[3] = {cg1 * gp[0] + cq1 * gq[0], cg1 * gp[1] + cq1 * gq[1], cg1 * gp[2] + cq1 * gq[2]};
+    if (kp.accel_out) {
+      const uint32_t id = rec_id(mo);
+      acc_out[3 * size_t(id) + 0] = -double(d1[0]);
+      acc_out[3 * size_t(id) + 1] = -double(d1[1]);
+      acc_out[3 * size_t(id) + 2] = -double(d1[2]);
+    } else {
+      R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
+      if (kp.diag) {
+        dg[0] = double(px * px + py * py + pz * pz);
+        dg[1] = double(px);
+        dg[2] = double(py);
+        dg[3] = double(pz);
+      }
+      const R cg2 = R(kp.cg2), cq2 = R(kp.cq2);
+      px -= cg2 * gp[0] + cq2 * gq[0];
+      py -= cg2 * gp[1] + cq2 * gq[1];
+      pz -= cg2 * gp[2] + cq2 * gq[2];
+      uint32_t ncell = cell;
+      R fx = ps.y, fy = ps.z, fz = ps.w;
+      if (kp.drift != 0.0) {
+        const R dr = R(kp.drift);
+        fx += px * dr;
+        fy += py * dr;
+        fz += pz * dr;
+        if (!finite3(fx, fy, fz) || !finite3(px, py, pz)) {
+          atomicOr(err, ERR_NONFINITE);
+          fx = ps.y;
+          fy = ps.z;
+          fz = ps.w;
+        }
+        int ccx = carry(fx), ccy = carry(fy), ccz = carry(fz);
+        if (ccx | ccy | ccz) {
+          int64_t ix = (int64_t(cx) + ccx) % nn, iy = (int64_t(cy) + ccy) % nn, iz = (int64_t(cz) + ccz) % nn;
+          ix += ix < 0 ? nn : 0;
+          iy += iy < 0 ? nn : 0;
+          iz += iz < 0 ? nn : 0;
+          ncell = (uint32_t(iz) * uint32_t(nn) + uint32_t(iy)) * uint32_t(nn) + uint32_t(ix);
+        }
+      } else if (!finite3(px, py, pz)) {
+        atomicOr(err, ERR_NONFINITE);
+      }
+      pos[i] = make_pos(ncell, fx, fy, fz);
+      mom[i] = make_mom(px, py, pz, rec_id(mo));
+      keys[i] = ncell;
+    }
+  }
+  if (kp.diag) block_sum_store<4>(dg, part, gridDim.x);
+}
+
+// ---------------------------------------------------------------- power spectrum
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_power(const typename VT<R>::cplx* __restrict__ spec, Mesh m,
+                                                        int nbins, double* part) {
+  __shared__ double sb[3 * PK_MAX_BINS];
+  for (int b = threadIdx.x; b < 3 * nbins; b += blockDim.x) sb[b] = 0.0;
+  __syncthreads();
+  const int n = m.n, nh = m.n / 2 + 1;
+  const int64_t total = int64_t(n) * n * nh;
+  const double inv_n = 1.0 / double(n);
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    int jx = int(e % nh);
+    int64_t r = e / nh;
+    int jy = int(r % n);
+    int jz = int(r / n);
+    int mx = jx, my = jy <= n / 2 ? jy : jy - n, mz = jz <= n / 2 ? jz : jz - n;
+    double kk = sqrt(double(mx) * mx + double(my) * my + double(mz) * mz);
+    int shell = int(floor(kk + 0.5));
+    if (shell < 1 || shell > nbins) continue;
+    auto v = spec[e];
+    double p2 = double(v.x) * v.x + double(v.y) * v.y;
+    // CIC window prod_d sinc^2(k_d dx/2), k_d dx/2 = pi m_d / N
+    double win = 1.0;
+    const int md[3] = {mx, my, mz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (md[d] != 0) {
+        double t = double(md[d]) * inv_n;
+        double sc = sinpi(t) / (M_PI * t);
+        win *= sc * sc;
+      }
+    }
+    double w = (jx == 0 || jx == n / 2) ? 1.0 : 2.0;
+    atomicAdd(&sb[shell - 1], w);
+    atomicAdd(&sb[nbins + shell - 1], w * kk);
+    atomicAdd(&sb[2 * nbins + shell - 1], w * p2 / (win * win));
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 3 * nbins; b += blockDim.x) part[size_t(b) * gridDim.x + blockIdx.x] = sb[b];
+}
+
+// ---------------------------------------------------------------- helpers
+template <typename R>
+__global__ void k_get_particles(const typename VT<R>::v4* __restrict__ pos, const typename VT<R>::v4* __restrict__ mom,
+                                int64_t n, Mesh m, double dx, double* x, double* p) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto ps = pos[i];
+  auto mo = mom[i];
+  int cx, cy, cz;
+  split_cell(rec_cell(ps), m, cx, cy, cz);
+  size_t id = rec_id(mo);
+  x[3 * id + 0] = (double(cx) + double(ps.y)) * dx;
+  x[3 * id + 1] = (double(cy) + double(ps.z)) * dx;
+  x[3 * id + 2] = (double(cz) + double(ps.w)) * dx;
+  p[3 * id + 0] = double(mo.x);
+  p[3 * id + 1] = double(mo.y);
+  p[3 * id + 2] = double(mo.z);
+}
+
+template <typename R>
+__global__ void k_get_order(const typename VT<R>::v4* __restrict__ pos, const typename VT<R>::v4* __restrict__ mom,
+                            int64_t n, uint32_t* cell, uint32_t* id) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cell[i] = rec_cell(pos[i]);
+  id[i] = rec_id(mom[i]);
+}
+
+template <typename R>
+__global__ void k_to_double(const R* __restrict__ f, int64_t n, double* out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = double(f[i]);
+}
+template <typename R>
+__global__ void k_from_double(const double* __restrict__ f, int64_t n, R* out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = R(f[i]);
+}
+
+// ---------------------------------------------------------------- launch wrappers
+inline unsigned mesh_grid(uint32_t n3) { return (n3 + MESH_THREADS - 1) / MESH_THREADS; }
+
+template <typename R>
+cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, Mesh m, double inv_dx, void* pos,
+                                  void* mom, uint32_t* keys, uint32_t* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  using V4 = typename VT<R>::v4;
+  k_init_particles<R><<<unsigned((n + 255) / 256), 256, 0, s>>>(x, p, n, m, inv_dx, (V4*)pos, (V4*)mom, keys, err);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_deposit(const void* pos, const uint32_t* cs, int64_t n, Mesh m, double norm, R* rho,
+                           cudaStream_t s) {
+  using V4 = typename VT<R>::v4;
+  k_deposit<R><<<mesh_grid(m.n3), MESH_THREADS, 0, s>>>((const V4*)pos, cs, uint32_t(n), m, R(norm), rho);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s) {
+  using C = typename VT<R>::cplx;
+  k_green<R><<<RED_GRID, MESH_THREADS, 0, s>>>((C*)spec, m, R(coef), part);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s) {
+  k_stencil<R><<<RED_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
+                        KickParams kp, double* part, double* acc, uint32_t* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  using V4 = typename VT<R>::v4;
+  k_kick<R><<<kick_blocks(n), KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, part, acc, err);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s) {
+  using C = typename VT<R>::cplx;
+  k_power<R><<<RED_GRID, MESH_THREADS, 0, s>>>((const C*)spec, m, nbins, part);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Mesh m, double dx, double* x, double* p,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  using V4 = typename VT<R>::v4;
+  k_get_particles<R><<<unsigned((n + 255) / 256), 256, 0, s>>>((const V4*)pos, (const V4*)mom, n, m, dx, x, p);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_get_order(const void* pos, const void* mom, int64_t n, uint32_t* cell, uint32_t* id,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  using V4 = typename VT<R>::v4;
+  k_get_order<R><<<unsigned((n + 255) / 256), 256, 0, s>>>((const V4*)pos, (const V4*)mom, n, cell, id);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_to_double(const R* f, int64_t n, double* out, cudaStream_t s) {
+  k_to_double<R><<<RED_GRID, 256, 0, s>>>(f, n, out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_from_double(const double* f, int64_t n, R* out, cudaStream_t s) {
+  k_from_double<R><<<RED_GRID, 256, 0, s>>>(f, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pm

@@ -1,0 +1,50 @@
+// fp32 instantiation of the step kernels, plus the type-independent launchers.
+#include "pm_kernels.cuh"
+#include "pm_sort.cuh"
+
+namespace pm {
+
+cudaError_t launch_radix_upsweep(const uint32_t* keys, int64_t n, int shift, int bits, uint32_t* hist, int ntiles,
+                                 cudaStream_t s) {
+  size_t smem = (size_t(1) << bits) * sizeof(uint32_t);
+  k_radix_upsweep<<<ntiles, RS_THREADS, smem, s>>>(keys, n, shift, bits, hist, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radix_scan(uint32_t* hist, int ntiles, int bits, uint32_t* digit_total, cudaStream_t s) {
+  k_radix_scan<<<1 << bits, RS_THREADS, 0, s>>>(hist, ntiles, digit_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_start(const uint32_t* keys, int64_t n, uint32_t ncell, uint32_t* cell_start, cudaStream_t s) {
+  k_cell_start<<<unsigned((n + 1 + 255) / 256), 256, 0, s>>>(keys, n, ncell, cell_start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s) {
+  if (nvals <= 0) return cudaSuccess;
+  k_reduce<<<nvals, 256, 0, s>>>(part, nblocks, out);
+  return cudaGetLastError();
+}
+
+#define PM_INSTANTIATE(R)                                                                                         \
+  template cudaError_t launch_init_particles<R>(const double*, const double*, int64_t, Mesh, double, void*, void*, \
+                                                uint32_t*, uint32_t*, cudaStream_t);                              \
+  template cudaError_t launch_radix_downsweep<R>(bool, const uint32_t*, const uint32_t*, int64_t, int, int,       \
+                                                 const uint32_t*, const uint32_t*, int, uint32_t*, uint32_t*,     \
+                                                 const void*, const void*, void*, void*, cudaStream_t);           \
+  template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
+  template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
+  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, cudaStream_t);               \
+  template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
+                                      double*, double*, uint32_t*, cudaStream_t);                                 \
+  template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \
+  template cudaError_t launch_get_particles<R>(const void*, const void*, int64_t, Mesh, double, double*, double*, \
+                                               cudaStream_t);                                                     \
+  template cudaError_t launch_get_order<R>(const void*, const void*, int64_t, uint32_t*, uint32_t*, cudaStream_t); \
+  template cudaError_t launch_to_double<R>(const R*, int64_t, double*, cudaStream_t);                             \
+  template cudaError_t launch_from_double<R>(const double*, int64_t, R*, cudaStream_t);
+
+PM_INSTANTIATE(float)
+
+}  // namespace pm

@@ -1,0 +1,236 @@
+"""Python binding of the C ABI in include/pm.h (argument marshalling only).
+
+Every stage of the step runs in the CUDA kernels of libpm.so; PyTorch only
+provides the device arena and the stream.  There is no CPU fallback: if the
+library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpm.so")
+
+PM_OK = 0
+STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_NO_MEMORY", 3: "PM_ERR_CUDA",
+          4: "PM_ERR_CUFFT", 5: "PM_ERR_NONFINITE", 6: "PM_ERR_STATE"}
+FORCE_MESHGRAD, FORCE_HYBRID, FORCE_LAGRANGIAN = 0, 1, 2
+LAP_COMPACT, LAP_WIDE = 0, 1
+FP32, FP64 = 0, 1
+FIELD_RHO, FIELD_PHI, FIELD_Q = 0, 1, 2
+
+# every entry point declared in include/pm.h
+EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create", "pm_destroy",
+           "pm_set_particles", "pm_get_particles", "pm_deposit", "pm_forces", "pm_step", "pm_run",
+           "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
+           "pm_profile_begin", "pm_profile_end", "pm_last_error"]
+STAGES = ["sort_upsweep", "sort_scan", "sort_downsweep", "cell_start", "deposit", "fft_r2c", "green",
+          "fft_c2r", "stencil", "kick", "other"]
+CUFFT_STAGES = ("fft_r2c", "fft_c2r")
+
+
+class pm_config(C.Structure):
+    _fields_ = [("n_part", C.c_int64), ("n_mesh", C.c_int32), ("precision", C.c_int32),
+                ("box", C.c_double), ("omega_m", C.c_double), ("omega_l", C.c_double),
+                ("h", C.c_double), ("m22", C.c_double), ("quantum", C.c_int32),
+                ("force_mode", C.c_int32), ("lap", C.c_int32), ("cosmological", C.c_int32),
+                ("rho_floor", C.c_double), ("rho_fp64", C.c_double)]
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError("libpm.so not built (run paper_1608_00802_gb300.build.build()): %s" % path)
+    lib = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    vp = C.c_void_p
+    cfgp = C.POINTER(pm_config)
+    sig = {
+        "pm_config_default": (None, [cfgp]),
+        "pm_hbar_over_m": (C.c_double, [cfgp]),
+        "pm_arena_bytes": (C.c_size_t, [cfgp]),
+        "pm_create": (C.c_int, [cfgp, vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "pm_destroy": (C.c_int, [vp]),
+        "pm_set_particles": (C.c_int, [vp, dp, dp]),
+        "pm_get_particles": (C.c_int, [vp, dp, dp]),
+        "pm_deposit": (C.c_int, [vp, dp]),
+        "pm_forces": (C.c_int, [vp, C.c_double, dp]),
+        "pm_step": (C.c_int, [vp, C.c_double, C.c_double]),
+        "pm_run": (C.c_int, [vp, C.c_int32, C.c_double, C.c_double]),
+        "pm_energy": (C.c_int, [vp, C.c_double, dp]),
+        "pm_power_spectrum": (C.c_int, [vp, C.c_int32, dp, dp, C.POINTER(C.c_int64)]),
+        "pm_get_field": (C.c_int, [vp, C.c_int32, dp]),
+        "pm_set_density": (C.c_int, [vp, dp]),
+        "pm_get_order": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+        "pm_profile_begin": (C.c_int, [vp, C.c_int32]),
+        "pm_profile_end": (C.c_int, [vp, dp, C.POINTER(C.c_int64)]),
+        "pm_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_config(n_part, n_mesh, box, precision=FP32, omega_m=0.3, omega_l=0.7, h=0.7, m22=2.5,
+                quantum=True, force_mode=FORCE_MESHGRAD, lap=LAP_COMPACT, cosmological=True,
+                rho_floor=1e-6, rho_fp64=1e-2) -> pm_config:
+    cfg = pm_config()
+    lib().pm_config_default(C.byref(cfg))
+    cfg.n_part, cfg.n_mesh, cfg.box = int(n_part), int(n_mesh), float(box)
+    cfg.precision = int(precision)
+    cfg.omega_m, cfg.omega_l, cfg.h, cfg.m22 = float(omega_m), float(omega_l), float(h), float(m22)
+    cfg.quantum, cfg.force_mode, cfg.lap = int(bool(quantum)), int(force_mode), int(lap)
+    cfg.cosmological = int(bool(cosmological))
+    cfg.rho_floor, cfg.rho_fp64 = float(rho_floor), float(rho_fp64)
+    return cfg
+
+
+def arena_bytes(cfg: pm_config) -> int:
+    return int(lib().pm_arena_bytes(C.byref(cfg)))
+
+
+class Sim:
+    """One simulation: a device arena (a torch uint8 tensor) and a stream.
+
+    Methods mirror the C entry points; arrays are numpy float64 (n, 3) or
+    (N, N, N) indexed [z, y, x].
+    """
+
+    def __init__(self, cfg: pm_config, device=None, stream=None, arena=None):
+        import torch
+        self.cfg = cfg
+        self.n = int(cfg.n_part)
+        self.N = int(cfg.n_mesh)
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = arena_bytes(cfg)
+        if nbytes == 0:
+            raise PMError(1, lib().pm_last_error(None).decode())
+        if arena is None:
+            arena = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        elif arena.numel() * arena.element_size() < nbytes:
+            raise PMError(2, "arena too small")
+        self.arena = arena
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = lib().pm_create(C.byref(cfg), C.c_void_p(arena.data_ptr()), C.c_size_t(nbytes),
+                             C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != PM_OK:
+            raise PMError(st, lib().pm_last_error(None).decode())
+        self.handle = h
+
+    # -- helpers
+    def _check(self, st):
+        if st != PM_OK:
+            raise PMError(st, lib().pm_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C ABI
+    def set_particles(self, x, p):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        assert x.shape == (self.n, 3) and p.shape == (self.n, 3)
+        self._check(lib().pm_set_particles(self.handle, _dptr(x), _dptr(p)))
+
+    def get_particles(self, x=None, p=None):
+        """Positions and momenta in id order; x, p may be preallocated (e.g.
+        pinned) float64 (n, 3) arrays."""
+        x = np.empty((self.n, 3)) if x is None else x
+        p = np.empty((self.n, 3)) if p is None else p
+        assert x.dtype == np.float64 and x.flags.c_contiguous and x.shape == (self.n, 3)
+        assert p.dtype == np.float64 and p.flags.c_contiguous and p.shape == (self.n, 3)
+        self._check(lib().pm_get_particles(self.handle, _dptr(x), _dptr(p)))
+        return x, p
+
+    def deposit(self, copy=True):
+        if not copy:
+            self._check(lib().pm_deposit(self.handle, None))
+            return None
+        rho = np.empty((self.N, self.N, self.N))
+        self._check(lib().pm_deposit(self.handle, _dptr(rho)))
+        return rho
+
+    def forces(self, a):
+        acc = np.empty((self.n, 3))
+        self._check(lib().pm_forces(self.handle, float(a), _dptr(acc)))
+        return acc
+
+    def step(self, a0, a1):
+        self._check(lib().pm_step(self.handle, float(a0), float(a1)))
+
+    def run(self, nsteps, a_start, a_end):
+        self._check(lib().pm_run(self.handle, int(nsteps), float(a_start), float(a_end)))
+
+    def energy(self, a):
+        out = np.empty(6)
+        self._check(lib().pm_energy(self.handle, float(a), _dptr(out)))
+        return out
+
+    def power_spectrum(self, nbins=None):
+        nbins = self.N // 2 if nbins is None else int(nbins)
+        k = np.empty(nbins)
+        pk = np.empty(nbins)
+        cnt = np.empty(nbins, dtype=np.int64)
+        self._check(lib().pm_power_spectrum(self.handle, nbins, _dptr(k), _dptr(pk),
+                                            cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+        return k, pk, cnt
+
+    def get_field(self, which):
+        f = np.empty((self.N, self.N, self.N))
+        self._check(lib().pm_get_field(self.handle, int(which), _dptr(f)))
+        return f
+
+    def set_density(self, rho):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        assert rho.shape == (self.N, self.N, self.N)
+        self._check(lib().pm_set_density(self.handle, _dptr(rho)))
+
+    def get_order(self):
+        cell = np.empty(self.n, dtype=np.uint32)
+        ids = np.empty(self.n, dtype=np.uint32)
+        self._check(lib().pm_get_order(self.handle, cell.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                       ids.ctypes.data_as(C.POINTER(C.c_uint32))))
+        return cell, ids
+
+    def profile_begin(self, capacity):
+        self._check(lib().pm_profile_begin(self.handle, int(capacity)))
+
+    def profile_end(self):
+        """{stage: (total ms, launches)} of the launches since profile_begin."""
+        ms = np.zeros(len(STAGES))
+        cnt = np.zeros(len(STAGES), dtype=np.int64)
+        self._check(lib().pm_profile_end(self.handle, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(STAGES)}
