@@ -211,7 +211,7 @@ def oracle_step_rate(w, budget_s=30.0):
         n_side, n_mesh, box, est = n_side // 2, n_mesh // 2, box / 2, est / 8
     a = schedule(w)
     x, p = ics.zeldovich(n_side, n_mesh, box, a[0], w["seed"], m22=w["m22"])
-    cfg = O.Config(n_mesh=n_mesh, box=box, m22=w["m22"])
+    cfg = O.Config(n_mesh=n_mesh, box=box, m22=w["m22"], force_mode=O.HYBRID)
     parts = O.force_parts(x, cfg)
     t0 = time.perf_counter()
     O.kdk_step(x, p, a[0], a[1], cfg, parts)
@@ -241,7 +241,7 @@ def run_reference(args):
         n_side, n_mesh, box, est = n_side // 2, n_mesh // 2, box / 2, est / 8
     a = schedule(w)
     x, p = ics.zeldovich(n_side, n_mesh, box, a[0], w["seed"], m22=w["m22"])
-    cfg = O.Config(n_mesh=n_mesh, box=box, m22=w["m22"])
+    cfg = O.Config(n_mesh=n_mesh, box=box, m22=w["m22"], force_mode=O.HYBRID)
     parts = None
     for i in range(args.warmup):
         x, p, parts = O.kdk_step(x, p, a[i], a[i + 1], cfg, parts)
@@ -285,7 +285,7 @@ def run_gpu(args):
     x, p = ics.zeldovich(w["n_side"], w["n_mesh"], w["box"], a[0], w["seed"] + rank, m22=w["m22"])
     n = len(x)
     cfg = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP32, m22=w["m22"],
-                         force_mode=pm.FORCE_MESHGRAD)
+                         force_mode=pm.FORCE_HYBRID)
     stream = torch.cuda.Stream()
     sim = pm.Sim(cfg, stream=stream)
     sim.set_particles(x, p)
@@ -359,7 +359,7 @@ def run_gpu(args):
     fp64 = None
     if not args.no_fp64:
         cfg64 = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP64, m22=w["m22"],
-                               force_mode=pm.FORCE_MESHGRAD)
+                               force_mode=pm.FORCE_HYBRID)
         del sim
         torch.cuda.empty_cache()
         s64 = pm.Sim(cfg64, stream=stream)
@@ -389,7 +389,7 @@ def run_gpu(args):
             "warmup": W, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "precision": "fp32 cell+offset, fp32 mesh/FFT",
-                       "force_mode": "meshgrad", "parallelism": "replicas" if world > 1 else "single",
+                       "force_mode": "hybrid (PM gravity + Q by the kernel gradient, Sec. II.A step iii)", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.5 GB touched per step), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64,

@@ -17,7 +17,8 @@ cudaError_t launch_radix_scan(uint32_t* hist, int ntiles, int bits, uint32_t* di
 }
 
 cudaError_t launch_cell_start(const uint32_t* keys, int64_t n, uint32_t ncell, uint32_t* cell_start, cudaStream_t s) {
-  k_cell_start<<<unsigned((n + 1 + 255) / 256), 256, 0, s>>>(keys, n, ncell, cell_start);
+  const int64_t warps = n / 32 + 1;  // slots 0..n, the last warp covers the tail up to ncell
+  k_cell_start<<<unsigned((warps * 32 + 255) / 256), 256, 0, s>>>(keys, n, ncell, cell_start);
   return cudaGetLastError();
 }
 

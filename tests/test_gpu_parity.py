@@ -244,10 +244,13 @@ def test_power_spectrum_matches_oracle(pm, precision):
     np.testing.assert_allclose(pk, po, rtol=1e-4 if precision == "fp32" else 1e-10)
 
 
-def test_power_spectrum_after_full_run_fp64(pm):
-    """32^3 particles on 64^3, z = 100 -> 3 in 200 steps, fp64 path vs oracle:
-    P(k) within 0.1% for k <= k_Nyq/2."""
-    sim, ocfg = make(pm, 32, 64, 1.0, "fp64")
+@pytest.mark.parametrize("precision,mode", [("fp64", "hybrid"), ("fp64", "lagrangian"), ("fp32", "hybrid")])
+def test_power_spectrum_after_full_run(pm, precision, mode):
+    """32^3 particles on 64^3, z = 100 -> 3 in 200 steps (the 32^3/64^3
+    workload) vs the oracle: P(k) within 0.1% for k <= k_Nyq/2.  (The central-
+    difference Q force is chaotic on this 2x CIC mesh, see the design notes,
+    so the full-run comparison uses the kernel-gradient Q force.)"""
+    sim, ocfg = make(pm, 32, 64, 1.0, precision, mode=mode)
     x0, p0 = sim.get_particles()
     sim.run(200, 1 / 101.0, 1 / 4.0)
     k, pk, _ = sim.power_spectrum()
