@@ -6,7 +6,7 @@ L = 2 Mpc/h, m = 2.5e-22 eV, Omega_m = 0.3, Omega_L = 0.7, h = 0.7, fp32
 conditions at z = 100 from the seed-42 Gaussian field with
 P ~ k^0.96 T_BBKS^2 T_FDM^2, 500 leapfrog steps (uniform in ln a) to z = 3.
 A step is one pass of the whole path: interpolate + kick + drift, radix sort
-by cell, cell starts, deterministic CIC deposit, R2C FFT, Green's function,
+by cell, row starts, deterministic CIC deposit, R2C FFT, Green's function,
 C2R FFT, quantum-pressure stencil.  The timed steps are W..W+K of that
 schedule.  Each step touches ~0.5 GB (> the 126 MB L2), so no L2 flush is
 inserted between steps.
@@ -53,8 +53,8 @@ def algorithmic_bytes(stage, n, n_mesh, rsz=4):
     return {
         # pos + mom read and written, new key written; phi~ and Q~ read once
         "kick": n * (4 * rec + 4) + 2 * n3 * rsz,
-        # particle positions read once, cell starts read once, rho written
-        "deposit": n * rec + n3 * 4 + n3 * rsz,
+        # particle positions read once, row starts read once, rho written
+        "deposit": n * rec + n_mesh * n_mesh * 4 + n3 * rsz,
         # rho read, Q~ written
         "stencil": 2 * n3 * rsz,
         # half spectrum read and written
@@ -64,7 +64,7 @@ def algorithmic_bytes(stage, n, n_mesh, rsz=4):
         # keys read once per upsweep; per downsweep keys + values read and written
         "sort_upsweep": n * 4,
         "sort_downsweep": n * 16,
-        "cell_start": n * 4 + n3 * 4,
+        "row_start": n * 4 + n_mesh * n_mesh * 4,
     }.get(stage)
 
 
@@ -328,7 +328,7 @@ def run_gpu(args):
     achieved = d["GBps"]
     kernel_names = {"kick": "k_kick", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
                     "sort_downsweep": "k_radix_downsweep", "sort_upsweep": "k_radix_upsweep",
-                    "cell_start": "k_cell_start", "sort_scan": "k_radix_scan"}
+                    "row_start": "k_row_start", "sort_scan": "k_radix_scan"}
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": ncu_traffic(kernel_names.get(dom, dom), "c2"), "peak_source": peak_kind,

@@ -164,7 +164,7 @@ pm_status pm_get_order(pm_sim* sim, uint32_t* cell, uint32_t* id);
  * the simulation's stream).  The cuFFT stages cover one cufftExec call each. */
 enum {
   PM_STAGE_SORT_UPSWEEP = 0, PM_STAGE_SORT_SCAN = 1, PM_STAGE_SORT_DOWNSWEEP = 2,
-  PM_STAGE_CELL_START = 3, PM_STAGE_DEPOSIT = 4, PM_STAGE_FFT_R2C = 5, PM_STAGE_GREEN = 6,
+  PM_STAGE_ROW_START = 3, PM_STAGE_DEPOSIT = 4, PM_STAGE_FFT_R2C = 5, PM_STAGE_GREEN = 6,
   PM_STAGE_FFT_C2R = 7, PM_STAGE_STENCIL = 8, PM_STAGE_KICK = 9, PM_STAGE_OTHER = 10,
   PM_NSTAGES = 11
 };

@@ -87,7 +87,7 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[3], vals[2], cell_start, rho, phi, q, spec, work, staging, hist, digit_total, part,
+  size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, digit_total, part,
       part_aux, red, err, total;
   int key_bits, passes, digit_bits, ntiles;
 };
@@ -154,7 +154,7 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   for (int k = 0; k < 2; ++k) L.mom[k] = take(n * recsz);
   for (int k = 0; k < 3; ++k) L.keys[k] = take(n * 4);
   for (int k = 0; k < 2; ++k) L.vals[k] = take(n * 4);
-  L.cell_start = take((n3 + 1) * 4);
+  L.row_start = take((N * N + 1) * 4);
   L.rho = take(n3 * rsz);
   L.phi = take(n3 * rsz);
   L.q = take(n3 * rsz);
@@ -334,8 +334,8 @@ pm_status sort_particles(pm_sim* s) {
     }
   }
   {
-    PROF(s, PM_STAGE_CELL_START);
-    CU(s, launch_cell_start(s->keys, n, s->mesh.n3, s->at<uint32_t>(L.cell_start), s->stream));
+    PROF(s, PM_STAGE_ROW_START);
+    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->stream));
   }
   s->sorted = true;
   return PM_OK;
@@ -387,7 +387,7 @@ pm_status deposit(pm_sim* s) {
     if (st != PM_OK) return st;
   }
   PROF(s, PM_STAGE_DEPOSIT);
-  CU(s, launch_deposit<R>(s->pos(), s->at<uint32_t>(s->L.cell_start), s->n(), s->mesh, s->norm, s->at<R>(s->L.rho),
+  CU(s, launch_deposit<R>(s->pos(), s->at<uint32_t>(s->L.row_start), s->n(), s->mesh, s->norm, s->at<R>(s->L.rho),
                           s->stream));
   return PM_OK;
 }

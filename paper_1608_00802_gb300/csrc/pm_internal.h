@@ -56,7 +56,7 @@ enum : uint32_t { ERR_NONFINITE = 1u };
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 16;
+constexpr int RS_ITEMS = 4;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_MAX_BITS = 10;
 
@@ -81,10 +81,10 @@ cudaError_t launch_radix_downsweep(bool last, const uint32_t* keys_in, const uin
                                    int shift, int bits, const uint32_t* hist, const uint32_t* digit_total,
                                    int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
                                    const void* mom_in, void* pos_out, void* mom_out, cudaStream_t s);
-cudaError_t launch_cell_start(const uint32_t* keys, int64_t n, uint32_t ncell, uint32_t* cell_start,
-                              cudaStream_t s);
+cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start,
+                             cudaStream_t s);
 template <typename R>
-cudaError_t launch_deposit(const void* pos, const uint32_t* cell_start, int64_t n, Mesh m, double norm, R* rho,
+cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
                            cudaStream_t s);
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);

@@ -60,6 +60,56 @@ __device__ __forceinline__ D4 ldg<D4>(const D4* p) {
   return r;
 }
 
+// Typed math: each call names its precision, so that fp32 code never takes
+// an fp64 routine (fp64 runs at a small fraction of the fp32 rate here).
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return ::sqrt(x); }
+__device__ __forceinline__ float r_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double r_floor(double x) { return ::floor(x); }
+__device__ __forceinline__ bool r_finite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool r_finite(double x) { return isfinite(x); }
+
+// ---------------------------------------------------------------- float-float
+// Extended precision from pairs of fp32 numbers (error-free transformations of
+// Dekker 1971 / Knuth TAOCP 4.2.2): value = hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits on the fp32 pipes.  Used where the method asks for
+// more than fp32 (near-empty nodes, diagnostic sums) because fp64 throughput
+// is a small fraction of fp32 throughput on this GPU.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // needs |a| >= |b|
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  return fast_two_sum(p, fmaf(a.lo, b, e));
+}
+__device__ __forceinline__ ff ff_sqrt(float x) {  // x > 0
+  float s = sqrtf(x);
+  float r = fmaf(-s, s, x);
+  return fast_two_sum(s, r / (2.0f * s));
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  float q1 = a.hi / b.hi;
+  ff r = ff_sub(a, ff_mul_f(b, q1));
+  return fast_two_sum(q1, r.hi / b.hi);
+}
+__device__ __forceinline__ ff ff_shfl_down(ff v, int o) {
+  return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
 __device__ __forceinline__ void split_cell(uint32_t c, const Mesh& m, int& x, int& y, int& z) {
   if (m.log2n >= 0) {
     uint32_t mask = uint32_t(m.n) - 1u;
@@ -81,6 +131,31 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Block sum of NV fp32 values per thread: float-float inside each warp, fp64
+// across warps and blocks (fixed order, so the sums are reproducible).
+template <int NV>
+__device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, int nblocks) {
+  __shared__ double shf[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    ff s = {v[k], 0.0f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
+    if (lane == 0) shf[warp][k] = double(s.hi) + double(s.lo);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += shf[w][k];
+      part[k * nblocks + blockIdx.x] = s;
+    }
+  }
 }
 
 // Block sum of NV doubles (fixed order); thread 0 gets the totals.
@@ -141,130 +216,76 @@ __global__ void k_init_particles(const double* __restrict__ x, const double* __r
   keys[i] = cell;
 }
 
-// ---------------------------------------------------------------- S1: deposit (gather)
-// rho_n = norm * sum over the particles of the eight cells n - {0,1}^3 of the
-// cloud-in-cell weight prod_d (1 - f_d or f_d), i.e. Eq. (rhodis) with the
-// tent kernel.  One thread per node, fixed summation order: (dz, dy) in
-// lexicographic order, cell x-1 before cell x, particles in storage order.
+// ---------------------------------------------------------------- S1: deposit
+// rho_n = norm * sum_i W(x_n - q_i): Eq. (rhodis) with the cloud-in-cell
+// tent, no floating-point atomics.  One warp owns one mesh row (z, y) and
+// keeps it in shared memory (N + 1 slots, slot N = node 0 seen from cell
+// N-1).  For each of the four source rows (z - dz, y - dy) it loads that
+// row's particles 32 at a time (they are contiguous after the sort) and adds
+// the x-weights f_x (to node c + 1) and 1 - f_x (to node c), times the y and z
+// weights, through a segmented warp scan: lanes with the same target node are
+// adjacent, the scan sums each run in a fixed tree order and the run's last
+// lane adds it to the node.  The order of all additions is fixed by the
+// particle order, so the result is reproducible.
+constexpr int DEP_WARPS = 8;
+
 template <typename R>
-__global__ void __launch_bounds__(MESH_THREADS) k_deposit(const typename VT<R>::v4* __restrict__ pos,
-                                                          const uint32_t* __restrict__ cs, uint32_t np, Mesh m,
-                                                          R norm, R* __restrict__ rho) {
-  using V4 = typename VT<R>::v4;
-  uint32_t node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= m.n3) return;
-  int x, y, z;
-  split_cell(node, m, x, y, z);
-  const int n = m.n;
-  R acc = R(0);
+__device__ __forceinline__ void seg_add(R v, int t, bool valid, R* acc) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int dz = 0; dz < 2; ++dz) {
-    const int zc = wrap(z - dz, n);
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const int yc = wrap(y - dy, n);
-      const uint32_t row = (uint32_t(zc) * n + uint32_t(yc)) * n;
-      const uint32_t own = row + uint32_t(x);  // the cell whose lower x-corner is this node
-      uint32_t b0, e0, b1, e1;
-      if (x > 0) {
-        b0 = __ldg(cs + own - 1);
-        e0 = __ldg(cs + own + 1);
-        b1 = e1 = 0;
-      } else {
-        b0 = __ldg(cs + row + n - 1);
-        e0 = __ldg(cs + row + n);
-        b1 = __ldg(cs + row);
-        e1 = __ldg(cs + row + 1);
-      }
-      // cell starts are clamped to the particle count so that no read leaves pos[]
-      e0 = min(e0, np);
-      e1 = min(e1, np);
-      R part = R(0);
-      for (uint32_t j = b0; j < e0; ++j) {
-        V4 r = ldg(pos + j);
-        R wx = (rec_cell(r) == own) ? R(1) - r.y : r.y;
-        R wy = dy ? r.z : R(1) - r.z;
-        R wz = dz ? r.w : R(1) - r.w;
-        part += wx * wy * wz;
-      }
-      for (uint32_t j = b1; j < e1; ++j) {
-        V4 r = ldg(pos + j);
-        R wx = R(1) - r.y;  // cell 0 == own
-        R wy = dy ? r.z : R(1) - r.z;
-        R wz = dz ? r.w : R(1) - r.w;
-        part += wx * wy * wz;
-      }
-      acc += part;
-    }
+  for (int off = 1; off < 32; off <<= 1) {
+    const R u = __shfl_up_sync(0xffffffffu, v, off);
+    const int tu = __shfl_up_sync(0xffffffffu, t, off);
+    if (lane >= off && tu == t) v += u;
   }
-  rho[node] = acc * norm;
+  const int tn = __shfl_down_sync(0xffffffffu, t, 1);
+  if (valid && (lane == 31 || tn != t)) acc[t] += v;
+  __syncwarp();
 }
 
-// Row-segment form of the same gather: one thread owns DEP_SEG consecutive
-// x-nodes of one row and, for each (dz, dy), walks the particles of the cells
-// x0-1 .. x0+DEP_SEG-1 of row (z-dz, y-dy) once, in storage order.  Every node
-// receives exactly the terms of the per-node gather in the same order (cell
-// x-1 before cell x), so the result is identical; each particle is read 4
-// times instead of 8, the loads are sequential and the stores vectorised.
-constexpr int DEP_SEG = 8;
-
 template <typename R>
-__global__ void __launch_bounds__(MESH_THREADS) k_deposit_rows(const typename VT<R>::v4* __restrict__ pos,
-                                                               const uint32_t* __restrict__ cs, uint32_t np, Mesh m,
-                                                               R norm, R* __restrict__ rho) {
+__global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
+                                                            const uint32_t* __restrict__ row_start, uint32_t np,
+                                                            Mesh m, R norm, R* __restrict__ rho) {
   using V4 = typename VT<R>::v4;
+  extern __shared__ __align__(16) unsigned char dep_smem[];
   const int n = m.n;
-  const int segs = n / DEP_SEG;
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m.n2 * uint32_t(segs)) return;
-  const int seg = int(t % uint32_t(segs));
-  const uint32_t rowid = t / uint32_t(segs);  // z*N + y
-  const int y = int(rowid % uint32_t(n)), z = int(rowid / uint32_t(n));
-  const int x0 = seg * DEP_SEG;
-  R acc[DEP_SEG];
-#pragma unroll
-  for (int k = 0; k < DEP_SEG; ++k) acc[k] = R(0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t orow = blockIdx.x * DEP_WARPS + warp;  // z*N + y
+  if (orow >= m.n2) return;
+  R* acc = reinterpret_cast<R*>(dep_smem) + warp * (n + 1);
+  for (int i = lane; i <= n; i += 32) acc[i] = R(0);
+  __syncwarp();
+  const int y = int(orow % uint32_t(n)), z = int(orow / uint32_t(n));
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz) {
-    const int zc = wrap(z - dz, n);
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
-      const int yc = wrap(y - dy, n);
-      const uint32_t row = (uint32_t(zc) * n + uint32_t(yc)) * n;
-      R part[DEP_SEG];
-#pragma unroll
-      for (int k = 0; k < DEP_SEG; ++k) part[k] = R(0);
-      // cells x0-1 (wrapped) then x0 .. x0+DEP_SEG-1
-      uint32_t bw, ew, b, e;
-      if (x0 > 0) {
-        bw = ew = 0;
-        b = __ldg(cs + row + x0 - 1);
-      } else {
-        bw = __ldg(cs + row + n - 1);
-        ew = min(__ldg(cs + row + n), np);
-        b = __ldg(cs + row);
+      const uint32_t srow = uint32_t(wrap(z - dz, n)) * uint32_t(n) + uint32_t(wrap(y - dy, n));
+      const uint32_t base_cell = srow * uint32_t(n);
+      const uint32_t b = __ldg(row_start + srow);
+      const uint32_t e = min(__ldg(row_start + srow + 1), np);
+      for (uint32_t j0 = b; j0 < e; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const bool valid = j < e;
+        R lo = R(0), hi = R(0);
+        int c = n + 1 + lane;  // invalid lanes: unique targets past the row
+        if (valid) {
+          const V4 r = ldg(pos + j);
+          c = int(rec_cell(r) - base_cell);
+          const R wyz = (dy ? r.z : R(1) - r.z) * (dz ? r.w : R(1) - r.w);
+          hi = r.y * wyz;
+          lo = (R(1) - r.y) * wyz;
+        }
+        seg_add(hi, valid ? c + 1 : c, valid, acc);  // f_x to the node above (slot N = node 0)
+        seg_add(lo, c, valid, acc);                  // 1 - f_x to the node of the cell
       }
-      e = min(__ldg(cs + row + x0 + DEP_SEG), np);
-      for (uint32_t j = bw; j < ew; ++j) {  // cell N-1 feeds node 0 with weight f_x
-        V4 r = ldg(pos + j);
-        R wyz = (dy ? r.z : R(1) - r.z) * (dz ? r.w : R(1) - r.w);
-        part[0] += r.y * wyz;
-      }
-      for (uint32_t j = b; j < e; ++j) {
-        V4 r = ldg(pos + j);
-        const int kx = int(rec_cell(r) - row) - x0;  // -1 .. DEP_SEG-1
-        const R wyz = (dy ? r.z : R(1) - r.z) * (dz ? r.w : R(1) - r.w);
-        const R lo = (R(1) - r.y) * wyz, hi = r.y * wyz;
-#pragma unroll
-        for (int k = 0; k < DEP_SEG; ++k) part[k] += (k == kx) ? lo : ((k == kx + 1) ? hi : R(0));
-      }
-#pragma unroll
-      for (int k = 0; k < DEP_SEG; ++k) acc[k] += part[k];
     }
   }
-  R* out = rho + rowid * uint32_t(n) + x0;
-#pragma unroll
-  for (int k = 0; k < DEP_SEG; ++k) out[k] = acc[k] * norm;
+  if (lane == 0) acc[0] += acc[n];
+  __syncwarp();
+  R* out = rho + size_t(orow) * n;
+  for (int i = lane; i < n; i += 32) out[i] = acc[i] * norm;
 }
 
 // ---------------------------------------------------------------- S3: Green's function
@@ -286,26 +307,26 @@ template <typename R>
 __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef,
                                                         double* part) {
   const int n = m.n, nh = m.n / 2 + 1;
-  const int64_t total = int64_t(n) * n * nh;
   const R inv_n = R(1) / R(n);
   R wsum = R(0);
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    int jx = int(e % nh);
-    int64_t r = e / nh;
-    int jy = int(r % n);
-    int jz = int(r / n);
-    R s = sinpi_sq(R(jx) * inv_n) + sinpi_sq(R(jy) * inv_n) + sinpi_sq(R(jz) * inv_n);
-    auto v = spec[e];
-    R g = (e == 0) ? R(0) : coef / s;
-    R re = v.x, im = v.y;
-    R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
-    wsum += w * g * (re * re + im * im);
-    v.x = re * g;
-    v.y = im * g;
-    spec[e] = v;
+  // one (jz, jy) row of the half spectrum per block iteration, jx over threads
+  for (uint32_t row = blockIdx.x; row < m.n2; row += gridDim.x) {
+    const int jy = int(row % uint32_t(n)), jz = int(row / uint32_t(n));
+    const R syz = sinpi_sq(R(jy) * inv_n) + sinpi_sq(R(jz) * inv_n);
+    typename VT<R>::cplx* line = spec + size_t(row) * nh;
+    for (int jx = threadIdx.x; jx < nh; jx += blockDim.x) {
+      const R s = syz + sinpi_sq(R(jx) * inv_n);
+      auto v = line[jx];
+      const R g = (row == 0 && jx == 0) ? R(0) : coef / s;
+      const R re = v.x, im = v.y;
+      const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
+      wsum += w * g * (re * re + im * im);
+      v.x = re * g;
+      v.y = im * g;
+      line[jx] = v;
+    }
   }
-  double acc[1] = {double(wsum)};
+  R acc[1] = {wsum};
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
@@ -318,18 +339,21 @@ __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* sp
 // (s_{n+step e_d} - s_{n-step e_d})^2 / 4 with step = 1 for the printed form.
 template <typename R>
 __device__ __forceinline__ R sfloor(R rho, R fl) {
-  return sqrt(rho > fl ? rho : fl);
+  return r_sqrt(rho > fl ? rho : fl);
 }
 
-// fp64 evaluation of Q~ at one near-empty node (taken by few nodes; kept out
-// of line so that the fp32 path does not pay for fp64 arithmetic).
-static __device__ __noinline__ float q_fp64(float r0, float rxp, float rxm, float ryp, float rym, float rzp, float rzm,
-                                     double floor_, double qcoef) {
-  double t0 = sfloor(double(r0), floor_);
-  double l = ((sfloor(double(rxp), floor_) - t0) + (sfloor(double(rxm), floor_) - t0)) +
-             ((sfloor(double(ryp), floor_) - t0) + (sfloor(double(rym), floor_) - t0)) +
-             ((sfloor(double(rzp), floor_) - t0) + (sfloor(double(rzm), floor_) - t0));
-  return float(qcoef * l / t0);
+// Extended-precision evaluation of Q~ at one near-empty node (float-float:
+// sqrt, neighbour differences, sum and ratio), kept out of line so that the
+// common path does not pay for it.
+static __device__ __noinline__ float q_ext(float r0, float rxp, float rxm, float ryp, float rym, float rzp, float rzm,
+                                           float fl, float qcoef) {
+  const ff t0 = ff_sqrt(fmaxf(r0, fl));
+  const ff d[6] = {ff_sub(ff_sqrt(fmaxf(rxp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rxm, fl)), t0),
+                   ff_sub(ff_sqrt(fmaxf(ryp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rym, fl)), t0),
+                   ff_sub(ff_sqrt(fmaxf(rzp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rzm, fl)), t0)};
+  const ff l = ff_add(ff_add(ff_add(d[0], d[1]), ff_add(d[2], d[3])), ff_add(d[4], d[5]));
+  const ff r = ff_div(l, t0);
+  return r.hi * qcoef + r.lo * qcoef;
 }
 
 template <typename R>
@@ -358,8 +382,8 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
     R szp = sfloor(rzp, fl), szm = sfloor(rzm, fl);
     R lap = ((sxp - s0) + (sxm - s0)) + ((syp - s0) + (sym - s0)) + ((szp - s0) + (szm - s0));
     R qv = qc * lap / s0;
-    if (r0 < lim64) qv = R(q_fp64(float(r0), float(rxp), float(rxm), float(ryp), float(rym), float(rzp), float(rzm),
-                                  sp.rho_floor, sp.qcoef));
+    if (r0 < lim64) qv = R(q_ext(float(r0), float(rxp), float(rxm), float(ryp), float(rym), float(rzp), float(rzm),
+                                 float(sp.rho_floor), float(sp.qcoef)));
     q[node] = qv;
     if (st == 1) {
       R a = sxp - s0, b = syp - s0, c = szp - s0;
@@ -376,7 +400,7 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
       ksum += R(0.25) * (a * a + b * b + c * c);
     }
   }
-  double acc[1] = {double(ksum)};
+  R acc[1] = {ksum};
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
@@ -450,13 +474,13 @@ __device__ __forceinline__ void grad_central(const R* __restrict__ f, const Sten
 
 template <typename R>
 __device__ __forceinline__ bool finite3(R a, R b, R c) {
-  return isfinite(a) && isfinite(b) && isfinite(c);
+  return r_finite(a) && r_finite(b) && r_finite(c);
 }
 
 // Moves an offset o (cell units) into [0,1) and returns the integer carry.
 template <typename R>
 __device__ __forceinline__ int carry(R& o) {
-  R fl = floor(o);
+  R fl = r_floor(o);
   fl = fl > R(1 << 29) ? R(1 << 29) : (fl < R(-(1 << 29)) ? R(-(1 << 29)) : fl);
   int c = int(fl);
   o -= fl;
@@ -475,7 +499,7 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, 
                                                        double* part, double* acc_out, uint32_t* err) {
   using V4 = typename VT<R>::v4;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  double dg[4] = {0.0, 0.0, 0.0, 0.0};
+  R dg[4] = {R(0), R(0), R(0), R(0)};
   if (i < n) {
     V4 ps = pos[i];
     V4 mo = mom[i];
@@ -513,10 +537,10 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, 
     } else {
       R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
       if (kp.diag) {
-        dg[0] = double(px * px + py * py + pz * pz);
-        dg[1] = double(px);
-        dg[2] = double(py);
-        dg[3] = double(pz);
+        dg[0] = px * px + py * py + pz * pz;
+        dg[1] = px;
+        dg[2] = py;
+        dg[3] = pz;
       }
       const R cg2 = R(kp.cg2), cq2 = R(kp.cq2);
       px -= cg2 * gp[0] + cq2 * gq[0];
@@ -648,16 +672,16 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
 }
 
 template <typename R>
-cudaError_t launch_deposit(const void* pos, const uint32_t* cs, int64_t n, Mesh m, double norm, R* rho,
+cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
                            cudaStream_t s) {
   using V4 = typename VT<R>::v4;
-  if (m.n % DEP_SEG == 0) {
-    const uint32_t threads = m.n2 * uint32_t(m.n / DEP_SEG);
-    k_deposit_rows<R><<<(threads + MESH_THREADS - 1) / MESH_THREADS, MESH_THREADS, 0, s>>>((const V4*)pos, cs,
-                                                                                          uint32_t(n), m, R(norm), rho);
-  } else {
-    k_deposit<R><<<mesh_grid(m.n3), MESH_THREADS, 0, s>>>((const V4*)pos, cs, uint32_t(n), m, R(norm), rho);
+  const size_t smem = size_t(DEP_WARPS) * (m.n + 1) * sizeof(R);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_deposit<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
   }
+  const unsigned blocks = (m.n2 + DEP_WARPS - 1) / DEP_WARPS;
+  k_deposit<R><<<blocks, DEP_WARPS * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho);
   return cudaGetLastError();
 }
 

@@ -16,9 +16,8 @@ cudaError_t launch_radix_scan(uint32_t* hist, int ntiles, int bits, uint32_t* di
   return cudaGetLastError();
 }
 
-cudaError_t launch_cell_start(const uint32_t* keys, int64_t n, uint32_t ncell, uint32_t* cell_start, cudaStream_t s) {
-  const int64_t warps = n / 32 + 1;  // slots 0..n, the last warp covers the tail up to ncell
-  k_cell_start<<<unsigned((warps * 32 + 255) / 256), 256, 0, s>>>(keys, n, ncell, cell_start);
+cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s) {
+  k_row_start<<<unsigned((n + 1 + 255) / 256), 256, 0, s>>>(keys, n, n_mesh, n_mesh * n_mesh, row_start);
   return cudaGetLastError();
 }
 

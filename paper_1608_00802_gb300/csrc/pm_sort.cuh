@@ -214,34 +214,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_downsweep(
   }
 }
 
-// cell_start[c] = first sorted slot whose key >= c, for c = 0..ncell.
-// One warp per 32 consecutive slots i0..i0+31 covers the cell range
-// (key[i0-1], key[i0+31]] (with key[-1] = -1 and key[n] = ncell); its lanes
-// write that range 32 cells at a time, each finding its slot by a binary
-// search over the warp's keys held in registers (shuffles), so the stores
-// are coalesced whatever the gaps between occupied cells.
-static __global__ void k_cell_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t ncell,
-                                    uint32_t* cell_start) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t i0 = warp * 32;
-  if (i0 > n) return;
-  const int64_t i = i0 + lane;
-  // key of slot i (ncell past the end) and the key before the warp's first slot
-  const int64_t k = i < n ? int64_t(__ldg(keys + i)) : int64_t(ncell);
-  const int64_t before = i0 == 0 ? -1 : int64_t(__ldg(keys + i0 - 1));
-  const int64_t last = __shfl_sync(0xffffffffu, k, 31);  // key of slot i0+31 (or ncell)
-  for (int64_t c0 = before + 1; c0 <= last; c0 += 32) {
-    const int64_t c = c0 + lane;
-    // first lane j with key_j >= c (exists for c <= last)
-    int lo = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int64_t kj = __shfl_sync(0xffffffffu, k, lo + step - 1);
-      if (kj < c) lo += step;
-    }
-    if (c <= last) cell_start[c] = uint32_t(i0 + lo);
-  }
+// row_start[r] = first sorted slot whose mesh row (key / N = z*N + y) is >= r,
+// for r = 0..N^2.  Each slot i fills the rows between the row of slot i-1 and
+// its own (rows are rarely empty, so almost every thread writes once or not
+// at all).
+static __global__ void k_row_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_mesh, uint32_t nrows,
+                                   uint32_t* row_start) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const int64_t prev = i == 0 ? -1 : int64_t(__ldg(keys + i - 1) / n_mesh);
+  const int64_t cur = i == n ? int64_t(nrows) : int64_t(__ldg(keys + i) / n_mesh);
+  for (int64_t r = prev + 1; r <= cur; ++r) row_start[r] = uint32_t(i);
 }
 
 // Fixed-order fp64 reduction of per-block partials: out[v] = sum_b part[v*nblocks + b].

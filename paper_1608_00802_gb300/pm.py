@@ -27,7 +27,7 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_set_particles", "pm_get_particles", "pm_deposit", "pm_forces", "pm_step", "pm_run",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
            "pm_profile_begin", "pm_profile_end", "pm_last_error"]
-STAGES = ["sort_upsweep", "sort_scan", "sort_downsweep", "cell_start", "deposit", "fft_r2c", "green",
+STAGES = ["sort_upsweep", "sort_scan", "sort_downsweep", "row_start", "deposit", "fft_r2c", "green",
           "fft_c2r", "stencil", "kick", "other"]
 CUFFT_STAGES = ("fft_r2c", "fft_c2r")
 
