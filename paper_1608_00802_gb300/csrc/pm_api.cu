@@ -374,7 +374,9 @@ pm_status mesh_from_density(pm_sim* s) {
     sp.rho_fp64 = s->cfg.rho_fp64;
     sp.qcoef = -0.5 * s->hbm * s->hbm / ((sp.step * s->dx) * (sp.step * s->dx));
     PROF(s, PM_STAGE_STENCIL);
-    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->stream));
+    // the half spectrum is free after the inverse FFT: it holds the near-empty node list
+    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->at<uint32_t>(L.spec),
+                            s->errword() + 1, s->stream));
   }
   s->fields_valid = true;
   return PM_OK;

@@ -306,25 +306,22 @@ __device__ __forceinline__ double sinpi_sq(double t) {
 template <typename R>
 __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef,
                                                         double* part) {
-  const int n = m.n, nh = m.n / 2 + 1;
+  const uint32_t n = uint32_t(m.n), nh = n / 2 + 1;
+  const uint32_t total = m.n2 * nh;  // < 2^30 for N <= 1024
   const R inv_n = R(1) / R(n);
   R wsum = R(0);
-  // one (jz, jy) row of the half spectrum per block iteration, jx over threads
-  for (uint32_t row = blockIdx.x; row < m.n2; row += gridDim.x) {
-    const int jy = int(row % uint32_t(n)), jz = int(row / uint32_t(n));
-    const R syz = sinpi_sq(R(jy) * inv_n) + sinpi_sq(R(jz) * inv_n);
-    typename VT<R>::cplx* line = spec + size_t(row) * nh;
-    for (int jx = threadIdx.x; jx < nh; jx += blockDim.x) {
-      const R s = syz + sinpi_sq(R(jx) * inv_n);
-      auto v = line[jx];
-      const R g = (row == 0 && jx == 0) ? R(0) : coef / s;
-      const R re = v.x, im = v.y;
-      const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
-      wsum += w * g * (re * re + im * im);
-      v.x = re * g;
-      v.y = im * g;
-      line[jx] = v;
-    }
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const uint32_t row = e / nh, jx = e - row * nh;
+    const uint32_t jz = row / n, jy = row - jz * n;
+    const R s = sinpi_sq(R(jx) * inv_n) + sinpi_sq(R(jy) * inv_n) + sinpi_sq(R(jz) * inv_n);
+    auto v = spec[e];
+    const R g = (e == 0) ? R(0) : coef / s;
+    const R re = v.x, im = v.y;
+    const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
+    wsum += w * g * (re * re + im * im);
+    v.x = re * g;
+    v.y = im * g;
+    spec[e] = v;
   }
   R acc[1] = {wsum};
   block_sum_store<1>(acc, part, gridDim.x);
@@ -343,9 +340,8 @@ __device__ __forceinline__ R sfloor(R rho, R fl) {
 }
 
 // Extended-precision evaluation of Q~ at one near-empty node (float-float:
-// sqrt, neighbour differences, sum and ratio), kept out of line so that the
-// common path does not pay for it.
-static __device__ __noinline__ float q_ext(float r0, float rxp, float rxm, float ryp, float rym, float rzp, float rzm,
+// sqrt, neighbour differences, sum and ratio).
+static __device__ __forceinline__ float q_ext(float r0, float rxp, float rxm, float ryp, float rym, float rzp, float rzm,
                                            float fl, float qcoef) {
   const ff t0 = ff_sqrt(fmaxf(r0, fl));
   const ff d[6] = {ff_sub(ff_sqrt(fmaxf(rxp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rxm, fl)), t0),
@@ -402,6 +398,99 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
   }
   R acc[1] = {ksum};
   block_sum_store<1>(acc, part, gridDim.x);
+}
+
+// fp32 compact-Laplacian stencil, four consecutive x-nodes per thread (N a
+// multiple of 4): one float4 per neighbour row, s = sqrt(max(rho, floor))
+// shared by the four nodes, Q~ written as one float4.  Nodes with
+// rho < rho_fp64 are appended to `list` (warp-aggregated, order irrelevant:
+// each listed node is recomputed independently by k_stencil_ext).
+static __global__ void __launch_bounds__(MESH_THREADS) k_stencil4(const float* __restrict__ rho, Mesh m, float fl, float qc,
+                                                           float lim, float* __restrict__ q, uint32_t* list,
+                                                           uint32_t* list_count, double* part) {
+  const uint32_t n = uint32_t(m.n), nq = n / 4;
+  const uint32_t total = m.n3 / 4;
+  const int lane = threadIdx.x & 31;
+  float ksum = 0.0f;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const uint32_t t = base + threadIdx.x;
+    uint32_t flags = 0, node0 = 0;
+    if (t < total) {
+      const uint32_t row = t / nq, x0 = (t - row * nq) * 4;
+      const uint32_t z = row / n, y = row - z * n;
+      node0 = row * n + x0;
+      const float* c = rho + size_t(row) * n;
+      const float4 r0 = __ldg(reinterpret_cast<const float4*>(c + x0));
+      const float rxm = __ldg(c + (x0 == 0 ? n - 1 : x0 - 1));
+      const float rxp = __ldg(c + (x0 + 4 == n ? 0 : x0 + 4));
+      const uint32_t yp = (y + 1 == n ? 0 : y + 1), ym = (y == 0 ? n - 1 : y - 1);
+      const uint32_t zp = (z + 1 == n ? 0 : z + 1), zm = (z == 0 ? n - 1 : z - 1);
+      const float4 ryp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + yp) * n + x0));
+      const float4 rym = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + ym) * n + x0));
+      const float4 rzp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zp) * n + y) * n + x0));
+      const float4 rzm = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zm) * n + y) * n + x0));
+      const float rc[6] = {rxm, r0.x, r0.y, r0.z, r0.w, rxp};
+      const float ra[4][4] = {{ryp.x, ryp.y, ryp.z, ryp.w}, {rym.x, rym.y, rym.z, rym.w},
+                              {rzp.x, rzp.y, rzp.z, rzp.w}, {rzm.x, rzm.y, rzm.z, rzm.w}};
+      float sc[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sc[i] = sqrtf(fmaxf(rc[i], fl));
+      float out[4];
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) {
+        const float s0 = sc[k2 + 1];
+        const float syp = sqrtf(fmaxf(ra[0][k2], fl)), sym = sqrtf(fmaxf(ra[1][k2], fl));
+        const float szp = sqrtf(fmaxf(ra[2][k2], fl)), szm = sqrtf(fmaxf(ra[3][k2], fl));
+        const float dxp = sc[k2 + 2] - s0, dyp = syp - s0, dzp = szp - s0;
+        const float lap = (dxp + (sc[k2] - s0)) + (dyp + (sym - s0)) + (dzp + (szm - s0));
+        out[k2] = qc * lap * __frcp_rn(s0);
+        ksum += dxp * dxp + dyp * dyp + dzp * dzp;
+        flags |= (rc[k2 + 1] < lim ? 1u : 0u) << k2;
+      }
+      *reinterpret_cast<float4*>(q + node0) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    // append flagged nodes: warp prefix of the counts, one atomic per warp
+    const uint32_t cnt = __popc(flags);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    if (wtotal) {
+      uint32_t wbase = 0;
+      if (lane == 31) wbase = atomicAdd(list_count, wtotal);
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      uint32_t idx = wbase + incl - cnt;
+      for (int k2 = 0; k2 < 4; ++k2)
+        if (flags & (1u << k2)) list[idx++] = node0 + k2;
+    }
+  }
+  float acc[1] = {ksum};
+  block_sum_store<1>(acc, part, gridDim.x);
+}
+
+// Recomputes Q~ in float-float at the listed near-empty nodes.
+static __global__ void __launch_bounds__(MESH_THREADS) k_stencil_ext(const float* __restrict__ rho, Mesh m, float fl,
+                                                              float qc, const uint32_t* __restrict__ list,
+                                                              const uint32_t* __restrict__ list_count,
+                                                              float* __restrict__ q) {
+  const uint32_t cnt = *list_count;
+  const int n = m.n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const uint32_t node = __ldg(list + i);
+    int x, y, z;
+    split_cell(node, m, x, y, z);
+    const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
+    const float r0 = __ldg(rho + node);
+    const float rxp = __ldg(rho + zn + yn + wrap(x + 1, n)), rxm = __ldg(rho + zn + yn + wrap(x - 1, n));
+    const float ryp = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
+    const float rym = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
+    const float rzp = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
+    const float rzm = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
+    q[node] = q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
+  }
 }
 
 // ---------------------------------------------------------------- S6: interpolate + kick + drift
@@ -693,8 +782,19 @@ cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStre
 }
 
 template <typename R>
-cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s) {
-  k_stencil<R><<<RED_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
+                           uint32_t* list_count, cudaStream_t s) {
+  if (sizeof(R) == 4 && sp.step == 1 && m.n % 4 == 0) {
+    // fp32 compact path: four nodes per thread, near-empty nodes redone in float-float
+    cudaError_t e = cudaMemsetAsync(list_count, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_stencil4<<<RED_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
+                                                 float(sp.rho_fp64), (float*)q, list, list_count, part);
+    k_stencil_ext<<<RED_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
+                                                    list, list_count, (float*)q);
+  } else {
+    k_stencil<R><<<RED_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
+  }
   return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
                                                  const void*, const void*, void*, void*, cudaStream_t);           \
   template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
-  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, cudaStream_t);               \
+  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,     \
+                                          cudaStream_t);               \
   template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
                                       double*, double*, uint32_t*, cudaStream_t);                                 \
   template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \
