@@ -61,9 +61,9 @@ def algorithmic_bytes(stage, n, n_mesh, rsz=4):
         "green": 2 * spec,
         "fft_r2c": n3 * rsz + spec,
         "fft_c2r": spec + n3 * rsz,
-        # keys read once per upsweep; per downsweep keys + values read and written
-        "sort_upsweep": n * 4,
-        "sort_downsweep": n * 16,
+        # keys read once for all histograms; per pass keys + values read and written
+        "sort_histogram": n * 4,
+        "sort_pass": n * 16,
         "row_start": n * 4 + n_mesh * n_mesh * 4,
     }.get(stage)
 
@@ -327,8 +327,8 @@ def run_gpu(args):
     d = per_stage[dom]
     achieved = d["GBps"]
     kernel_names = {"kick": "k_kick", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
-                    "sort_downsweep": "k_radix_downsweep", "sort_upsweep": "k_radix_upsweep",
-                    "row_start": "k_row_start", "sort_scan": "k_radix_scan"}
+                    "sort_pass": "k_sort_pass", "sort_histogram": "k_sort_histogram",
+                    "row_start": "k_row_start"}
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": ncu_traffic(kernel_names.get(dom, dom), "c2"), "peak_source": peak_kind,

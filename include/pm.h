@@ -45,7 +45,8 @@ typedef enum {
   PM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in pm_last_error) */
   PM_ERR_CUFFT = 4,       /* a cuFFT call failed */
   PM_ERR_NONFINITE = 5,   /* a NaN/Inf reached a particle or a diagnostic */
-  PM_ERR_STATE = 6        /* call out of order (e.g. no particles set yet) */
+  PM_ERR_STATE = 6,       /* call out of order (e.g. no particles set yet) */
+  PM_ERR_TIMEOUT = 7      /* a bounded device-side wait gave up (results of that call are invalid) */
 } pm_status;
 
 /* how a mesh potential becomes a particle force (Sec. II.A, step (iii)) */
@@ -163,10 +164,9 @@ pm_status pm_get_order(pm_sim* sim, uint32_t* cell, uint32_t* id);
 /* Stages timed by the profiler (one CUDA-event pair per launch, recorded on
  * the simulation's stream).  The cuFFT stages cover one cufftExec call each. */
 enum {
-  PM_STAGE_SORT_UPSWEEP = 0, PM_STAGE_SORT_SCAN = 1, PM_STAGE_SORT_DOWNSWEEP = 2,
-  PM_STAGE_ROW_START = 3, PM_STAGE_DEPOSIT = 4, PM_STAGE_FFT_R2C = 5, PM_STAGE_GREEN = 6,
-  PM_STAGE_FFT_C2R = 7, PM_STAGE_STENCIL = 8, PM_STAGE_KICK = 9, PM_STAGE_OTHER = 10,
-  PM_NSTAGES = 11
+  PM_STAGE_SORT_HISTOGRAM = 0, PM_STAGE_SORT_PASS = 1, PM_STAGE_ROW_START = 2, PM_STAGE_DEPOSIT = 3,
+  PM_STAGE_FFT_R2C = 4, PM_STAGE_GREEN = 5, PM_STAGE_FFT_C2R = 6, PM_STAGE_STENCIL = 7, PM_STAGE_KICK = 8,
+  PM_STAGE_OTHER = 9, PM_NSTAGES = 10
 };
 
 /* Starts recording a CUDA-event pair around every launch of this handle, for

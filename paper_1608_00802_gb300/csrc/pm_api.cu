@@ -87,7 +87,7 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, digit_total, part,
+  size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, status, part,
       part_aux, red, err, total;
   int key_bits, passes, digit_bits, ntiles;
 };
@@ -163,8 +163,9 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   size_t stage = 6 * n * 8;
   if (n3 * 8 > stage) stage = n3 * 8;
   L.staging = take(stage);
-  L.hist = take((size_t(1) << L.digit_bits) * size_t(L.ntiles) * 4);
-  L.digit_total = take((size_t(1) << L.digit_bits) * 4);
+  // digit histograms of all passes (radix_max stride) + one tile counter per pass
+  L.hist = take((3 * (size_t(1) << RS_MAX_BITS) + 4) * 4);
+  L.status = take((size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8);
   size_t nkb = size_t(kick_blocks(int64_t(n)));
   size_t npart = 4 * nkb;
   if (size_t(RED_GRID) * 3 * PK_MAX_BINS > npart) npart = size_t(RED_GRID) * 3 * PK_MAX_BINS;
@@ -214,6 +215,7 @@ struct pm_sim {
   uint32_t* keys_tmp[2];
   cufftHandle plan_fwd, plan_inv;
   bool have_particles, sorted, fields_valid;
+  uint32_t sort_epoch = 0;
   std::string err;
   // profiler: event pairs around launches while enabled
   bool prof_on = false;
@@ -289,8 +291,14 @@ pm_status sort_particles(pm_sim* s) {
   const Layout& L = s->L;
   const int64_t n = s->n();
   uint32_t* hist = s->at<uint32_t>(L.hist);
-  uint32_t* dtot = s->at<uint32_t>(L.digit_total);
+  uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
+  uint64_t* status = s->at<uint64_t>(L.status);
   uint32_t* vals[2] = {s->at<uint32_t>(L.vals[0]), s->at<uint32_t>(L.vals[1])};
+  CU(s, cudaMemsetAsync(hist, 0, (3 * (size_t(1) << RS_MAX_BITS) + 4) * 4, s->stream));
+  {
+    PROF(s, PM_STAGE_SORT_HISTOGRAM);
+    CU(s, launch_sort_histogram(s->keys, n, L.passes, L.digit_bits, L.key_bits, hist, s->stream));
+  }
   const uint32_t* kin = s->keys;
   const uint32_t* vin = nullptr;
   int tmp = 0;
@@ -298,20 +306,15 @@ pm_status sort_particles(pm_sim* s) {
     const int shift = p * L.digit_bits;
     const int bits = (shift + L.digit_bits <= L.key_bits) ? L.digit_bits : (L.key_bits - shift);
     const bool last = p == L.passes - 1;
-    {
-      PROF(s, PM_STAGE_SORT_UPSWEEP);
-      CU(s, launch_radix_upsweep(kin, n, shift, bits, hist, L.ntiles, s->stream));
-    }
-    {
-      PROF(s, PM_STAGE_SORT_SCAN);
-      CU(s, launch_radix_scan(hist, L.ntiles, bits, dtot, s->stream));
-    }
+    s->sort_epoch = (s->sort_epoch + 1) & 0xffffu;
+    if (s->sort_epoch == 0) s->sort_epoch = 1;  // epoch 0 marks never-written status words
+    const uint32_t* dtot = hist + p * (1 << RS_MAX_BITS);
+    PROF(s, PM_STAGE_SORT_PASS);
     if (!last) {
       uint32_t* kout = s->keys_tmp[tmp];
       uint32_t* vout = vals[tmp];
-      PROF(s, PM_STAGE_SORT_DOWNSWEEP);
-      CU(s, launch_radix_downsweep<R>(false, kin, vin, n, shift, bits, hist, dtot, L.ntiles, kout, vout, nullptr,
-                                      nullptr, nullptr, nullptr, s->stream));
+      CU(s, launch_sort_pass<R>(false, kin, vin, n, shift, bits, dtot, status, counters + p, s->sort_epoch, L.ntiles,
+                                kout, vout, nullptr, nullptr, nullptr, nullptr, s->errword(), s->stream));
       kin = kout;
       vin = vout;
       tmp ^= 1;
@@ -319,12 +322,9 @@ pm_status sort_particles(pm_sim* s) {
       // the sorted keys go to a buffer that is not the input
       uint32_t* kout = (kin == s->keys) ? s->keys_tmp[tmp] : s->keys;
       const int nxt = s->cur ^ 1;
-      {
-        PROF(s, PM_STAGE_SORT_DOWNSWEEP);
-        CU(s, launch_radix_downsweep<R>(true, kin, vin, n, shift, bits, hist, dtot, L.ntiles, kout, nullptr,
-                                      s->pos(), s->mom(), s->arena + L.pos[nxt], s->arena + L.mom[nxt],
-                                        s->stream));
-      }
+      CU(s, launch_sort_pass<R>(true, kin, vin, n, shift, bits, dtot, status, counters + p, s->sort_epoch, L.ntiles,
+                                kout, nullptr, s->pos(), s->mom(), s->arena + L.pos[nxt], s->arena + L.mom[nxt],
+                                s->errword(), s->stream));
       if (kout != s->keys) {  // swap roles so that s->keys holds the sorted keys
         for (int k = 0; k < 2; ++k)
           if (s->keys_tmp[k] == kout) s->keys_tmp[k] = s->keys;
@@ -374,9 +374,7 @@ pm_status mesh_from_density(pm_sim* s) {
     sp.rho_fp64 = s->cfg.rho_fp64;
     sp.qcoef = -0.5 * s->hbm * s->hbm / ((sp.step * s->dx) * (sp.step * s->dx));
     PROF(s, PM_STAGE_STENCIL);
-    // the half spectrum is free after the inverse FFT: it holds the near-empty node list
-    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->at<uint32_t>(L.spec),
-                            s->errword() + 1, s->stream));
+    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->stream));
   }
   s->fields_valid = true;
   return PM_OK;
@@ -427,6 +425,17 @@ pm_status kick(pm_sim* s, const KickParams& kp, double* acc) {
 }
 
 #define DISPATCH(s, fn, ...) ((s)->fp64() ? fn<double>(__VA_ARGS__) : fn<float>(__VA_ARGS__))
+
+// Reads (after the stream has drained) and clears the device error word.
+pm_status device_errors(pm_sim* s) {
+  uint32_t e = 0;
+  CU(s, cudaMemcpyAsync(&e, s->errword(), 4, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  if (!e) return PM_OK;
+  CU(s, cudaMemsetAsync(s->errword(), 0, 4, s->stream));
+  if (e & ERR_TIMEOUT) return fail(s, PM_ERR_TIMEOUT, "a bounded device wait expired (sort look-back)");
+  return fail(s, PM_ERR_NONFINITE, "non-finite position or momentum");
+}
 
 pm_status check(pm_sim* s) {
   if (!s) return PM_ERR_INVALID_ARG;
@@ -540,6 +549,8 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     }
   }
   if (cudaMemsetAsync(s->errword(), 0, 4, s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->arena + L.status, 0, (size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8, s->stream) !=
+          cudaSuccess ||
       cudaStreamSynchronize(s->stream) != cudaSuccess) {
     cufftDestroy(s->plan_fwd);
     cufftDestroy(s->plan_inv);
@@ -575,14 +586,7 @@ pm_status pm_set_particles(pm_sim* s, const double* x, const double* p) {
   s->sorted = s->fields_valid = false;
   pm_status st = DISPATCH(s, sort_particles, s);
   if (st != PM_OK) return st;
-  CU(s, cudaStreamSynchronize(s->stream));
-  uint32_t e = 0;
-  CU(s, cudaMemcpy(&e, s->errword(), 4, cudaMemcpyDeviceToHost));
-  if (e & ERR_NONFINITE) {
-    cudaMemset(s->errword(), 0, 4);
-    return fail(s, PM_ERR_NONFINITE, "non-finite input position");
-  }
-  return PM_OK;
+  return device_errors(s);
 }
 
 pm_status pm_get_particles(pm_sim* s, double* x, double* p) {
@@ -595,8 +599,7 @@ pm_status pm_get_particles(pm_sim* s, double* x, double* p) {
   const size_t bytes = size_t(s->n()) * 3 * sizeof(double);
   CU(s, cudaMemcpyAsync(x, dx, bytes, cudaMemcpyDeviceToHost, s->stream));
   CU(s, cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDeviceToHost, s->stream));
-  CU(s, cudaStreamSynchronize(s->stream));
-  return PM_OK;
+  return device_errors(s);
 }
 
 pm_status pm_deposit(pm_sim* s, double* rho_host) {
@@ -625,8 +628,7 @@ pm_status pm_forces(pm_sim* s, double a, double* acc_host) {
   st = DISPATCH(s, kick, s, kp, dacc);
   if (st != PM_OK) return st;
   CU(s, cudaMemcpyAsync(acc_host, dacc, size_t(s->n()) * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  CU(s, cudaStreamSynchronize(s->stream));
-  return PM_OK;
+  return device_errors(s);
 }
 
 pm_status pm_step(pm_sim* s, double a0, double a1) {
@@ -685,9 +687,8 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   CU(s, launch_reduce(wg_part(s), RED_GRID, s->cfg.quantum ? 2 : 1, red + 4, s->stream));
   double h[6];
   CU(s, cudaMemcpyAsync(h, red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  uint32_t e = 0;
-  CU(s, cudaMemcpyAsync(&e, s->errword(), 4, cudaMemcpyDeviceToHost, s->stream));
-  CU(s, cudaStreamSynchronize(s->stream));
+  st = device_errors(s);
+  if (st != PM_OK) return st;
   const double aa = s->cfg.cosmological ? a : 1.0;
   const double box = s->cfg.box;
   const double mp = box * box * box / double(s->n());
@@ -698,7 +699,7 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   out[3] = mp * h[1];
   out[4] = mp * h[2];
   out[5] = mp * h[3];
-  bool bad = (e & ERR_NONFINITE) != 0;
+  bool bad = false;
   for (int k = 0; k < 6; ++k) bad |= !isfinite(out[k]);
   if (bad) return fail(s, PM_ERR_NONFINITE, "non-finite momentum or energy");
   return PM_OK;
@@ -788,8 +789,7 @@ pm_status pm_get_order(pm_sim* s, uint32_t* cell, uint32_t* id) {
   CU(s, DISPATCH(s, launch_get_order, s->pos(), s->mom(), s->n(), d, d + s->n(), s->stream));
   CU(s, cudaMemcpyAsync(cell, d, size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
   CU(s, cudaMemcpyAsync(id, d + s->n(), size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
-  CU(s, cudaStreamSynchronize(s->stream));
-  return PM_OK;
+  return device_errors(s);
 }
 
 pm_status pm_profile_begin(pm_sim* s, int32_t capacity) {

@@ -52,11 +52,11 @@ struct StencilParams {
 };
 
 // error bits of the device error word
-enum : uint32_t { ERR_NONFINITE = 1u };
+enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 4;
+constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_MAX_BITS = 10;
 
@@ -73,14 +73,13 @@ inline size_t radix_smem_bytes(int bits) {
 template <typename R>
 cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, Mesh m, double inv_dx,
                                   void* pos, void* mom, uint32_t* keys, uint32_t* err, cudaStream_t s);
-cudaError_t launch_radix_upsweep(const uint32_t* keys, int64_t n, int shift, int bits, uint32_t* hist,
-                                 int ntiles, cudaStream_t s);
-cudaError_t launch_radix_scan(uint32_t* hist, int ntiles, int bits, uint32_t* digit_total, cudaStream_t s);
+cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, int digit_bits, int key_bits,
+                                  uint32_t* hist, cudaStream_t s);
 template <typename R>
-cudaError_t launch_radix_downsweep(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
-                                   int shift, int bits, const uint32_t* hist, const uint32_t* digit_total,
-                                   int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
-                                   const void* mom_in, void* pos_out, void* mom_out, cudaStream_t s);
+cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
+                             int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
+                             uint32_t epoch, int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
+                             const void* mom_in, void* pos_out, void* mom_out, uint32_t* err, cudaStream_t s);
 cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start,
                              cudaStream_t s);
 template <typename R>
@@ -89,8 +88,7 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
 template <typename R>
-cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
-                           uint32_t* list_count, cudaStream_t s);
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s);
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
                         KickParams kp, double* part, double* acc, uint32_t* err, cudaStream_t s);

@@ -306,22 +306,31 @@ __device__ __forceinline__ double sinpi_sq(double t) {
 template <typename R>
 __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef,
                                                         double* part) {
+  extern __shared__ __align__(16) unsigned char green_smem[];
+  R* s2 = reinterpret_cast<R*>(green_smem);  // sin^2(pi j / N), j = 0..N-1
   const uint32_t n = uint32_t(m.n), nh = n / 2 + 1;
-  const uint32_t total = m.n2 * nh;  // < 2^30 for N <= 1024
   const R inv_n = R(1) / R(n);
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) s2[j] = sinpi_sq(R(j) * inv_n);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = blockDim.x >> 5;
   R wsum = R(0);
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const uint32_t row = e / nh, jx = e - row * nh;
+  // one (jz, jy) row of the half spectrum per warp, jx over lanes
+  for (uint32_t row = blockIdx.x * warps + (threadIdx.x >> 5); row < m.n2; row += gridDim.x * warps) {
     const uint32_t jz = row / n, jy = row - jz * n;
-    const R s = sinpi_sq(R(jx) * inv_n) + sinpi_sq(R(jy) * inv_n) + sinpi_sq(R(jz) * inv_n);
-    auto v = spec[e];
-    const R g = (e == 0) ? R(0) : coef / s;
-    const R re = v.x, im = v.y;
-    const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
-    wsum += w * g * (re * re + im * im);
-    v.x = re * g;
-    v.y = im * g;
-    spec[e] = v;
+    const R syz = s2[jy] + s2[jz];
+    typename VT<R>::cplx* line = spec + size_t(row) * nh;
+    for (uint32_t jx = lane; jx < nh; jx += 32) {
+      const R s = syz + s2[jx];
+      auto v = line[jx];
+      const R g = (row == 0 && jx == 0) ? R(0) : coef / s;
+      const R re = v.x, im = v.y;
+      const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
+      wsum += w * g * (re * re + im * im);
+      v.x = re * g;
+      v.y = im * g;
+      line[jx] = v;
+    }
   }
   R acc[1] = {wsum};
   block_sum_store<1>(acc, part, gridDim.x);
@@ -403,14 +412,32 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
 // fp32 compact-Laplacian stencil, four consecutive x-nodes per thread (N a
 // multiple of 4): one float4 per neighbour row, s = sqrt(max(rho, floor))
 // shared by the four nodes, Q~ written as one float4.  Nodes with
-// rho < rho_fp64 are appended to `list` (warp-aggregated, order irrelevant:
-// each listed node is recomputed independently by k_stencil_ext).
-static __global__ void __launch_bounds__(MESH_THREADS) k_stencil4(const float* __restrict__ rho, Mesh m, float fl, float qc,
-                                                           float lim, float* __restrict__ q, uint32_t* list,
-                                                           uint32_t* list_count, double* part) {
+// rho < rho_fp64 are then recomputed in float-float by the same warp: the
+// warp compacts its flagged nodes (at most 128) into shared memory and its
+// lanes take them 32 at a time, so the extended branch costs one convergent
+// round per warp instead of divergent per-lane calls.
+__device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_t node, const Mesh& m, float fl,
+                                          float qc) {
+  int x, y, z;
+  split_cell(node, m, x, y, z);
+  const int n = m.n;
+  const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
+  const float r0 = __ldg(rho + node);
+  const float rxp = __ldg(rho + zn + yn + wrap(x + 1, n)), rxm = __ldg(rho + zn + yn + wrap(x - 1, n));
+  const float ryp = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
+  const float rym = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
+  const float rzp = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
+  const float rzm = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
+  return q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
+}
+
+static __global__ void __launch_bounds__(MESH_THREADS) k_stencil4(const float* __restrict__ rho, Mesh m, float fl,
+                                                                  float qc, float lim, float* __restrict__ q,
+                                                                  double* part) {
+  __shared__ uint32_t flagged[MESH_THREADS / 32][128];
   const uint32_t n = uint32_t(m.n), nq = n / 4;
   const uint32_t total = m.n3 / 4;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float ksum = 0.0f;
   for (uint32_t base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
     const uint32_t t = base + threadIdx.x;
@@ -449,48 +476,28 @@ static __global__ void __launch_bounds__(MESH_THREADS) k_stencil4(const float* _
       }
       *reinterpret_cast<float4*>(q + node0) = make_float4(out[0], out[1], out[2], out[3]);
     }
-    // append flagged nodes: warp prefix of the counts, one atomic per warp
-    const uint32_t cnt = __popc(flags);
-    uint32_t incl = cnt;
+    if (__any_sync(0xffffffffu, flags != 0)) {
+      const uint32_t cnt = __popc(flags);
+      uint32_t incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
-    if (wtotal) {
-      uint32_t wbase = 0;
-      if (lane == 31) wbase = atomicAdd(list_count, wtotal);
-      wbase = __shfl_sync(0xffffffffu, wbase, 31);
-      uint32_t idx = wbase + incl - cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+      uint32_t idx = incl - cnt;
       for (int k2 = 0; k2 < 4; ++k2)
-        if (flags & (1u << k2)) list[idx++] = node0 + k2;
+        if (flags & (1u << k2)) flagged[warp][idx++] = node0 + k2;
+      __syncwarp();  // also orders the fp32 stores above before the overwrites below
+      for (uint32_t j = lane; j < wtotal; j += 32) {
+        const uint32_t node = flagged[warp][j];
+        q[node] = q_ext_at(rho, node, m, fl, qc);
+      }
+      __syncwarp();
     }
   }
   float acc[1] = {ksum};
   block_sum_store<1>(acc, part, gridDim.x);
-}
-
-// Recomputes Q~ in float-float at the listed near-empty nodes.
-static __global__ void __launch_bounds__(MESH_THREADS) k_stencil_ext(const float* __restrict__ rho, Mesh m, float fl,
-                                                              float qc, const uint32_t* __restrict__ list,
-                                                              const uint32_t* __restrict__ list_count,
-                                                              float* __restrict__ q) {
-  const uint32_t cnt = *list_count;
-  const int n = m.n;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-    const uint32_t node = __ldg(list + i);
-    int x, y, z;
-    split_cell(node, m, x, y, z);
-    const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
-    const float r0 = __ldg(rho + node);
-    const float rxp = __ldg(rho + zn + yn + wrap(x + 1, n)), rxm = __ldg(rho + zn + yn + wrap(x - 1, n));
-    const float ryp = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
-    const float rym = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
-    const float rzp = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
-    const float rzm = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
-    q[node] = q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
-  }
 }
 
 // ---------------------------------------------------------------- S6: interpolate + kick + drift
@@ -777,21 +784,16 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s) {
   using C = typename VT<R>::cplx;
-  k_green<R><<<RED_GRID, MESH_THREADS, 0, s>>>((C*)spec, m, R(coef), part);
+  k_green<R><<<RED_GRID, MESH_THREADS, m.n * sizeof(R), s>>>((C*)spec, m, R(coef), part);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
-                           uint32_t* list_count, cudaStream_t s) {
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s) {
   if (sizeof(R) == 4 && sp.step == 1 && m.n % 4 == 0) {
     // fp32 compact path: four nodes per thread, near-empty nodes redone in float-float
-    cudaError_t e = cudaMemsetAsync(list_count, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
     k_stencil4<<<RED_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
-                                                 float(sp.rho_fp64), (float*)q, list, list_count, part);
-    k_stencil_ext<<<RED_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
-                                                    list, list_count, (float*)q);
+                                                 float(sp.rho_fp64), (float*)q, part);
   } else {
     k_stencil<R><<<RED_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
   }

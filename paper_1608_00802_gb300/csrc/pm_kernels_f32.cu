@@ -4,15 +4,12 @@
 
 namespace pm {
 
-cudaError_t launch_radix_upsweep(const uint32_t* keys, int64_t n, int shift, int bits, uint32_t* hist, int ntiles,
-                                 cudaStream_t s) {
-  size_t smem = (size_t(1) << bits) * sizeof(uint32_t);
-  k_radix_upsweep<<<ntiles, RS_THREADS, smem, s>>>(keys, n, shift, bits, hist, ntiles);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_radix_scan(uint32_t* hist, int ntiles, int bits, uint32_t* digit_total, cudaStream_t s) {
-  k_radix_scan<<<1 << bits, RS_THREADS, 0, s>>>(hist, ntiles, digit_total);
+cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, int digit_bits, int key_bits,
+                                  uint32_t* hist, cudaStream_t s) {
+  int64_t blocks = (n + RS_THREADS * 16 - 1) / (RS_THREADS * 16);
+  if (blocks > 2 * 152) blocks = 2 * 152;
+  if (blocks < 1) blocks = 1;
+  k_sort_histogram<<<unsigned(blocks), RS_THREADS, 0, s>>>(keys, n, passes, digit_bits, key_bits, hist);
   return cudaGetLastError();
 }
 
@@ -30,13 +27,13 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
 #define PM_INSTANTIATE(R)                                                                                         \
   template cudaError_t launch_init_particles<R>(const double*, const double*, int64_t, Mesh, double, void*, void*, \
                                                 uint32_t*, uint32_t*, cudaStream_t);                              \
-  template cudaError_t launch_radix_downsweep<R>(bool, const uint32_t*, const uint32_t*, int64_t, int, int,       \
-                                                 const uint32_t*, const uint32_t*, int, uint32_t*, uint32_t*,     \
-                                                 const void*, const void*, void*, void*, cudaStream_t);           \
+  template cudaError_t launch_sort_pass<R>(bool, const uint32_t*, const uint32_t*, int64_t, int, int,             \
+                                           const uint32_t*, uint64_t*, uint32_t*, uint32_t, int, uint32_t*,        \
+                                           uint32_t*, const void*, const void*, void*, void*, uint32_t*,           \
+                                           cudaStream_t);                                                         \
   template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
-  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,     \
-                                          cudaStream_t);               \
+  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, cudaStream_t);               \
   template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
                                       double*, double*, uint32_t*, cudaStream_t);                                 \
   template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \

@@ -1,14 +1,24 @@
 // Stable least-significant-digit radix sort of the particles by cell key,
 // hand-written (no library sort).  Keys are linear cell indices
-// (iz*N + iy)*N + ix of ceil(log2 N^3) bits, split into 2..3 digits of at most
-// RS_MAX_BITS bits.  Each pass is reduce-then-scan over tiles of RS_TILE keys:
-//   upsweep   : per-tile digit histogram (warp-aggregated shared atomics on
-//               integer counts, so the result is exact),
-//   scan      : per digit, exclusive scan over tiles (one block per digit),
-//   downsweep : stable rank inside the tile (warp match + per-warp counters,
-//               tile order = warp, round, lane), staging in shared memory,
-//               coalesced scatter.  The last pass gathers the 16/32-byte
-//               particle records directly into sorted order.
+// (iz*N + iy)*N + ix of ceil(log2 N^3) bits, split into passes of at most
+// RS_MAX_BITS bits.
+//   k_sort_histogram : one read of the keys gives the digit histograms of all
+//                      passes (warp-aggregated shared atomics on integers).
+//   k_sort_pass      : one kernel per pass.  Each block takes the next tile
+//                      (RS_TILE keys, tile ids from an atomic counter), ranks
+//                      its keys stably (warp match + per-warp counters, tile
+//                      order = warp, round, lane), publishes its per-digit
+//                      counts, and finds the global start of each digit for its
+//                      tile by decoupled look-back over the status words of
+//                      the preceding tiles (Merrill & Garland's single-pass
+//                      scan, as used by Onesweep, Adinets & Merrill 2022).  The
+//                      keys are then staged in shared memory and scattered
+//                      with coalesced stores; the last pass gathers the 16/32
+//                      byte particle records straight into sorted order.
+// Status words are 64-bit: epoch (16 bits) | flag (16) | count (32); a new
+// epoch per pass makes old words invalid without clearing them.  Every wait
+// on a predecessor is bounded: after RS_SPIN_LIMIT polls the kernel sets
+// ERR_TIMEOUT in the error word and goes on, so a fault cannot hang the GPU.
 // Equal keys keep their previous order, so the order after a step is the
 // stable sort of the new cells with ties broken by the previous order.
 #pragma once
@@ -25,25 +35,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-static __global__ void __launch_bounds__(RS_THREADS) k_radix_upsweep(const uint32_t* __restrict__ keys, int64_t n,
-                                                              int shift, int bits, uint32_t* __restrict__ hist,
-                                                              int ntiles) {
-  extern __shared__ uint32_t sh_hist[];
-  const int radix = 1 << bits;
-  const uint32_t mask = uint32_t(radix - 1);
-  for (int d = threadIdx.x; d < radix; d += blockDim.x) sh_hist[d] = 0;
-  __syncthreads();
-  const int64_t base = int64_t(blockIdx.x) * RS_TILE;
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    const int64_t i = base + int64_t(j) * RS_THREADS + threadIdx.x;
-    const bool valid = i < n;
-    const uint32_t d = valid ? (__ldg(keys + i) >> shift) & mask : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh_hist[d], uint32_t(__popc(peers)));
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < radix; d += blockDim.x) hist[size_t(d) * ntiles + blockIdx.x] = sh_hist[d];
+constexpr uint64_t RS_FLAG_AGG = 1ull << 32;
+constexpr uint64_t RS_FLAG_PREFIX = 2ull << 32;
+constexpr int RS_SPIN_LIMIT = 1 << 18;
+
+__device__ __forceinline__ uint64_t rs_word(uint32_t epoch, uint64_t flag, uint32_t v) {
+  return (uint64_t(epoch) << 48) | flag | uint64_t(v);
 }
 
 // Block-wide exclusive scan of one value per thread (RS_THREADS threads).
@@ -73,38 +70,39 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
   return warp_off + incl - v;
 }
 
-// One block per digit: hist[d][*] <- exclusive scan over tiles; digit_total[d] <- sum.
-static __global__ void __launch_bounds__(RS_THREADS) k_radix_scan(uint32_t* hist, int ntiles, uint32_t* digit_total) {
-  __shared__ uint32_t scratch[64];
-  uint32_t* row = hist + size_t(blockIdx.x) * ntiles;
-  uint32_t carry = 0;
-  for (int base = 0; base < ntiles; base += RS_THREADS * 4) {
-    uint32_t v[4], s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      int t = base + threadIdx.x * 4 + k;
-      v[k] = t < ntiles ? row[t] : 0u;
-      s += v[k];
+// Digit histograms of every pass: hist[p * radix_max + d].
+static __global__ void __launch_bounds__(RS_THREADS) k_sort_histogram(const uint32_t* __restrict__ keys, int64_t n,
+                                                                      int passes, int digit_bits, int key_bits,
+                                                                      uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[3 * (1 << RS_MAX_BITS)];
+  const int radix = 1 << digit_bits;
+  for (int i = threadIdx.x; i < passes * radix; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t key = valid ? __ldg(keys + i) : 0u;
+    for (int p = 0; p < passes; ++p) {
+      const int shift = p * digit_bits;
+      const int bits = min(digit_bits, key_bits - shift);
+      const uint32_t d = valid ? (key >> shift) & ((1u << bits) - 1u) : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p * radix + d], uint32_t(__popc(peers)));
     }
-    uint32_t total;
-    uint32_t off = block_excl_scan(s, scratch, total) + carry;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      int t = base + threadIdx.x * 4 + k;
-      if (t < ntiles) row[t] = off;
-      off += v[k];
-    }
-    carry += total;
   }
-  if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * radix; i += blockDim.x)
+    if (sh[i]) atomicAdd(hist + (i / radix) * (1 << RS_MAX_BITS) + (i % radix), sh[i]);
 }
 
 template <bool LAST, typename V4>
-__global__ void __launch_bounds__(RS_THREADS) k_radix_downsweep(
+__global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n, int shift, int bits,
-    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ digit_total, int ntiles,
+    const uint32_t* __restrict__ digit_total, uint64_t* status, uint32_t* tile_counter, uint32_t epoch,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const V4* __restrict__ pos_in,
-    const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out) {
+    const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out, uint32_t* err) {
   extern __shared__ uint32_t smem[];
   const int radix = 1 << bits;
   const uint32_t mask = uint32_t(radix - 1);
@@ -113,42 +111,48 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_downsweep(
   uint32_t* tile_start = digit_base + radix;           // [radix] start of digit inside the tile
   uint32_t* s_keys = tile_start + radix;               // [RS_TILE]
   uint32_t* s_vals = s_keys + RS_TILE;                 // [RS_TILE]
-  uint32_t* scratch = s_vals + RS_TILE;                // [64]
+  uint32_t* scratch = s_vals + RS_TILE;                // [64] (+1: tile id)
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t tile_base = int64_t(blockIdx.x) * RS_TILE;
+  if (threadIdx.x == 0) scratch[63] = atomicAdd(tile_counter, 1u);
+  for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
+  __syncthreads();
+  const uint32_t tile = scratch[63];
+  const int64_t tile_base = int64_t(tile) * RS_TILE;
   const int64_t rem = n - tile_base;
   const int tile_n = rem < RS_TILE ? int(rem) : RS_TILE;
+  const int per = (radix + RS_THREADS - 1) / RS_THREADS;  // <= 4
 
-  for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
-  // global digit starts: exclusive scan of digit_total, plus this tile's prefix
+  // exclusive scan of the pass histogram -> global start of each digit
   {
-    const int per = (radix + RS_THREADS - 1) / RS_THREADS;  // <= 4
-    uint32_t v[4], s = 0;
+    uint32_t v[4], sum = 0;
     for (int k = 0; k < per; ++k) {
-      int d = threadIdx.x * per + k;
+      const int d = threadIdx.x * per + k;
       v[k] = d < radix ? __ldg(digit_total + d) : 0u;
-      s += v[k];
+      sum += v[k];
     }
     uint32_t total;
-    uint32_t off = block_excl_scan(s, scratch, total);
+    uint32_t off = block_excl_scan(sum, scratch, total);
     for (int k = 0; k < per; ++k) {
-      int d = threadIdx.x * per + k;
-      if (d < radix) digit_base[d] = off + __ldg(hist + size_t(d) * ntiles + blockIdx.x);
+      const int d = threadIdx.x * per + k;
+      if (d < radix) digit_base[d] = off;
       off += v[k];
     }
   }
-  __syncthreads();
 
-  // rank: warp w owns items [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) in rounds of 32
+  // stable rank: warp w owns items [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) in rounds of 32
   uint32_t key[RS_ITEMS], rank[RS_ITEMS];
   const uint32_t lt = lanemask_lt();
   uint32_t* my_cnt = warp_cnt + warp * radix;
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
+    key[r] = li < tile_n ? __ldg(keys_in + tile_base + li) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
     const bool valid = li < tile_n;
-    key[r] = valid ? __ldg(keys_in + tile_base + li) : 0u;
     const uint32_t d = valid ? (key[r] >> shift) & mask : 0xffffffffu;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = valid ? my_cnt[d] : 0u;
@@ -159,29 +163,55 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_downsweep(
     rank[r] = before + within;
   }
   __syncthreads();
-  // per digit: exclusive scan over warps; tile total per digit
+  // per digit: exclusive scan over warps; the tile's count, published at once
   for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
     uint32_t run = 0;
     for (int w = 0; w < RS_WARPS; ++w) {
-      uint32_t t = warp_cnt[w * radix + d];
+      const uint32_t t = warp_cnt[w * radix + d];
       warp_cnt[w * radix + d] = run;
       run += t;
     }
     tile_start[d] = run;
+    __stcg(reinterpret_cast<unsigned long long*>(status + size_t(tile) * radix + d),
+           rs_word(epoch, tile == 0 ? RS_FLAG_PREFIX : RS_FLAG_AGG, run));
+  }
+  // decoupled look-back: sum the counts of the preceding tiles for each digit
+  for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
+    uint32_t excl = 0;
+    if (tile > 0) {
+      int64_t t = int64_t(tile) - 1;
+      int polls = 0;
+      while (t >= 0) {
+        const uint64_t w = __ldcv(reinterpret_cast<const unsigned long long*>(status + size_t(t) * radix + d));
+        if (uint32_t(w >> 48) == epoch && (w & (RS_FLAG_AGG | RS_FLAG_PREFIX))) {
+          excl += uint32_t(w);
+          if (w & RS_FLAG_PREFIX) break;
+          --t;
+        } else if (++polls > RS_SPIN_LIMIT) {
+          atomicOr(err, ERR_TIMEOUT);
+          break;
+        } else {
+          __nanosleep(32);
+        }
+      }
+      __stcg(reinterpret_cast<unsigned long long*>(status + size_t(tile) * radix + d),
+             rs_word(epoch, RS_FLAG_PREFIX, excl + tile_start[d]));
+    }
+    digit_base[d] += excl;
   }
   __syncthreads();
+  // exclusive scan of the tile counts -> start of each digit inside the tile
   {
-    const int per = (radix + RS_THREADS - 1) / RS_THREADS;
-    uint32_t v[4], s = 0;
+    uint32_t v[4], sum = 0;
     for (int k = 0; k < per; ++k) {
-      int d = threadIdx.x * per + k;
+      const int d = threadIdx.x * per + k;
       v[k] = d < radix ? tile_start[d] : 0u;
-      s += v[k];
+      sum += v[k];
     }
     uint32_t total;
-    uint32_t off = block_excl_scan(s, scratch, total);
+    uint32_t off = block_excl_scan(sum, scratch, total);
     for (int k = 0; k < per; ++k) {
-      int d = threadIdx.x * per + k;
+      const int d = threadIdx.x * per + k;
       if (d < radix) tile_start[d] = off;
       off += v[k];
     }
@@ -203,6 +233,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_downsweep(
     const uint32_t k = s_keys[li];
     const uint32_t d = (k >> shift) & mask;
     const uint32_t dest = digit_base[d] + uint32_t(li) - tile_start[d];
+    if (dest >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
+      atomicOr(err, ERR_TIMEOUT);
+      continue;
+    }
     keys_out[dest] = k;
     if (LAST) {
       const uint32_t src = s_vals[li];
@@ -243,24 +277,25 @@ static __global__ void k_reduce(const double* __restrict__ part, int nblocks, do
 }
 
 template <typename R>
-cudaError_t launch_radix_downsweep(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
-                                   int bits, const uint32_t* hist, const uint32_t* digit_total, int ntiles,
-                                   uint32_t* keys_out, uint32_t* vals_out, const void* pos_in, const void* mom_in,
-                                   void* pos_out, void* mom_out, cudaStream_t s) {
+cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
+                             int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
+                             uint32_t epoch, int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
+                             const void* mom_in, void* pos_out, void* mom_out, uint32_t* err, cudaStream_t s) {
   using V4 = typename VT<R>::v4;
   const size_t smem = radix_smem_bytes(bits);
   if (last) {
-    auto k = k_radix_downsweep<true, V4>;
+    auto k = k_sort_pass<true, V4>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k<<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, hist, digit_total, ntiles, keys_out,
-                                       vals_out, (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out, (V4*)mom_out);
+    k<<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status, tile_counter, epoch,
+                                       keys_out, vals_out, (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
+                                       (V4*)mom_out, err);
   } else {
-    auto k = k_radix_downsweep<false, V4>;
+    auto k = k_sort_pass<false, V4>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k<<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, hist, digit_total, ntiles, keys_out,
-                                       vals_out, nullptr, nullptr, nullptr, nullptr);
+    k<<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status, tile_counter, epoch,
+                                       keys_out, vals_out, nullptr, nullptr, nullptr, nullptr, err);
   }
   return cudaGetLastError();
 }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libpm.so")
 
 PM_OK = 0
 STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_NO_MEMORY", 3: "PM_ERR_CUDA",
-          4: "PM_ERR_CUFFT", 5: "PM_ERR_NONFINITE", 6: "PM_ERR_STATE"}
+          4: "PM_ERR_CUFFT", 5: "PM_ERR_NONFINITE", 6: "PM_ERR_STATE", 7: "PM_ERR_TIMEOUT"}
 FORCE_MESHGRAD, FORCE_HYBRID, FORCE_LAGRANGIAN = 0, 1, 2
 LAP_COMPACT, LAP_WIDE = 0, 1
 FP32, FP64 = 0, 1
@@ -27,8 +27,8 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_set_particles", "pm_get_particles", "pm_deposit", "pm_forces", "pm_step", "pm_run",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
            "pm_profile_begin", "pm_profile_end", "pm_last_error"]
-STAGES = ["sort_upsweep", "sort_scan", "sort_downsweep", "row_start", "deposit", "fft_r2c", "green",
-          "fft_c2r", "stencil", "kick", "other"]
+STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
+          "kick", "other"]
 CUFFT_STAGES = ("fft_r2c", "fft_c2r")
 
 
