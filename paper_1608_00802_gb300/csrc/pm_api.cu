@@ -170,7 +170,7 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   size_t npart = 4 * nkb;
   if (size_t(RED_GRID) * 3 * PK_MAX_BINS > npart) npart = size_t(RED_GRID) * 3 * PK_MAX_BINS;
   L.part = take(npart * 8);
-  L.part_aux = take(2 * RED_GRID * 8);
+  L.part_aux = take(2 * MESH_GRID * 8);
   L.red = take(3 * PK_MAX_BINS * 8 + 64);
   L.err = take(256);
   L.total = off;
@@ -282,9 +282,9 @@ struct ProfScope {
 
 // Partials: the kick diagnostics and the power spectrum use `part`; the
 // gravity-energy and K_rho sums of the last force evaluation live in
-// `part_aux` (one RED_GRID-long row each) until the next evaluation.
+// `part_aux` (one MESH_GRID-long row each) until the next evaluation.
 double* wg_part(pm_sim* s) { return s->at<double>(s->L.part_aux); }
-double* kr_part(pm_sim* s) { return wg_part(s) + RED_GRID; }
+double* kr_part(pm_sim* s) { return wg_part(s) + MESH_GRID; }
 
 template <typename R>
 pm_status sort_particles(pm_sim* s) {
@@ -684,7 +684,7 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   const int nkb = kick_blocks(s->n());
   double* red = s->red();
   CU(s, launch_reduce(s->part(), nkb, 4, red, s->stream));
-  CU(s, launch_reduce(wg_part(s), RED_GRID, s->cfg.quantum ? 2 : 1, red + 4, s->stream));
+  CU(s, launch_reduce(wg_part(s), MESH_GRID, s->cfg.quantum ? 2 : 1, red + 4, s->stream));
   double h[6];
   CU(s, cudaMemcpyAsync(h, red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   st = device_errors(s);

@@ -62,7 +62,8 @@ constexpr int RS_MAX_BITS = 10;
 
 constexpr int KICK_THREADS = 256;
 constexpr int MESH_THREADS = 256;
-constexpr int RED_GRID = 608;   // 4 blocks per SM on 152 SMs, fixed for deterministic reductions
+constexpr int RED_GRID = 608;    // 4 blocks per SM on 152 SMs, fixed for deterministic reductions
+constexpr int MESH_GRID = 1216;  // grid-stride mesh kernels with block partials (8 blocks per SM)
 constexpr int PK_MAX_BINS = 512;
 
 inline size_t radix_smem_bytes(int bits) {

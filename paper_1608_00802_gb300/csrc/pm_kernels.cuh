@@ -96,15 +96,23 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   float e = fmaf(a.hi, b, -p);
   return fast_two_sum(p, fmaf(a.lo, b, e));
 }
+// sqrt and quotient start from the hardware approximations (a few ulp) and are
+// refined by one Newton step whose residual is formed exactly with fma, which
+// brings them to float-float accuracy.
 __device__ __forceinline__ ff ff_sqrt(float x) {  // x > 0
-  float s = sqrtf(x);
-  float r = fmaf(-s, s, x);
-  return fast_two_sum(s, r / (2.0f * s));
+  const float rs = rsqrtf(x);
+  const float s = x * rs;
+  const float r = fmaf(-s, s, x);  // x - s^2, exact
+  return fast_two_sum(s, r * (0.5f * rs));
 }
 __device__ __forceinline__ ff ff_div(ff a, ff b) {
-  float q1 = a.hi / b.hi;
-  ff r = ff_sub(a, ff_mul_f(b, q1));
-  return fast_two_sum(q1, r.hi / b.hi);
+  const float inv = __frcp_rn(b.hi);
+  const float q1 = a.hi * inv;
+  const ff r = ff_sub(a, ff_mul_f(b, q1));
+  const float q2 = r.hi * inv;
+  const ff q = fast_two_sum(q1, q2);
+  const ff r2 = ff_sub(a, ff_add(ff_mul_f(b, q.hi), ff_mul_f(b, q.lo)));
+  return ff_add(q, {r2.hi * inv, 0.0f});
 }
 __device__ __forceinline__ ff ff_shfl_down(ff v, int o) {
   return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
@@ -412,89 +420,48 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
 // fp32 compact-Laplacian stencil, four consecutive x-nodes per thread (N a
 // multiple of 4): one float4 per neighbour row, s = sqrt(max(rho, floor))
 // shared by the four nodes, Q~ written as one float4.  Nodes with
-// rho < rho_fp64 are then recomputed in float-float by the same warp: the
-// warp compacts its flagged nodes (at most 128) into shared memory and its
-// lanes take them 32 at a time, so the extended branch costs one convergent
-// round per warp instead of divergent per-lane calls.
-__device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_t node, const Mesh& m, float fl,
-                                          float qc) {
-  int x, y, z;
-  split_cell(node, m, x, y, z);
-  const int n = m.n;
-  const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
-  const float r0 = __ldg(rho + node);
-  const float rxp = __ldg(rho + zn + yn + wrap(x + 1, n)), rxm = __ldg(rho + zn + yn + wrap(x - 1, n));
-  const float ryp = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
-  const float rym = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
-  const float rzp = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
-  const float rzm = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
-  return q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
-}
-
+// rho < rho_fp64 are recomputed in float-float from the densities already in
+// registers.
 static __global__ void __launch_bounds__(MESH_THREADS) k_stencil4(const float* __restrict__ rho, Mesh m, float fl,
                                                                   float qc, float lim, float* __restrict__ q,
                                                                   double* part) {
-  __shared__ uint32_t flagged[MESH_THREADS / 32][128];
   const uint32_t n = uint32_t(m.n), nq = n / 4;
   const uint32_t total = m.n3 / 4;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float ksum = 0.0f;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
-    const uint32_t t = base + threadIdx.x;
-    uint32_t flags = 0, node0 = 0;
-    if (t < total) {
-      const uint32_t row = t / nq, x0 = (t - row * nq) * 4;
-      const uint32_t z = row / n, y = row - z * n;
-      node0 = row * n + x0;
-      const float* c = rho + size_t(row) * n;
-      const float4 r0 = __ldg(reinterpret_cast<const float4*>(c + x0));
-      const float rxm = __ldg(c + (x0 == 0 ? n - 1 : x0 - 1));
-      const float rxp = __ldg(c + (x0 + 4 == n ? 0 : x0 + 4));
-      const uint32_t yp = (y + 1 == n ? 0 : y + 1), ym = (y == 0 ? n - 1 : y - 1);
-      const uint32_t zp = (z + 1 == n ? 0 : z + 1), zm = (z == 0 ? n - 1 : z - 1);
-      const float4 ryp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + yp) * n + x0));
-      const float4 rym = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + ym) * n + x0));
-      const float4 rzp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zp) * n + y) * n + x0));
-      const float4 rzm = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zm) * n + y) * n + x0));
-      const float rc[6] = {rxm, r0.x, r0.y, r0.z, r0.w, rxp};
-      const float ra[4][4] = {{ryp.x, ryp.y, ryp.z, ryp.w}, {rym.x, rym.y, rym.z, rym.w},
-                              {rzp.x, rzp.y, rzp.z, rzp.w}, {rzm.x, rzm.y, rzm.z, rzm.w}};
-      float sc[6];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const uint32_t row = t / nq, x0 = (t - row * nq) * 4;
+    const uint32_t z = row / n, y = row - z * n;
+    const uint32_t node0 = row * n + x0;
+    const float* c = rho + size_t(row) * n;
+    const float4 r0 = __ldg(reinterpret_cast<const float4*>(c + x0));
+    const float rxm = __ldg(c + (x0 == 0 ? n - 1 : x0 - 1));
+    const float rxp = __ldg(c + (x0 + 4 == n ? 0 : x0 + 4));
+    const uint32_t yp = (y + 1 == n ? 0 : y + 1), ym = (y == 0 ? n - 1 : y - 1);
+    const uint32_t zp = (z + 1 == n ? 0 : z + 1), zm = (z == 0 ? n - 1 : z - 1);
+    const float4 ryp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + yp) * n + x0));
+    const float4 rym = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + ym) * n + x0));
+    const float4 rzp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zp) * n + y) * n + x0));
+    const float4 rzm = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zm) * n + y) * n + x0));
+    const float rc[6] = {rxm, r0.x, r0.y, r0.z, r0.w, rxp};
+    const float ra[4][4] = {{ryp.x, ryp.y, ryp.z, ryp.w}, {rym.x, rym.y, rym.z, rym.w},
+                            {rzp.x, rzp.y, rzp.z, rzp.w}, {rzm.x, rzm.y, rzm.z, rzm.w}};
+    float sc[6];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) sc[i] = sqrtf(fmaxf(rc[i], fl));
-      float out[4];
+    for (int i = 0; i < 6; ++i) sc[i] = sqrtf(fmaxf(rc[i], fl));
+    float out[4];
 #pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) {
-        const float s0 = sc[k2 + 1];
-        const float syp = sqrtf(fmaxf(ra[0][k2], fl)), sym = sqrtf(fmaxf(ra[1][k2], fl));
-        const float szp = sqrtf(fmaxf(ra[2][k2], fl)), szm = sqrtf(fmaxf(ra[3][k2], fl));
-        const float dxp = sc[k2 + 2] - s0, dyp = syp - s0, dzp = szp - s0;
-        const float lap = (dxp + (sc[k2] - s0)) + (dyp + (sym - s0)) + (dzp + (szm - s0));
-        out[k2] = qc * lap * __frcp_rn(s0);
-        ksum += dxp * dxp + dyp * dyp + dzp * dzp;
-        flags |= (rc[k2 + 1] < lim ? 1u : 0u) << k2;
-      }
-      *reinterpret_cast<float4*>(q + node0) = make_float4(out[0], out[1], out[2], out[3]);
+    for (int k2 = 0; k2 < 4; ++k2) {
+      const float s0 = sc[k2 + 1];
+      const float syp = sqrtf(fmaxf(ra[0][k2], fl)), sym = sqrtf(fmaxf(ra[1][k2], fl));
+      const float szp = sqrtf(fmaxf(ra[2][k2], fl)), szm = sqrtf(fmaxf(ra[3][k2], fl));
+      const float dxp = sc[k2 + 2] - s0, dyp = syp - s0, dzp = szp - s0;
+      const float lap = (dxp + (sc[k2] - s0)) + (dyp + (sym - s0)) + (dzp + (szm - s0));
+      out[k2] = qc * lap * __frcp_rn(s0);
+      ksum += dxp * dxp + dyp * dyp + dzp * dzp;
+      if (rc[k2 + 1] < lim)
+        out[k2] = q_ext(rc[k2 + 1], rc[k2 + 2], rc[k2], ra[0][k2], ra[1][k2], ra[2][k2], ra[3][k2], fl, qc);
     }
-    if (__any_sync(0xffffffffu, flags != 0)) {
-      const uint32_t cnt = __popc(flags);
-      uint32_t incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-      }
-      const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
-      uint32_t idx = incl - cnt;
-      for (int k2 = 0; k2 < 4; ++k2)
-        if (flags & (1u << k2)) flagged[warp][idx++] = node0 + k2;
-      __syncwarp();  // also orders the fp32 stores above before the overwrites below
-      for (uint32_t j = lane; j < wtotal; j += 32) {
-        const uint32_t node = flagged[warp][j];
-        q[node] = q_ext_at(rho, node, m, fl, qc);
-      }
-      __syncwarp();
-    }
+    *reinterpret_cast<float4*>(q + node0) = make_float4(out[0], out[1], out[2], out[3]);
   }
   float acc[1] = {ksum};
   block_sum_store<1>(acc, part, gridDim.x);
@@ -784,7 +751,7 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s) {
   using C = typename VT<R>::cplx;
-  k_green<R><<<RED_GRID, MESH_THREADS, m.n * sizeof(R), s>>>((C*)spec, m, R(coef), part);
+  k_green<R><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>((C*)spec, m, R(coef), part);
   return cudaGetLastError();
 }
 
@@ -792,10 +759,10 @@ template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s) {
   if (sizeof(R) == 4 && sp.step == 1 && m.n % 4 == 0) {
     // fp32 compact path: four nodes per thread, near-empty nodes redone in float-float
-    k_stencil4<<<RED_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
-                                                 float(sp.rho_fp64), (float*)q, part);
+    k_stencil4<<<MESH_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
+                                                  float(sp.rho_fp64), (float*)q, part);
   } else {
-    k_stencil<R><<<RED_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
+    k_stencil<R><<<MESH_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
   }
   return cudaGetLastError();
 }

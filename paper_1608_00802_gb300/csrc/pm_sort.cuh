@@ -88,8 +88,14 @@ static __global__ void __launch_bounds__(RS_THREADS) k_sort_histogram(const uint
       const int shift = p * digit_bits;
       const int bits = min(digit_bits, key_bits - shift);
       const uint32_t d = valid ? (key >> shift) & ((1u << bits) - 1u) : 0xffffffffu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p * radix + d], uint32_t(__popc(peers)));
+      // runs of equal digits in neighbouring lanes: the first lane of a run adds its length
+      const uint32_t dprev = __shfl_up_sync(0xffffffffu, d, 1);
+      const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || d != dprev);
+      if (valid && ((heads >> lane) & 1u)) {
+        const uint32_t after = heads & ~((2u << lane) - 1u);  // run heads above this lane
+        const int end = after ? __ffs(after) - 1 : 32;
+        atomicAdd(&sh[p * radix + d], uint32_t(end - lane));
+      }
     }
   }
   __syncthreads();
@@ -126,16 +132,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
   // exclusive scan of the pass histogram -> global start of each digit
   {
     uint32_t v[4], sum = 0;
-    for (int k = 0; k < per; ++k) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       const int d = threadIdx.x * per + k;
-      v[k] = d < radix ? __ldg(digit_total + d) : 0u;
+      v[k] = (k < per && d < radix) ? __ldg(digit_total + d) : 0u;
       sum += v[k];
     }
     uint32_t total;
     uint32_t off = block_excl_scan(sum, scratch, total);
-    for (int k = 0; k < per; ++k) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       const int d = threadIdx.x * per + k;
-      if (d < radix) digit_base[d] = off;
+      if (k < per && d < radix) digit_base[d] = off;
       off += v[k];
     }
   }
@@ -203,16 +211,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
   // exclusive scan of the tile counts -> start of each digit inside the tile
   {
     uint32_t v[4], sum = 0;
-    for (int k = 0; k < per; ++k) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       const int d = threadIdx.x * per + k;
-      v[k] = d < radix ? tile_start[d] : 0u;
+      v[k] = (k < per && d < radix) ? tile_start[d] : 0u;
       sum += v[k];
     }
     uint32_t total;
     uint32_t off = block_excl_scan(sum, scratch, total);
-    for (int k = 0; k < per; ++k) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       const int d = threadIdx.x * per + k;
-      if (d < radix) tile_start[d] = off;
+      if (k < per && d < radix) tile_start[d] = off;
       off += v[k];
     }
   }
@@ -229,22 +239,45 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
     }
   }
   __syncthreads();
-  for (int li = threadIdx.x; li < tile_n; li += RS_THREADS) {
-    const uint32_t k = s_keys[li];
-    const uint32_t d = (k >> shift) & mask;
-    const uint32_t dest = digit_base[d] + uint32_t(li) - tile_start[d];
-    if (dest >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
-      atomicOr(err, ERR_TIMEOUT);
-      continue;
+  // each thread moves RS_ITEMS elements; all loads are issued before the stores
+  uint32_t dst[RS_ITEMS], kk[RS_ITEMS], vv[RS_ITEMS];
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int li = r * RS_THREADS + threadIdx.x;
+    dst[r] = 0xffffffffu;
+    if (li < tile_n) {
+      kk[r] = s_keys[li];
+      vv[r] = s_vals[li];
+      const uint32_t d = (kk[r] >> shift) & mask;
+      dst[r] = digit_base[d] + uint32_t(li) - tile_start[d];
+      if (dst[r] >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
+        atomicOr(err, ERR_TIMEOUT);
+        dst[r] = 0xffffffffu;
+      }
     }
-    keys_out[dest] = k;
-    if (LAST) {
-      const uint32_t src = s_vals[li];
-      pos_out[dest] = pos_in[src];
-      mom_out[dest] = mom_in[src];
-    } else {
-      vals_out[dest] = s_vals[li];
-    }
+  }
+  if (LAST) {
+    V4 pr[RS_ITEMS], mr[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r)
+      if (dst[r] != 0xffffffffu) {
+        pr[r] = pos_in[vv[r]];
+        mr[r] = mom_in[vv[r]];
+      }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r)
+      if (dst[r] != 0xffffffffu) {
+        keys_out[dst[r]] = kk[r];
+        pos_out[dst[r]] = pr[r];
+        mom_out[dst[r]] = mr[r];
+      }
+  } else {
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r)
+      if (dst[r] != 0xffffffffu) {
+        keys_out[dst[r]] = kk[r];
+        vals_out[dst[r]] = vv[r];
+      }
   }
 }
 
