@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -87,7 +88,7 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, status, part,
+  size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, status, st_list, st_count, part,
       part_aux, red, err, total;
   int key_bits, passes, digit_bits, ntiles;
 };
@@ -170,7 +171,10 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   size_t npart = 4 * nkb;
   if (size_t(RED_GRID) * 3 * PK_MAX_BINS > npart) npart = size_t(RED_GRID) * 3 * PK_MAX_BINS;
   L.part = take(npart * 8);
-  L.part_aux = take(2 * MESH_GRID * 8);
+  L.st_list = take(c.precision == PM_FP32 ? stencil_list_entries(int(N)) * 4 : 4);
+  L.st_count = take(size_t(stencil_block_count(int(N))) * 4);
+  const size_t aux = std::max<size_t>(MESH_GRID, size_t(stencil_block_count(int(N))));
+  L.part_aux = take(2 * aux * 8);
   L.red = take(3 * PK_MAX_BINS * 8 + 64);
   L.err = take(256);
   L.total = off;
@@ -284,7 +288,14 @@ struct ProfScope {
 // gravity-energy and K_rho sums of the last force evaluation live in
 // `part_aux` (one MESH_GRID-long row each) until the next evaluation.
 double* wg_part(pm_sim* s) { return s->at<double>(s->L.part_aux); }
-double* kr_part(pm_sim* s) { return wg_part(s) + MESH_GRID; }
+size_t aux_len(const pm_sim* s) {
+  return std::max<size_t>(MESH_GRID, size_t(stencil_block_count(s->cfg.n_mesh)));
+}
+double* kr_part(pm_sim* s) { return wg_part(s) + aux_len(s); }
+int kr_blocks(const pm_sim* s) {
+  const bool tiled = !s->fp64() && s->cfg.lap == PM_LAP_COMPACT;
+  return tiled ? stencil_block_count(s->cfg.n_mesh) : MESH_GRID;
+}
 
 template <typename R>
 pm_status sort_particles(pm_sim* s) {
@@ -374,7 +385,8 @@ pm_status mesh_from_density(pm_sim* s) {
     sp.rho_fp64 = s->cfg.rho_fp64;
     sp.qcoef = -0.5 * s->hbm * s->hbm / ((sp.step * s->dx) * (sp.step * s->dx));
     PROF(s, PM_STAGE_STENCIL);
-    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->stream));
+    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->at<uint32_t>(L.st_list),
+                            s->at<uint32_t>(L.st_count), s->stream));
   }
   s->fields_valid = true;
   return PM_OK;
@@ -684,7 +696,8 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   const int nkb = kick_blocks(s->n());
   double* red = s->red();
   CU(s, launch_reduce(s->part(), nkb, 4, red, s->stream));
-  CU(s, launch_reduce(wg_part(s), MESH_GRID, s->cfg.quantum ? 2 : 1, red + 4, s->stream));
+  CU(s, launch_reduce(wg_part(s), MESH_GRID, 1, red + 4, s->stream));
+  if (s->cfg.quantum) CU(s, launch_reduce(kr_part(s), kr_blocks(s), 1, red + 5, s->stream));
   double h[6];
   CU(s, cudaMemcpyAsync(h, red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   st = device_errors(s);

@@ -89,7 +89,11 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
 template <typename R>
-cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s);
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
+                           uint32_t* list_count, cudaStream_t s);
+// fp32 stencil tiling (defined with the kernels): list length and block count
+size_t stencil_list_entries(int n);
+int stencil_block_count(int n);
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
                         KickParams kp, double* part, double* acc, uint32_t* err, cudaStream_t s);

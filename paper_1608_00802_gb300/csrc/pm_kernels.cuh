@@ -144,9 +144,11 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Block sum of NV fp32 values per thread: float-float inside each warp, fp64
 // across warps and blocks (fixed order, so the sums are reproducible).
 template <int NV>
-__device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, int nblocks) {
+__device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, int nblocks, int bid = -1) {
   __shared__ double shf[32][NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, warp = tid >> 5;
+  if (bid < 0) bid = blockIdx.x;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     ff s = {v[k], 0.0f};
@@ -155,13 +157,13 @@ __device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, in
     if (lane == 0) shf[warp][k] = double(s.hi) + double(s.lo);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+  if (tid == 0) {
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double s = 0.0;
       for (int w = 0; w < nw; ++w) s += shf[w][k];
-      part[k * nblocks + blockIdx.x] = s;
+      part[k * nblocks + bid] = s;
     }
   }
 }
@@ -417,54 +419,103 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
-// fp32 compact-Laplacian stencil, four consecutive x-nodes per thread (N a
-// multiple of 4): one float4 per neighbour row, s = sqrt(max(rho, floor))
-// shared by the four nodes, Q~ written as one float4.  Nodes with
-// rho < rho_fp64 are recomputed in float-float from the densities already in
-// registers.
-static __global__ void __launch_bounds__(MESH_THREADS) k_stencil4(const float* __restrict__ rho, Mesh m, float fl,
-                                                                  float qc, float lim, float* __restrict__ q,
-                                                                  double* part) {
-  const uint32_t n = uint32_t(m.n), nq = n / 4;
-  const uint32_t total = m.n3 / 4;
-  float ksum = 0.0f;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const uint32_t row = t / nq, x0 = (t - row * nq) * 4;
-    const uint32_t z = row / n, y = row - z * n;
-    const uint32_t node0 = row * n + x0;
-    const float* c = rho + size_t(row) * n;
-    const float4 r0 = __ldg(reinterpret_cast<const float4*>(c + x0));
-    const float rxm = __ldg(c + (x0 == 0 ? n - 1 : x0 - 1));
-    const float rxp = __ldg(c + (x0 + 4 == n ? 0 : x0 + 4));
-    const uint32_t yp = (y + 1 == n ? 0 : y + 1), ym = (y == 0 ? n - 1 : y - 1);
-    const uint32_t zp = (z + 1 == n ? 0 : z + 1), zm = (z == 0 ? n - 1 : z - 1);
-    const float4 ryp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + yp) * n + x0));
-    const float4 rym = __ldg(reinterpret_cast<const float4*>(rho + (size_t(z) * n + ym) * n + x0));
-    const float4 rzp = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zp) * n + y) * n + x0));
-    const float4 rzm = __ldg(reinterpret_cast<const float4*>(rho + (size_t(zm) * n + y) * n + x0));
-    const float rc[6] = {rxm, r0.x, r0.y, r0.z, r0.w, rxp};
-    const float ra[4][4] = {{ryp.x, ryp.y, ryp.z, ryp.w}, {rym.x, rym.y, rym.z, rym.w},
-                            {rzp.x, rzp.y, rzp.z, rzp.w}, {rzm.x, rzm.y, rzm.z, rzm.w}};
-    float sc[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sc[i] = sqrtf(fmaxf(rc[i], fl));
-    float out[4];
-#pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) {
-      const float s0 = sc[k2 + 1];
-      const float syp = sqrtf(fmaxf(ra[0][k2], fl)), sym = sqrtf(fmaxf(ra[1][k2], fl));
-      const float szp = sqrtf(fmaxf(ra[2][k2], fl)), szm = sqrtf(fmaxf(ra[3][k2], fl));
-      const float dxp = sc[k2 + 2] - s0, dyp = syp - s0, dzp = szp - s0;
-      const float lap = (dxp + (sc[k2] - s0)) + (dyp + (sym - s0)) + (dzp + (szm - s0));
-      out[k2] = qc * lap * __frcp_rn(s0);
-      ksum += dxp * dxp + dyp * dyp + dzp * dzp;
-      if (rc[k2 + 1] < lim)
-        out[k2] = q_ext(rc[k2 + 1], rc[k2 + 2], rc[k2], ra[0][k2], ra[1][k2], ra[2][k2], ra[3][k2], fl, qc);
+// fp32 compact-Laplacian stencil on shared-memory tiles.  A block owns a
+// column of ST_X x ST_Y nodes and marches along z over ST_ZCH consecutive
+// planes, keeping s = sqrt(max(rho, floor)) of three planes (z-1, z, z+1, each
+// with a one-node halo in x and y) in a rolling shared-memory window, so each
+// density is read about once from memory and its square root taken about
+// once.  Q~ and the K_rho terms follow from the window; nodes with
+// rho < rho_fp64 go to the block's own region of `list` (shared-memory
+// counter, no global atomics) and are recomputed in float-float by
+// k_stencil_ext afterwards.
+constexpr int ST_X = 32, ST_Y = 8, ST_ZCH = 8;
+
+__device__ __forceinline__ float s_of(float r, float fl) {
+  const float x = fmaxf(r, fl);
+  return x * rsqrtf(x);
+}
+
+static __global__ void __launch_bounds__(ST_X * ST_Y) k_stencil_tiled(const float* __restrict__ rho, Mesh m,
+                                                                       float fl, float qc, float slim, int zlen,
+                                                                       float* __restrict__ q, uint32_t* list,
+                                                                       uint32_t* list_count, double* part) {
+  __shared__ float S[3][ST_Y + 2][ST_X + 2];
+  __shared__ uint32_t s_cnt;
+  const int n = m.n;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_X + tx;
+  const int x0 = blockIdx.x * ST_X, y0 = blockIdx.y * ST_Y;
+  const int z0 = blockIdx.z * zlen, z1 = min(z0 + zlen, n);
+  const uint32_t blin = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
+  if (tid == 0) s_cnt = 0;
+  // fills slot with s of plane z (wrapped) over the tile and its halo
+  auto load_plane = [&](int slot, int z) {
+    const int zw = wrap(z, n);
+    for (int i = tid; i < (ST_Y + 2) * (ST_X + 2); i += ST_X * ST_Y) {
+      const int hy = i / (ST_X + 2), hx = i - hy * (ST_X + 2);
+      const int gx = wrap(x0 + hx - 1, n), gy = wrap(y0 + hy - 1, n);
+      S[slot][hy][hx] = s_of(__ldg(rho + (size_t(zw) * n + gy) * n + gx), fl);
     }
-    *reinterpret_cast<float4*>(q + node0) = make_float4(out[0], out[1], out[2], out[3]);
+  };
+  load_plane(0, z0 - 1);
+  load_plane(1, z0);
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool inside = gx < n && gy < n;
+  float ksum = 0.0f;
+  int sm = 0, sc = 1, sp = 2;  // slots of planes z-1, z, z+1
+  for (int z = z0; z < z1; ++z) {
+    load_plane(sp, z + 1);
+    __syncthreads();
+    if (inside) {
+      const float s0 = S[sc][ty + 1][tx + 1];
+      const float dxp = S[sc][ty + 1][tx + 2] - s0, dxm = S[sc][ty + 1][tx] - s0;
+      const float dyp = S[sc][ty + 2][tx + 1] - s0, dym = S[sc][ty][tx + 1] - s0;
+      const float dzp = S[sp][ty + 1][tx + 1] - s0, dzm = S[sm][ty + 1][tx + 1] - s0;
+      const float lap = (dxp + dxm) + (dyp + dym) + (dzp + dzm);
+      const size_t node = (size_t(z) * n + gy) * n + gx;
+      q[node] = qc * lap * __frcp_rn(s0);
+      ksum += dxp * dxp + dyp * dyp + dzp * dzp;
+      if (s0 < slim) my_list[atomicAdd(&s_cnt, 1u)] = uint32_t(node);
+    }
+    __syncthreads();  // the slot of plane z-1 is refilled next
+    const int t = sm;
+    sm = sc;
+    sc = sp;
+    sp = t;
   }
+  if (tid == 0) list_count[blin] = s_cnt;
   float acc[1] = {ksum};
-  block_sum_store<1>(acc, part, gridDim.x);
+  block_sum_store<1>(acc, part, gridDim.x * gridDim.y * gridDim.z, int(blin));
+}
+
+__device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_t node, const Mesh& m, float fl,
+                                          float qc) {
+  int x, y, z;
+  split_cell(node, m, x, y, z);
+  const int n = m.n;
+  const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
+  const float r0 = __ldg(rho + node);
+  const float rxp = __ldg(rho + zn + yn + wrap(x + 1, n)), rxm = __ldg(rho + zn + yn + wrap(x - 1, n));
+  const float ryp = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
+  const float rym = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
+  const float rzp = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
+  const float rzm = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
+  return q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
+}
+
+// Float-float recomputation of the listed near-empty nodes: block b takes the
+// list region of stencil block b (same grid).
+static __global__ void __launch_bounds__(ST_X * ST_Y) k_stencil_ext(const float* __restrict__ rho, Mesh m, float fl,
+                                                                     float qc, int zlen, const uint32_t* list,
+                                                                     const uint32_t* list_count,
+                                                                     float* __restrict__ q) {
+  const uint32_t blin = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const uint32_t cnt = list_count[blin];
+  const uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
+  for (uint32_t i = threadIdx.y * ST_X + threadIdx.x; i < cnt; i += ST_X * ST_Y) {
+    const uint32_t node = my_list[i];
+    q[node] = q_ext_at(rho, node, m, fl, qc);
+  }
 }
 
 // ---------------------------------------------------------------- S6: interpolate + kick + drift
@@ -755,12 +806,32 @@ cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStre
   return cudaGetLastError();
 }
 
+inline dim3 stencil_grid(int n) {
+  return dim3((n + ST_X - 1) / ST_X, (n + ST_Y - 1) / ST_Y, ST_ZCH);
+}
+inline int stencil_zlen(int n) { return (n + ST_ZCH - 1) / ST_ZCH; }
+// entries of the near-empty node list (one region per stencil block)
+inline size_t stencil_list_len(int n) {
+  const dim3 g = stencil_grid(n);
+  return size_t(g.x) * g.y * g.z * ST_X * ST_Y * stencil_zlen(n);
+}
+inline int stencil_blocks(int n) {
+  const dim3 g = stencil_grid(n);
+  return int(g.x * g.y * g.z);
+}
+
 template <typename R>
-cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, cudaStream_t s) {
-  if (sizeof(R) == 4 && sp.step == 1 && m.n % 4 == 0) {
-    // fp32 compact path: four nodes per thread, near-empty nodes redone in float-float
-    k_stencil4<<<MESH_GRID, MESH_THREADS, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef),
-                                                  float(sp.rho_fp64), (float*)q, part);
+cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
+                           uint32_t* list_count, cudaStream_t s) {
+  if (sizeof(R) == 4 && sp.step == 1) {
+    // fp32 compact path: shared-memory tiles, near-empty nodes redone in float-float
+    const dim3 g = stencil_grid(m.n), b(ST_X, ST_Y);
+    const int zlen = stencil_zlen(m.n);
+    const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;
+    k_stencil_tiled<<<g, b, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, zlen, (float*)q,
+                                    list, list_count, part);
+    k_stencil_ext<<<g, b, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), zlen, list, list_count,
+                                  (float*)q);
   } else {
     k_stencil<R><<<MESH_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
   }

@@ -18,6 +18,9 @@ cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, u
   return cudaGetLastError();
 }
 
+size_t stencil_list_entries(int n) { return stencil_list_len(n); }
+int stencil_block_count(int n) { return stencil_blocks(n); }
+
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s) {
   if (nvals <= 0) return cudaSuccess;
   k_reduce<<<nvals, 256, 0, s>>>(part, nblocks, out);
@@ -33,7 +36,8 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
                                            cudaStream_t);                                                         \
   template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
-  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, cudaStream_t);               \
+  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,       \
+                                          cudaStream_t);               \
   template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
                                       double*, double*, uint32_t*, cudaStream_t);                                 \
   template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \

@@ -13,7 +13,8 @@ namespace pm {
                                            cudaStream_t);                                                         \
   template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
-  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, cudaStream_t);               \
+  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,       \
+                                          cudaStream_t);               \
   template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
                                       double*, double*, uint32_t*, cudaStream_t);                                 \
   template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \

@@ -239,45 +239,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
     }
   }
   __syncthreads();
-  // each thread moves RS_ITEMS elements; all loads are issued before the stores
-  uint32_t dst[RS_ITEMS], kk[RS_ITEMS], vv[RS_ITEMS];
-#pragma unroll
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int li = r * RS_THREADS + threadIdx.x;
-    dst[r] = 0xffffffffu;
-    if (li < tile_n) {
-      kk[r] = s_keys[li];
-      vv[r] = s_vals[li];
-      const uint32_t d = (kk[r] >> shift) & mask;
-      dst[r] = digit_base[d] + uint32_t(li) - tile_start[d];
-      if (dst[r] >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
-        atomicOr(err, ERR_TIMEOUT);
-        dst[r] = 0xffffffffu;
-      }
+  for (int li = threadIdx.x; li < tile_n; li += RS_THREADS) {
+    const uint32_t k = s_keys[li];
+    const uint32_t d = (k >> shift) & mask;
+    const uint32_t dest = digit_base[d] + uint32_t(li) - tile_start[d];
+    if (dest >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
+      atomicOr(err, ERR_TIMEOUT);
+      continue;
     }
-  }
-  if (LAST) {
-    V4 pr[RS_ITEMS], mr[RS_ITEMS];
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r)
-      if (dst[r] != 0xffffffffu) {
-        pr[r] = pos_in[vv[r]];
-        mr[r] = mom_in[vv[r]];
-      }
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r)
-      if (dst[r] != 0xffffffffu) {
-        keys_out[dst[r]] = kk[r];
-        pos_out[dst[r]] = pr[r];
-        mom_out[dst[r]] = mr[r];
-      }
-  } else {
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r)
-      if (dst[r] != 0xffffffffu) {
-        keys_out[dst[r]] = kk[r];
-        vals_out[dst[r]] = vv[r];
-      }
+    keys_out[dest] = k;
+    if (LAST) {
+      const uint32_t src = s_vals[li];
+      pos_out[dest] = pos_in[src];
+      mom_out[dest] = mom_in[src];
+    } else {
+      vals_out[dest] = s_vals[li];
+    }
   }
 }
 
