@@ -448,23 +448,44 @@ static __global__ void __launch_bounds__(ST_X * ST_Y) k_stencil_tiled(const floa
   const uint32_t blin = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
   if (tid == 0) s_cnt = 0;
-  // fills slot with s of plane z (wrapped) over the tile and its halo
-  auto load_plane = [&](int slot, int z) {
-    const int zw = wrap(z, n);
-    for (int i = tid; i < (ST_Y + 2) * (ST_X + 2); i += ST_X * ST_Y) {
-      const int hy = i / (ST_X + 2), hx = i - hy * (ST_X + 2);
-      const int gx = wrap(x0 + hx - 1, n), gy = wrap(y0 + hy - 1, n);
-      S[slot][hy][hx] = s_of(__ldg(rho + (size_t(zw) * n + gy) * n + gx), fl);
-    }
+  // each thread owns up to two nodes of the (ST_Y+2) x (ST_X+2) halo tile of a
+  // plane; densities of plane z+2 are fetched into registers while plane z is
+  // computed, then committed to the window as s
+  constexpr int HALO = (ST_Y + 2) * (ST_X + 2);
+  constexpr int NPT = (HALO + ST_X * ST_Y - 1) / (ST_X * ST_Y);
+  uint32_t hoff[NPT];
+  int hslot[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int i = tid + j * ST_X * ST_Y;
+    hslot[j] = i < HALO ? i : -1;
+    const int hy = i / (ST_X + 2), hx = i - hy * (ST_X + 2);
+    hoff[j] = uint32_t(wrap(y0 + hy - 1, n)) * uint32_t(n) + uint32_t(wrap(x0 + hx - 1, n));
+  }
+  float pre[NPT];
+  auto fetch = [&](int z) {
+    const float* plane = rho + size_t(wrap(z, n)) * m.n2;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) pre[j] = hslot[j] >= 0 ? __ldg(plane + hoff[j]) : 0.0f;
   };
-  load_plane(0, z0 - 1);
-  load_plane(1, z0);
+  auto commit = [&](int slot) {
+    float* dst = &S[slot][0][0];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+      if (hslot[j] >= 0) dst[hslot[j]] = s_of(pre[j], fl);
+  };
+  fetch(z0 - 1);
+  commit(0);
+  fetch(z0);
+  commit(1);
+  fetch(z0 + 1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool inside = gx < n && gy < n;
   float ksum = 0.0f;
   int sm = 0, sc = 1, sp = 2;  // slots of planes z-1, z, z+1
   for (int z = z0; z < z1; ++z) {
-    load_plane(sp, z + 1);
+    commit(sp);                  // plane z+1
+    if (z + 2 <= z1) fetch(z + 2);
     __syncthreads();
     if (inside) {
       const float s0 = S[sc][ty + 1][tx + 1];
