@@ -419,94 +419,21 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
-// fp32 compact-Laplacian stencil on shared-memory tiles.  A block owns a
-// column of ST_X x ST_Y nodes and marches along z over ST_ZCH consecutive
+// fp32 compact-Laplacian stencil on shared-memory tiles.  A block of
+// ST_X x ST_TY threads owns a column of ST_X x ST_Y nodes (each thread two
+// rows, ST_Y = 2 ST_TY) and marches along z over one of ST_ZCH chunks of
 // planes, keeping s = sqrt(max(rho, floor)) of three planes (z-1, z, z+1, each
-// with a one-node halo in x and y) in a rolling shared-memory window, so each
-// density is read about once from memory and its square root taken about
-// once.  Q~ and the K_rho terms follow from the window; nodes with
-// rho < rho_fp64 go to the block's own region of `list` (shared-memory
-// counter, no global atomics) and are recomputed in float-float by
-// k_stencil_ext afterwards.
-constexpr int ST_X = 32, ST_Y = 8, ST_ZCH = 8;
+// with a one-node halo in x and y) in a rolling shared-memory window; the
+// densities of plane z+2 are fetched into registers while plane z is
+// computed.  Each density is read about once from memory and its square root
+// taken about once.  Nodes with rho < rho_fp64 are collected in the block's
+// own region of `list` (shared-memory counter) and recomputed in float-float
+// by the same block after its sweep.
+constexpr int ST_X = 32, ST_TY = 8, ST_Y = 2 * ST_TY, ST_ZCH = 8;
 
 __device__ __forceinline__ float s_of(float r, float fl) {
   const float x = fmaxf(r, fl);
   return x * rsqrtf(x);
-}
-
-static __global__ void __launch_bounds__(ST_X * ST_Y) k_stencil_tiled(const float* __restrict__ rho, Mesh m,
-                                                                       float fl, float qc, float slim, int zlen,
-                                                                       float* __restrict__ q, uint32_t* list,
-                                                                       uint32_t* list_count, double* part) {
-  __shared__ float S[3][ST_Y + 2][ST_X + 2];
-  __shared__ uint32_t s_cnt;
-  const int n = m.n;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_X + tx;
-  const int x0 = blockIdx.x * ST_X, y0 = blockIdx.y * ST_Y;
-  const int z0 = blockIdx.z * zlen, z1 = min(z0 + zlen, n);
-  const uint32_t blin = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
-  if (tid == 0) s_cnt = 0;
-  // each thread owns up to two nodes of the (ST_Y+2) x (ST_X+2) halo tile of a
-  // plane; densities of plane z+2 are fetched into registers while plane z is
-  // computed, then committed to the window as s
-  constexpr int HALO = (ST_Y + 2) * (ST_X + 2);
-  constexpr int NPT = (HALO + ST_X * ST_Y - 1) / (ST_X * ST_Y);
-  uint32_t hoff[NPT];
-  int hslot[NPT];
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int i = tid + j * ST_X * ST_Y;
-    hslot[j] = i < HALO ? i : -1;
-    const int hy = i / (ST_X + 2), hx = i - hy * (ST_X + 2);
-    hoff[j] = uint32_t(wrap(y0 + hy - 1, n)) * uint32_t(n) + uint32_t(wrap(x0 + hx - 1, n));
-  }
-  float pre[NPT];
-  auto fetch = [&](int z) {
-    const float* plane = rho + size_t(wrap(z, n)) * m.n2;
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) pre[j] = hslot[j] >= 0 ? __ldg(plane + hoff[j]) : 0.0f;
-  };
-  auto commit = [&](int slot) {
-    float* dst = &S[slot][0][0];
-#pragma unroll
-    for (int j = 0; j < NPT; ++j)
-      if (hslot[j] >= 0) dst[hslot[j]] = s_of(pre[j], fl);
-  };
-  fetch(z0 - 1);
-  commit(0);
-  fetch(z0);
-  commit(1);
-  fetch(z0 + 1);
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool inside = gx < n && gy < n;
-  float ksum = 0.0f;
-  int sm = 0, sc = 1, sp = 2;  // slots of planes z-1, z, z+1
-  for (int z = z0; z < z1; ++z) {
-    commit(sp);                  // plane z+1
-    if (z + 2 <= z1) fetch(z + 2);
-    __syncthreads();
-    if (inside) {
-      const float s0 = S[sc][ty + 1][tx + 1];
-      const float dxp = S[sc][ty + 1][tx + 2] - s0, dxm = S[sc][ty + 1][tx] - s0;
-      const float dyp = S[sc][ty + 2][tx + 1] - s0, dym = S[sc][ty][tx + 1] - s0;
-      const float dzp = S[sp][ty + 1][tx + 1] - s0, dzm = S[sm][ty + 1][tx + 1] - s0;
-      const float lap = (dxp + dxm) + (dyp + dym) + (dzp + dzm);
-      const size_t node = (size_t(z) * n + gy) * n + gx;
-      q[node] = qc * lap * __frcp_rn(s0);
-      ksum += dxp * dxp + dyp * dyp + dzp * dzp;
-      if (s0 < slim) my_list[atomicAdd(&s_cnt, 1u)] = uint32_t(node);
-    }
-    __syncthreads();  // the slot of plane z-1 is refilled next
-    const int t = sm;
-    sm = sc;
-    sc = sp;
-    sp = t;
-  }
-  if (tid == 0) list_count[blin] = s_cnt;
-  float acc[1] = {ksum};
-  block_sum_store<1>(acc, part, gridDim.x * gridDim.y * gridDim.z, int(blin));
 }
 
 __device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_t node, const Mesh& m, float fl,
@@ -524,19 +451,85 @@ __device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_
   return q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
 }
 
-// Float-float recomputation of the listed near-empty nodes: block b takes the
-// list region of stencil block b (same grid).
-static __global__ void __launch_bounds__(ST_X * ST_Y) k_stencil_ext(const float* __restrict__ rho, Mesh m, float fl,
-                                                                     float qc, int zlen, const uint32_t* list,
-                                                                     const uint32_t* list_count,
-                                                                     float* __restrict__ q) {
+static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const float* __restrict__ rho, Mesh m,
+                                                                        float fl, float qc, float slim, int zlen,
+                                                                        float* __restrict__ q, uint32_t* list,
+                                                                        uint32_t* list_count, double* part) {
+  constexpr int HX = ST_X + 2, HY = ST_Y + 2, HALO = HX * HY, NT = ST_X * ST_TY;
+  constexpr int NPT = (HALO + NT - 1) / NT;
+  __shared__ float S[3][HY][HX];
+  __shared__ uint32_t s_cnt;
+  const uint32_t n = uint32_t(m.n);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_X + tx;
+  const int x0 = blockIdx.x * ST_X, y0 = blockIdx.y * ST_Y;
+  const int z0 = blockIdx.z * zlen, z1 = min(z0 + zlen, int(n));
   const uint32_t blin = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  const uint32_t cnt = list_count[blin];
-  const uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
-  for (uint32_t i = threadIdx.y * ST_X + threadIdx.x; i < cnt; i += ST_X * ST_Y) {
+  uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
+  if (tid == 0) s_cnt = 0;
+  uint32_t hoff[NPT];
+  int hslot[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int i = tid + j * NT;
+    hslot[j] = i < HALO ? i : -1;
+    const int hy = i / HX, hx = i - hy * HX;
+    hoff[j] = uint32_t(wrap(y0 + hy - 1, int(n))) * n + uint32_t(wrap(x0 + hx - 1, int(n)));
+  }
+  float pre[NPT];
+  auto fetch = [&](int z) {
+    const float* plane = rho + uint32_t(wrap(z, int(n))) * m.n2;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) pre[j] = hslot[j] >= 0 ? __ldg(plane + hoff[j]) : 0.0f;
+  };
+  auto commit = [&](int slot) {
+    float* dst = &S[slot][0][0];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+      if (hslot[j] >= 0) dst[hslot[j]] = s_of(pre[j], fl);
+  };
+  fetch(z0 - 1);
+  commit(0);
+  fetch(z0);
+  commit(1);
+  fetch(z0 + 1);
+  const uint32_t gx = uint32_t(x0 + tx);
+  float ksum = 0.0f;
+  int sm = 0, sc = 1, sp = 2;  // slots of planes z-1, z, z+1
+  for (int z = z0; z < z1; ++z) {
+    commit(sp);  // plane z+1
+    if (z + 2 <= z1) fetch(z + 2);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int ly = ty + r * ST_TY;
+      const uint32_t gy = uint32_t(y0 + ly);
+      if (gx < n && gy < n) {
+        const float s0 = S[sc][ly + 1][tx + 1];
+        const float dxp = S[sc][ly + 1][tx + 2] - s0, dxm = S[sc][ly + 1][tx] - s0;
+        const float dyp = S[sc][ly + 2][tx + 1] - s0, dym = S[sc][ly][tx + 1] - s0;
+        const float dzp = S[sp][ly + 1][tx + 1] - s0, dzm = S[sm][ly + 1][tx + 1] - s0;
+        const float lap = (dxp + dxm) + (dyp + dym) + (dzp + dzm);
+        const uint32_t node = uint32_t(z) * m.n2 + gy * n + gx;
+        q[node] = __fdividef(qc * lap, s0);
+        ksum += dxp * dxp + dyp * dyp + dzp * dzp;
+        if (s0 < slim) my_list[atomicAdd(&s_cnt, 1u)] = node;
+      }
+    }
+    __syncthreads();  // the slot of plane z-1 is refilled next
+    const int t = sm;
+    sm = sc;
+    sc = sp;
+    sp = t;
+  }
+  // near-empty nodes of this block, recomputed in float-float
+  const uint32_t cnt = s_cnt;
+  for (uint32_t i = tid; i < cnt; i += NT) {
     const uint32_t node = my_list[i];
     q[node] = q_ext_at(rho, node, m, fl, qc);
   }
+  if (tid == 0) list_count[blin] = cnt;
+  float acc[1] = {ksum};
+  block_sum_store<1>(acc, part, gridDim.x * gridDim.y * gridDim.z, int(blin));
 }
 
 // ---------------------------------------------------------------- S6: interpolate + kick + drift
@@ -827,9 +820,7 @@ cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStre
   return cudaGetLastError();
 }
 
-inline dim3 stencil_grid(int n) {
-  return dim3((n + ST_X - 1) / ST_X, (n + ST_Y - 1) / ST_Y, ST_ZCH);
-}
+inline dim3 stencil_grid(int n) { return dim3((n + ST_X - 1) / ST_X, (n + ST_Y - 1) / ST_Y, ST_ZCH); }
 inline int stencil_zlen(int n) { return (n + ST_ZCH - 1) / ST_ZCH; }
 // entries of the near-empty node list (one region per stencil block)
 inline size_t stencil_list_len(int n) {
@@ -846,13 +837,11 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
                            uint32_t* list_count, cudaStream_t s) {
   if (sizeof(R) == 4 && sp.step == 1) {
     // fp32 compact path: shared-memory tiles, near-empty nodes redone in float-float
-    const dim3 g = stencil_grid(m.n), b(ST_X, ST_Y);
+    const dim3 g = stencil_grid(m.n), b(ST_X, ST_TY);
     const int zlen = stencil_zlen(m.n);
     const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;
     k_stencil_tiled<<<g, b, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, zlen, (float*)q,
                                     list, list_count, part);
-    k_stencil_ext<<<g, b, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), zlen, list, list_count,
-                                  (float*)q);
   } else {
     k_stencil<R><<<MESH_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
   }
