@@ -178,6 +178,36 @@ pm_status pm_profile_begin(pm_sim* sim, int32_t capacity);
  * device time in ms and the number of launches (arrays of PM_NSTAGES).  Sync. */
 pm_status pm_profile_end(pm_sim* sim, double* ms, int64_t* launches);
 
+/* ---- allocation-free deposit ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory: cudaFree synchronises the whole device and
+ * cudaMalloc may block, which a latency-critical serving loop or a real-time
+ * thread cannot afford, and a process that has already given its whole device
+ * memory budget to fixed arenas has nothing left to allocate from.
+ *
+ * pm_deposit_noalloc computes the same cloud-in-cell density as pm_deposit
+ * (step (i); fp32 path: cell + offset positions, stable radix sort by cell,
+ * deterministic gather) from n_part positions x_dev (device memory, n_part x 3
+ * doubles in [0, box), wrapped periodically otherwise) into rho_dev (device
+ * memory, n_mesh^3 floats, [z][y][x], mean 1), enqueued on the cudaStream_t
+ * `stream` (NULL = legacy default stream); async.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine: all temporaries live in one
+ * file-scope static device array of PM_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads the library holds until the process exits.  Limits:
+ * 1 <= n_part <= PM_NOALLOC_MAX_PARTICLES and n_mesh even in
+ * [8, PM_NOALLOC_MAX_MESH]; larger sizes return PM_ERR_INVALID_ARG and
+ * pm_last_error(NULL) says which limit was exceeded.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call
+ * reuses the same array and clears what must start at zero, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise them.
+ * Non-finite positions are placed at 0. */
+#define PM_NOALLOC_MAX_PARTICLES 65536
+#define PM_NOALLOC_MAX_MESH 128
+#define PM_NOALLOC_SCRATCH_BYTES (8u << 20)
+pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh, double box, float* rho_dev,
+                             void* stream);
+
 /* Message of the last failure on this handle (or of the last pm_create
  * failure when sim is NULL). */
 const char* pm_last_error(const pm_sim* sim);

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpm.so")
-SOURCES = ["pm_api.cu", "pm_kernels_f32.cu", "pm_kernels_f64.cu"]
+SOURCES = ["pm_api.cu", "pm_kernels_f32.cu", "pm_kernels_f64.cu", "pm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

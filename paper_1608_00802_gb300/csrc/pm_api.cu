@@ -206,6 +206,8 @@ bool fft_work_bytes(const pm_config& c, size_t* out, std::string* why) {
 
 }  // namespace
 
+void pm::set_global_error(const char* msg) { g_create_error = msg; }
+
 // ---------------------------------------------------------------- the handle
 struct pm_sim {
   pm_config cfg;

@@ -111,6 +111,9 @@ cudaError_t launch_to_double(const R* f, int64_t n, double* out, cudaStream_t s)
 template <typename R>
 cudaError_t launch_from_double(const double* f, int64_t n, R* out, cudaStream_t s);
 
+// stores the message that pm_last_error(NULL) returns (host side)
+void set_global_error(const char* msg);
+
 inline int kick_blocks(int64_t n) { return int((n + KICK_THREADS - 1) / KICK_THREADS); }
 
 }  // namespace pm

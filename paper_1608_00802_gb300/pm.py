@@ -26,7 +26,9 @@ FIELD_RHO, FIELD_PHI, FIELD_Q = 0, 1, 2
 EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create", "pm_destroy",
            "pm_set_particles", "pm_get_particles", "pm_deposit", "pm_forces", "pm_step", "pm_run",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
-           "pm_profile_begin", "pm_profile_end", "pm_last_error"]
+           "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error"]
+NOALLOC_MAX_PARTICLES = 65536
+NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
           "kick", "other"]
 CUFFT_STAGES = ("fft_r2c", "fft_c2r")
@@ -72,6 +74,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_get_order": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
         "pm_profile_begin": (C.c_int, [vp, C.c_int32]),
         "pm_profile_end": (C.c_int, [vp, dp, C.POINTER(C.c_int64)]),
+        "pm_deposit_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, C.c_double, vp, vp]),
         "pm_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -234,3 +237,17 @@ class Sim:
         cnt = np.zeros(len(STAGES), dtype=np.int64)
         self._check(lib().pm_profile_end(self.handle, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
         return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(STAGES)}
+
+
+def deposit_noalloc(x_dev, n_mesh, box, rho_dev, stream=None):
+    """pm_deposit_noalloc on torch CUDA tensors: x_dev float64 (n, 3), rho_dev
+    float32 (N, N, N); enqueued on `stream` (default: the current stream)."""
+    import torch
+    assert x_dev.is_cuda and x_dev.dtype == torch.float64 and x_dev.is_contiguous() and x_dev.shape[1] == 3
+    assert rho_dev.is_cuda and rho_dev.dtype == torch.float32 and rho_dev.is_contiguous()
+    assert rho_dev.numel() == n_mesh ** 3
+    st_obj = stream if stream is not None else torch.cuda.current_stream(x_dev.device)
+    st = lib().pm_deposit_noalloc(C.c_void_p(x_dev.data_ptr()), int(x_dev.shape[0]), int(n_mesh), float(box),
+                                  C.c_void_p(rho_dev.data_ptr()), C.c_void_p(st_obj.cuda_stream))
+    if st != PM_OK:
+        raise PMError(st, lib().pm_last_error(None).decode())
