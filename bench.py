@@ -378,6 +378,12 @@ def run_gpu(args):
                 "steps": K64, "ms_per_step": t64 / K64}
         s64.close()
 
+    batched = None
+    if not args.no_batch:
+        torch.cuda.empty_cache()
+        batched = run_batched(pm, ics, K, W, stream)
+        t_b = max_over_ranks(dist, batched["ms_per_step"])
+        batched["value"] = sum_over_ranks(dist, batched["particles"] * K) / (t_b * K / 1e3)
     if rank != 0:
         return 0
     cpu = None
@@ -392,10 +398,51 @@ def run_gpu(args):
                        "force_mode": "hybrid (PM gravity + Q by the kernel gradient, Sec. II.A step iii)", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.5 GB touched per step), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64,
+            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "batched": batched,
             "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None}
     print(json.dumps(line))
     return 0
+
+
+BATCH = dict(name="48 sims: 32^3/64^3/128^3 particles on 2x meshes (16 each), m22 in {1,2.5,5,10}, "
+                   "seeds 0-47, L ~ U(1,4) Mpc/h, z=100->3 in 200 steps, fp32, hybrid force, graph-captured",
+             nsims=48, sizes=(32, 64, 128), masses=(1.0, 2.5, 5.0, 10.0), nsteps=200, z_start=100.0, z_end=3.0)
+
+
+def batch_members():
+    """(n_side, n_mesh, box, m22, seed) of the 48-simulation batch: size class
+    i mod 3, mass (i div 3) mod 4, box 1 + 3 U_i from Philox(0xB00), seed i."""
+    u = np.random.Generator(np.random.Philox(0xB00)).uniform(size=BATCH["nsims"])
+    out = []
+    for i in range(BATCH["nsims"]):
+        n = BATCH["sizes"][i % 3]
+        out.append((n, 2 * n, 1.0 + 3.0 * float(u[i]), BATCH["masses"][(i // 3) % 4], i))
+    return out
+
+
+def run_batched(pm, ics, K, W, stream):
+    import torch
+    members = batch_members()
+    a = schedule(dict(z_start=BATCH["z_start"], z_end=BATCH["z_end"], nsteps=BATCH["nsteps"]))
+    cfgs = [pm.make_config(n ** 3, nm, box, precision=pm.FP32, m22=m22, force_mode=pm.FORCE_HYBRID)
+            for n, nm, box, m22, _ in members]
+    batch = pm.Batch(cfgs, stream=stream)
+    for mem, (n, nm, box, m22, seed) in zip(batch.members, members):
+        mem.set_particles(*ics.zeldovich(n, nm, box, a[0], seed, m22=m22))
+    with torch.cuda.stream(stream):
+        if W > 0:
+            batch.run(W, a[0], a[W])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run(K, a[W], a[W + K])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1)
+    units = sum(n ** 3 for n, *_ in members) * K
+    batch.close()
+    return {"value": units / (t / 1e3), "unit": "particle-steps/s", "steps": K, "ms_per_step": t / K,
+            "workload": BATCH["name"], "particles": sum(n ** 3 for n, *_ in members)}
 
 
 def main():
@@ -406,6 +453,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("steps >= 1, warmup >= 0")

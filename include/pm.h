@@ -178,6 +178,41 @@ pm_status pm_profile_begin(pm_sim* sim, int32_t capacity);
  * device time in ms and the number of launches (arrays of PM_NSTAGES).  Sync. */
 pm_status pm_profile_end(pm_sim* sim, double* ms, int64_t* launches);
 
+/* ---- batches of independent simulations ------------------------------------
+ * A batch steps many simulations of different sizes together on one GPU (the
+ * paper's runs are independent; the batch is only an execution unit).  Each
+ * member is an ordinary pm_sim (use pm_batch_member with the single-simulation
+ * calls: pm_set_particles, pm_energy, pm_get_particles, ...) with its own
+ * stream; pm_batch_run captures two leapfrog steps of all members as one CUDA
+ * graph (members run concurrently inside it) and replays it, so a step costs
+ * one graph launch.  Per-step kick and drift weights come from a table in the
+ * batch arena indexed by a per-member step counter on the device. */
+typedef struct pm_batch pm_batch;
+#define PM_BATCH_MAX_STEPS 8192
+
+/* Device bytes of a batch arena for n member configurations (0 if one is invalid). */
+size_t pm_batch_arena_bytes(const pm_config* cfgs, int32_t n);
+
+/* Creates n members (1 <= n <= 4096) in the caller's arena, each on a new
+ * stream; `stream` is the batch's own stream (NULL = legacy default).  Sync. */
+pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, size_t arena_bytes, void* stream,
+                          pm_batch** out);
+
+/* Destroys the members, their streams and the graph; the arena stays the caller's. Sync. */
+pm_status pm_batch_destroy(pm_batch* b);
+
+/* Member i (0-based), or NULL if out of range.  Owned by the batch. */
+pm_sim* pm_batch_member(pm_batch* b, int32_t i);
+
+/* nsteps leapfrog steps for every member, member i from a_start[i] to a_end[i]
+ * (uniform in ln a, or in t for static members), the same steps as pm_run;
+ * momenta are synchronised at the end.  1 <= nsteps <= PM_BATCH_MAX_STEPS.
+ * Async with respect to the host; the batch stream waits for all members. */
+pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const double* a_end);
+
+/* Message of the last failure of a batch call. */
+const char* pm_batch_last_error(const pm_batch* b);
+
 /* ---- allocation-free deposit ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory: cudaFree synchronises the whole device and

@@ -221,7 +221,6 @@ struct pm_sim {
   uint32_t* keys_tmp[2];
   cufftHandle plan_fwd, plan_inv;
   bool have_particles, sorted, fields_valid;
-  uint32_t sort_epoch = 0;
   std::string err;
   // profiler: event pairs around launches while enabled
   bool prof_on = false;
@@ -310,7 +309,7 @@ pm_status sort_particles(pm_sim* s) {
   CU(s, cudaMemsetAsync(hist, 0, (3 * (size_t(1) << RS_MAX_BITS) + 4) * 4, s->stream));
   {
     PROF(s, PM_STAGE_SORT_HISTOGRAM);
-    CU(s, launch_sort_histogram(s->keys, n, L.passes, L.digit_bits, L.key_bits, hist, s->stream));
+    CU(s, launch_sort_histogram(s->keys, n, L.passes, L.digit_bits, L.key_bits, hist, s->errword() + 1, s->stream));
   }
   const uint32_t* kin = s->keys;
   const uint32_t* vin = nullptr;
@@ -319,15 +318,13 @@ pm_status sort_particles(pm_sim* s) {
     const int shift = p * L.digit_bits;
     const int bits = (shift + L.digit_bits <= L.key_bits) ? L.digit_bits : (L.key_bits - shift);
     const bool last = p == L.passes - 1;
-    s->sort_epoch = (s->sort_epoch + 1) & 0xffffu;
-    if (s->sort_epoch == 0) s->sort_epoch = 1;  // epoch 0 marks never-written status words
     const uint32_t* dtot = hist + p * (1 << RS_MAX_BITS);
     PROF(s, PM_STAGE_SORT_PASS);
     if (!last) {
       uint32_t* kout = s->keys_tmp[tmp];
       uint32_t* vout = vals[tmp];
-      CU(s, launch_sort_pass<R>(false, kin, vin, n, shift, bits, dtot, status, counters + p, s->sort_epoch, L.ntiles,
-                                kout, vout, nullptr, nullptr, nullptr, nullptr, s->errword(), s->stream));
+      CU(s, launch_sort_pass<R>(false, kin, vin, n, shift, bits, dtot, status, counters + p, s->errword() + 1, p,
+                                L.ntiles, kout, vout, nullptr, nullptr, nullptr, nullptr, s->errword(), s->stream));
       kin = kout;
       vin = vout;
       tmp ^= 1;
@@ -335,9 +332,9 @@ pm_status sort_particles(pm_sim* s) {
       // the sorted keys go to a buffer that is not the input
       uint32_t* kout = (kin == s->keys) ? s->keys_tmp[tmp] : s->keys;
       const int nxt = s->cur ^ 1;
-      CU(s, launch_sort_pass<R>(true, kin, vin, n, shift, bits, dtot, status, counters + p, s->sort_epoch, L.ntiles,
-                                kout, nullptr, s->pos(), s->mom(), s->arena + L.pos[nxt], s->arena + L.mom[nxt],
-                                s->errword(), s->stream));
+      CU(s, launch_sort_pass<R>(true, kin, vin, n, shift, bits, dtot, status, counters + p, s->errword() + 1, p,
+                                L.ntiles, kout, nullptr, s->pos(), s->mom(), s->arena + L.pos[nxt],
+                                s->arena + L.mom[nxt], s->errword(), s->stream));
       if (kout != s->keys) {  // swap roles so that s->keys holds the sorted keys
         for (int k = 0; k < 2; ++k)
           if (s->keys_tmp[k] == kout) s->keys_tmp[k] = s->keys;
@@ -424,12 +421,13 @@ KickParams base_kick(const pm_sim* s) {
 }
 
 template <typename R>
-pm_status kick(pm_sim* s, const KickParams& kp, double* acc) {
+pm_status kick(pm_sim* s, const KickParams& kp, double* acc, const KickParams* kp_tab = nullptr,
+               const uint32_t* step = nullptr) {
   const Layout& L = s->L;
   {
     PROF(s, PM_STAGE_KICK);
-    CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, s->part(),
-                         acc, s->errword(), s->stream));
+    CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, kp_tab,
+                         step, s->part(), acc, s->errword(), s->stream));
   }
   if (kp.drift != 0.0) {
     s->sorted = false;
@@ -472,6 +470,28 @@ pm_status pass(pm_sim* s, Weights w1, Weights w2, double d, bool diag) {
   kp.drift = d / s->dx;
   kp.diag = diag;
   return DISPATCH(s, kick, s, kp, nullptr);
+}
+
+double run_a(const pm_config& c, int i, int nsteps, double a_start, double a_end) {
+  if (i == nsteps) return a_end;
+  const double t = double(i) / nsteps;
+  return c.cosmological ? a_start * pow(a_end / a_start, t) : a_start + (a_end - a_start) * t;
+}
+
+// leapfrog weights of pm_run's step i (merged kicks): returns the kick of the
+// step and updates `pending` to the closing half kick
+KickParams step_params(const pm_sim* s, int i, int nsteps, double a_start, double a_end, Weights* pending) {
+  const double a0 = run_a(s->cfg, i, nsteps, a_start, a_end), a1 = run_a(s->cfg, i + 1, nsteps, a_start, a_end);
+  const double ah = half_point(s->cfg, a0, a1);
+  const Weights w2 = time_weights(s->cfg, a0, ah);
+  KickParams kp = base_kick(s);
+  kp.cg1 = pending->kg;
+  kp.cq1 = pending->kq;
+  kp.cg2 = w2.kg;
+  kp.cq2 = w2.kq;
+  kp.drift = time_weights(s->cfg, a0, a1).kq / s->dx;
+  *pending = time_weights(s->cfg, ah, a1);
+  return kp;
 }
 
 }  // namespace
@@ -562,7 +582,7 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
       return fail(nullptr, PM_ERR_CUFFT, "cuFFT plan setup failed (%d)", int(r));
     }
   }
-  if (cudaMemsetAsync(s->errword(), 0, 4, s->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(s->errword(), 0, 8, s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->arena + L.status, 0, (size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8, s->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(s->stream) != cudaSuccess) {
@@ -666,24 +686,17 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
   if (st != PM_OK) return st;
   if (nsteps < 1) return fail(s, PM_ERR_INVALID_ARG, "nsteps must be >= 1");
   if (s->cfg.cosmological && !(a_start > 0 && a_end > 0)) return fail(s, PM_ERR_INVALID_ARG, "a must be positive");
-  auto a_at = [&](int i) {
-    if (i == nsteps) return a_end;
-    double t = double(i) / nsteps;
-    return s->cfg.cosmological ? a_start * pow(a_end / a_start, t) : a_start + (a_end - a_start) * t;
-  };
   st = ensure_fields(s);
   if (st != PM_OK) return st;
-  const Weights zero = {0.0, 0.0};
-  Weights pending = zero;  // closing half kick of the previous step
+  Weights pending = {0.0, 0.0};  // closing half kick of the previous step
   for (int i = 0; i < nsteps; ++i) {
-    const double a0 = a_at(i), a1 = a_at(i + 1), ah = half_point(s->cfg, a0, a1);
-    st = pass(s, pending, time_weights(s->cfg, a0, ah), time_weights(s->cfg, a0, a1).kq, false);
+    const KickParams kp = step_params(s, i, nsteps, a_start, a_end, &pending);
+    st = DISPATCH(s, kick, s, kp, nullptr);
     if (st != PM_OK) return st;
     st = ensure_fields(s);
     if (st != PM_OK) return st;
-    pending = time_weights(s->cfg, ah, a1);
   }
-  return pass(s, pending, zero, 0.0, true);
+  return pass(s, pending, Weights{0.0, 0.0}, 0.0, true);
 }
 
 pm_status pm_energy(pm_sim* s, double a, double out[6]) {
@@ -842,5 +855,236 @@ pm_status pm_profile_end(pm_sim* s, double* ms, int64_t* launches) {
 }
 
 const char* pm_last_error(const pm_sim* s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"
+
+// ================================================================ batches
+struct pm_batch {
+  std::vector<pm_sim*> sims;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t stream = nullptr;
+  char* arena = nullptr;
+  size_t table_off = 0, step_off = 0;
+  std::string err;
+};
+
+namespace {
+
+pm_status bfail(pm_batch* b, pm_status st, const std::string& msg) {
+  if (b)
+    b->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+struct BatchLayout {
+  std::vector<size_t> off, bytes;
+  size_t table_off, step_off, total;
+};
+
+bool batch_layout(const pm_config* cfgs, int n, BatchLayout* L, std::string* why) {
+  size_t off = 0;
+  L->off.resize(n);
+  L->bytes.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const size_t b = pm_arena_bytes(&cfgs[i]);
+    if (b == 0) {
+      *why = "member " + std::to_string(i) + ": " + g_create_error;
+      return false;
+    }
+    L->off[i] = off;
+    L->bytes[i] = b;
+    off = align_up(off + b);
+  }
+  L->table_off = off;
+  off = align_up(off + size_t(n) * PM_BATCH_MAX_STEPS * sizeof(KickParams));
+  L->step_off = off;
+  off = align_up(off + size_t(n) * sizeof(uint32_t));
+  L->total = off;
+  return true;
+}
+
+// member i's part of a captured step: table-driven kick + drift, then steps (i)-(iii)
+pm_status batch_member_step(pm_sim* s, const KickParams* tab, uint32_t* step) {
+  KickParams kp = base_kick(s);
+  kp.drift = 1.0;  // host-side marker only: the positions move, the weights come from the table
+  pm_status st = DISPATCH(s, kick, s, kp, nullptr, tab, step);
+  if (st != PM_OK) return st;
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  CU(s, launch_step_inc(step, s->stream));
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pm_batch_arena_bytes(const pm_config* cfgs, int32_t n) {
+  if (!cfgs || n < 1 || n > 4096) {
+    g_create_error = "need 1..4096 member configurations";
+    return 0;
+  }
+  BatchLayout L;
+  std::string why;
+  if (!batch_layout(cfgs, n, &L, &why)) {
+    g_create_error = why;
+    return 0;
+  }
+  return L.total;
+}
+
+pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, size_t bytes, void* stream,
+                          pm_batch** out) {
+  if (!out) return bfail(nullptr, PM_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!cfgs || n < 1 || n > 4096) return bfail(nullptr, PM_ERR_INVALID_ARG, "need 1..4096 member configurations");
+  if (!dev_arena || (reinterpret_cast<uintptr_t>(dev_arena) & 255))
+    return bfail(nullptr, PM_ERR_INVALID_ARG, "arena must be a 256-byte aligned device pointer");
+  BatchLayout L;
+  std::string why;
+  if (!batch_layout(cfgs, n, &L, &why)) return bfail(nullptr, PM_ERR_INVALID_ARG, why);
+  if (bytes < L.total)
+    return bfail(nullptr, PM_ERR_NO_MEMORY,
+                 "arena has " + std::to_string(bytes) + " bytes, needs " + std::to_string(L.total));
+  pm_batch* b = new pm_batch();
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->arena = reinterpret_cast<char*>(dev_arena);
+  b->table_off = L.table_off;
+  b->step_off = L.step_off;
+  auto cleanup = [&](pm_status st, const std::string& msg) {
+    for (pm_sim* s : b->sims) pm_destroy(s);
+    for (cudaStream_t st2 : b->streams) cudaStreamDestroy(st2);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+    return bfail(nullptr, st, msg);
+  };
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(PM_ERR_CUDA, "event creation failed");
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t st2;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(PM_ERR_CUDA, "stream creation failed");
+    b->streams.push_back(st2);
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(PM_ERR_CUDA, "event creation failed");
+    b->join.push_back(ev);
+    pm_sim* s = nullptr;
+    pm_status r = pm_create(&cfgs[i], b->arena + L.off[i], L.bytes[i], st2, &s);
+    if (r != PM_OK) return cleanup(r, "member " + std::to_string(i) + ": " + g_create_error);
+    b->sims.push_back(s);
+  }
+  *out = b;
+  return PM_OK;
+}
+
+pm_status pm_batch_destroy(pm_batch* b) {
+  if (!b) return PM_ERR_INVALID_ARG;
+  for (pm_sim* s : b->sims) pm_destroy(s);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+  return PM_OK;
+}
+
+pm_sim* pm_batch_member(pm_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= int32_t(b->sims.size())) return nullptr;
+  return b->sims[i];
+}
+
+pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const double* a_end) {
+  if (!b) return PM_ERR_INVALID_ARG;
+  if (!a_start || !a_end || nsteps < 1 || nsteps > PM_BATCH_MAX_STEPS)
+    return bfail(b, PM_ERR_INVALID_ARG, "need a_start, a_end and 1 <= nsteps <= PM_BATCH_MAX_STEPS");
+  const int n = int(b->sims.size());
+  for (int i = 0; i < n; ++i) {
+    pm_sim* s = b->sims[i];
+    if (!s->have_particles) return bfail(b, PM_ERR_STATE, "member " + std::to_string(i) + " has no particles");
+    if (s->cfg.cosmological && !(a_start[i] > 0 && a_end[i] > 0))
+      return bfail(b, PM_ERR_INVALID_ARG, "member " + std::to_string(i) + ": a must be positive");
+    if (s->prof_on) return bfail(b, PM_ERR_STATE, "profiling must be off during pm_batch_run");
+  }
+  auto member_error = [&](int i) { return bfail(b, PM_ERR_CUDA, "member " + std::to_string(i) + ": " + b->sims[i]->err); };
+#define BCU(expr)                                                                                  \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+  // per-member weights of every step, and the closing half kicks
+  std::vector<KickParams> tab(size_t(n) * nsteps);
+  std::vector<Weights> closing(n);
+  for (int i = 0; i < n; ++i) {
+    Weights pending = {0.0, 0.0};
+    for (int k = 0; k < nsteps; ++k)
+      tab[size_t(i) * nsteps + k] = step_params(b->sims[i], k, nsteps, a_start[i], a_end[i], &pending);
+    closing[i] = pending;
+  }
+  KickParams* tab_dev = reinterpret_cast<KickParams*>(b->arena + b->table_off);
+  uint32_t* steps_dev = reinterpret_cast<uint32_t*>(b->arena + b->step_off);
+  BCU(cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(KickParams), cudaMemcpyHostToDevice, b->stream));
+  BCU(cudaMemsetAsync(steps_dev, 0, size_t(n) * sizeof(uint32_t), b->stream));
+  BCU(cudaEventRecord(b->fork, b->stream));
+  // forces at the start of every member (outside the graph), on the member streams
+  for (int i = 0; i < n; ++i) {
+    BCU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+    if (ensure_fields(b->sims[i]) != PM_OK) return member_error(i);
+    BCU(cudaEventRecord(b->join[i], b->streams[i]));
+    BCU(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+  }
+  const int pairs = nsteps / 2;
+  if (pairs > 0) {
+    // capture two steps of every member (the record buffers alternate each step)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeGlobal));
+    pm_status st = PM_OK;
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) st = PM_ERR_CUDA;
+    for (int i = 0; i < n && st == PM_OK; ++i) {
+      pm_sim* s = b->sims[i];
+      if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) st = PM_ERR_CUDA;
+      for (int r = 0; r < 2 && st == PM_OK; ++r) st = batch_member_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i);
+      if (st == PM_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) st = PM_ERR_CUDA;
+      if (st == PM_OK && cudaStreamWaitEvent(b->stream, b->join[i], 0) != cudaSuccess) st = PM_ERR_CUDA;
+      if (st != PM_OK) b->err = "capture of member " + std::to_string(i) + " failed: " + s->err;
+    }
+    cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    if (st != PM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return PM_ERR_CUDA;
+    }
+    if (ec != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+    for (int k = 0; k < pairs; ++k) {
+      ec = cudaGraphLaunch(exec, b->stream);
+      if (ec != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(exec);
+    if (ec != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ec));
+  }
+  // an odd last step, then the closing half kicks, on the member streams
+  BCU(cudaEventRecord(b->fork, b->stream));
+  for (int i = 0; i < n; ++i) {
+    pm_sim* s = b->sims[i];
+    BCU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+    if (nsteps & 1) {
+      if (batch_member_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i) != PM_OK) return member_error(i);
+    }
+    if (pass(s, closing[i], Weights{0.0, 0.0}, 0.0, true) != PM_OK) return member_error(i);
+    BCU(cudaEventRecord(b->join[i], b->streams[i]));
+    BCU(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+  }
+#undef BCU
+  return PM_OK;
+}
+
+const char* pm_batch_last_error(const pm_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"

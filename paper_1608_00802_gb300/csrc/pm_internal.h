@@ -75,12 +75,14 @@ template <typename R>
 cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, Mesh m, double inv_dx,
                                   void* pos, void* mom, uint32_t* keys, uint32_t* err, cudaStream_t s);
 cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, int digit_bits, int key_bits,
-                                  uint32_t* hist, cudaStream_t s);
+                                  uint32_t* hist, uint32_t* epoch, cudaStream_t s);
 template <typename R>
 cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
                              int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
-                             uint32_t epoch, int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
-                             const void* mom_in, void* pos_out, void* mom_out, uint32_t* err, cudaStream_t s);
+                             const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
+                             const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
+                             cudaStream_t s);
+cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s);
 cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start,
                              cudaStream_t s);
 template <typename R>
@@ -96,7 +98,8 @@ size_t stencil_list_entries(int n);
 int stencil_block_count(int n);
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
-                        KickParams kp, double* part, double* acc, uint32_t* err, cudaStream_t s);
+                        KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
+                        uint32_t* err, cudaStream_t s);
 template <typename R>
 cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);

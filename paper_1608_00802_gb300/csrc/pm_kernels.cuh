@@ -623,9 +623,13 @@ __device__ __forceinline__ int carry(R& o) {
 template <typename R>
 __global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
                                                        uint32_t* keys, int64_t n, const R* __restrict__ phi,
-                                                       const R* __restrict__ qf, Mesh m, KickParams kp,
-                                                       double* part, double* acc_out, uint32_t* err) {
+                                                       const R* __restrict__ qf, Mesh m, KickParams kp_arg,
+                                                       const KickParams* __restrict__ kp_tab,
+                                                       const uint32_t* __restrict__ step, double* part,
+                                                       double* acc_out, uint32_t* err) {
   using V4 = typename VT<R>::v4;
+  // weights by value, or (graph replay) from a per-step table indexed by a device step counter
+  const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   R dg[4] = {R(0), R(0), R(0), R(0)};
   if (i < n) {
@@ -805,8 +809,16 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
   using V4 = typename VT<R>::v4;
   const size_t smem = size_t(DEP_WARPS) * (m.n + 1) * sizeof(R);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_deposit<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
+    // once per device, for the largest mesh, so that no attribute call falls inside a stream capture
+    static bool done[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      const int most = int(size_t(DEP_WARPS) * (1024 + 1) * sizeof(R));
+      cudaError_t e = cudaFuncSetAttribute(k_deposit<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
   }
   const unsigned blocks = (m.n2 + DEP_WARPS - 1) / DEP_WARPS;
   k_deposit<R><<<blocks, DEP_WARPS * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho);
@@ -850,10 +862,12 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
 
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
-                        KickParams kp, double* part, double* acc, uint32_t* err, cudaStream_t s) {
+                        KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
+                        uint32_t* err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   using V4 = typename VT<R>::v4;
-  k_kick<R><<<kick_blocks(n), KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, part, acc, err);
+  k_kick<R><<<kick_blocks(n), KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part,
+                                                    acc, err);
   return cudaGetLastError();
 }
 

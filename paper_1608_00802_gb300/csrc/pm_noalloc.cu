@@ -136,10 +136,10 @@ pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh
   // the array keeps the previous call's contents: clear what must start at zero
   NA_CU(cudaMemsetAsync(hist, 0, (3 * kRadixMax + 4) * 4, s));
   NA_CU(cudaMemsetAsync(status, 0, size_t(ntiles) * (size_t(1) << digit_bits) * 8, s));
-  NA_CU(cudaMemsetAsync(err, 0, 4, s));
+  NA_CU(cudaMemsetAsync(err, 0, 8, s));  // error word and sort epoch word
   NA_CU(cudaMemsetAsync(zero_p, 0, size_t(n) * 24, s));
   NA_CU(launch_init_particles<float>(x_dev, zero_p, n, m, double(n_mesh) / box, pos[0], mom[0], keys[0], err, s));
-  NA_CU(launch_sort_histogram(keys[0], n, passes, digit_bits, bits, hist, s));
+  NA_CU(launch_sort_histogram(keys[0], n, passes, digit_bits, bits, hist, err + 1, s));
   const uint32_t* kin = keys[0];
   const uint32_t* vin = nullptr;
   int tmp = 0;
@@ -148,17 +148,16 @@ pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh
     const int shift = p * digit_bits;
     const int pb = (shift + digit_bits <= bits) ? digit_bits : (bits - shift);
     const bool last = p == passes - 1;
-    const uint32_t epoch = uint32_t(p + 1);  // status words were cleared above
     if (!last) {
-      NA_CU(launch_sort_pass<float>(false, kin, vin, n, shift, pb, hist + p * kRadixMax, status, counters + p, epoch,
-                                    ntiles, keys[1 + tmp], vals[tmp], nullptr, nullptr, nullptr, nullptr, err, s));
+      NA_CU(launch_sort_pass<float>(false, kin, vin, n, shift, pb, hist + p * kRadixMax, status, counters + p, err + 1,
+                                    p, ntiles, keys[1 + tmp], vals[tmp], nullptr, nullptr, nullptr, nullptr, err, s));
       kin = keys[1 + tmp];
       vin = vals[tmp];
       tmp ^= 1;
     } else {
       uint32_t* kout = (kin == keys[0]) ? keys[1 + tmp] : keys[0];
-      NA_CU(launch_sort_pass<float>(true, kin, vin, n, shift, pb, hist + p * kRadixMax, status, counters + p, epoch,
-                                    ntiles, kout, nullptr, pos[0], mom[0], pos[1], mom[1], err, s));
+      NA_CU(launch_sort_pass<float>(true, kin, vin, n, shift, pb, hist + p * kRadixMax, status, counters + p, err + 1,
+                                    p, ntiles, kout, nullptr, pos[0], mom[0], pos[1], mom[1], err, s));
       sorted_keys = kout;
     }
   }

@@ -71,10 +71,16 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
 }
 
 // Digit histograms of every pass: hist[p * radix_max + d].
+// Block 0 also advances the sort's epoch word: the passes of this sort use
+// epochs base .. base + passes - 1, never 0 and never those of the previous
+// sort, so status words left by earlier sorts (or by an earlier replay of a
+// captured graph) are never mistaken for current ones.
 static __global__ void __launch_bounds__(RS_THREADS) k_sort_histogram(const uint32_t* __restrict__ keys, int64_t n,
                                                                       int passes, int digit_bits, int key_bits,
-                                                                      uint32_t* __restrict__ hist) {
+                                                                      uint32_t* __restrict__ hist,
+                                                                      uint32_t* __restrict__ epoch) {
   __shared__ uint32_t sh[3 * (1 << RS_MAX_BITS)];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *epoch = (*epoch + uint32_t(passes)) % 65530u + 1u;
   const int radix = 1 << digit_bits;
   for (int i = threadIdx.x; i < passes * radix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
@@ -106,7 +112,8 @@ static __global__ void __launch_bounds__(RS_THREADS) k_sort_histogram(const uint
 template <bool LAST, typename V4>
 __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, int64_t n, int shift, int bits,
-    const uint32_t* __restrict__ digit_total, uint64_t* status, uint32_t* tile_counter, uint32_t epoch,
+    const uint32_t* __restrict__ digit_total, uint64_t* status, uint32_t* tile_counter,
+    const uint32_t* __restrict__ epoch_base, int pass,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const V4* __restrict__ pos_in,
     const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out, uint32_t* err) {
   extern __shared__ uint32_t smem[];
@@ -120,6 +127,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
   uint32_t* scratch = s_vals + RS_TILE;                // [64] (+1: tile id)
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t epoch = *epoch_base + uint32_t(pass);
   if (threadIdx.x == 0) scratch[63] = atomicAdd(tile_counter, 1u);
   for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
   __syncthreads();
@@ -289,23 +297,32 @@ static __global__ void k_reduce(const double* __restrict__ part, int nblocks, do
 template <typename R>
 cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
                              int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
-                             uint32_t epoch, int ntiles, uint32_t* keys_out, uint32_t* vals_out, const void* pos_in,
-                             const void* mom_in, void* pos_out, void* mom_out, uint32_t* err, cudaStream_t s) {
+                             const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
+                             const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
+                             cudaStream_t s) {
   using V4 = typename VT<R>::v4;
   const size_t smem = radix_smem_bytes(bits);
+  // shared-memory limits are raised once per device (for the largest digit), outside any capture
+  static bool done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !done[dev]) {
+    const int most = int(radix_smem_bytes(RS_MAX_BITS));
+    cudaError_t e = cudaFuncSetAttribute(k_sort_pass<true, V4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sort_pass<false, V4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+  }
   if (last) {
-    auto k = k_sort_pass<true, V4>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    k<<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status, tile_counter, epoch,
-                                       keys_out, vals_out, (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
-                                       (V4*)mom_out, err);
+    k_sort_pass<true, V4><<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
+                                                           tile_counter, epoch, pass, keys_out, vals_out,
+                                                           (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
+                                                           (V4*)mom_out, err);
   } else {
-    auto k = k_sort_pass<false, V4>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    k<<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status, tile_counter, epoch,
-                                       keys_out, vals_out, nullptr, nullptr, nullptr, nullptr, err);
+    k_sort_pass<false, V4><<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
+                                                            tile_counter, epoch, pass, keys_out, vals_out, nullptr,
+                                                            nullptr, nullptr, nullptr, err);
   }
   return cudaGetLastError();
 }

@@ -26,7 +26,9 @@ FIELD_RHO, FIELD_PHI, FIELD_Q = 0, 1, 2
 EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create", "pm_destroy",
            "pm_set_particles", "pm_get_particles", "pm_deposit", "pm_forces", "pm_step", "pm_run",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
-           "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error"]
+           "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error",
+           "pm_batch_arena_bytes", "pm_batch_create", "pm_batch_destroy", "pm_batch_member", "pm_batch_run",
+           "pm_batch_last_error"]
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
@@ -76,6 +78,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_profile_end": (C.c_int, [vp, dp, C.POINTER(C.c_int64)]),
         "pm_deposit_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, C.c_double, vp, vp]),
         "pm_last_error": (C.c_char_p, [vp]),
+        "pm_batch_arena_bytes": (C.c_size_t, [cfgp, C.c_int32]),
+        "pm_batch_create": (C.c_int, [cfgp, C.c_int32, vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "pm_batch_destroy": (C.c_int, [vp]),
+        "pm_batch_member": (vp, [vp, C.c_int32]),
+        "pm_batch_run": (C.c_int, [vp, C.c_int32, dp, dp]),
+        "pm_batch_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -123,9 +131,13 @@ class Sim:
     (N, N, N) indexed [z, y, x].
     """
 
-    def __init__(self, cfg: pm_config, device=None, stream=None, arena=None):
+    def __init__(self, cfg: pm_config, device=None, stream=None, arena=None, handle=None):
         import torch
         self.cfg = cfg
+        if handle is not None:  # a batch member: the batch owns the handle and the arena
+            self.n, self.N, self.handle, self.owned = int(cfg.n_part), int(cfg.n_mesh), handle, False
+            return
+        self.owned = True
         self.n = int(cfg.n_part)
         self.N = int(cfg.n_mesh)
         self.device = torch.device(device if device is not None else "cuda")
@@ -151,9 +163,9 @@ class Sim:
             raise PMError(st, lib().pm_last_error(self.handle).decode())
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "owned", True):
             lib().pm_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -251,3 +263,46 @@ def deposit_noalloc(x_dev, n_mesh, box, rho_dev, stream=None):
                                   C.c_void_p(rho_dev.data_ptr()), C.c_void_p(st_obj.cuda_stream))
     if st != PM_OK:
         raise PMError(st, lib().pm_last_error(None).decode())
+
+
+class Batch:
+    """Many independent simulations stepped together (pm_batch_*)."""
+
+    def __init__(self, cfgs, device=None, stream=None):
+        import torch
+        self.cfgs = list(cfgs)
+        arr = (pm_config * len(self.cfgs))(*self.cfgs)
+        self._arr = arr
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = int(lib().pm_batch_arena_bytes(arr, len(self.cfgs)))
+        if nbytes == 0:
+            raise PMError(1, lib().pm_last_error(None).decode())
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = lib().pm_batch_create(arr, len(self.cfgs), C.c_void_p(self.arena.data_ptr()), C.c_size_t(nbytes),
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != PM_OK:
+            raise PMError(st, lib().pm_last_error(None).decode())
+        self.handle = h
+        self.members = [Sim(c, handle=C.c_void_p(lib().pm_batch_member(h, i))) for i, c in enumerate(self.cfgs)]
+
+    def run(self, nsteps, a_start, a_end):
+        a0 = np.ascontiguousarray(np.broadcast_to(np.asarray(a_start, dtype=np.float64), (len(self.cfgs),)))
+        a1 = np.ascontiguousarray(np.broadcast_to(np.asarray(a_end, dtype=np.float64), (len(self.cfgs),)))
+        st = lib().pm_batch_run(self.handle, int(nsteps), _dptr(a0), _dptr(a1))
+        if st != PM_OK:
+            raise PMError(st, lib().pm_batch_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for m in self.members:
+                m.handle = None
+            lib().pm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
