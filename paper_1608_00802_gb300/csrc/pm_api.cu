@@ -863,8 +863,9 @@ struct pm_batch {
   std::vector<pm_sim*> sims;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
-  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  cudaStream_t stream = nullptr;  // the caller's stream
+  cudaStream_t cap = nullptr;     // the batch's own stream: graphs are captured and launched here
   char* arena = nullptr;
   size_t table_off = 0, step_off = 0;
   std::string err;
@@ -960,11 +961,15 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
     for (cudaStream_t st2 : b->streams) cudaStreamDestroy(st2);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return bfail(nullptr, st, msg);
   };
-  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
-    return cleanup(PM_ERR_CUDA, "event creation failed");
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(PM_ERR_CUDA, "event or stream creation failed");
   for (int i = 0; i < n; ++i) {
     cudaStream_t st2;
     cudaEvent_t ev;
@@ -989,6 +994,8 @@ pm_status pm_batch_destroy(pm_batch* b) {
   for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return PM_OK;
 }
@@ -1025,35 +1032,38 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
       tab[size_t(i) * nsteps + k] = step_params(b->sims[i], k, nsteps, a_start[i], a_end[i], &pending);
     closing[i] = pending;
   }
+  // the batch's own stream follows the caller's stream (the legacy default stream cannot be captured)
+  BCU(cudaEventRecord(b->done, b->stream));
+  BCU(cudaStreamWaitEvent(b->cap, b->done, 0));
   KickParams* tab_dev = reinterpret_cast<KickParams*>(b->arena + b->table_off);
   uint32_t* steps_dev = reinterpret_cast<uint32_t*>(b->arena + b->step_off);
-  BCU(cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(KickParams), cudaMemcpyHostToDevice, b->stream));
-  BCU(cudaMemsetAsync(steps_dev, 0, size_t(n) * sizeof(uint32_t), b->stream));
-  BCU(cudaEventRecord(b->fork, b->stream));
+  BCU(cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(KickParams), cudaMemcpyHostToDevice, b->cap));
+  BCU(cudaMemsetAsync(steps_dev, 0, size_t(n) * sizeof(uint32_t), b->cap));
+  BCU(cudaEventRecord(b->fork, b->cap));
   // forces at the start of every member (outside the graph), on the member streams
   for (int i = 0; i < n; ++i) {
     BCU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
     if (ensure_fields(b->sims[i]) != PM_OK) return member_error(i);
     BCU(cudaEventRecord(b->join[i], b->streams[i]));
-    BCU(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+    BCU(cudaStreamWaitEvent(b->cap, b->join[i], 0));
   }
   const int pairs = nsteps / 2;
   if (pairs > 0) {
     // capture two steps of every member (the record buffers alternate each step)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    BCU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeGlobal));
+    BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeGlobal));
     pm_status st = PM_OK;
-    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) st = PM_ERR_CUDA;
+    if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) st = PM_ERR_CUDA;
     for (int i = 0; i < n && st == PM_OK; ++i) {
       pm_sim* s = b->sims[i];
       if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) st = PM_ERR_CUDA;
       for (int r = 0; r < 2 && st == PM_OK; ++r) st = batch_member_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i);
       if (st == PM_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) st = PM_ERR_CUDA;
-      if (st == PM_OK && cudaStreamWaitEvent(b->stream, b->join[i], 0) != cudaSuccess) st = PM_ERR_CUDA;
+      if (st == PM_OK && cudaStreamWaitEvent(b->cap, b->join[i], 0) != cudaSuccess) st = PM_ERR_CUDA;
       if (st != PM_OK) b->err = "capture of member " + std::to_string(i) + " failed: " + s->err;
     }
-    cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
     if (st != PM_OK) {
       if (graph) cudaGraphDestroy(graph);
       return PM_ERR_CUDA;
@@ -1063,14 +1073,14 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     cudaGraphDestroy(graph);
     if (ec != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
     for (int k = 0; k < pairs; ++k) {
-      ec = cudaGraphLaunch(exec, b->stream);
+      ec = cudaGraphLaunch(exec, b->cap);
       if (ec != cudaSuccess) break;
     }
     cudaGraphExecDestroy(exec);
     if (ec != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ec));
   }
   // an odd last step, then the closing half kicks, on the member streams
-  BCU(cudaEventRecord(b->fork, b->stream));
+  BCU(cudaEventRecord(b->fork, b->cap));
   for (int i = 0; i < n; ++i) {
     pm_sim* s = b->sims[i];
     BCU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
@@ -1079,8 +1089,11 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     }
     if (pass(s, closing[i], Weights{0.0, 0.0}, 0.0, true) != PM_OK) return member_error(i);
     BCU(cudaEventRecord(b->join[i], b->streams[i]));
-    BCU(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+    BCU(cudaStreamWaitEvent(b->cap, b->join[i], 0));
   }
+  // and the caller's stream follows the batch
+  BCU(cudaEventRecord(b->done, b->cap));
+  BCU(cudaStreamWaitEvent(b->stream, b->done, 0));
 #undef BCU
   return PM_OK;
 }
