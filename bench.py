@@ -384,6 +384,11 @@ def run_gpu(args):
         batched = run_batched(pm, ics, K, W, stream)
         t_b = max_over_ranks(dist, batched["ms_per_step"])
         batched["value"] = sum_over_ranks(dist, batched["particles"] * K) / (t_b * K / 1e3)
+    served = None
+    if args.serve_requests > 0:
+        from paper_1608_00802_gb300 import serve
+        torch.cuda.empty_cache()
+        served = run_served(serve, args.serve_requests)
     if rank != 0:
         return 0
     cpu = None
@@ -398,7 +403,7 @@ def run_gpu(args):
                        "force_mode": "hybrid (PM gravity + Q by the kernel gradient, Sec. II.A step iii)", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.5 GB touched per step), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "batched": batched,
+            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "batched": batched, "served": served,
             "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None}
     print(json.dumps(line))
     return 0
@@ -445,6 +450,34 @@ def run_batched(pm, ics, K, W, stream):
             "workload": BATCH["name"], "particles": sum(n ** 3 for n, *_ in members)}
 
 
+SERVE = dict(name="Poisson arrivals 20 req/s, particles {32,64,128,192}^3 (weights .4/.3/.2/.1), mesh 2x, "
+                   "m22 log-uniform 1-10, L ~ U(1,4), z=50->5 in 200 steps, fp32, hybrid force, HBM budget 64 GB",
+             rate=20.0, budget=64 << 30, chunk=10)
+
+
+def _initial_conditions(req):
+    from paper_1608_00802_gb300 import serve
+    return serve.initial_conditions(req)
+
+
+def run_served(serve, n_requests):
+    """Continuous batching on the request stream; initial conditions are made
+    before the timed stream (in a spawned process pool), the rest is timed."""
+    import multiprocessing as mp
+    reqs = serve.request_stream(n_requests, rate=SERVE["rate"], seed=0)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        initial = dict(zip([r.rid for r in reqs], pool.map(_initial_conditions, reqs)))
+    srv = serve.Server(SERVE["budget"], max_slots=64, chunk_steps=SERVE["chunk"])
+    res = srv.run(reqs, realtime=True, initial=initial)
+    lat = serve.latency_percentiles(res)
+    offered = SERVE["rate"] * float(np.mean([r.n_side ** 3 * r.nsteps for r in reqs]))
+    return {"value": srv.stats["particle_steps"] / srv.stats["makespan"], "unit": "particle-steps/s",
+            "p50_s": lat["p50"], "p99_s": lat["p99"], "requests": n_requests,
+            "offered_particle_steps_per_s": offered, "makespan_s": srv.stats["makespan"],
+            "max_active": srv.stats["max_active"], "peak_arena_gb": srv.stats["peak_bytes"] / 2 ** 30,
+            "workload": SERVE["name"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,6 +487,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=60)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("steps >= 1, warmup >= 0")
