@@ -117,7 +117,7 @@ def zeldovich(n_part_side, n_mesh, box, a_init, seed, om=0.3, ol=0.7, h=0.7, m22
     for kc in (kx, ky, kz):
         psik = 1j * kc * dk / k2
         psik[0, 0, 0] = 0
-        psi.append(np.fft.irfftn(psik, s=(n, n, n)))
+        psi.append(np.fft.irfftn(psik, s=(n, n, n), axes=(0, 1, 2)))
     iz, iy, ix = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     q = np.stack([(ix * r + 0.5) * dxm, (iy * r + 0.5) * dxm, (iz * r + 0.5) * dxm], axis=-1).reshape(-1, 3)
     psi = np.stack([c.reshape(-1) for c in psi], axis=1)

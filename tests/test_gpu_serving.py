@@ -34,7 +34,8 @@ def test_served_results_equal_results_alone(mods):
         np.testing.assert_array_equal(out.x, x)
         np.testing.assert_array_equal(out.p, p)
         np.testing.assert_array_equal(out.energy, e)
-        np.testing.assert_array_equal(out.pk, pk)
+        # P(k) bins are summed with fp64 shared-memory atomics (order-dependent at 1 ulp)
+        np.testing.assert_allclose(out.pk, pk, rtol=1e-12)
         assert out.finished >= out.admitted >= 0.0
 
 
