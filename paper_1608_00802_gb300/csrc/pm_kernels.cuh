@@ -419,17 +419,18 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
-// fp32 compact-Laplacian stencil on shared-memory tiles.  A block of
-// ST_X x ST_TY threads owns a column of ST_X x ST_Y nodes (each thread two
-// rows, ST_Y = 2 ST_TY) and marches along z over one of ST_ZCH chunks of
-// planes, keeping s = sqrt(max(rho, floor)) of three planes (z-1, z, z+1, each
-// with a one-node halo in x and y) in a rolling shared-memory window; the
-// densities of plane z+2 are fetched into registers while plane z is
-// computed.  Each density is read about once from memory and its square root
-// taken about once.  Nodes with rho < rho_fp64 are collected in the block's
-// own region of `list` (shared-memory counter) and recomputed in float-float
-// by the same block after its sweep.
-constexpr int ST_X = 32, ST_TY = 8, ST_Y = 2 * ST_TY, ST_ZCH = 8;
+// fp32 compact-Laplacian stencil, register columns.  A block of 32 x ST_TY
+// threads (one warp per y-row of a 32-wide x strip) owns ST_TY rows and one
+// of ST_ZCH chunks of z.  Each thread marches its (x, y) column along z with
+// s = sqrt(max(rho, floor)) at z-1, z, z+1 in registers (the density of
+// plane z+2 is fetched while plane z is computed); x-neighbours come from
+// warp shuffles (the two edge lanes load theirs), y-neighbours from a
+// shared-memory copy of plane z (two warps also load the halo rows).  Each
+// density is read about once and its square root taken about once, at ~35
+// instructions per node.  Nodes with rho < rho_fp64 are collected in the
+// block's region of `list` (shared-memory counter) and recomputed in
+// float-float by the same block after its sweep.
+constexpr int ST_X = 32, ST_TY = 16, ST_Y = ST_TY, ST_ZCH = 8;
 
 __device__ __forceinline__ float s_of(float r, float fl) {
   const float x = fmaxf(r, fl);
@@ -455,75 +456,78 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
                                                                         float fl, float qc, float slim, int zlen,
                                                                         float* __restrict__ q, uint32_t* list,
                                                                         uint32_t* list_count, double* part) {
-  constexpr int HX = ST_X + 2, HY = ST_Y + 2, HALO = HX * HY, NT = ST_X * ST_TY;
-  constexpr int NPT = (HALO + NT - 1) / NT;
-  __shared__ float S[3][HY][HX];
+  __shared__ float S[ST_TY + 2][ST_X];  // s of plane z, rows y0-1 .. y0+ST_TY
   __shared__ uint32_t s_cnt;
-  const uint32_t n = uint32_t(m.n);
+  const int n = m.n;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ST_X + tx;
   const int x0 = blockIdx.x * ST_X, y0 = blockIdx.y * ST_Y;
-  const int z0 = blockIdx.z * zlen, z1 = min(z0 + zlen, int(n));
+  const int z0 = blockIdx.z * zlen, z1 = min(z0 + zlen, n);
   const uint32_t blin = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   uint32_t* my_list = list + size_t(blin) * (ST_X * ST_Y) * zlen;
   if (tid == 0) s_cnt = 0;
-  uint32_t hoff[NPT];
-  int hslot[NPT];
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    const int i = tid + j * NT;
-    hslot[j] = i < HALO ? i : -1;
-    const int hy = i / HX, hx = i - hy * HX;
-    hoff[j] = uint32_t(wrap(y0 + hy - 1, int(n))) * n + uint32_t(wrap(x0 + hx - 1, int(n)));
-  }
-  float pre[NPT];
-  auto fetch = [&](int z) {
-    const float* plane = rho + uint32_t(wrap(z, int(n))) * m.n2;
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) pre[j] = hslot[j] >= 0 ? __ldg(plane + hoff[j]) : 0.0f;
-  };
-  auto commit = [&](int slot) {
-    float* dst = &S[slot][0][0];
-#pragma unroll
-    for (int j = 0; j < NPT; ++j)
-      if (hslot[j] >= 0) dst[hslot[j]] = s_of(pre[j], fl);
-  };
-  fetch(z0 - 1);
-  commit(0);
-  fetch(z0);
-  commit(1);
-  fetch(z0 + 1);
-  const uint32_t gx = uint32_t(x0 + tx);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool live = x < n && y < n;
+  const int xc = min(x, n - 1), yc = min(y, n - 1);  // clamped: dead lanes read valid memory
+  const uint32_t col = uint32_t(yc) * n + uint32_t(xc);
+  // x-neighbours outside the warp's contiguous strip (edge lanes, or the periodic wrap)
+  const bool own_xm = tx == 0, own_xp = (tx == ST_X - 1) || (x + 1 >= n);
+  const uint32_t col_xm = uint32_t(yc) * n + uint32_t(wrap(xc - 1, n));
+  const uint32_t col_xp = uint32_t(yc) * n + uint32_t(wrap(xc + 1, n));
+  // warps 0 and 1 also carry the halo rows y0-1 and y0+ST_TY of the strip
+  const bool halo = ty < 2;
+  const int hy = ty == 0 ? wrap(y0 - 1, n) : wrap(min(y0 + ST_TY, n) % n, n);
+  const int hslot = ty == 0 ? 0 : (min(y0 + ST_TY, n) - y0 + 1);
+  const uint32_t col_h = uint32_t(hy) * n + uint32_t(xc);
+  auto plane = [&](int z) { return rho + uint32_t(wrap(z, n)) * m.n2; };
+  // column registers
+  float sm = s_of(__ldg(plane(z0 - 1) + col), fl);
+  float sc = s_of(__ldg(plane(z0) + col), fl);
+  float sp = s_of(__ldg(plane(z0 + 1) + col), fl);
+  float pre = __ldg(plane(z0 + 2) + col);
+  float exm = own_xm ? __ldg(plane(z0) + col_xm) : 0.0f, exp_ = own_xp ? __ldg(plane(z0) + col_xp) : 0.0f;
+  float eh = halo ? __ldg(plane(z0) + col_h) : 0.0f;
   float ksum = 0.0f;
-  int sm = 0, sc = 1, sp = 2;  // slots of planes z-1, z, z+1
   for (int z = z0; z < z1; ++z) {
-    commit(sp);  // plane z+1
-    if (z + 2 <= z1) fetch(z + 2);
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int ly = ty + r * ST_TY;
-      const uint32_t gy = uint32_t(y0 + ly);
-      if (gx < n && gy < n) {
-        const float s0 = S[sc][ly + 1][tx + 1];
-        const float dxp = S[sc][ly + 1][tx + 2] - s0, dxm = S[sc][ly + 1][tx] - s0;
-        const float dyp = S[sc][ly + 2][tx + 1] - s0, dym = S[sc][ly][tx + 1] - s0;
-        const float dzp = S[sp][ly + 1][tx + 1] - s0, dzm = S[sm][ly + 1][tx + 1] - s0;
-        const float lap = (dxp + dxm) + (dyp + dym) + (dzp + dzm);
-        const uint32_t node = uint32_t(z) * m.n2 + gy * n + gx;
-        q[node] = __fdividef(qc * lap, s0);
-        ksum += dxp * dxp + dyp * dyp + dzp * dzp;
-        if (s0 < slim) my_list[atomicAdd(&s_cnt, 1u)] = node;
-      }
+    // plane z into shared memory (own row and the halo rows; rows past the mesh
+    // do not write, their slot may be the halo slot)
+    if (y < n) S[ty + 1][tx] = sc;
+    if (halo) S[hslot][tx] = s_of(eh, fl);
+    const float sxm_e = s_of(exm, fl), sxp_e = s_of(exp_, fl);
+    // fetch for the next plane while this one is computed
+    const bool more = z + 1 < z1;
+    float exm_n = 0.0f, exp_n = 0.0f, eh_n = 0.0f, pre_n = 0.0f;
+    if (more) {
+      const float* pl = plane(z + 1);
+      if (own_xm) exm_n = __ldg(pl + col_xm);
+      if (own_xp) exp_n = __ldg(pl + col_xp);
+      if (halo) eh_n = __ldg(pl + col_h);
+      pre_n = __ldg(plane(z + 3) + col);
     }
-    __syncthreads();  // the slot of plane z-1 is refilled next
-    const int t = sm;
+    __syncthreads();
+    float sxm = __shfl_up_sync(0xffffffffu, sc, 1), sxp = __shfl_down_sync(0xffffffffu, sc, 1);
+    if (own_xm) sxm = sxm_e;
+    if (own_xp) sxp = sxp_e;
+    const float sym = S[ty][tx], syp = S[ty + 2][tx];
+    if (live) {
+      const float dxp = sxp - sc, dyp = syp - sc, dzp = sp - sc;
+      const float lap = (dxp + (sxm - sc)) + (dyp + (sym - sc)) + (dzp + (sm - sc));
+      const uint32_t node = uint32_t(z) * m.n2 + col;
+      q[node] = __fdividef(qc * lap, sc);
+      ksum += dxp * dxp + dyp * dyp + dzp * dzp;
+      if (sc < slim) my_list[atomicAdd(&s_cnt, 1u)] = node;
+    }
+    __syncthreads();  // S is rewritten next
     sm = sc;
     sc = sp;
-    sp = t;
+    sp = s_of(pre, fl);
+    pre = pre_n;
+    exm = exm_n;
+    exp_ = exp_n;
+    eh = eh_n;
   }
   // near-empty nodes of this block, recomputed in float-float
   const uint32_t cnt = s_cnt;
-  for (uint32_t i = tid; i < cnt; i += NT) {
+  for (uint32_t i = tid; i < cnt; i += ST_X * ST_TY) {
     const uint32_t node = my_list[i];
     q[node] = q_ext_at(rho, node, m, fl, qc);
   }
@@ -620,8 +624,10 @@ __device__ __forceinline__ int carry(R& o) {
   return c;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
+// MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync; 2: write
+// the accelerations only.  Separate instantiations keep the common pass lean.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(KICK_THREADS, 4) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
                                                        uint32_t* keys, int64_t n, const R* __restrict__ phi,
                                                        const R* __restrict__ qf, Mesh m, KickParams kp_arg,
                                                        const KickParams* __restrict__ kp_tab,
@@ -661,14 +667,14 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, 
     }
     const R cg1 = R(kp.cg1), cq1 = R(kp.cq1);
     R d1[3] = {cg1 * gp[0] + cq1 * gq[0], cg1 * gp[1] + cq1 * gq[1], cg1 * gp[2] + cq1 * gq[2]};
-    if (kp.accel_out) {
+    if (MODE == 2) {
       const uint32_t id = rec_id(mo);
       acc_out[3 * size_t(id) + 0] = -double(d1[0]);
       acc_out[3 * size_t(id) + 1] = -double(d1[1]);
       acc_out[3 * size_t(id) + 2] = -double(d1[2]);
     } else {
       R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
-      if (kp.diag) {
+      if (MODE == 1) {
         dg[0] = px * px + py * py + pz * pz;
         dg[1] = px;
         dg[2] = py;
@@ -707,7 +713,7 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(typename VT<R>::v4* pos, 
       keys[i] = ncell;
     }
   }
-  if (kp.diag) block_sum_store<4>(dg, part, gridDim.x);
+  if (MODE == 1) block_sum_store<4>(dg, part, gridDim.x);
 }
 
 // ---------------------------------------------------------------- power spectrum
@@ -866,8 +872,13 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R
                         uint32_t* err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   using V4 = typename VT<R>::v4;
-  k_kick<R><<<kick_blocks(n), KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part,
-                                                    acc, err);
+  const unsigned g = kick_blocks(n);
+  if (kp.accel_out)
+    k_kick<R, 2><<<g, KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+  else if (kp.diag)
+    k_kick<R, 1><<<g, KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+  else
+    k_kick<R, 0><<<g, KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   return cudaGetLastError();
 }
 

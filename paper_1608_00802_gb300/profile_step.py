@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--mode", choices=["meshgrad", "hybrid", "lagrangian"], default="hybrid")
+    ap.add_argument("--rho-fp64", type=float, default=1e-2,
+                    help="density below which Q is recomputed in extended precision (0: never)")
     args = ap.parse_args()
     import torch
 
@@ -35,7 +37,7 @@ def main():
     a0, a1 = 1 / 101.0, 1 / 4.0
     x, p = ics.zeldovich(args.n_side, args.n_mesh, args.box, a0, 42, m22=args.m22)
     cfg = pm.make_config(len(x), args.n_mesh, args.box, m22=args.m22, force_mode=modes[args.mode],
-                         precision=pm.FP64 if args.precision == "fp64" else pm.FP32)
+                         precision=pm.FP64 if args.precision == "fp64" else pm.FP32, rho_fp64=args.rho_fp64)
     sim = pm.Sim(cfg)
     sim.set_particles(x, p)
     sim.profile_begin(64 * (args.steps + 1))
