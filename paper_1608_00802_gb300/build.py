@@ -38,6 +38,11 @@ def _run(cmd):
 
 
 def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
+    """Compiles libpm.so if a source is newer than it (or `force`).  Extra nvcc
+    flags may also come from the PM_EXTRA_NVCC_FLAGS environment variable
+    (space separated, e.g. -DPM_ST_PF=6); they always force a rebuild."""
+    env_flags = tuple(os.environ.get("PM_EXTRA_NVCC_FLAGS", "").split())
+    extra_flags = tuple(extra_flags) + env_flags
     home = cuda_home()
     nvcc = os.path.join(home, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)

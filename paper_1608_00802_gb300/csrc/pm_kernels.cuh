@@ -430,7 +430,13 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
 // instructions per node.  Nodes with rho < rho_fp64 are collected in the
 // block's region of `list` (shared-memory counter) and recomputed in
 // float-float by the same block after its sweep.
-constexpr int ST_X = 32, ST_TY = 16, ST_Y = ST_TY, ST_ZCH = 8;
+#ifndef PM_ST_TY
+#define PM_ST_TY 16
+#endif
+#ifndef PM_ST_ZCH
+#define PM_ST_ZCH 8
+#endif
+constexpr int ST_X = 32, ST_TY = PM_ST_TY, ST_Y = ST_TY, ST_ZCH = PM_ST_ZCH;
 
 __device__ __forceinline__ float s_of(float r, float fl) {
   const float x = fmaxf(r, fl);
