@@ -340,3 +340,31 @@ def test_invalid_arguments_are_reported(pm):
     x = np.full((10, 3), np.nan)
     with pytest.raises(pm.PMError):
         sim.set_particles(x, np.zeros((10, 3)))
+
+
+# ------------------------------------------------------------------ largest configuration
+def test_largest_configuration_256_on_512(pm):
+    """256^3 particles on a 512^3 mesh, L = 10 Mpc/h, m22 = 1 (the largest
+    single-simulation workload), fp32, hybrid force, in the launch shapes of
+    the bench: bit-exact keys and order, full-mesh density, and the
+    accelerations of 20,000 sampled particles (the oracle computes the mesh
+    fields in full and interpolates at the sample only)."""
+    n_side, n_mesh, box, m22 = 256, 512, 10.0, 1.0
+    sim, ocfg = make(pm, n_side, n_mesh, box, "fp32", m22=m22, mode="hybrid")
+    xg, _ = sim.get_particles()
+    cell, ids = sim.get_order()
+    keys, order = oracle_order(xg, ocfg, np.arange(len(xg)))
+    np.testing.assert_array_equal(ids, order)
+    np.testing.assert_array_equal(cell, keys[order])
+    del cell, ids, keys, order
+    a = 1 / 101.0
+    acc = sim.forces(a)
+    rho = sim.get_field(pm.FIELD_RHO)
+    ref = O.cic_deposit(xg, ocfg)
+    assert np.abs(rho - ref).max() < 2e-6 * np.abs(ref).max()
+    fields = (ref, O.poisson_phi(ref, ocfg), O.quantum_potential(ref, ocfg))
+    del rho
+    sample = np.random.default_rng(7).choice(len(xg), 20000, replace=False)
+    gphi, gq = O.force_parts(xg[sample], ocfg, fields=fields)
+    ref_acc = gphi / a + gq / (a * a)
+    assert rel_rms(acc[sample], ref_acc) < 1e-5
