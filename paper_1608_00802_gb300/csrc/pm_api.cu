@@ -89,7 +89,7 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
   size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, status, st_list, st_count, part,
-      part_aux, red, err, total;
+      part_aux, red, err, ktab, total;
   int key_bits, passes, digit_bits, ntiles;
 };
 
@@ -177,6 +177,7 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   L.part_aux = take(2 * aux * 8);
   L.red = take(3 * PK_MAX_BINS * 8 + 64);
   L.err = take(256);
+  L.ktab = take(size_t(PM_RUN_GRAPH_MAX_STEPS) * sizeof(KickParams));
   L.total = off;
   return L;
 }
@@ -227,6 +228,9 @@ struct pm_sim {
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_stage;
   size_t prof_used = 0;
+  // pm_run replays captured steps on its own stream, joined to `stream` by events
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
   template <typename T>
   T* at(size_t off) const {
@@ -494,6 +498,19 @@ KickParams step_params(const pm_sim* s, int i, int nsteps, double a_start, doubl
   return kp;
 }
 
+// one captured step: table-driven kick + drift, then steps (i)-(iii), then the
+// device step counter advances
+pm_status table_step(pm_sim* s, const KickParams* tab, uint32_t* step) {
+  KickParams kp = base_kick(s);
+  kp.drift = 1.0;  // host-side marker only: the positions move, the weights come from the table
+  pm_status st = DISPATCH(s, kick, s, kp, nullptr, tab, step);
+  if (st != PM_OK) return st;
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  CU(s, launch_step_inc(step, s->stream));
+  return PM_OK;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -598,6 +615,12 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
 pm_status pm_destroy(pm_sim* s) {
   if (!s) return PM_ERR_INVALID_ARG;
   cudaStreamSynchronize(s->stream);
+  if (s->cap) {
+    cudaStreamSynchronize(s->cap);
+    cudaStreamDestroy(s->cap);
+    cudaEventDestroy(s->ev_in);
+    cudaEventDestroy(s->ev_out);
+  }
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   cufftDestroy(s->plan_fwd);
   cufftDestroy(s->plan_inv);
@@ -689,12 +712,54 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
   st = ensure_fields(s);
   if (st != PM_OK) return st;
   Weights pending = {0.0, 0.0};  // closing half kick of the previous step
-  for (int i = 0; i < nsteps; ++i) {
-    const KickParams kp = step_params(s, i, nsteps, a_start, a_end, &pending);
-    st = DISPATCH(s, kick, s, kp, nullptr);
+  if (nsteps >= 4 && nsteps <= PM_RUN_GRAPH_MAX_STEPS && !s->prof_on) {
+    // two steps captured as a CUDA graph and replayed: the weights of every
+    // step come from a device table indexed by a device step counter
+    std::vector<KickParams> tab(nsteps);
+    for (int i = 0; i < nsteps; ++i) tab[i] = step_params(s, i, nsteps, a_start, a_end, &pending);
+    KickParams* tab_dev = s->at<KickParams>(s->L.ktab);
+    uint32_t* step_dev = s->errword() + 2;
+    CU(s, cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(KickParams), cudaMemcpyHostToDevice, s->stream));
+    CU(s, cudaMemsetAsync(step_dev, 0, sizeof(uint32_t), s->stream));
+    if (!s->cap) {
+      CU(s, cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+      CU(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+      CU(s, cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+    }
+    CU(s, cudaEventRecord(s->ev_in, s->stream));
+    CU(s, cudaStreamWaitEvent(s->cap, s->ev_in, 0));
+    cudaStream_t user = s->stream;
+    s->stream = s->cap;
+    CF(s, cufftSetStream(s->plan_fwd, s->cap));
+    CF(s, cufftSetStream(s->plan_inv, s->cap));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ec = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeGlobal);
+    if (ec == cudaSuccess) {
+      for (int r = 0; r < 2 && st == PM_OK; ++r) st = table_step(s, tab_dev, step_dev);
+      cudaError_t ee = cudaStreamEndCapture(s->cap, &graph);
+      if (st == PM_OK && ee != cudaSuccess) ec = ee;
+    }
+    if (ec == cudaSuccess && st == PM_OK) ec = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (int k = 0; ec == cudaSuccess && st == PM_OK && k < nsteps / 2; ++k) ec = cudaGraphLaunch(exec, s->cap);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ec == cudaSuccess && st == PM_OK && (nsteps & 1)) st = table_step(s, tab_dev, step_dev);
+    s->stream = user;
+    cufftSetStream(s->plan_fwd, user);
+    cufftSetStream(s->plan_inv, user);
     if (st != PM_OK) return st;
-    st = ensure_fields(s);
-    if (st != PM_OK) return st;
+    if (ec != cudaSuccess) return fail(s, PM_ERR_CUDA, "captured steps: %s", cudaGetErrorString(ec));
+    CU(s, cudaEventRecord(s->ev_out, s->cap));
+    CU(s, cudaStreamWaitEvent(s->stream, s->ev_out, 0));
+  } else {
+    for (int i = 0; i < nsteps; ++i) {
+      const KickParams kp = step_params(s, i, nsteps, a_start, a_end, &pending);
+      st = DISPATCH(s, kick, s, kp, nullptr);
+      if (st != PM_OK) return st;
+      st = ensure_fields(s);
+      if (st != PM_OK) return st;
+    }
   }
   return pass(s, pending, Weights{0.0, 0.0}, 0.0, true);
 }
@@ -908,17 +973,6 @@ bool batch_layout(const pm_config* cfgs, int n, BatchLayout* L, std::string* why
   return true;
 }
 
-// member i's part of a captured step: table-driven kick + drift, then steps (i)-(iii)
-pm_status batch_member_step(pm_sim* s, const KickParams* tab, uint32_t* step) {
-  KickParams kp = base_kick(s);
-  kp.drift = 1.0;  // host-side marker only: the positions move, the weights come from the table
-  pm_status st = DISPATCH(s, kick, s, kp, nullptr, tab, step);
-  if (st != PM_OK) return st;
-  st = ensure_fields(s);
-  if (st != PM_OK) return st;
-  CU(s, launch_step_inc(step, s->stream));
-  return PM_OK;
-}
 
 }  // namespace
 
@@ -1058,7 +1112,7 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     for (int i = 0; i < n && st == PM_OK; ++i) {
       pm_sim* s = b->sims[i];
       if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) st = PM_ERR_CUDA;
-      for (int r = 0; r < 2 && st == PM_OK; ++r) st = batch_member_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i);
+      for (int r = 0; r < 2 && st == PM_OK; ++r) st = table_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i);
       if (st == PM_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) st = PM_ERR_CUDA;
       if (st == PM_OK && cudaStreamWaitEvent(b->cap, b->join[i], 0) != cudaSuccess) st = PM_ERR_CUDA;
       if (st != PM_OK) b->err = "capture of member " + std::to_string(i) + " failed: " + s->err;
@@ -1085,7 +1139,7 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     pm_sim* s = b->sims[i];
     BCU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
     if (nsteps & 1) {
-      if (batch_member_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i) != PM_OK) return member_error(i);
+      if (table_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i) != PM_OK) return member_error(i);
     }
     if (pass(s, closing[i], Weights{0.0, 0.0}, 0.0, true) != PM_OK) return member_error(i);
     BCU(cudaEventRecord(b->join[i], b->streams[i]));
