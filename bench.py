@@ -457,7 +457,7 @@ def run_batched(pm, ics, K, W, stream):
 
 SERVE = dict(name="Poisson arrivals 20 req/s, particles {32,64,128,192}^3 (weights .4/.3/.2/.1), mesh 2x, "
                    "m22 log-uniform 1-10, L ~ U(1,4), z=50->5 in 200 steps, fp32, hybrid force, HBM budget 64 GB",
-             rate=20.0, budget=64 << 30, chunk=10)
+             rate=20.0, budget=64 << 30, chunk=20)
 
 
 def _initial_conditions(req):

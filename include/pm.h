@@ -134,9 +134,10 @@ pm_status pm_step(pm_sim* sim, double a0, double a1);
 /* nsteps leapfrog steps from a_start to a_end, uniform in ln a (in t for static
  * runs), with the closing half kick of each step merged into the opening half
  * kick of the next; momenta are synchronised at a_end.  For
- * 4 <= nsteps <= PM_RUN_GRAPH_MAX_STEPS (and the profiler off) two steps are
- * captured once as a CUDA graph on an internal stream (joined to the
- * simulation's stream by events) and replayed.  Async. */
+ * 2 <= nsteps <= PM_RUN_GRAPH_MAX_STEPS (and the profiler off) two steps run as
+ * one CUDA graph on an internal stream (joined to the simulation's stream by
+ * events); the graphs are captured at the first such call and kept until
+ * pm_destroy.  Async. */
 #define PM_RUN_GRAPH_MAX_STEPS 4096
 pm_status pm_run(pm_sim* sim, int32_t nsteps, double a_start, double a_end);
 

@@ -231,6 +231,19 @@ struct pm_sim {
   // pm_run replays captured steps on its own stream, joined to `stream` by events
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // pinned staging of the kick table (a pageable source would serialise the
+  // host with this stream); ev_tab marks the end of the last upload
+  KickParams* tab_host = nullptr;
+  cudaEvent_t ev_tab = nullptr;
+  bool tab_pending = false;
+  // captured two-step graphs, one per entry state of the record buffers
+  // (cur, sorted-key buffer); every pointer they hold is fixed for the
+  // simulation's lifetime, so they are kept until pm_destroy
+  struct RunGraph {
+    int cur = -1;
+    const uint32_t* keys = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } run_graph[2];
 
   template <typename T>
   T* at(size_t off) const {
@@ -620,7 +633,11 @@ pm_status pm_destroy(pm_sim* s) {
     cudaStreamDestroy(s->cap);
     cudaEventDestroy(s->ev_in);
     cudaEventDestroy(s->ev_out);
+    cudaEventDestroy(s->ev_tab);
+    cudaFreeHost(s->tab_host);
   }
+  for (auto& g : s->run_graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   cufftDestroy(s->plan_fwd);
   cufftDestroy(s->plan_inv);
@@ -712,44 +729,76 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
   st = ensure_fields(s);
   if (st != PM_OK) return st;
   Weights pending = {0.0, 0.0};  // closing half kick of the previous step
-  if (nsteps >= 4 && nsteps <= PM_RUN_GRAPH_MAX_STEPS && !s->prof_on) {
+  if (nsteps >= 2 && nsteps <= PM_RUN_GRAPH_MAX_STEPS && !s->prof_on) {
     // two steps captured as a CUDA graph and replayed: the weights of every
     // step come from a device table indexed by a device step counter
-    std::vector<KickParams> tab(nsteps);
-    for (int i = 0; i < nsteps; ++i) tab[i] = step_params(s, i, nsteps, a_start, a_end, &pending);
-    KickParams* tab_dev = s->at<KickParams>(s->L.ktab);
-    uint32_t* step_dev = s->errword() + 2;
-    CU(s, cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(KickParams), cudaMemcpyHostToDevice, s->stream));
-    CU(s, cudaMemsetAsync(step_dev, 0, sizeof(uint32_t), s->stream));
     if (!s->cap) {
       CU(s, cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
       CU(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
       CU(s, cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+      CU(s, cudaEventCreateWithFlags(&s->ev_tab, cudaEventDisableTiming));
+      CU(s, cudaMallocHost(&s->tab_host, size_t(PM_RUN_GRAPH_MAX_STEPS) * sizeof(KickParams)));
     }
+    if (s->tab_pending) CU(s, cudaEventSynchronize(s->ev_tab));  // the previous upload has left the buffer
+    for (int i = 0; i < nsteps; ++i) s->tab_host[i] = step_params(s, i, nsteps, a_start, a_end, &pending);
+    KickParams* tab_dev = s->at<KickParams>(s->L.ktab);
+    uint32_t* step_dev = s->errword() + 2;
+    CU(s, cudaMemcpyAsync(tab_dev, s->tab_host, size_t(nsteps) * sizeof(KickParams), cudaMemcpyHostToDevice,
+                          s->stream));
+    CU(s, cudaEventRecord(s->ev_tab, s->stream));
+    s->tab_pending = true;
+    CU(s, cudaMemsetAsync(step_dev, 0, sizeof(uint32_t), s->stream));
     CU(s, cudaEventRecord(s->ev_in, s->stream));
     CU(s, cudaStreamWaitEvent(s->cap, s->ev_in, 0));
     cudaStream_t user = s->stream;
     s->stream = s->cap;
     CF(s, cufftSetStream(s->plan_fwd, s->cap));
     CF(s, cufftSetStream(s->plan_inv, s->cap));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaError_t ec = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeGlobal);
-    if (ec == cudaSuccess) {
-      for (int r = 0; r < 2 && st == PM_OK; ++r) st = table_step(s, tab_dev, step_dev);
-      cudaError_t ee = cudaStreamEndCapture(s->cap, &graph);
-      if (st == PM_OK && ee != cudaSuccess) ec = ee;
+    // graphs for the present state and for the other record buffer (the state
+    // after an odd number of steps); capturing executes nothing, so the host
+    // state is flipped for the second capture and restored
+    cudaError_t ec = cudaSuccess;
+    const int cur0 = s->cur;
+    for (int v = 0; v < 2 && ec == cudaSuccess && st == PM_OK; ++v) {
+      const int want = v == 0 ? cur0 : 1 - cur0;
+      if (v == 1 && s->L.passes < 2) break;  // a single sort pass also swaps the key buffers
+      bool have = false;
+      for (auto& g : s->run_graph) have |= g.exec && g.cur == want && g.keys == s->keys;
+      if (have) continue;
+      auto& slot = s->run_graph[want];
+      if (slot.exec) cudaGraphExecDestroy(slot.exec);
+      slot = pm_sim::RunGraph();
+      s->cur = want;
+      const bool sorted0 = s->sorted, fields0 = s->fields_valid;
+      cudaGraph_t graph = nullptr;
+      ec = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+      if (ec == cudaSuccess) {
+        for (int r = 0; r < 2 && st == PM_OK; ++r) st = table_step(s, tab_dev, step_dev);
+        cudaError_t ee = cudaStreamEndCapture(s->cap, &graph);
+        if (st == PM_OK && ee != cudaSuccess) ec = ee;
+      }
+      if (ec == cudaSuccess && st == PM_OK) ec = cudaGraphInstantiate(&slot.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (ec == cudaSuccess && st == PM_OK) {
+        slot.cur = want;
+        slot.keys = s->keys;
+      }
+      s->cur = cur0;
+      s->sorted = sorted0;
+      s->fields_valid = fields0;
     }
-    if (ec == cudaSuccess && st == PM_OK) ec = cudaGraphInstantiate(&exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : s->run_graph)
+      if (g.exec && g.cur == s->cur && g.keys == s->keys) exec = g.exec;
+    if (!exec && ec == cudaSuccess && st == PM_OK) ec = cudaErrorUnknown;
     for (int k = 0; ec == cudaSuccess && st == PM_OK && k < nsteps / 2; ++k) ec = cudaGraphLaunch(exec, s->cap);
-    if (exec) cudaGraphExecDestroy(exec);
     if (ec == cudaSuccess && st == PM_OK && (nsteps & 1)) st = table_step(s, tab_dev, step_dev);
     s->stream = user;
     cufftSetStream(s->plan_fwd, user);
     cufftSetStream(s->plan_inv, user);
     if (st != PM_OK) return st;
     if (ec != cudaSuccess) return fail(s, PM_ERR_CUDA, "captured steps: %s", cudaGetErrorString(ec));
+    // the replays leave the state as it was before them (two sorts per graph)
     CU(s, cudaEventRecord(s->ev_out, s->cap));
     CU(s, cudaStreamWaitEvent(s->stream, s->ev_out, 0));
   } else {
@@ -1106,7 +1155,7 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     // capture two steps of every member (the record buffers alternate each step)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeGlobal));
+    BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     pm_status st = PM_OK;
     if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) st = PM_ERR_CUDA;
     for (int i = 0; i < n && st == PM_OK; ++i) {

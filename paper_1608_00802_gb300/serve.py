@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import math
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -97,15 +98,20 @@ class Server:
     """Admits requests under an HBM budget and steps the admitted simulations
     together; `run` returns one Result per request."""
 
-    def __init__(self, hbm_budget_bytes, max_slots=64, chunk_steps=10, keep_particles=False, device="cuda"):
+    def __init__(self, hbm_budget_bytes, max_slots=64, chunk_steps=20, keep_particles=False, device="cuda",
+                 admit_threads=4):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
         self.max_slots = int(max_slots)
         self.chunk = int(chunk_steps)
         self.keep_particles = keep_particles
-        self.device = torch.device(device)
+        dev = torch.device(device)
+        self.device = dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
         self.in_use = 0
+        # admissions (arena, plans, upload and first sort) run on worker threads so that the
+        # loop keeps feeding the running simulations meanwhile
+        self.admit_threads = int(admit_threads)
         self.stats = {"admitted": 0, "max_active": 0, "chunks": 0, "particle_steps": 0, "peak_bytes": 0}
 
     def _bytes(self, req):
@@ -113,6 +119,7 @@ class Server:
 
     def _admit(self, req, now, initial=None):
         torch = self.torch
+        torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(device=self.device)
         sim = pm.Sim(req.config(), device=self.device, stream=stream)
         x, p = initial if initial is not None else initial_conditions(req)
@@ -140,7 +147,9 @@ class Server:
             if sizes[r.rid] > self.budget:
                 raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, sizes[r.rid]))
         waiting = []            # arrived, not admitted (FIFO)
+        admitting = []          # admissions in flight on the worker threads
         active = []
+        pool = ThreadPoolExecutor(max(1, self.admit_threads))
         results = {}
         t0 = time.perf_counter()
         i = 0
@@ -148,39 +157,49 @@ class Server:
         def now():
             return time.perf_counter() - t0
 
-        while i < len(pending) or waiting or active:
+        while i < len(pending) or waiting or admitting or active:
             t = now()
             while i < len(pending) and (not realtime or pending[i].arrival <= t):
                 waiting.append(pending[i])
                 i += 1
             # admission: FIFO while memory and slots allow
-            while waiting and len(active) < self.max_slots and self.in_use + sizes[waiting[0].rid] <= self.budget:
+            while (waiting and len(active) + len(admitting) < self.max_slots
+                   and self.in_use + sizes[waiting[0].rid] <= self.budget):
                 req = waiting.pop(0)
                 self.in_use += sizes[req.rid]
-                active.append(self._admit(req, now(), None if initial is None else initial.get(req.rid)))
+                admitting.append(pool.submit(self._admit, req, now(),
+                                             None if initial is None else initial.get(req.rid)))
                 self.stats["admitted"] += 1
+            ready = [f for f in admitting if f.done()]
+            admitting = [f for f in admitting if not f.done()]
+            active.extend(f.result() for f in ready)
             self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self.in_use)
             self.stats["max_active"] = max(self.stats["max_active"], len(active))
             if not active:
+                if admitting:
+                    time.sleep(0.0005)
+                    continue
                 if i < len(pending):
                     time.sleep(max(0.0, min(0.01, pending[i].arrival - now())))
                 continue
-            # one chunk of steps for every active simulation, each on its own stream
-            for act in active:
-                k1 = min(act.req.nsteps, act.done_steps + self.chunk)
-                a0, a1 = self._schedule(act.req, act.done_steps, k1)
-                act.sim.run(k1 - act.done_steps, a0, a1)
-                self.stats["particle_steps"] += act.req.n_side ** 3 * (k1 - act.done_steps)
-                act.done_steps = k1
-                act.event = torch.cuda.Event()
-                act.event.record(act.stream)
-            self.stats["chunks"] += 1
-            for act in active:
-                act.event.synchronize()
-            # retire finished simulations
+            # every simulation whose last chunk has finished gets its next chunk (on
+            # its own stream) or is retired; the others keep running meanwhile
+            progressed = False
             still = []
             for act in active:
+                if act.event is not None and not act.event.query():
+                    still.append(act)
+                    continue
+                progressed = True
                 if act.done_steps < act.req.nsteps:
+                    k1 = min(act.req.nsteps, act.done_steps + self.chunk)
+                    a0, a1 = self._schedule(act.req, act.done_steps, k1)
+                    act.sim.run(k1 - act.done_steps, a0, a1)
+                    self.stats["particle_steps"] += act.req.n_side ** 3 * (k1 - act.done_steps)
+                    self.stats["chunks"] += 1
+                    act.done_steps = k1
+                    act.event = torch.cuda.Event()
+                    act.event.record(act.stream)
                     still.append(act)
                     continue
                 e = act.sim.energy(act.req.a_end)
@@ -194,6 +213,9 @@ class Server:
                 del act.sim
                 self.in_use -= sizes[act.req.rid]
             active = still
+            if not progressed:
+                time.sleep(0.0002)
+        pool.shutdown()
         self.stats["makespan"] = now()
         return [results[r.rid] for r in sorted(requests, key=lambda r: r.rid)]
 
