@@ -61,9 +61,13 @@ def algorithmic_bytes(stage, n, n_mesh, rsz=4):
         "green": 2 * spec,
         "fft_r2c": n3 * rsz + spec,
         "fft_c2r": spec + n3 * rsz,
-        # keys read once for all histograms; per pass keys + values read and written
-        "sort_histogram": n * 4,
-        "sort_pass": n * 16,
+        # re-sort after a drift: keys read twice (count, scatter), stayer keys + previous slots written
+        "sort_partition": n * 16,
+        # stayers (key, slot) read, sorted keys written, records gathered (read) and written
+        "sort_merge": n * (8 + 4 + 4 * rec),
+        # the histogram and radix passes see only the movers, a data-dependent count
+        "sort_histogram": None,
+        "sort_pass": None,
         "row_start": n * 4 + n_mesh * n_mesh * 4,
     }.get(stage)
 
@@ -325,13 +329,14 @@ def run_gpu(args):
         avg = ms / cnt
         per_stage[name] = {"ms_per_step": ms / K, "launches": cnt, "avg_launch_ms": avg,
                            "GBps": (b / (avg / 1e3) / 1e9) if b else None}
-    ours = {k: v for k, v in per_stage.items() if k not in pm.CUFFT_STAGES}
+    ours = {k: v for k, v in per_stage.items() if k not in pm.CUFFT_STAGES and v["GBps"] is not None}
     dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
     d = per_stage[dom]
     achieved = d["GBps"]
     kernel_names = {"kick": "k_kick", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
                     "sort_pass": "k_sort_pass", "sort_histogram": "k_sort_histogram",
-                    "row_start": "k_row_start"}
+                    "row_start": "k_row_start", "sort_partition": "k_mover_scatter",
+                    "sort_merge": "k_merge_gather"}
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": ncu_traffic(kernel_names.get(dom, dom), "c2"), "peak_source": peak_kind,

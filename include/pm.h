@@ -171,7 +171,7 @@ pm_status pm_get_order(pm_sim* sim, uint32_t* cell, uint32_t* id);
 enum {
   PM_STAGE_SORT_HISTOGRAM = 0, PM_STAGE_SORT_PASS = 1, PM_STAGE_ROW_START = 2, PM_STAGE_DEPOSIT = 3,
   PM_STAGE_FFT_R2C = 4, PM_STAGE_GREEN = 5, PM_STAGE_FFT_C2R = 6, PM_STAGE_STENCIL = 7, PM_STAGE_KICK = 8,
-  PM_STAGE_OTHER = 9, PM_NSTAGES = 10
+  PM_STAGE_SORT_PARTITION = 9, PM_STAGE_SORT_MERGE = 10, PM_STAGE_OTHER = 11, PM_NSTAGES = 12
 };
 
 /* Starts recording a CUDA-event pair around every launch of this handle, for

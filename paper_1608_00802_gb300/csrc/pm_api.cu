@@ -88,8 +88,8 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[3], vals[2], row_start, rho, phi, q, spec, work, staging, hist, status, st_list, st_count, part,
-      part_aux, red, err, ktab, total;
+  size_t pos[2], mom[2], keys[4], vals[3], tile_cnt, row_start, rho, phi, q, spec, work, staging, hist, status,
+      st_list, st_count, part, part_aux, red, err, ktab, total;
   int key_bits, passes, digit_bits, ntiles;
 };
 
@@ -153,8 +153,9 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   };
   for (int k = 0; k < 2; ++k) L.pos[k] = take(n * recsz);
   for (int k = 0; k < 2; ++k) L.mom[k] = take(n * recsz);
-  for (int k = 0; k < 3; ++k) L.keys[k] = take(n * 4);
-  for (int k = 0; k < 2; ++k) L.vals[k] = take(n * 4);
+  for (int k = 0; k < 4; ++k) L.keys[k] = take(n * 4);
+  for (int k = 0; k < 3; ++k) L.vals[k] = take(n * 4);
+  L.tile_cnt = take((size_t(L.ntiles) + 2) * 4);  // movers per tile, then (stayers, movers)
   L.row_start = take((N * N + 1) * 4);
   L.rho = take(n3 * rsz);
   L.phi = take(n3 * rsz);
@@ -220,6 +221,7 @@ struct pm_sim {
   int cur;  // which of pos[2]/mom[2] holds the state
   uint32_t* keys;  // sorted (current) keys
   uint32_t* keys_tmp[2];
+  bool keys_marked = false;  // a drift has flagged the movers in `keys` since the last sort
   cufftHandle plan_fwd, plan_inv;
   bool have_particles, sorted, fields_valid;
   std::string err;
@@ -315,8 +317,62 @@ int kr_blocks(const pm_sim* s) {
   return tiled ? stencil_block_count(s->cfg.n_mesh) : MESH_GRID;
 }
 
+// Incremental re-sort after a drift: the stayers are still in order, so the
+// movers are split off (stable partition), radix-sorted by (key, previous
+// slot) with their count known only on the device, and merged back; the merge
+// gathers the records into the other buffer.  Same order as the full sort.
+template <typename R>
+pm_status resort_movers(pm_sim* s) {
+  const Layout& L = s->L;
+  const int64_t n = s->n();
+  uint32_t* hist = s->at<uint32_t>(L.hist);
+  uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
+  uint64_t* status = s->at<uint64_t>(L.status);
+  uint32_t* tcnt = s->at<uint32_t>(L.tile_cnt);
+  uint32_t* counts = tcnt + L.ntiles;
+  uint32_t* sk = s->keys_tmp[0];
+  uint32_t* sv = s->at<uint32_t>(L.vals[0]);
+  uint32_t* mk[2] = {s->keys_tmp[1], s->at<uint32_t>(L.keys[3])};
+  uint32_t* mv[2] = {s->at<uint32_t>(L.vals[1]), s->at<uint32_t>(L.vals[2])};
+  CU(s, cudaMemsetAsync(hist, 0, (3 * (size_t(1) << RS_MAX_BITS) + 4) * 4, s->stream));
+  {
+    PROF(s, PM_STAGE_SORT_PARTITION);
+    CU(s, launch_mover_partition(s->keys, n, tcnt, counts, sk, sv, mk[0], mv[0], s->stream));
+  }
+  {
+    PROF(s, PM_STAGE_SORT_HISTOGRAM);
+    CU(s, launch_sort_histogram(mk[0], n, L.passes, L.digit_bits, L.key_bits, hist, s->errword() + 1, s->stream,
+                                counts + 1));
+  }
+  int b = 0;
+  for (int p = 0; p < L.passes; ++p) {
+    const int shift = p * L.digit_bits;
+    const int bits = (shift + L.digit_bits <= L.key_bits) ? L.digit_bits : (L.key_bits - shift);
+    PROF(s, PM_STAGE_SORT_PASS);
+    CU(s, launch_sort_pass<R>(false, mk[b], mv[b], n, shift, bits, hist + p * (1 << RS_MAX_BITS), status,
+                              counters + p, s->errword() + 1, p, L.ntiles, mk[b ^ 1], mv[b ^ 1], nullptr, nullptr,
+                              nullptr, nullptr, s->errword(), s->stream, counts + 1));
+    b ^= 1;
+  }
+  const int nxt = s->cur ^ 1;
+  {
+    PROF(s, PM_STAGE_SORT_MERGE);
+    CU(s, launch_merge_gather<R>(sk, sv, mk[b], mv[b], counts, n, s->keys, s->pos(), s->mom(),
+                                 s->arena + L.pos[nxt], s->arena + L.mom[nxt], s->stream));
+  }
+  s->cur = nxt;
+  s->keys_marked = false;
+  {
+    PROF(s, PM_STAGE_ROW_START);
+    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->stream));
+  }
+  s->sorted = true;
+  return PM_OK;
+}
+
 template <typename R>
 pm_status sort_particles(pm_sim* s) {
+  if (s->keys_marked) return resort_movers<R>(s);
   const Layout& L = s->L;
   const int64_t n = s->n();
   uint32_t* hist = s->at<uint32_t>(L.hist);
@@ -441,6 +497,10 @@ template <typename R>
 pm_status kick(pm_sim* s, const KickParams& kp, double* acc, const KickParams* kp_tab = nullptr,
                const uint32_t* step = nullptr) {
   const Layout& L = s->L;
+  if (kp.drift != 0.0 && !s->sorted) {  // movers are marked against the sorted cells
+    pm_status st = sort_particles<R>(s);
+    if (st != PM_OK) return st;
+  }
   {
     PROF(s, PM_STAGE_KICK);
     CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, kp_tab,
@@ -449,6 +509,7 @@ pm_status kick(pm_sim* s, const KickParams& kp, double* acc, const KickParams* k
   if (kp.drift != 0.0) {
     s->sorted = false;
     s->fields_valid = false;
+    s->keys_marked = true;
   }
   return PM_OK;
 }
@@ -657,7 +718,7 @@ pm_status pm_set_particles(pm_sim* s, const double* x, const double* p) {
   CU(s, DISPATCH(s, launch_init_particles, dx, dp, s->n(), s->mesh, 1.0 / s->dx, s->pos(), s->mom(), s->keys,
                  s->errword(), s->stream));
   s->have_particles = true;
-  s->sorted = s->fields_valid = false;
+  s->sorted = s->fields_valid = s->keys_marked = false;
   pm_status st = DISPATCH(s, sort_particles, s);
   if (st != PM_OK) return st;
   return device_errors(s);
@@ -769,7 +830,7 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
       if (slot.exec) cudaGraphExecDestroy(slot.exec);
       slot = pm_sim::RunGraph();
       s->cur = want;
-      const bool sorted0 = s->sorted, fields0 = s->fields_valid;
+      const bool sorted0 = s->sorted, fields0 = s->fields_valid, marked0 = s->keys_marked;
       cudaGraph_t graph = nullptr;
       ec = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
       if (ec == cudaSuccess) {
@@ -786,6 +847,7 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
       s->cur = cur0;
       s->sorted = sorted0;
       s->fields_valid = fields0;
+      s->keys_marked = marked0;
     }
     cudaGraphExec_t exec = nullptr;
     for (auto& g : s->run_graph)

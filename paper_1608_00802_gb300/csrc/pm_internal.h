@@ -59,6 +59,8 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_MAX_BITS = 10;
+// set in a sort key by the drift when the particle's cell changed (keys use at most 30 bits)
+constexpr uint32_t KEY_MOVER = 0x80000000u;
 
 constexpr int KICK_THREADS = 256;
 constexpr int MESH_THREADS = 256;
@@ -74,14 +76,28 @@ inline size_t radix_smem_bytes(int bits) {
 template <typename R>
 cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, Mesh m, double inv_dx,
                                   void* pos, void* mom, uint32_t* keys, uint32_t* err, cudaStream_t s);
+// n_dev (may be null): device word that overrides n (the grid is sized for n, which must bound it)
 cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, int digit_bits, int key_bits,
-                                  uint32_t* hist, uint32_t* epoch, cudaStream_t s);
+                                  uint32_t* hist, uint32_t* epoch, cudaStream_t s,
+                                  const uint32_t* n_dev = nullptr);
 template <typename R>
 cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
                              int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
                              const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
                              const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
-                             cudaStream_t s);
+                             cudaStream_t s, const uint32_t* n_dev = nullptr);
+// incremental re-sort after a drift (keys carry KEY_MOVER): per-tile mover
+// counts + their scan (counts[0] = stayers, counts[1] = movers), stable
+// partition into stayers (s_keys, s_vals) and movers (m_keys, m_vals), and
+// the merge of stayers with the sorted movers that gathers the records
+cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint32_t* tile_cnt, uint32_t* counts,
+                                   uint32_t* s_keys, uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals,
+                                   cudaStream_t s);
+template <typename R>
+cudaError_t launch_merge_gather(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
+                                const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,
+                                const void* pos_in, const void* mom_in, void* pos_out, void* mom_out,
+                                cudaStream_t s);
 cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s);
 cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start,
                              cudaStream_t s);

@@ -716,7 +716,9 @@ __global__ void __launch_bounds__(KICK_THREADS, 4) k_kick(typename VT<R>::v4* po
       }
       pos[i] = make_pos(ncell, fx, fy, fz);
       mom[i] = make_mom(px, py, pz, rec_id(mo));
-      keys[i] = ncell;
+      // the drift marks the particles that changed cell for the incremental re-sort;
+      // without a drift the keys (marked or not) stay as they are
+      if (kp.drift != 0.0) keys[i] = ncell | (ncell != cell ? KEY_MOVER : 0u);
     }
   }
   if (MODE == 1) block_sum_store<4>(dg, part, gridDim.x);

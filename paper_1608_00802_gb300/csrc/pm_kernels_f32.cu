@@ -1,6 +1,7 @@
 // fp32 instantiation of the step kernels, plus the type-independent launchers.
 #include "pm_kernels.cuh"
 #include "pm_sort.cuh"
+#include "pm_instantiate.cuh"
 
 namespace pm {
 
@@ -12,11 +13,22 @@ cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s) {
 }
 
 cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, int digit_bits, int key_bits,
-                                  uint32_t* hist, uint32_t* epoch, cudaStream_t s) {
+                                  uint32_t* hist, uint32_t* epoch, cudaStream_t s, const uint32_t* n_dev) {
   int64_t blocks = (n + RS_THREADS * 16 - 1) / (RS_THREADS * 16);
   if (blocks > 2 * 152) blocks = 2 * 152;
   if (blocks < 1) blocks = 1;
-  k_sort_histogram<<<unsigned(blocks), RS_THREADS, 0, s>>>(keys, n, passes, digit_bits, key_bits, hist, epoch);
+  k_sort_histogram<<<unsigned(blocks), RS_THREADS, 0, s>>>(keys, n, passes, digit_bits, key_bits, hist, epoch,
+                                                            n_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint32_t* tile_cnt, uint32_t* counts,
+                                   uint32_t* s_keys, uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals,
+                                   cudaStream_t s) {
+  const int ntiles = int((n + RS_TILE - 1) / RS_TILE);
+  k_mover_count<<<unsigned(ntiles), RS_THREADS, 0, s>>>(keys, n, tile_cnt);
+  k_mover_scan<<<1, RS_THREADS, 0, s>>>(tile_cnt, ntiles, n, counts);
+  k_mover_scatter<<<unsigned(ntiles), RS_THREADS, 0, s>>>(keys, n, tile_cnt, s_keys, s_vals, m_keys, m_vals);
   return cudaGetLastError();
 }
 
@@ -33,27 +45,6 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
   k_reduce<<<nvals, 256, 0, s>>>(part, nblocks, out);
   return cudaGetLastError();
 }
-
-#define PM_INSTANTIATE(R)                                                                                         \
-  template cudaError_t launch_init_particles<R>(const double*, const double*, int64_t, Mesh, double, void*, void*, \
-                                                uint32_t*, uint32_t*, cudaStream_t);                              \
-  template cudaError_t launch_sort_pass<R>(bool, const uint32_t*, const uint32_t*, int64_t, int, int,             \
-                                           const uint32_t*, uint64_t*, uint32_t*, const uint32_t*, int, int,       \
-                                           uint32_t*, uint32_t*, const void*, const void*, void*, void*,           \
-                                           uint32_t*, cudaStream_t);                                              \
-  template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
-  template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
-  template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,       \
-                                          cudaStream_t);               \
-  template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
-                                      const KickParams*, const uint32_t*, double*, double*, uint32_t*,            \
-                                      cudaStream_t);                                                              \
-  template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \
-  template cudaError_t launch_get_particles<R>(const void*, const void*, int64_t, Mesh, double, double*, double*, \
-                                               cudaStream_t);                                                     \
-  template cudaError_t launch_get_order<R>(const void*, const void*, int64_t, uint32_t*, uint32_t*, cudaStream_t); \
-  template cudaError_t launch_to_double<R>(const R*, int64_t, double*, cudaStream_t);                             \
-  template cudaError_t launch_from_double<R>(const double*, int64_t, R*, cudaStream_t);
 
 PM_INSTANTIATE(float)
 

@@ -78,8 +78,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
 static __global__ void __launch_bounds__(RS_THREADS) k_sort_histogram(const uint32_t* __restrict__ keys, int64_t n,
                                                                       int passes, int digit_bits, int key_bits,
                                                                       uint32_t* __restrict__ hist,
-                                                                      uint32_t* __restrict__ epoch) {
+                                                                      uint32_t* __restrict__ epoch,
+                                                                      const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t sh[3 * (1 << RS_MAX_BITS)];
+  if (n_dev) n = *n_dev;  // element count known on the device only
   if (blockIdx.x == 0 && threadIdx.x == 0) *epoch = (*epoch + uint32_t(passes)) % 65530u + 1u;
   const int radix = 1 << digit_bits;
   for (int i = threadIdx.x; i < passes * radix; i += blockDim.x) sh[i] = 0;
@@ -115,8 +117,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
     const uint32_t* __restrict__ digit_total, uint64_t* status, uint32_t* tile_counter,
     const uint32_t* __restrict__ epoch_base, int pass,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const V4* __restrict__ pos_in,
-    const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out, uint32_t* err) {
+    const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out, uint32_t* err,
+    const uint32_t* __restrict__ n_dev) {
   extern __shared__ uint32_t smem[];
+  if (n_dev) n = *n_dev;  // element count known on the device only: surplus tiles exit below
   const int radix = 1 << bits;
   const uint32_t mask = uint32_t(radix - 1);
   uint32_t* warp_cnt = smem;                          // [RS_WARPS][radix]
@@ -133,6 +137,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
   __syncthreads();
   const uint32_t tile = scratch[63];
   const int64_t tile_base = int64_t(tile) * RS_TILE;
+  if (tile_base >= n) return;  // whole block: tile ids past the data (grid sized for the largest count)
   const int64_t rem = n - tile_base;
   const int tile_n = rem < RS_TILE ? int(rem) : RS_TILE;
   const int per = (radix + RS_THREADS - 1) / RS_THREADS;  // <= 4
@@ -294,12 +299,221 @@ static __global__ void k_reduce(const double* __restrict__ part, int nblocks, do
   if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
+// ---------------------------------------------------------------- incremental re-sort
+// After a drift the kick marks particles whose cell changed ("movers") by
+// setting bit 31 of their new key.  The others ("stayers") keep their key, so
+// in storage order they are still sorted by (key, previous slot).  The stable
+// sort by new key with ties in previous order is then: partition stably into
+// stayers and movers, radix-sort the movers (usually a few per cent), and merge
+// the two sequences by (key, previous slot) while gathering the records.  The
+// result is identical to the full sort.
+// movers per tile of RS_TILE slots
+static __global__ void __launch_bounds__(RS_THREADS) k_mover_count(const uint32_t* __restrict__ keys, int64_t n,
+                                                                   uint32_t* __restrict__ tile_cnt) {
+  __shared__ uint32_t warp_sum[RS_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = int64_t(blockIdx.x) * RS_TILE;
+  uint32_t c = 0;
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int64_t i = base + r * RS_THREADS + threadIdx.x;
+    const bool mv = i < n && (__ldg(keys + i) & KEY_MOVER);
+    c += __popc(__ballot_sync(0xffffffffu, mv));
+  }
+  if (lane == 0) warp_sum[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < RS_WARPS; ++w) t += warp_sum[w];
+    tile_cnt[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the per-tile mover counts (one block); counts[0] = stayers,
+// counts[1] = movers
+static __global__ void __launch_bounds__(RS_THREADS) k_mover_scan(uint32_t* tile_cnt, int ntiles, int64_t n,
+                                                                  uint32_t* counts) {
+  __shared__ uint32_t scratch[64];
+  uint32_t carry = 0;
+  for (int base = 0; base < ntiles; base += RS_THREADS * 4) {
+    uint32_t v[4], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int t = base + threadIdx.x * 4 + k;
+      v[k] = t < ntiles ? tile_cnt[t] : 0u;
+      sum += v[k];
+    }
+    uint32_t total;
+    uint32_t off = block_excl_scan(sum, scratch, total) + carry;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int t = base + threadIdx.x * 4 + k;
+      if (t < ntiles) tile_cnt[t] = off;
+      off += v[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) {
+    counts[0] = uint32_t(n) - carry;
+    counts[1] = carry;
+  }
+}
+
+// stable partition: stayers to (s_keys, s_vals), movers (flag cleared) to
+// (m_keys, m_vals); values are the previous slots
+static __global__ void __launch_bounds__(RS_THREADS) k_mover_scatter(const uint32_t* __restrict__ keys, int64_t n,
+                                                                     const uint32_t* __restrict__ tile_off,
+                                                                     uint32_t* __restrict__ s_keys,
+                                                                     uint32_t* __restrict__ s_vals,
+                                                                     uint32_t* __restrict__ m_keys,
+                                                                     uint32_t* __restrict__ m_vals) {
+  __shared__ uint32_t wm[RS_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile_base = int64_t(blockIdx.x) * RS_TILE;
+  const uint32_t lt = lanemask_lt();
+  // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32
+  uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
+    key[r] = i < n ? __ldg(keys + i) : 0u;
+    const uint32_t b = __ballot_sync(0xffffffffu, (key[r] & KEY_MOVER) != 0);
+    rank[r] = mcount + __popc(b & lt);  // movers before this slot in the warp
+    mcount += __popc(b);
+  }
+  if (lane == 0) wm[warp] = mcount;
+  __syncthreads();
+  // movers in the earlier warps of the tile: lane w < warp contributes wm[w]
+  uint32_t mbase = lane < warp ? wm[lane] : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mbase += __shfl_xor_sync(0xffffffffu, mbase, o);
+  mbase += tile_off[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
+    if (i < n) {
+      const uint32_t before = mbase + rank[r];  // movers before slot i
+      if (key[r] & KEY_MOVER) {
+        m_keys[before] = key[r] & ~KEY_MOVER;
+        m_vals[before] = uint32_t(i);
+      } else {
+        s_keys[uint32_t(i) - before] = key[r];
+        s_vals[uint32_t(i) - before] = uint32_t(i);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool kv_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
+// number of stayers among the first d outputs of the merge (merge path)
+__device__ __forceinline__ uint32_t merge_split(const uint32_t* sk, const uint32_t* sv, uint32_t ns,
+                                                const uint32_t* mk, const uint32_t* mv, uint32_t nm, uint32_t d) {
+  uint32_t lo = d > nm ? d - nm : 0u, hi = d < ns ? d : ns;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint32_t j = d - 1 - mid;  // the mover compared with stayer mid
+    if (kv_less(sk[mid], sv[mid], mk[j], mv[j]))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+constexpr int MG_TILE = RS_TILE;  // outputs per block
+inline size_t merge_smem_bytes() { return size_t(MG_TILE) * 6 * sizeof(uint32_t); }
+
+// merge of the stayers with the sorted movers, by (key, previous slot); writes
+// the sorted keys and gathers the records of the previous slots
+template <typename V4>
+__global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
+    const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ mk,
+    const uint32_t* __restrict__ mv, const uint32_t* __restrict__ counts, int64_t n, uint32_t* __restrict__ keys_out,
+    const V4* __restrict__ pos_in, const V4* __restrict__ mom_in, V4* __restrict__ pos_out,
+    V4* __restrict__ mom_out) {
+  extern __shared__ uint32_t msm[];
+  uint32_t* a_k = msm;               // stayers of this tile
+  uint32_t* a_v = a_k + MG_TILE;
+  uint32_t* b_k = a_v + MG_TILE;     // movers of this tile
+  uint32_t* b_v = b_k + MG_TILE;
+  uint32_t* o_k = b_v + MG_TILE;     // merged
+  uint32_t* o_v = o_k + MG_TILE;
+  __shared__ uint32_t split[2];
+  const uint32_t ns = counts[0], nm = counts[1];
+  const uint32_t d0 = blockIdx.x * uint32_t(MG_TILE);
+  const uint32_t d1 = int64_t(d0) + MG_TILE < n ? d0 + uint32_t(MG_TILE) : uint32_t(n);
+  if (threadIdx.x < 2) split[threadIdx.x] = merge_split(sk, sv, ns, mk, mv, nm, threadIdx.x ? d1 : d0);
+  __syncthreads();
+  const uint32_t a0 = split[0], a1 = split[1];
+  const uint32_t b0 = d0 - a0, b1 = d1 - a1;
+  const uint32_t na = a1 - a0, nb = b1 - b0;
+  for (uint32_t t = threadIdx.x; t < na; t += RS_THREADS) {
+    a_k[t] = sk[a0 + t];
+    a_v[t] = sv[a0 + t];
+  }
+  for (uint32_t t = threadIdx.x; t < nb; t += RS_THREADS) {
+    b_k[t] = mk[b0 + t];
+    b_v[t] = mv[b0 + t];
+  }
+  __syncthreads();
+  // each thread merges RS_ITEMS consecutive outputs of the tile
+  const uint32_t tn = d1 - d0;
+  const uint32_t q0 = min(uint32_t(threadIdx.x) * RS_ITEMS, tn), q1 = min(q0 + RS_ITEMS, tn);
+  if (q0 < q1) {
+    uint32_t ia = merge_split(a_k, a_v, na, b_k, b_v, nb, q0);
+    uint32_t ib = q0 - ia;
+    for (uint32_t q = q0; q < q1; ++q) {
+      const bool take_a = ib >= nb || (ia < na && kv_less(a_k[ia], a_v[ia], b_k[ib], b_v[ib]));
+      if (take_a) {
+        o_k[q] = a_k[ia];
+        o_v[q] = a_v[ia];
+        ++ia;
+      } else {
+        o_k[q] = b_k[ib];
+        o_v[q] = b_v[ib];
+        ++ib;
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < tn; q += RS_THREADS) {
+    const uint32_t src = o_v[q];
+    keys_out[d0 + q] = o_k[q];
+    pos_out[d0 + q] = pos_in[src];
+    mom_out[d0 + q] = mom_in[src];
+  }
+}
+
+template <typename R>
+cudaError_t launch_merge_gather(const uint32_t* sk, const uint32_t* sv, const uint32_t* mk, const uint32_t* mv,
+                                const uint32_t* counts, int64_t n, uint32_t* keys_out, const void* pos_in,
+                                const void* mom_in, void* pos_out, void* mom_out, cudaStream_t s) {
+  using V4 = typename VT<R>::v4;
+  static bool done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_merge_gather<V4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(merge_smem_bytes()));
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+  }
+  const unsigned blocks = unsigned((n + MG_TILE - 1) / MG_TILE);
+  k_merge_gather<V4><<<blocks, RS_THREADS, merge_smem_bytes(), s>>>(sk, sv, mk, mv, counts, n, keys_out,
+                                                                    (const V4*)pos_in, (const V4*)mom_in,
+                                                                    (V4*)pos_out, (V4*)mom_out);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int shift,
                              int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
                              const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
                              const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
-                             cudaStream_t s) {
+                             cudaStream_t s, const uint32_t* n_dev) {
   using V4 = typename VT<R>::v4;
   const size_t smem = radix_smem_bytes(bits);
   // shared-memory limits are raised once per device (for the largest digit), outside any capture
@@ -318,11 +532,11 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
     k_sort_pass<true, V4><<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
                                                            tile_counter, epoch, pass, keys_out, vals_out,
                                                            (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
-                                                           (V4*)mom_out, err);
+                                                           (V4*)mom_out, err, n_dev);
   } else {
     k_sort_pass<false, V4><<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
                                                             tile_counter, epoch, pass, keys_out, vals_out, nullptr,
-                                                            nullptr, nullptr, nullptr, err);
+                                                            nullptr, nullptr, nullptr, err, n_dev);
   }
   return cudaGetLastError();
 }

@@ -32,7 +32,7 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
-          "kick", "other"]
+          "kick", "sort_partition", "sort_merge", "other"]
 CUFFT_STAGES = ("fft_r2c", "fft_c2r")
 
 

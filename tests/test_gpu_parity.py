@@ -82,6 +82,77 @@ def test_sort_after_step_is_stable_wrt_previous_order(pm):
     assert np.any(ids != ids0)       # particles did change cells
 
 
+def _check_steps_resort(sim, ocfg, a_sched):
+    """steps one by one; after each, the storage order must be the stable order
+    of the new keys with ties in the previous storage order; returns the
+    fraction of particles that changed cell in each step"""
+    cell_prev, ids_prev = sim.get_order()
+    moved = []
+    for k in range(len(a_sched) - 1):
+        sim.step(a_sched[k], a_sched[k + 1])
+        xg, _ = sim.get_particles()
+        cell, ids = sim.get_order()
+        keys, order = oracle_order(xg, ocfg, ids_prev)
+        np.testing.assert_array_equal(ids, order)
+        np.testing.assert_array_equal(cell, keys[order])
+        before = np.empty_like(cell_prev)
+        before[ids_prev] = cell_prev
+        moved.append(float(np.mean(keys != before)))
+        cell_prev, ids_prev = cell, ids
+    return moved
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_resort_of_movers_over_several_steps(pm, precision):
+    # 24^3 = 13,824 particles: six full sort tiles and a ragged seventh
+    sim, ocfg = make(pm, 24, 48, 1.0, precision, amplitude=8.0, mode="hybrid")
+    moved = _check_steps_resort(sim, ocfg, np.geomspace(1 / 101.0, 1 / 40.0, 6))
+    assert 0.0 < min(moved) and max(moved) < 1.0
+
+
+def test_resort_when_every_particle_moves(pm):
+    # static box, no quantum pressure, uniform velocity of 1.5 cells per step:
+    # every particle changes cell, so all of them take the movers' radix sort
+    rng = np.random.default_rng(3)
+    n, n_mesh, box = 7000, 32, 1.0
+    x = rng.uniform(0, box, size=(n, 3))
+    dt = 0.01
+    p = np.zeros((n, 3))
+    p[:, 0] = 1.5 * (box / n_mesh) / dt
+    p[:, 1] = -1.25 * (box / n_mesh) / dt
+    sim, ocfg = make(pm, 0, n_mesh, box, "fp32", x=x, p=p, quantum=False, cosmological=False)
+    moved = _check_steps_resort(sim, ocfg, [1.0, 1.0 + dt, 1.0 + 2 * dt, 1.0 + 3 * dt])
+    assert min(moved) == 1.0
+
+
+def test_resort_when_no_particle_moves(pm):
+    # particles at rest at cell centres, a static box without forces: no movers
+    n_mesh, box = 16, 1.0
+    g = (np.arange(n_mesh) + 0.5) * box / n_mesh
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x = np.concatenate([x, x])                # two particles per cell: ties kept in order
+    p = np.zeros_like(x)
+    sim, ocfg = make(pm, 0, n_mesh, box, "fp32", x=x, p=p, quantum=False, cosmological=False)
+    moved = _check_steps_resort(sim, ocfg, [1.0, 1.1, 1.2])
+    assert max(moved) == 0.0
+
+
+def test_resort_with_fewer_particles_than_a_warp(pm):
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 1.0, size=(19, 3))
+    p = rng.normal(scale=3.0, size=(19, 3))
+    sim, ocfg = make(pm, 0, 8, 1.0, "fp32", x=x, p=p, quantum=False, cosmological=False)
+    moved = _check_steps_resort(sim, ocfg, [1.0, 1.02, 1.04, 1.06])
+    assert max(moved) > 0.0
+
+
+def test_resort_at_bench_size(pm):
+    # 128^3 particles on 256^3, L = 2 Mpc/h, hybrid force, three steps
+    sim, ocfg = make(pm, 128, 256, 2.0, "fp32", mode="hybrid")
+    moved = _check_steps_resort(sim, ocfg, np.geomspace(1 / 101.0, 1 / 90.0, 4))
+    assert max(moved) > 0.0
+
+
 # ------------------------------------------------------------------ S1 deposit
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
 @pytest.mark.parametrize("n_side,n_mesh,box", [(32, 64, 1.0), (24, 48, 1.5), (128, 256, 2.0)])
