@@ -520,7 +520,10 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
       const uint32_t node = uint32_t(z) * m.n2 + col;
       q[node] = __fdividef(qc * lap, sc);
       ksum += dxp * dxp + dyp * dyp + dzp * dzp;
-      if (sc < slim) my_list[atomicAdd(&s_cnt, 1u)] = node;
+      // near-empty: redone in float-float unless all seven values are equal
+      // (then the Laplacian is exactly zero either way)
+      if (sc < slim && !((sxp == sc) & (sxm == sc) & (syp == sc) & (sym == sc) & (sp == sc) & (sm == sc)))
+        my_list[atomicAdd(&s_cnt, 1u)] = node;
     }
     __syncthreads();  // S is rewritten next
     sm = sc;
@@ -561,7 +564,7 @@ __device__ __forceinline__ void grad_kernel(const R* __restrict__ f, const Stenc
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) c[dz][dy][dx] = __ldg(f + s.zi[dz + 1] + s.yi[dy + 1] + s.xi[dx + 1]);
+      for (int dx = 0; dx < 2; ++dx) c[dz][dy][dx] = __ldg(f + (s.zi[dz + 1] + s.yi[dy + 1] + s.xi[dx + 1]));
   R gx = 0, gy = 0, gz = 0;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
@@ -579,29 +582,42 @@ __device__ __forceinline__ void grad_kernel(const R* __restrict__ f, const Stenc
 template <typename R>
 __device__ __forceinline__ void grad_central(const R* __restrict__ f, const Stencil& s, const R (&wx)[2],
                                              const R (&wy)[2], const R (&wz)[2], R inv_dx, R (&g)[3]) {
+  // the 32 distinct nodes: the inner 2x2x2 cube and its two-sided extensions
+  // along each axis, each loaded once
+  R c[2][2][2], ex[2][2][2], ey[2][2][2], ez[2][2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) c[a][b][d] = __ldg(f + (s.zi[a + 1] + s.yi[b + 1] + s.xi[d + 1]));
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        ex[a][b][e] = __ldg(f + (s.zi[a + 1] + s.yi[b + 1] + s.xi[3 * e]));
+        ey[a][b][e] = __ldg(f + (s.zi[a + 1] + s.yi[3 * e] + s.xi[b + 1]));
+        ez[a][b][e] = __ldg(f + (s.zi[3 * e] + s.yi[a + 1] + s.xi[b + 1]));
+      }
+    }
   R gx = 0, gy = 0, gz = 0;
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
-      const R* row = f + s.zi[dz + 1] + s.yi[dy + 1];
-      R u0 = __ldg(row + s.xi[0]), u1 = __ldg(row + s.xi[1]), u2 = __ldg(row + s.xi[2]), u3 = __ldg(row + s.xi[3]);
+      const R u0 = ex[dz][dy][0], u1 = c[dz][dy][0], u2 = c[dz][dy][1], u3 = ex[dz][dy][1];
       gx += wz[dz] * wy[dy] * (wx[0] * (u2 - u0) + wx[1] * (u3 - u1));
     }
 #pragma unroll
   for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-      const R* col = f + s.zi[dz + 1] + s.xi[dx + 1];
-      R u0 = __ldg(col + s.yi[0]), u1 = __ldg(col + s.yi[1]), u2 = __ldg(col + s.yi[2]), u3 = __ldg(col + s.yi[3]);
+      const R u0 = ey[dz][dx][0], u1 = c[dz][0][dx], u2 = c[dz][1][dx], u3 = ey[dz][dx][1];
       gy += wz[dz] * wx[dx] * (wy[0] * (u2 - u0) + wy[1] * (u3 - u1));
     }
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-      const R* pil = f + s.yi[dy + 1] + s.xi[dx + 1];
-      R u0 = __ldg(pil + s.zi[0]), u1 = __ldg(pil + s.zi[1]), u2 = __ldg(pil + s.zi[2]), u3 = __ldg(pil + s.zi[3]);
+      const R u0 = ez[dy][dx][0], u1 = c[0][dy][dx], u2 = c[1][dy][dx], u3 = ez[dy][dx][1];
       gz += wy[dy] * wx[dx] * (wz[0] * (u2 - u0) + wz[1] * (u3 - u1));
     }
   const R h = R(0.5) * inv_dx;

@@ -24,11 +24,14 @@ def main():
     ap.add_argument("--box", type=float, default=2.0)
     ap.add_argument("--m22", type=float, default=2.5)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--start", type=int, default=0, help="steps run before the profiled ones")
+    ap.add_argument("--nsteps", type=int, default=500, help="steps of the whole run (z = 100 -> 3)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--mode", choices=["meshgrad", "hybrid", "lagrangian"], default="hybrid")
     ap.add_argument("--rho-fp64", type=float, default=1e-2,
                     help="density below which Q is recomputed in extended precision (0: never)")
     args = ap.parse_args()
+    import numpy as np
     import torch
 
     from paper_1608_00802_gb300 import build, ics, pm
@@ -40,8 +43,11 @@ def main():
                          precision=pm.FP64 if args.precision == "fp64" else pm.FP32, rho_fp64=args.rho_fp64)
     sim = pm.Sim(cfg)
     sim.set_particles(x, p)
+    a = a0 * (a1 / a0) ** (np.arange(args.nsteps + 1) / args.nsteps)
+    if args.start:
+        sim.run(args.start, a[0], a[args.start])
     sim.profile_begin(64 * (args.steps + 1))
-    sim.run(args.steps, a0, a0 * (a1 / a0) ** (args.steps / 500.0))
+    sim.run(args.steps, a[args.start], a[args.start + args.steps])
     stages = sim.profile_end()
     torch.cuda.synchronize()
     print(json.dumps({k: {"ms": v[0], "launches": v[1]} for k, v in stages.items() if v[1]}))
