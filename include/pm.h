@@ -166,6 +166,39 @@ pm_status pm_set_density(pm_sim* sim, const double* rho_host);
 /* Current storage order: cell key (iz*N+iy)*N+ix and id of each slot. Sync. */
 pm_status pm_get_order(pm_sim* sim, uint32_t* cell, uint32_t* id);
 
+/* ---- launch shapes and the autotuner ---------------------------------------
+ * Each simulation launches its kernels in shapes chosen for its mesh size (a
+ * default from the mesh size, or measured by pm_autotune).  The mesh fields,
+ * forces and particle states do not depend on the shapes; the diagnostic sums
+ * of pm_energy differ only by the grouping of their partial sums. */
+typedef struct {
+  int32_t stencil_rows;    /* fp32 compact stencil: mesh rows per block (1, 2, 4 or 8, dividing n_mesh,
+                              n_mesh a multiple of 4), the block's density arriving by bulk copies;
+                              0 = the register-column kernel (any even n_mesh) */
+  int32_t stencil_planes;  /* z planes per stencil block: 2..16 for one-shot tiles, 4..n_mesh for
+                              sweeps (ignored when stencil_rows = 0) */
+  int32_t stencil_stages;  /* 0 = one-shot tile (the block loads its whole input at once); 4..8 = a
+                              sweep along z through a ring of that many planes (ignored when rows = 0) */
+  int32_t kick_threads;    /* threads (particles) per interpolate+kick+drift block: 128 or 256 */
+  int32_t deposit_warps;   /* mesh rows (one warp each) per deposit block: 1..8 */
+} pm_tuning;
+
+/* Current shapes. */
+pm_status pm_get_tuning(pm_sim* sim, pm_tuning* out);
+
+/* Sets the shapes (e.g. a cached autotuner result).  PM_ERR_INVALID_ARG if a
+ * value is outside the ranges above or the stencil tile does not fit the mesh
+ * or the 227 KB of shared memory of a block.  Drops captured steps; the next
+ * force evaluation recomputes the fields.  Sync. */
+pm_status pm_set_tuning(pm_sim* sim, const pm_tuning* t);
+
+/* Times the candidate shapes of the stencil, the deposit and the kick on this
+ * simulation's current state (reps launches each, after one untimed), keeps
+ * the fastest of each and returns them in `out` (may be null).  Needs
+ * particles (PM_ERR_STATE).  The state is not changed; the fields are
+ * recomputed with the chosen shapes.  Sync. */
+pm_status pm_autotune(pm_sim* sim, int32_t reps, pm_tuning* out);
+
 /* Stages timed by the profiler (one CUDA-event pair per launch, recorded on
  * the simulation's stream).  The cuFFT stages cover one cufftExec call each. */
 enum {

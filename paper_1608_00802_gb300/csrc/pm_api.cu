@@ -168,13 +168,13 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   // digit histograms of all passes (radix_max stride) + one tile counter per pass
   L.hist = take((3 * (size_t(1) << RS_MAX_BITS) + 4) * 4);
   L.status = take((size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8);
-  size_t nkb = size_t(kick_blocks(int64_t(n)));
+  size_t nkb = size_t(kick_blocks(int64_t(n), KICK_MIN_THREADS));
   size_t npart = 4 * nkb;
   if (size_t(RED_GRID) * 3 * PK_MAX_BINS > npart) npart = size_t(RED_GRID) * 3 * PK_MAX_BINS;
   L.part = take(npart * 8);
   L.st_list = take(c.precision == PM_FP32 ? stencil_list_entries(int(N)) * 4 : 4);
-  L.st_count = take(size_t(stencil_block_count(int(N))) * 4);
-  const size_t aux = std::max<size_t>(MESH_GRID, size_t(stencil_block_count(int(N))));
+  L.st_count = take(size_t(stencil_max_blocks(int(N))) * 4);
+  const size_t aux = std::max<size_t>(MESH_GRID, size_t(stencil_max_blocks(int(N))));
   L.part_aux = take(2 * aux * 8);
   L.red = take(3 * PK_MAX_BINS * 8 + 64);
   L.err = take(256);
@@ -222,6 +222,8 @@ struct pm_sim {
   uint32_t* keys;  // sorted (current) keys
   uint32_t* keys_tmp[2];
   bool keys_marked = false;  // a drift has flagged the movers in `keys` since the last sort
+  Tuning tune;                // launch shapes
+  bool krho_valid = false;    // the K_rho partials belong to the current Q~
   cufftHandle plan_fwd, plan_inv;
   bool have_particles, sorted, fields_valid;
   std::string err;
@@ -309,12 +311,12 @@ struct ProfScope {
 // `part_aux` (one MESH_GRID-long row each) until the next evaluation.
 double* wg_part(pm_sim* s) { return s->at<double>(s->L.part_aux); }
 size_t aux_len(const pm_sim* s) {
-  return std::max<size_t>(MESH_GRID, size_t(stencil_block_count(s->cfg.n_mesh)));
+  return std::max<size_t>(MESH_GRID, size_t(stencil_max_blocks(s->cfg.n_mesh)));
 }
 double* kr_part(pm_sim* s) { return wg_part(s) + aux_len(s); }
 int kr_blocks(const pm_sim* s) {
   const bool tiled = !s->fp64() && s->cfg.lap == PM_LAP_COMPACT;
-  return tiled ? stencil_block_count(s->cfg.n_mesh) : MESH_GRID;
+  return tiled ? stencil_launch_blocks(s->cfg.n_mesh, s->tune.st_ty, s->tune.st_zlen) : MESH_GRID;
 }
 
 // Incremental re-sort after a drift: the stayers are still in order, so the
@@ -424,6 +426,26 @@ pm_status sort_particles(pm_sim* s) {
   return PM_OK;
 }
 
+// Q~ (and the K_rho partials) from the density on the mesh
+template <typename R>
+pm_status stencil_stage(pm_sim* s, bool diag = false) {
+  const Layout& L = s->L;
+  StencilParams sp;
+  sp.step = s->cfg.lap == PM_LAP_WIDE ? 2 : 1;
+  sp.rho_floor = s->cfg.rho_floor;
+  sp.rho_fp64 = s->cfg.rho_fp64;
+  sp.qcoef = -0.5 * s->hbm * s->hbm / ((sp.step * s->dx) * (sp.step * s->dx));
+  sp.ty = s->tune.st_ty;
+  sp.zlen = s->tune.st_zlen;
+  sp.stages = s->tune.st_stages;
+  sp.diag = diag ? 1 : 0;
+  s->krho_valid = diag || s->fp64() || s->cfg.lap != PM_LAP_COMPACT;  // the generic kernel always sums
+  PROF(s, PM_STAGE_STENCIL);
+  CU(s, launch_stencil<R>(s->at<R>(L.rho), s->mesh, sp, s->at<R>(L.q), kr_part(s), s->at<uint32_t>(L.st_list),
+                          s->at<uint32_t>(L.st_count), s->errword(), s->stream));
+  return PM_OK;
+}
+
 template <typename R>
 pm_status mesh_from_density(pm_sim* s) {
   const Layout& L = s->L;
@@ -451,14 +473,8 @@ pm_status mesh_from_density(pm_sim* s) {
     }
   }
   if (s->cfg.quantum) {
-    StencilParams sp;
-    sp.step = s->cfg.lap == PM_LAP_WIDE ? 2 : 1;
-    sp.rho_floor = s->cfg.rho_floor;
-    sp.rho_fp64 = s->cfg.rho_fp64;
-    sp.qcoef = -0.5 * s->hbm * s->hbm / ((sp.step * s->dx) * (sp.step * s->dx));
-    PROF(s, PM_STAGE_STENCIL);
-    CU(s, launch_stencil<R>(rho, s->mesh, sp, s->at<R>(L.q), kr_part(s), s->at<uint32_t>(L.st_list),
-                            s->at<uint32_t>(L.st_count), s->stream));
+    pm_status st = stencil_stage<R>(s);
+    if (st != PM_OK) return st;
   }
   s->fields_valid = true;
   return PM_OK;
@@ -472,7 +488,7 @@ pm_status deposit(pm_sim* s) {
   }
   PROF(s, PM_STAGE_DEPOSIT);
   CU(s, launch_deposit<R>(s->pos(), s->at<uint32_t>(s->L.row_start), s->n(), s->mesh, s->norm, s->at<R>(s->L.rho),
-                          s->stream));
+                          s->stream, s->tune.dep_warps));
   return PM_OK;
 }
 
@@ -504,7 +520,7 @@ pm_status kick(pm_sim* s, const KickParams& kp, double* acc, const KickParams* k
   {
     PROF(s, PM_STAGE_KICK);
     CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, kp_tab,
-                         step, s->part(), acc, s->errword(), s->stream));
+                         step, s->part(), acc, s->errword(), s->tune.kick_threads, s->stream));
   }
   if (kp.drift != 0.0) {
     s->sorted = false;
@@ -523,7 +539,7 @@ pm_status device_errors(pm_sim* s) {
   CU(s, cudaStreamSynchronize(s->stream));
   if (!e) return PM_OK;
   CU(s, cudaMemsetAsync(s->errword(), 0, 4, s->stream));
-  if (e & ERR_TIMEOUT) return fail(s, PM_ERR_TIMEOUT, "a bounded device wait expired (sort look-back)");
+  if (e & ERR_TIMEOUT) return fail(s, PM_ERR_TIMEOUT, "a bounded device wait expired (sort look-back or stencil copy)");
   return fail(s, PM_ERR_NONFINITE, "non-finite position or momentum");
 }
 
@@ -585,6 +601,110 @@ pm_status table_step(pm_sim* s, const KickParams* tab, uint32_t* step) {
   return PM_OK;
 }
 
+void to_public(const Tuning& t, pm_tuning* o) {
+  o->stencil_rows = t.st_ty;
+  o->stencil_planes = t.st_zlen;
+  o->stencil_stages = t.st_stages;
+  o->kick_threads = t.kick_threads;
+  o->deposit_warps = t.dep_warps;
+}
+
+// drops the captured steps (they hold the launch shapes)
+void drop_graphs(pm_sim* s) {
+  cudaStreamSynchronize(s->stream);
+  if (s->cap) cudaStreamSynchronize(s->cap);
+  for (auto& g : s->run_graph) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = pm_sim::RunGraph();
+  }
+}
+
+// ms per launch of `reps` back-to-back launches on the simulation's stream
+// (after one untimed launch); negative on error
+template <typename F>
+double time_launches(pm_sim* s, int reps, F&& launch) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+  double ms = -1.0;
+  if (launch() == PM_OK && cudaEventRecord(e0, s->stream) == cudaSuccess) {
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) ok = launch() == PM_OK;
+    float t = 0.0f;
+    if (ok && cudaEventRecord(e1, s->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+      ms = double(t) / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+template <typename R>
+pm_status autotune(pm_sim* s, int reps) {
+  pm_status st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  const int n = s->cfg.n_mesh;
+  const bool prof = s->prof_on;
+  s->prof_on = false;
+  Tuning best = s->tune;
+  // stencil tiles (fp32 compact Laplacian)
+  if (!s->fp64() && s->cfg.quantum && s->cfg.lap == PM_LAP_COMPACT) {
+    double tbest = -1.0;
+    // register-column kernel, one-shot tiles (stages 0) and sweeping tiles (ring of 4..8 planes)
+    const int tys[] = {0, 1, 2, 4, 8}, zls[] = {2, 4, 8, 16, 32, 64}, sts[] = {0, 4, 6, 8};
+    for (int ty : tys)
+      for (int zl : zls)
+        for (int sg : sts) {
+          if (ty == 0 && (zl != 8 || sg != 4)) continue;  // one register-column candidate
+          if (ty > 0 && sg > 0 && zl < 8) continue;        // sweeps of fewer planes re-read too much
+          if (ty > 0 && !stencil_shape_ok(n, ty, zl, sg)) continue;
+          s->tune.st_ty = ty;
+          s->tune.st_zlen = ty ? zl : 0;
+          s->tune.st_stages = ty ? sg : 0;
+          const double t = time_launches(s, reps, [&] { return stencil_stage<R>(s); });
+          if (t > 0 && (tbest < 0 || t < tbest)) {
+            tbest = t;
+            best.st_ty = s->tune.st_ty;
+            best.st_zlen = s->tune.st_zlen;
+            best.st_stages = s->tune.st_stages;
+          }
+        }
+    s->tune = best;
+  }
+  // deposit: rows (warps) per block
+  {
+    double tbest = -1.0;
+    for (int w : {2, 4, 8}) {
+      s->tune.dep_warps = w;
+      const double t = time_launches(s, reps, [&] { return deposit<R>(s); });
+      if (t > 0 && (tbest < 0 || t < tbest)) {
+        tbest = t;
+        best.dep_warps = w;
+      }
+    }
+    s->tune = best;
+  }
+  // kick: threads per block, timed with zero weights and no drift (the state is unchanged)
+  {
+    KickParams kp = base_kick(s);
+    double tbest = -1.0;
+    for (int th : {128, 256}) {
+      s->tune.kick_threads = th;
+      const double t = time_launches(s, reps, [&] { return kick<R>(s, kp, nullptr); });
+      if (t > 0 && (tbest < 0 || t < tbest)) {
+        tbest = t;
+        best.kick_threads = th;
+      }
+    }
+    s->tune = best;
+  }
+  s->prof_on = prof;
+  // the fields (and their partial sums) again, with the chosen shapes
+  s->fields_valid = false;
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  return device_errors(s);
+}
 }  // namespace
 
 // ================================================================ C ABI
@@ -656,6 +776,7 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
   s->keys_tmp[0] = s->at<uint32_t>(L.keys[1]);
   s->keys_tmp[1] = s->at<uint32_t>(L.keys[2]);
   s->have_particles = s->sorted = s->fields_valid = false;
+  s->tune = default_tuning(N);
   cufftType fwd = c->precision == PM_FP64 ? CUFFT_D2Z : CUFFT_R2C;
   cufftType inv = c->precision == PM_FP64 ? CUFFT_Z2D : CUFFT_C2R;
   cufftHandle* plans[2] = {&s->plan_fwd, &s->plan_inv};
@@ -884,7 +1005,11 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   // K_v and momentum of the current (synchronised) momenta
   st = pass(s, Weights{0.0, 0.0}, Weights{0.0, 0.0}, 0.0, true);
   if (st != PM_OK) return st;
-  const int nkb = kick_blocks(s->n());
+  if (s->cfg.quantum && !s->krho_valid) {  // the steps skip the K_rho sums: Q~ again, with them
+    st = DISPATCH(s, stencil_stage, s, true);
+    if (st != PM_OK) return st;
+  }
+  const int nkb = kick_blocks(s->n(), s->tune.kick_threads);
   double* red = s->red();
   CU(s, launch_reduce(s->part(), nkb, 4, red, s->stream));
   CU(s, launch_reduce(wg_part(s), MESH_GRID, 1, red + 4, s->stream));
@@ -978,6 +1103,42 @@ pm_status pm_set_density(pm_sim* s, const double* rho_host) {
   pm_status st = DISPATCH(s, mesh_from_density, s);
   if (st != PM_OK) return st;
   CU(s, cudaStreamSynchronize(s->stream));
+  return PM_OK;
+}
+
+pm_status pm_get_tuning(pm_sim* s, pm_tuning* out) {
+  if (!s || !out) return PM_ERR_INVALID_ARG;
+  to_public(s->tune, out);
+  return PM_OK;
+}
+
+pm_status pm_set_tuning(pm_sim* s, const pm_tuning* t) {
+  if (!s || !t) return PM_ERR_INVALID_ARG;
+  const int n = s->cfg.n_mesh;
+  if (t->kick_threads != 128 && t->kick_threads != 256)
+    return fail(s, PM_ERR_INVALID_ARG, "kick_threads must be 128 or 256");
+  if (t->deposit_warps < 1 || t->deposit_warps > 8) return fail(s, PM_ERR_INVALID_ARG, "deposit_warps must be 1..8");
+  if (!stencil_shape_ok(n, t->stencil_rows, t->stencil_planes, t->stencil_stages))
+    return fail(s, PM_ERR_INVALID_ARG, "stencil shape (%d rows, %d planes, %d stages) is not valid for N = %d",
+                t->stencil_rows, t->stencil_planes, t->stencil_stages, n);
+  drop_graphs(s);
+  s->tune.st_ty = t->stencil_rows;
+  s->tune.st_zlen = t->stencil_rows ? t->stencil_planes : 0;
+  s->tune.st_stages = t->stencil_rows ? t->stencil_stages : 0;
+  s->tune.kick_threads = t->kick_threads;
+  s->tune.dep_warps = t->deposit_warps;
+  s->fields_valid = false;  // K_rho partials follow the stencil's block count
+  return PM_OK;
+}
+
+pm_status pm_autotune(pm_sim* s, int32_t reps, pm_tuning* out) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (reps < 1) reps = 5;
+  drop_graphs(s);
+  st = DISPATCH(s, autotune, s, int(reps));
+  if (st != PM_OK) return st;
+  if (out) to_public(s->tune, out);
   return PM_OK;
 }
 

@@ -12,12 +12,12 @@
   template cudaError_t launch_merge_gather<R>(const uint32_t*, const uint32_t*, const uint32_t*, const uint32_t*, \
                                               const uint32_t*, int64_t, uint32_t*, const void*, const void*,      \
                                               void*, void*, cudaStream_t);                                        \
-  template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t);           \
+  template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t, int);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
   template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,       \
-                                          cudaStream_t);               \
+                                          uint32_t*, cudaStream_t);               \
   template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \
-                                      const KickParams*, const uint32_t*, double*, double*, uint32_t*,            \
+                                      const KickParams*, const uint32_t*, double*, double*, uint32_t*, int,       \
                                       cudaStream_t);                                                              \
   template cudaError_t launch_power<R>(const void*, Mesh, int, double*, cudaStream_t);                            \
   template cudaError_t launch_get_particles<R>(const void*, const void*, int64_t, Mesh, double, double*, double*, \

@@ -49,7 +49,21 @@ struct StencilParams {
   double rho_floor;   // s = sqrt(max(rho, rho_floor))
   double rho_fp64;    // nodes below take the fp64 branch (fp32 path)
   double qcoef;       // -(hbar/m)^2 / 2 / (step*dx)^2
+  // fp32 compact tiles: ty mesh rows x zlen planes per block with a ring of
+  // `stages` bulk-copied planes; ty = 0 selects the register-column kernel
+  int ty, zlen, stages;
+  int diag;           // also write the K_rho partials (the fp32 compact kernels skip them otherwise)
 };
+
+// Launch shapes of one simulation (defaults by mesh size, or measured by the
+// autotuner).  Kernel results do not depend on them; the diagnostic sums
+// differ only in the grouping of their partial sums.
+struct Tuning {
+  int st_ty, st_zlen, st_stages;  // fp32 compact stencil tiles (see StencilParams)
+  int kick_threads;               // 128 or 256
+  int dep_warps;                  // mesh rows (one warp each) per deposit block, 1..8
+};
+constexpr int KICK_MIN_THREADS = 128;
 
 // error bits of the device error word
 enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
@@ -103,19 +117,24 @@ cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, u
                              cudaStream_t s);
 template <typename R>
 cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
-                           cudaStream_t s);
+                           cudaStream_t s, int warps = 8);
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
 template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
-                           uint32_t* list_count, cudaStream_t s);
-// fp32 stencil tiling (defined with the kernels): list length and block count
+                           uint32_t* list_count, uint32_t* err, cudaStream_t s);
+// fp32 stencil tiling (defined with the kernels): list length of the
+// register-column kernel, blocks (= K_rho partials) of a shape and the most
+// over every valid shape, shape validity and the default shape
 size_t stencil_list_entries(int n);
-int stencil_block_count(int n);
+int stencil_launch_blocks(int n, int ty, int zlen);
+int stencil_max_blocks(int n);
+bool stencil_shape_ok(int n, int ty, int zlen, int stages);
+Tuning default_tuning(int n);
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
                         KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
-                        uint32_t* err, cudaStream_t s);
+                        uint32_t* err, int threads, cudaStream_t s);
 template <typename R>
 cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);
@@ -133,6 +152,6 @@ cudaError_t launch_from_double(const double* f, int64_t n, R* out, cudaStream_t 
 // stores the message that pm_last_error(NULL) returns (host side)
 void set_global_error(const char* msg);
 
-inline int kick_blocks(int64_t n) { return int((n + KICK_THREADS - 1) / KICK_THREADS); }
+inline int kick_blocks(int64_t n, int threads = KICK_THREADS) { return int((n + threads - 1) / threads); }
 
 }  // namespace pm

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "pm_internal.h"
+#include "pm_bulk.cuh"
 
 namespace pm {
 
@@ -144,14 +145,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Block sum of NV fp32 values per thread: float-float inside each warp, fp64
 // across warps and blocks (fixed order, so the sums are reproducible).
 template <int NV>
-__device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, int nblocks, int bid = -1) {
+__device__ __forceinline__ void block_sum_store_ff(const ff (&v)[NV], double* part, int nblocks, int bid) {
   __shared__ double shf[32][NV];
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int lane = tid & 31, warp = tid >> 5;
-  if (bid < 0) bid = blockIdx.x;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    ff s = {v[k], 0.0f};
+    ff s = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
     if (lane == 0) shf[warp][k] = double(s.hi) + double(s.lo);
@@ -166,6 +166,27 @@ __device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, in
       part[k * nblocks + bid] = s;
     }
   }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_store(float (&v)[NV], double* part, int nblocks, int bid = -1) {
+  ff f[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) f[k] = ff{v[k], 0.0f};
+  block_sum_store_ff<NV>(f, part, nblocks, bid < 0 ? int(blockIdx.x) : bid);
+}
+
+// sum of squared forward differences of one node, rounded the same way in
+// every kernel (explicit fused multiply-adds)
+__device__ __forceinline__ float krho_term(float dx, float dy, float dz) {
+  return fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// running float-float sum of fp32 terms (the error of each addition is kept)
+__device__ __forceinline__ void ff_accumulate(ff& a, float v) {
+  const ff t = two_sum(a.hi, v);
+  a.hi = t.hi;
+  a.lo += t.lo;
 }
 
 // Block sum of NV doubles (fixed order); thread 0 gets the totals.
@@ -261,7 +282,7 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
   extern __shared__ __align__(16) unsigned char dep_smem[];
   const int n = m.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t orow = blockIdx.x * DEP_WARPS + warp;  // z*N + y
+  const uint32_t orow = blockIdx.x * (blockDim.x >> 5) + warp;  // z*N + y
   if (orow >= m.n2) return;
   R* acc = reinterpret_cast<R*>(dep_smem) + warp * (n + 1);
   for (int i = lane; i <= n; i += 32) acc[i] = R(0);
@@ -461,7 +482,8 @@ __device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_
 static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const float* __restrict__ rho, Mesh m,
                                                                         float fl, float qc, float slim, int zlen,
                                                                         float* __restrict__ q, uint32_t* list,
-                                                                        uint32_t* list_count, double* part) {
+                                                                        uint32_t* list_count, double* part,
+                                                                        int diag) {
   __shared__ float S[ST_TY + 2][ST_X];  // s of plane z, rows y0-1 .. y0+ST_TY
   __shared__ uint32_t s_cnt;
   const int n = m.n;
@@ -492,7 +514,7 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
   float pre = __ldg(plane(z0 + 2) + col);
   float exm = own_xm ? __ldg(plane(z0) + col_xm) : 0.0f, exp_ = own_xp ? __ldg(plane(z0) + col_xp) : 0.0f;
   float eh = halo ? __ldg(plane(z0) + col_h) : 0.0f;
-  float ksum = 0.0f;
+  ff ksum = {0.0f, 0.0f};
   for (int z = z0; z < z1; ++z) {
     // plane z into shared memory (own row and the halo rows; rows past the mesh
     // do not write, their slot may be the halo slot)
@@ -519,11 +541,13 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
       const float lap = (dxp + (sxm - sc)) + (dyp + (sym - sc)) + (dzp + (sm - sc));
       const uint32_t node = uint32_t(z) * m.n2 + col;
       q[node] = __fdividef(qc * lap, sc);
-      ksum += dxp * dxp + dyp * dyp + dzp * dzp;
+      if (diag) ff_accumulate(ksum, krho_term(dxp, dyp, dzp));
       // near-empty: redone in float-float unless all seven values are equal
       // (then the Laplacian is exactly zero either way)
-      if (sc < slim && !((sxp == sc) & (sxm == sc) & (syp == sc) & (sym == sc) & (sp == sc) & (sm == sc)))
-        my_list[atomicAdd(&s_cnt, 1u)] = node;
+      if (sc < slim) {
+        if (!((sxp == sc) & (sxm == sc) & (syp == sc) & (sym == sc) & (sp == sc) & (sm == sc)))
+          my_list[atomicAdd(&s_cnt, 1u)] = node;
+      }
     }
     __syncthreads();  // S is rewritten next
     sm = sc;
@@ -541,8 +565,274 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
     q[node] = q_ext_at(rho, node, m, fl, qc);
   }
   if (tid == 0) list_count[blin] = cnt;
-  float acc[1] = {ksum};
-  block_sum_store<1>(acc, part, gridDim.x * gridDim.y * gridDim.z, int(blin));
+  if (diag) {
+    const ff acc[1] = {fast_two_sum(ksum.hi, ksum.lo)};
+    block_sum_store_ff<1>(acc, part, gridDim.x * gridDim.y * gridDim.z, int(blin));
+  }
+}
+
+// fp32 compact stencil fed by bulk copies.  A block owns `ty` whole mesh rows
+// (all of x, so the periodic x-neighbours are in the tile) of `zlen`
+// consecutive planes.  Thread 0 streams the density of each plane tile, with
+// its two halo rows, into a ring of `stages` shared-memory slots (three bulk
+// copies per plane, completed on the slot's mbarrier), so that stages-3
+// planes are in flight while the threads work.  When a plane arrives its
+// s = sqrt(max(rho, floor)) is taken once into a ring of three s planes; Q~ of
+// plane z then reads s of z-1, z, z+1 from shared memory in float4 groups
+// along x.  Near-empty nodes go to a per-plane list and are redone in
+// float-float from the densities still in the ring.  Per node the arithmetic
+// is that of k_stencil_tiled, so both kernels give the same bits.
+constexpr int SB_THREADS = 256;
+constexpr uint32_t SB_WAIT_LIMIT = 1u << 20;
+
+inline size_t stencil_bulk_smem(int n, int ty, int stages) {
+  const size_t slot = size_t(ty + 2) * n * sizeof(float);
+  const size_t list = (size_t(ty) * n * sizeof(uint16_t) + 15) & ~size_t(15);
+  return 16 * ((stages * 8 + 15) / 16) + (size_t(stages) + 3) * slot + list;
+}
+
+constexpr size_t SB_SMEM_MAX = 226 * 1024;  // dynamic shared memory per block, below the 227 KB opt-in
+
+inline size_t stencil_tile_smem(int n, int ty, int tz) { return 16 + size_t(ty + 2) * (tz + 2) * n * sizeof(float); }
+
+// one-shot tiles: ty rows x tz planes (tz <= n; the last tile of a column may be shorter)
+inline bool stencil_tile_shape_ok(int n, int ty, int tz) {
+  if (n % 4 || !(ty == 1 || ty == 2 || ty == 4 || ty == 8) || n % ty) return false;
+  if (tz < 2 || tz > 16 || tz > n) return false;
+  return stencil_tile_smem(n, ty, tz) <= SB_SMEM_MAX;
+}
+
+inline bool stencil_bulk_shape_ok(int n, int ty, int zlen, int stages) {
+  if (n % 4 || !(ty == 1 || ty == 2 || ty == 4 || ty == 8) || n % ty) return false;
+  if (zlen < 4 || zlen > n || stages < 4 || stages > 8) return false;
+  return stencil_bulk_smem(n, ty, stages) <= SB_SMEM_MAX;
+}
+
+static __global__ void __launch_bounds__(SB_THREADS) k_stencil_bulk(const float* __restrict__ rho, Mesh m, float fl,
+                                                                    float qc, float slim, int ty, int zlen,
+                                                                    int stages, float* __restrict__ q,
+                                                                    double* part, uint32_t* err, int diag) {
+  extern __shared__ __align__(16) unsigned char sb_smem[];
+  __shared__ uint32_t s_cnt;
+  __shared__ int s_abort;
+  const int n = m.n, lg = m.log2n;
+  const int slot = (ty + 2) * n;  // floats per plane tile
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sb_smem);
+  float* ring = reinterpret_cast<float*>(sb_smem + 16 * ((stages * 8 + 15) / 16));
+  float* sring = ring + size_t(stages) * slot;
+  uint16_t* list = reinterpret_cast<uint16_t*>(sring + 3 * size_t(slot));
+  const int tid = threadIdx.x;
+  const int y0 = blockIdx.x * ty;
+  const int z0 = blockIdx.y * zlen, z1 = min(z0 + zlen, n);
+  const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
+  const uint32_t row_bytes = uint32_t(n) * 4u;
+  if (tid == 0) {
+    for (int k = 0; k < stages; ++k) mbar_init(bar + k, 1);
+    mbar_init_fence();
+    s_abort = 0;
+  }
+  __syncthreads();
+  // plane z0-1+j into slot j % stages (thread 0 only)
+  auto issue = [&](int j) {
+    float* dst = ring + size_t(j % stages) * slot;
+    uint64_t* b = bar + (j % stages);
+    const float* pl = rho + size_t(wrap(z0 - 1 + j, n)) * m.n2;
+    mbar_arrive_expect(b, uint32_t(ty + 2) * row_bytes);
+    bulk_load(dst, pl + size_t(wrap(y0 - 1, n)) * n, row_bytes, b);
+    bulk_load(dst + n, pl + size_t(y0) * n, uint32_t(ty) * row_bytes, b);
+    bulk_load(dst + size_t(ty + 1) * n, pl + size_t(wrap(y0 + ty, n)) * n, row_bytes, b);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < stages && issued < nplanes; ++issued) issue(issued);
+  // waits for plane j and takes its s into sring[j % 3]; false after a timeout
+  auto take_s = [&](int j) {
+    if (!mbar_wait(bar + (j % stages), uint32_t(j / stages) & 1u, SB_WAIT_LIMIT)) {
+      atomicOr(err, ERR_TIMEOUT);
+      s_abort = 1;
+      return;
+    }
+    const float4* src = reinterpret_cast<const float4*>(ring + size_t(j % stages) * slot);
+    float4* dst = reinterpret_cast<float4*>(sring + size_t(j % 3) * slot);
+    for (int g = tid; g < slot / 4; g += SB_THREADS) {
+      const float4 r = src[g];
+      dst[g] = make_float4(s_of(r.x, fl), s_of(r.y, fl), s_of(r.z, fl), s_of(r.w, fl));
+    }
+  };
+  take_s(0);
+  take_s(1);
+  ff ksum = {0.0f, 0.0f};  // K_rho terms of this thread
+  const int groups = ty * n / 4;
+  for (int z = z0; z < z1; ++z) {
+    const int jc = z - z0 + 1;  // plane z in ring numbering
+    take_s(jc + 1);
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    if (s_abort) break;
+    const float* Sm = sring + size_t((jc + 2) % 3) * slot;
+    const float* Sc = sring + size_t(jc % 3) * slot;
+    const float* Sp = sring + size_t((jc + 1) % 3) * slot;
+    for (int g = tid; g < groups; g += SB_THREADS) {
+      const int e = g * 4;
+      const int r = 1 + (lg >= 0 ? e >> lg : e / n), x = e - (r - 1) * n;
+      const int o = r * n + x;
+      const float4 c4 = *reinterpret_cast<const float4*>(Sc + o);
+      const float4 ym4 = *reinterpret_cast<const float4*>(Sc + o - n);
+      const float4 yp4 = *reinterpret_cast<const float4*>(Sc + o + n);
+      const float4 zm4 = *reinterpret_cast<const float4*>(Sm + o);
+      const float4 zp4 = *reinterpret_cast<const float4*>(Sp + o);
+      const float xl = Sc[r * n + (x == 0 ? n - 1 : x - 1)], xr = Sc[r * n + (x + 4 == n ? 0 : x + 4)];
+      const float sc[4] = {c4.x, c4.y, c4.z, c4.w}, sym[4] = {ym4.x, ym4.y, ym4.z, ym4.w};
+      const float syp[4] = {yp4.x, yp4.y, yp4.z, yp4.w}, szm[4] = {zm4.x, zm4.y, zm4.z, zm4.w};
+      const float szp[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
+      float qv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float sxm = k ? sc[k - 1] : xl, sxp = k < 3 ? sc[k + 1] : xr;
+        const float dxp = sxp - sc[k], dyp = syp[k] - sc[k], dzp = szp[k] - sc[k];
+        const float lap = (dxp + (sxm - sc[k])) + (dyp + (sym[k] - sc[k])) + (dzp + (szm[k] - sc[k]));
+        qv[k] = __fdividef(qc * lap, sc[k]);
+        if (diag) ff_accumulate(ksum, krho_term(dxp, dyp, dzp));
+        if (sc[k] < slim) {
+          if (!((sxp == sc[k]) & (sxm == sc[k]) & (syp[k] == sc[k]) & (sym[k] == sc[k]) & (szp[k] == sc[k]) &
+                (szm[k] == sc[k])))
+            list[atomicAdd(&s_cnt, 1u)] = uint16_t(e + k);
+        }
+      }
+      *reinterpret_cast<float4*>(q + size_t(z) * m.n2 + size_t(y0) * n + e) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+    }
+    __syncthreads();
+    // near-empty nodes of this plane, from the densities of planes z-1, z, z+1
+    const uint32_t cnt = s_cnt;
+    if (cnt) {
+      const float* Rm = ring + size_t((jc - 1) % stages) * slot;
+      const float* Rc = ring + size_t(jc % stages) * slot;
+      const float* Rp = ring + size_t((jc + 1) % stages) * slot;
+      for (uint32_t i = tid; i < cnt; i += SB_THREADS) {
+        const int e = list[i];
+        const int r = 1 + (lg >= 0 ? e >> lg : e / n), x = e - (r - 1) * n;
+        const int o = r * n + x;
+        const float v = q_ext(Rc[o], Rc[r * n + (x + 1 == n ? 0 : x + 1)], Rc[r * n + (x == 0 ? n - 1 : x - 1)],
+                              Rc[o + n], Rc[o - n], Rp[o], Rm[o], fl, qc);
+        q[size_t(z) * m.n2 + size_t(y0) * n + e] = v;
+      }
+    }
+    __syncthreads();  // the slot of plane z-1 and the list are free again
+    if (tid == 0 && issued < nplanes) issue(issued++);
+  }
+  // after a timeout: let the copies still in flight land before the block exits
+  if (s_abort && tid == 0)
+    for (int j = (issued > stages ? issued - stages : 0); j < issued; ++j)
+      mbar_wait(bar + (j % stages), uint32_t(j / stages) & 1u, SB_WAIT_LIMIT);
+  if (diag) {
+    const ff acc[1] = {fast_two_sum(ksum.hi, ksum.lo)};
+    block_sum_store_ff<1>(acc, part, gridDim.x * gridDim.y, int(blockIdx.y * gridDim.x + blockIdx.x));
+  }
+}
+
+// fp32 compact stencil, one tile per block with no sweep: a block owns `ty`
+// whole rows of `tz` planes and requests its whole input tile at once (the
+// (ty+2) x (tz+2) rows with halos, three bulk copies per plane, one mbarrier),
+// takes s in place, then evaluates Q~ of the interior from shared memory.  The
+// input of several resident blocks is in flight together and nothing waits
+// on a plane-by-plane chain.  Near-empty nodes go to the block's region of a
+// global list and are redone in float-float (densities reread through L2).
+// Per node the arithmetic is that of k_stencil_tiled (same bits).
+static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float* __restrict__ rho, Mesh m, float fl,
+                                                                    float qc, float slim, int ty, int tz,
+                                                                    float* __restrict__ q, uint32_t* list,
+                                                                    double* part, uint32_t* err, int diag) {
+  extern __shared__ __align__(16) unsigned char st_smem[];
+  __shared__ uint32_t s_cnt;
+  __shared__ int s_ok;
+  const int n = m.n, lg = m.log2n;
+  const int row = n, plane = (ty + 2) * n;  // floats
+  uint64_t* bar = reinterpret_cast<uint64_t*>(st_smem);
+  float* S = reinterpret_cast<float*>(st_smem + 16);
+  const int tid = threadIdx.x;
+  const int y0 = blockIdx.x * ty;
+  const int z0 = blockIdx.y * tz, nz = min(tz, n - z0);  // planes of this tile
+  const uint32_t blin = blockIdx.y * gridDim.x + blockIdx.x;
+  uint32_t* my_list = list + size_t(blin) * size_t(ty) * tz * n;
+  const uint32_t row_bytes = uint32_t(n) * 4u;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+    s_cnt = 0;
+    s_ok = 1;
+    mbar_arrive_expect(bar, uint32_t(nz + 2) * uint32_t(ty + 2) * row_bytes);
+    for (int j = 0; j < nz + 2; ++j) {
+      const float* pl = rho + size_t(wrap(z0 - 1 + j, n)) * m.n2;
+      float* dst = S + size_t(j) * plane;
+      bulk_load(dst, pl + size_t(wrap(y0 - 1, n)) * n, row_bytes, bar);
+      bulk_load(dst + row, pl + size_t(y0) * n, uint32_t(ty) * row_bytes, bar);
+      bulk_load(dst + size_t(ty + 1) * row, pl + size_t(wrap(y0 + ty, n)) * n, row_bytes, bar);
+    }
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, 0, SB_WAIT_LIMIT)) {
+    atomicOr(err, ERR_TIMEOUT);
+    s_ok = 0;
+  }
+  __syncthreads();
+  if (!s_ok) {  // the copies may still land: wait for them (bounded) before the block exits
+    if (tid == 0) mbar_wait(bar, 0, SB_WAIT_LIMIT);
+    return;
+  }
+  // s in place
+  float4* S4 = reinterpret_cast<float4*>(S);
+  const int all4 = (nz + 2) * plane / 4;
+  for (int g = tid; g < all4; g += SB_THREADS) {
+    const float4 r = S4[g];
+    S4[g] = make_float4(s_of(r.x, fl), s_of(r.y, fl), s_of(r.z, fl), s_of(r.w, fl));
+  }
+  __syncthreads();
+  ff ksum = {0.0f, 0.0f};
+  const int rows_in = nz * ty;  // interior rows, plane-major
+  const int groups = rows_in * n / 4;
+  for (int g = tid; g < groups; g += SB_THREADS) {
+    const int e = g * 4;                                 // interior element, (plane, row, x)
+    const int ri = lg >= 0 ? e >> lg : e / n;           // interior row index
+    const int x = e - ri * n;
+    const int pz = ri / ty, r = ri - pz * ty;            // plane and row inside the tile
+    const int o = (pz + 1) * plane + (r + 1) * row + x;
+    const float4 c4 = *reinterpret_cast<const float4*>(S + o);
+    const float4 ym4 = *reinterpret_cast<const float4*>(S + o - row);
+    const float4 yp4 = *reinterpret_cast<const float4*>(S + o + row);
+    const float4 zm4 = *reinterpret_cast<const float4*>(S + o - plane);
+    const float4 zp4 = *reinterpret_cast<const float4*>(S + o + plane);
+    const int ob = o - x;
+    const float xl = S[ob + (x == 0 ? n - 1 : x - 1)], xr = S[ob + (x + 4 == n ? 0 : x + 4)];
+    const float sc[4] = {c4.x, c4.y, c4.z, c4.w}, sym[4] = {ym4.x, ym4.y, ym4.z, ym4.w};
+    const float syp[4] = {yp4.x, yp4.y, yp4.z, yp4.w}, szm[4] = {zm4.x, zm4.y, zm4.z, zm4.w};
+    const float szp[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
+    const uint32_t node0 = uint32_t(z0 + pz) * m.n2 + uint32_t(y0 + r) * uint32_t(n) + uint32_t(x);
+    float qv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float sxm = k ? sc[k - 1] : xl, sxp = k < 3 ? sc[k + 1] : xr;
+      const float dxp = sxp - sc[k], dyp = syp[k] - sc[k], dzp = szp[k] - sc[k];
+      const float lap = (dxp + (sxm - sc[k])) + (dyp + (sym[k] - sc[k])) + (dzp + (szm[k] - sc[k]));
+      qv[k] = __fdividef(qc * lap, sc[k]);
+      if (diag) ff_accumulate(ksum, krho_term(dxp, dyp, dzp));
+      if (sc[k] < slim) {
+        if (!((sxp == sc[k]) & (sxm == sc[k]) & (syp[k] == sc[k]) & (sym[k] == sc[k]) & (szp[k] == sc[k]) &
+              (szm[k] == sc[k])))
+          my_list[atomicAdd(&s_cnt, 1u)] = node0 + k;
+      }
+    }
+    *reinterpret_cast<float4*>(q + node0) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+  }
+  __syncthreads();
+  const uint32_t cnt = s_cnt;
+  for (uint32_t i = tid; i < cnt; i += SB_THREADS) {
+    const uint32_t node = my_list[i];
+    q[node] = q_ext_at(rho, node, m, fl, qc);
+  }
+  if (diag) {
+    const ff acc[1] = {fast_two_sum(ksum.hi, ksum.lo)};
+    block_sum_store_ff<1>(acc, part, gridDim.x * gridDim.y, int(blin));
+  }
 }
 
 // ---------------------------------------------------------------- S6: interpolate + kick + drift
@@ -835,9 +1125,10 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
 
 template <typename R>
 cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
-                           cudaStream_t s) {
+                           cudaStream_t s, int warps) {
   using V4 = typename VT<R>::v4;
-  const size_t smem = size_t(DEP_WARPS) * (m.n + 1) * sizeof(R);
+  if (warps < 1 || warps > DEP_WARPS) warps = DEP_WARPS;
+  const size_t smem = size_t(warps) * (m.n + 1) * sizeof(R);
   if (smem > 48 * 1024) {
     // once per device, for the largest mesh, so that no attribute call falls inside a stream capture
     static bool done[64];
@@ -850,8 +1141,8 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  const unsigned blocks = (m.n2 + DEP_WARPS - 1) / DEP_WARPS;
-  k_deposit<R><<<blocks, DEP_WARPS * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho);
+  const unsigned blocks = (m.n2 + warps - 1) / warps;
+  k_deposit<R><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho);
   return cudaGetLastError();
 }
 
@@ -867,7 +1158,9 @@ inline int stencil_zlen(int n) { return (n + ST_ZCH - 1) / ST_ZCH; }
 // entries of the near-empty node list (one region per stencil block)
 inline size_t stencil_list_len(int n) {
   const dim3 g = stencil_grid(n);
-  return size_t(g.x) * g.y * g.z * ST_X * ST_Y * stencil_zlen(n);
+  const size_t tiled = size_t(g.x) * g.y * g.z * ST_X * ST_Y * stencil_zlen(n);
+  const size_t tiles = size_t(n) * n * (n + 16);  // one-shot tiles, a ragged last tile included
+  return tiled > tiles ? tiled : tiles;
 }
 inline int stencil_blocks(int n) {
   const dim3 g = stencil_grid(n);
@@ -876,14 +1169,46 @@ inline int stencil_blocks(int n) {
 
 template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
-                           uint32_t* list_count, cudaStream_t s) {
+                           uint32_t* list_count, uint32_t* err, cudaStream_t s) {
   if (sizeof(R) == 4 && sp.step == 1) {
     // fp32 compact path: shared-memory tiles, near-empty nodes redone in float-float
+    const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;
+    if (sp.ty > 0 && sp.stages == 0 && stencil_tile_shape_ok(m.n, sp.ty, sp.zlen)) {
+      static bool done[64];
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64 || !done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(SB_SMEM_MAX));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done[dev] = true;
+      }
+      const dim3 g(unsigned(m.n / sp.ty), unsigned((m.n + sp.zlen - 1) / sp.zlen));
+      k_stencil_tile<<<g, SB_THREADS, stencil_tile_smem(m.n, sp.ty, sp.zlen), s>>>(
+          (const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, sp.ty, sp.zlen, (float*)q, list, part,
+          err, sp.diag);
+      return cudaGetLastError();
+    }
+    if (sp.ty > 0 && stencil_bulk_shape_ok(m.n, sp.ty, sp.zlen, sp.stages)) {
+      static bool done[64];  // the shared-memory opt-in, once per device (never inside a capture)
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64 || !done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(SB_SMEM_MAX));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done[dev] = true;
+      }
+      const dim3 g(unsigned(m.n / sp.ty), unsigned((m.n + sp.zlen - 1) / sp.zlen));
+      k_stencil_bulk<<<g, SB_THREADS, stencil_bulk_smem(m.n, sp.ty, sp.stages), s>>>(
+          (const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, sp.ty, sp.zlen, sp.stages, (float*)q,
+          part, err, sp.diag);
+      return cudaGetLastError();
+    }
     const dim3 g = stencil_grid(m.n), b(ST_X, ST_TY);
     const int zlen = stencil_zlen(m.n);
-    const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;
     k_stencil_tiled<<<g, b, 0, s>>>((const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, zlen, (float*)q,
-                                    list, list_count, part);
+                                    list, list_count, part, sp.diag);
   } else {
     k_stencil<R><<<MESH_GRID, MESH_THREADS, 0, s>>>(rho, m, sp, q, part);
   }
@@ -893,16 +1218,17 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
                         KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
-                        uint32_t* err, cudaStream_t s) {
+                        uint32_t* err, int threads, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   using V4 = typename VT<R>::v4;
-  const unsigned g = kick_blocks(n);
+  if (threads != 128 && threads != 256) threads = KICK_THREADS;
+  const unsigned g = kick_blocks(n, threads);
   if (kp.accel_out)
-    k_kick<R, 2><<<g, KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 2><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if (kp.diag)
-    k_kick<R, 1><<<g, KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 1><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else
-    k_kick<R, 0><<<g, KICK_THREADS, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 0><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   return cudaGetLastError();
 }
 

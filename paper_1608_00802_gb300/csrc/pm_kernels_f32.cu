@@ -38,7 +38,48 @@ cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, u
 }
 
 size_t stencil_list_entries(int n) { return stencil_list_len(n); }
-int stencil_block_count(int n) { return stencil_blocks(n); }
+
+int stencil_launch_blocks(int n, int ty, int zlen) {
+  if (ty <= 0) return stencil_blocks(n);
+  return (n / ty) * ((n + zlen - 1) / zlen);
+}
+
+// most blocks of any valid shape: one row per block, two planes (one-shot tiles)
+int stencil_max_blocks(int n) {
+  const int most = n * ((n + 1) / 2);
+  return most > stencil_blocks(n) ? most : stencil_blocks(n);
+}
+
+bool stencil_shape_ok(int n, int ty, int zlen, int stages) {
+  if (ty == 0) return true;
+  return stages == 0 ? stencil_tile_shape_ok(n, ty, zlen) : stencil_bulk_shape_ok(n, ty, zlen, stages);
+}
+
+Tuning default_tuning(int n) {
+  Tuning t;
+  t.kick_threads = KICK_THREADS;
+  t.dep_warps = 8;
+  // one-shot tiles of 4 rows x 4 planes where they fit (the multiple-of-4 meshes up to 1024)
+  if (stencil_tile_shape_ok(n, 4, 4)) {
+    t.st_ty = 4;
+    t.st_zlen = 4;
+    t.st_stages = 0;
+    return t;
+  }
+  t.st_ty = n <= 256 ? 4 : (n <= 512 ? 2 : 1);
+  t.st_zlen = n < 16 ? n : 16;
+  t.st_stages = 6;
+  while (t.st_ty > 0 && !stencil_bulk_shape_ok(n, t.st_ty, t.st_zlen, t.st_stages)) {
+    if (t.st_stages > 4) {
+      --t.st_stages;
+    } else {
+      t.st_ty >>= 1;
+      t.st_stages = 6;
+    }
+  }
+  if (t.st_ty == 0) t.st_zlen = t.st_stages = 0;  // the register-column kernel
+  return t;
+}
 
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s) {
   if (nvals <= 0) return cudaSuccess;

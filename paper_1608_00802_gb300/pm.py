@@ -28,7 +28,7 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
            "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error",
            "pm_batch_arena_bytes", "pm_batch_create", "pm_batch_destroy", "pm_batch_member", "pm_batch_run",
-           "pm_batch_last_error"]
+           "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune"]
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
@@ -42,6 +42,21 @@ class pm_config(C.Structure):
                 ("h", C.c_double), ("m22", C.c_double), ("quantum", C.c_int32),
                 ("force_mode", C.c_int32), ("lap", C.c_int32), ("cosmological", C.c_int32),
                 ("rho_floor", C.c_double), ("rho_fp64", C.c_double)]
+
+
+class pm_tuning(C.Structure):
+    _fields_ = [("stencil_rows", C.c_int32), ("stencil_planes", C.c_int32), ("stencil_stages", C.c_int32),
+                ("kick_threads", C.c_int32), ("deposit_warps", C.c_int32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        for name, _ in cls._fields_:
+            setattr(t, name, int(d[name]))
+        return t
 
 
 class PMError(RuntimeError):
@@ -84,6 +99,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_batch_member": (vp, [vp, C.c_int32]),
         "pm_batch_run": (C.c_int, [vp, C.c_int32, dp, dp]),
         "pm_batch_last_error": (C.c_char_p, [vp]),
+        "pm_get_tuning": (C.c_int, [vp, C.POINTER(pm_tuning)]),
+        "pm_set_tuning": (C.c_int, [vp, C.POINTER(pm_tuning)]),
+        "pm_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(pm_tuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -122,6 +140,33 @@ def make_config(n_part, n_mesh, box, precision=FP32, omega_m=0.3, omega_l=0.7, h
 
 def arena_bytes(cfg: pm_config) -> int:
     return int(lib().pm_arena_bytes(C.byref(cfg)))
+
+
+def tuning_key(cfg: pm_config) -> str:
+    """Configurations with the same key share launch shapes."""
+    return "n%d_N%d_p%d_q%d_f%d_l%d" % (cfg.n_part, cfg.n_mesh, cfg.precision, cfg.quantum, cfg.force_mode, cfg.lap)
+
+
+class TuningCache(dict):
+    """Autotuner results by configuration key, optionally kept in a JSON file
+    (written after every new entry)."""
+
+    def __init__(self, path=None):
+        super().__init__()
+        self.path = path
+        if path and os.path.exists(path):
+            import json
+            with open(path) as fh:
+                self.update(json.load(fh))
+
+    def __setitem__(self, key, value):
+        super().__setitem__(key, dict(value))
+        if self.path:
+            import json
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(dict(self), fh, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
 
 
 class Sim:
@@ -239,6 +284,29 @@ class Sim:
         self._check(lib().pm_get_order(self.handle, cell.ctypes.data_as(C.POINTER(C.c_uint32)),
                                        ids.ctypes.data_as(C.POINTER(C.c_uint32))))
         return cell, ids
+
+    def get_tuning(self):
+        t = pm_tuning()
+        self._check(lib().pm_get_tuning(self.handle, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, shapes):
+        t = pm_tuning.from_dict(shapes)
+        self._check(lib().pm_set_tuning(self.handle, C.byref(t)))
+
+    def autotune(self, reps=5, cache=None):
+        """Launch shapes for this simulation: taken from `cache` (a TuningCache)
+        when it holds this configuration, else measured on the current state
+        (particles must be set) and stored there.  Returns the shapes."""
+        key = tuning_key(self.cfg)
+        if cache is not None and key in cache:
+            self.set_tuning(cache[key])
+            return cache[key]
+        t = pm_tuning()
+        self._check(lib().pm_autotune(self.handle, int(reps), C.byref(t)))
+        if cache is not None:
+            cache[key] = t.as_dict()
+        return t.as_dict()
 
     def profile_begin(self, capacity):
         self._check(lib().pm_profile_begin(self.handle, int(capacity)))

@@ -30,6 +30,9 @@ def main():
     ap.add_argument("--mode", choices=["meshgrad", "hybrid", "lagrangian"], default="hybrid")
     ap.add_argument("--rho-fp64", type=float, default=1e-2,
                     help="density below which Q is recomputed in extended precision (0: never)")
+    ap.add_argument("--tuning", default=None, help="launch shapes as JSON (pm_tuning fields), e.g. "
+                    "'{\"stencil_rows\": 8, \"stencil_planes\": 8, \"stencil_stages\": 4}'")
+    ap.add_argument("--autotune", action="store_true", help="measure the launch shapes first")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -43,6 +46,11 @@ def main():
                          precision=pm.FP64 if args.precision == "fp64" else pm.FP32, rho_fp64=args.rho_fp64)
     sim = pm.Sim(cfg)
     sim.set_particles(x, p)
+    if args.tuning:
+        sim.set_tuning(dict(sim.get_tuning(), **json.loads(args.tuning)))
+    if args.autotune:
+        sim.autotune()
+    print(json.dumps({"tuning": sim.get_tuning()}))
     a = a0 * (a1 / a0) ** (np.arange(args.nsteps + 1) / args.nsteps)
     if args.start:
         sim.run(args.start, a[0], a[args.start])
