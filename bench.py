@@ -293,6 +293,12 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     sim = pm.Sim(cfg, stream=stream)
     sim.set_particles(x, p)
+    # launch shapes measured on this simulation (untimed), or given
+    if args.tuning:
+        sim.set_tuning(dict(sim.get_tuning(), **json.loads(args.tuning)))
+        tuning = sim.get_tuning()
+    else:
+        tuning = sim.autotune(reps=5)
     # warm-up steps (untimed): the first W steps of the schedule
     with torch.cuda.stream(stream):
         if W > 0:
@@ -413,6 +419,7 @@ def run_gpu(args):
                        "force_mode": "hybrid (PM gravity + Q by the kernel gradient, Sec. II.A step iii)", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.5 GB touched per step), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "launch_shapes": tuning,
             "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "batched": batched, "served": served,
             "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None}
     print(json.dumps(line))
@@ -442,8 +449,10 @@ def run_batched(pm, ics, K, W, stream):
     cfgs = [pm.make_config(n ** 3, nm, box, precision=pm.FP32, m22=m22, force_mode=pm.FORCE_HYBRID)
             for n, nm, box, m22, _ in members]
     batch = pm.Batch(cfgs, stream=stream)
+    cache = pm.TuningCache()  # one autotuner run per member size, shared by the others (untimed)
     for mem, (n, nm, box, m22, seed) in zip(batch.members, members):
         mem.set_particles(*ics.zeldovich(n, nm, box, a[0], seed, m22=m22))
+        mem.autotune(reps=5, cache=cache)
     with torch.cuda.stream(stream):
         if W > 0:
             batch.run(W, a[0], a[W])
@@ -477,7 +486,9 @@ def run_served(serve, n_requests):
     reqs = serve.request_stream(n_requests, rate=SERVE["rate"], seed=0)
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         initial = dict(zip([r.rid for r in reqs], pool.map(_initial_conditions, reqs)))
-    srv = serve.Server(SERVE["budget"], max_slots=64, chunk_steps=SERVE["chunk"])
+    # launch shapes of each request size, measured before the stream (untimed)
+    cache = serve.tune_sizes(sorted({(r.n_side, r.n_mesh) for r in reqs}))
+    srv = serve.Server(SERVE["budget"], max_slots=64, chunk_steps=SERVE["chunk"], tuning=cache)
     res = srv.run(reqs, realtime=True, initial=initial)
     lat = serve.latency_percentiles(res)
     offered = SERVE["rate"] * float(np.mean([r.n_side ** 3 * r.nsteps for r in reqs]))
@@ -498,6 +509,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--tuning", default=None, help="launch shapes (pm_tuning fields as JSON) instead of the "
+                    "autotuner's, for the single simulation")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("steps >= 1, warmup >= 0")

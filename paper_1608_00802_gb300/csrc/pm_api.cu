@@ -322,7 +322,8 @@ int kr_blocks(const pm_sim* s) {
 // Incremental re-sort after a drift: the stayers are still in order, so the
 // movers are split off (stable partition), radix-sorted by (key, previous
 // slot) with their count known only on the device, and merged back; the merge
-// gathers the records into the other buffer.  Same order as the full sort.
+// gathers the records into the other buffer and writes the row starts.  Same
+// order as the full sort.
 template <typename R>
 pm_status resort_movers(pm_sim* s) {
   const Layout& L = s->L;
@@ -360,14 +361,11 @@ pm_status resort_movers(pm_sim* s) {
   {
     PROF(s, PM_STAGE_SORT_MERGE);
     CU(s, launch_merge_gather<R>(sk, sv, mk[b], mv[b], counts, n, s->keys, s->pos(), s->mom(),
-                                 s->arena + L.pos[nxt], s->arena + L.mom[nxt], s->stream));
+                                 s->arena + L.pos[nxt], s->arena + L.mom[nxt], uint32_t(s->cfg.n_mesh),
+                                 s->at<uint32_t>(L.row_start), s->stream));
   }
   s->cur = nxt;
   s->keys_marked = false;
-  {
-    PROF(s, PM_STAGE_ROW_START);
-    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->stream));
-  }
   s->sorted = true;
   return PM_OK;
 }

@@ -11,7 +11,7 @@
                                            uint32_t*, cudaStream_t, const uint32_t*);                             \
   template cudaError_t launch_merge_gather<R>(const uint32_t*, const uint32_t*, const uint32_t*, const uint32_t*, \
                                               const uint32_t*, int64_t, uint32_t*, const void*, const void*,      \
-                                              void*, void*, cudaStream_t);                                        \
+                                              void*, void*, uint32_t, uint32_t*, cudaStream_t);                   \
   template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t, int);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
   template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,       \

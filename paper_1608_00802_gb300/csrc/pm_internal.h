@@ -103,7 +103,8 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
 // incremental re-sort after a drift (keys carry KEY_MOVER): per-tile mover
 // counts + their scan (counts[0] = stayers, counts[1] = movers), stable
 // partition into stayers (s_keys, s_vals) and movers (m_keys, m_vals), and
-// the merge of stayers with the sorted movers that gathers the records
+// the merge of stayers with the sorted movers that gathers the records and
+// writes the row starts
 cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint32_t* tile_cnt, uint32_t* counts,
                                    uint32_t* s_keys, uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals,
                                    cudaStream_t s);
@@ -111,7 +112,7 @@ template <typename R>
 cudaError_t launch_merge_gather(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
                                 const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,
                                 const void* pos_in, const void* mom_in, void* pos_out, void* mom_out,
-                                cudaStream_t s);
+                                uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);
 cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s);
 cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start,
                              cudaStream_t s);

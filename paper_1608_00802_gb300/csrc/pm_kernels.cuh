@@ -464,19 +464,48 @@ __device__ __forceinline__ float s_of(float r, float fl) {
   return x * rsqrtf(x);
 }
 
-__device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_t node, const Mesh& m, float fl,
-                                          float qc) {
+// the seven densities of a node: centre, x+, x-, y+, y-, z+, z-
+__device__ __forceinline__ void load7(const float* __restrict__ rho, uint32_t node, const Mesh& m, float (&r)[7]) {
   int x, y, z;
   split_cell(node, m, x, y, z);
   const int n = m.n;
   const uint32_t zn = uint32_t(z) * m.n2, yn = uint32_t(y) * uint32_t(n);
-  const float r0 = __ldg(rho + node);
-  const float rxp = __ldg(rho + zn + yn + wrap(x + 1, n)), rxm = __ldg(rho + zn + yn + wrap(x - 1, n));
-  const float ryp = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
-  const float rym = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
-  const float rzp = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
-  const float rzm = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
-  return q_ext(r0, rxp, rxm, ryp, rym, rzp, rzm, fl, qc);
+  r[0] = __ldg(rho + node);
+  r[1] = __ldg(rho + zn + yn + wrap(x + 1, n));
+  r[2] = __ldg(rho + zn + yn + wrap(x - 1, n));
+  r[3] = __ldg(rho + zn + uint32_t(wrap(y + 1, n)) * n + x);
+  r[4] = __ldg(rho + zn + uint32_t(wrap(y - 1, n)) * n + x);
+  r[5] = __ldg(rho + uint32_t(wrap(z + 1, n)) * m.n2 + yn + x);
+  r[6] = __ldg(rho + uint32_t(wrap(z - 1, n)) * m.n2 + yn + x);
+}
+
+__device__ __forceinline__ float q_ext_at(const float* __restrict__ rho, uint32_t node, const Mesh& m, float fl,
+                                          float qc) {
+  float r[7];
+  load7(rho, node, m, r);
+  return q_ext(r[0], r[1], r[2], r[3], r[4], r[5], r[6], fl, qc);
+}
+
+// the float-float pass over a block's list of near-empty nodes, two nodes per
+// thread at a time (their loads and dependent chains overlap)
+__device__ __forceinline__ void q_ext_list(const float* __restrict__ rho, const uint32_t* list, uint32_t cnt,
+                                           const Mesh& m, float fl, float qc, float* __restrict__ q, int tid,
+                                           int nthreads) {
+  uint32_t i = tid;
+  for (; i + nthreads < cnt; i += 2 * nthreads) {
+    const uint32_t a = list[i], b = list[i + nthreads];
+    float ra[7], rb[7];
+    load7(rho, a, m, ra);
+    load7(rho, b, m, rb);
+    const float qa = q_ext(ra[0], ra[1], ra[2], ra[3], ra[4], ra[5], ra[6], fl, qc);
+    const float qb = q_ext(rb[0], rb[1], rb[2], rb[3], rb[4], rb[5], rb[6], fl, qc);
+    q[a] = qa;
+    q[b] = qb;
+  }
+  if (i < cnt) {
+    const uint32_t a = list[i];
+    q[a] = q_ext_at(rho, a, m, fl, qc);
+  }
 }
 
 static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const float* __restrict__ rho, Mesh m,
@@ -560,10 +589,7 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
   }
   // near-empty nodes of this block, recomputed in float-float
   const uint32_t cnt = s_cnt;
-  for (uint32_t i = tid; i < cnt; i += ST_X * ST_TY) {
-    const uint32_t node = my_list[i];
-    q[node] = q_ext_at(rho, node, m, fl, qc);
-  }
+  q_ext_list(rho, my_list, cnt, m, fl, qc, q, tid, ST_X * ST_TY);
   if (tid == 0) list_count[blin] = cnt;
   if (diag) {
     const ff acc[1] = {fast_two_sum(ksum.hi, ksum.lo)};
@@ -647,11 +673,13 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_bulk(const float*
     for (; issued < stages && issued < nplanes; ++issued) issue(issued);
   // waits for plane j and takes its s into sring[j % 3]; false after a timeout
   auto take_s = [&](int j) {
-    if (!mbar_wait(bar + (j % stages), uint32_t(j / stages) & 1u, SB_WAIT_LIMIT)) {
-      atomicOr(err, ERR_TIMEOUT);
+    // warp 0 polls the slot's mbarrier, the block barrier publishes the plane
+    if (tid < 32 && !mbar_wait(bar + (j % stages), uint32_t(j / stages) & 1u, SB_WAIT_LIMIT)) {
+      if (tid == 0) atomicOr(err, ERR_TIMEOUT);
       s_abort = 1;
-      return;
     }
+    __syncthreads();
+    if (s_abort) return;
     const float4* src = reinterpret_cast<const float4*>(ring + size_t(j % stages) * slot);
     float4* dst = reinterpret_cast<float4*>(sring + size_t(j % 3) * slot);
     for (int g = tid; g < slot / 4; g += SB_THREADS) {
@@ -745,7 +773,7 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
   extern __shared__ __align__(16) unsigned char st_smem[];
   __shared__ uint32_t s_cnt;
   __shared__ int s_ok;
-  const int n = m.n, lg = m.log2n;
+  const int n = m.n, lg = m.log2n, lty = __ffs(ty) - 1;  // ty is a power of two
   const int row = n, plane = (ty + 2) * n;  // floats
   uint64_t* bar = reinterpret_cast<uint64_t*>(st_smem);
   float* S = reinterpret_cast<float*>(st_smem + 16);
@@ -770,8 +798,10 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
     }
   }
   __syncthreads();
-  if (!mbar_wait(bar, 0, SB_WAIT_LIMIT)) {
-    atomicOr(err, ERR_TIMEOUT);
+  // warp 0 polls the mbarrier (its acquire, then the block barrier, publish
+  // the copied tile to every thread); the other warps sleep at the barrier
+  if (tid < 32 && !mbar_wait(bar, 0, SB_WAIT_LIMIT)) {
+    if (tid == 0) atomicOr(err, ERR_TIMEOUT);
     s_ok = 0;
   }
   __syncthreads();
@@ -794,7 +824,7 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
     const int e = g * 4;                                 // interior element, (plane, row, x)
     const int ri = lg >= 0 ? e >> lg : e / n;           // interior row index
     const int x = e - ri * n;
-    const int pz = ri / ty, r = ri - pz * ty;            // plane and row inside the tile
+    const int pz = ri >> lty, r = ri - (pz << lty);      // plane and row inside the tile
     const int o = (pz + 1) * plane + (r + 1) * row + x;
     const float4 c4 = *reinterpret_cast<const float4*>(S + o);
     const float4 ym4 = *reinterpret_cast<const float4*>(S + o - row);
@@ -824,11 +854,7 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
     *reinterpret_cast<float4*>(q + node0) = make_float4(qv[0], qv[1], qv[2], qv[3]);
   }
   __syncthreads();
-  const uint32_t cnt = s_cnt;
-  for (uint32_t i = tid; i < cnt; i += SB_THREADS) {
-    const uint32_t node = my_list[i];
-    q[node] = q_ext_at(rho, node, m, fl, qc);
-  }
+  q_ext_list(rho, my_list, s_cnt, m, fl, qc, q, tid, SB_THREADS);
   if (diag) {
     const ff acc[1] = {fast_two_sum(ksum.hi, ksum.lo)};
     block_sum_store_ff<1>(acc, part, gridDim.x * gridDim.y, int(blin));

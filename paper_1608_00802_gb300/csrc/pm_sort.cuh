@@ -426,14 +426,56 @@ __device__ __forceinline__ uint32_t merge_split(const uint32_t* sk, const uint32
 constexpr int MG_TILE = RS_TILE;  // outputs per block
 inline size_t merge_smem_bytes() { return size_t(MG_TILE) * 6 * sizeof(uint32_t); }
 
+// Both ends of the block's output range on the merge path, found by the two
+// halves of the block at once with a 128-way search: each round probes 128
+// evenly spaced candidates, so about three rounds (one dependent global load
+// each) narrow two million candidates to one.  Returns the number of stayers
+// before output d0 (split[0]) and d1 (split[1]).
+__device__ __forceinline__ void merge_split_block(const uint32_t* sk, const uint32_t* sv, uint32_t ns,
+                                                  const uint32_t* mk, const uint32_t* mv, uint32_t nm, uint32_t d0,
+                                                  uint32_t d1, uint32_t* lo_s, uint32_t* hi_s) {
+  const int grp = threadIdx.x >> 7, t = threadIdx.x & 127;
+  const uint32_t d = grp ? d1 : d0;
+  if (t == 0) {
+    lo_s[grp] = d > nm ? d - nm : 0u;
+    hi_s[grp] = d < ns ? d : ns;
+    lo_s[2 + grp] = 0u;
+    hi_s[2 + grp] = 0xffffffffu;
+  }
+  __syncthreads();
+  for (;;) {
+    const uint32_t lo = lo_s[grp], hi = hi_s[grp];
+    if (!__syncthreads_or(lo < hi)) break;
+    // candidate a in [lo, hi): are there more than a stayers before d?  (stayer a precedes mover d-1-a)
+    if (lo < hi) {
+      const uint32_t a = lo + uint32_t((uint64_t(hi - lo) * uint32_t(t)) >> 7);
+      const uint32_t j = d - 1 - a;
+      if (kv_less(sk[a], sv[a], mk[j], mv[j]))
+        atomicMax(lo_s + 2 + grp, a + 1);
+      else
+        atomicMin(hi_s + 2 + grp, a);
+    }
+    __syncthreads();
+    if (t == 0 && lo < hi) {
+      if (lo_s[2 + grp] > lo) lo_s[grp] = lo_s[2 + grp];
+      if (hi_s[2 + grp] < hi) hi_s[grp] = hi_s[2 + grp];
+      lo_s[2 + grp] = 0u;
+      hi_s[2 + grp] = 0xffffffffu;
+    }
+    __syncthreads();
+  }
+}
+
 // merge of the stayers with the sorted movers, by (key, previous slot); writes
-// the sorted keys and gathers the records of the previous slots
+// the sorted keys, gathers the records of the previous slots and fills the
+// row starts (row_start[r] = first slot whose key is in row r or above;
+// row_start[N^2] = n)
 template <typename V4>
 __global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
     const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ mk,
     const uint32_t* __restrict__ mv, const uint32_t* __restrict__ counts, int64_t n, uint32_t* __restrict__ keys_out,
     const V4* __restrict__ pos_in, const V4* __restrict__ mom_in, V4* __restrict__ pos_out,
-    V4* __restrict__ mom_out) {
+    V4* __restrict__ mom_out, uint32_t n_mesh, uint32_t* __restrict__ row_start) {
   extern __shared__ uint32_t msm[];
   uint32_t* a_k = msm;               // stayers of this tile
   uint32_t* a_v = a_k + MG_TILE;
@@ -441,13 +483,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
   uint32_t* b_v = b_k + MG_TILE;
   uint32_t* o_k = b_v + MG_TILE;     // merged
   uint32_t* o_v = o_k + MG_TILE;
-  __shared__ uint32_t split[2];
+  __shared__ uint32_t lo_s[4], hi_s[4];
+  __shared__ uint32_t prev_key;
   const uint32_t ns = counts[0], nm = counts[1];
   const uint32_t d0 = blockIdx.x * uint32_t(MG_TILE);
   const uint32_t d1 = int64_t(d0) + MG_TILE < n ? d0 + uint32_t(MG_TILE) : uint32_t(n);
-  if (threadIdx.x < 2) split[threadIdx.x] = merge_split(sk, sv, ns, mk, mv, nm, threadIdx.x ? d1 : d0);
-  __syncthreads();
-  const uint32_t a0 = split[0], a1 = split[1];
+  merge_split_block(sk, sv, ns, mk, mv, nm, d0, d1, lo_s, hi_s);
+  const uint32_t a0 = lo_s[0], a1 = lo_s[1];
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
   const uint32_t na = a1 - a0, nb = b1 - b0;
   for (uint32_t t = threadIdx.x; t < na; t += RS_THREADS) {
@@ -457,6 +499,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
   for (uint32_t t = threadIdx.x; t < nb; t += RS_THREADS) {
     b_k[t] = mk[b0 + t];
     b_v[t] = mv[b0 + t];
+  }
+  if (threadIdx.x == 0 && d0 > 0) {
+    // the key at output d0-1: the larger of the last stayer and the last mover before this tile
+    uint32_t k = 0, v = 0;
+    bool have = false;
+    if (a0 > 0) {
+      k = sk[a0 - 1];
+      v = sv[a0 - 1];
+      have = true;
+    }
+    if (b0 > 0 && (!have || kv_less(k, v, mk[b0 - 1], mv[b0 - 1]))) k = mk[b0 - 1];
+    prev_key = k;
   }
   __syncthreads();
   // each thread merges RS_ITEMS consecutive outputs of the tile
@@ -479,18 +533,28 @@ __global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
     }
   }
   __syncthreads();
-  for (uint32_t q = threadIdx.x; q < tn; q += RS_THREADS) {
-    const uint32_t src = o_v[q];
-    keys_out[d0 + q] = o_k[q];
-    pos_out[d0 + q] = pos_in[src];
-    mom_out[d0 + q] = mom_in[src];
+  for (uint32_t q = threadIdx.x; q <= tn; q += RS_THREADS) {
+    const uint32_t i = d0 + q;
+    if (q < tn) {
+      const uint32_t src = o_v[q];
+      keys_out[i] = o_k[q];
+      pos_out[i] = pos_in[src];
+      mom_out[i] = mom_in[src];
+    } else if (i != uint32_t(n)) {
+      break;  // output n (the closing row starts) belongs to the last block
+    }
+    // rows (row of output i-1, row of output i] start at i
+    const int64_t prev = i == 0 ? -1 : int64_t((q ? o_k[q - 1] : prev_key) / n_mesh);
+    const int64_t cur = i == uint32_t(n) ? int64_t(n_mesh) * n_mesh : int64_t(o_k[q] / n_mesh);
+    for (int64_t r = prev + 1; r <= cur; ++r) row_start[r] = i;
   }
 }
 
 template <typename R>
 cudaError_t launch_merge_gather(const uint32_t* sk, const uint32_t* sv, const uint32_t* mk, const uint32_t* mv,
                                 const uint32_t* counts, int64_t n, uint32_t* keys_out, const void* pos_in,
-                                const void* mom_in, void* pos_out, void* mom_out, cudaStream_t s) {
+                                const void* mom_in, void* pos_out, void* mom_out, uint32_t n_mesh,
+                                uint32_t* row_start, cudaStream_t s) {
   using V4 = typename VT<R>::v4;
   static bool done[64];
   int dev = 0;
@@ -504,7 +568,7 @@ cudaError_t launch_merge_gather(const uint32_t* sk, const uint32_t* sv, const ui
   const unsigned blocks = unsigned((n + MG_TILE - 1) / MG_TILE);
   k_merge_gather<V4><<<blocks, RS_THREADS, merge_smem_bytes(), s>>>(sk, sv, mk, mv, counts, n, keys_out,
                                                                     (const V4*)pos_in, (const V4*)mom_in,
-                                                                    (V4*)pos_out, (V4*)mom_out);
+                                                                    (V4*)pos_out, (V4*)mom_out, n_mesh, row_start);
   return cudaGetLastError();
 }
 

@@ -99,7 +99,7 @@ class Server:
     together; `run` returns one Result per request."""
 
     def __init__(self, hbm_budget_bytes, max_slots=64, chunk_steps=20, keep_particles=False, device="cuda",
-                 admit_threads=4):
+                 admit_threads=4, tuning=None):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
@@ -112,6 +112,9 @@ class Server:
         # admissions (arena, plans, upload and first sort) run on worker threads so that the
         # loop keeps feeding the running simulations meanwhile
         self.admit_threads = int(admit_threads)
+        # launch shapes by configuration (a pm.TuningCache): a size not yet in it is measured
+        # by the autotuner on its first admission
+        self.tuning = tuning
         self.stats = {"admitted": 0, "max_active": 0, "chunks": 0, "particle_steps": 0, "peak_bytes": 0}
 
     def _bytes(self, req):
@@ -124,6 +127,8 @@ class Server:
         sim = pm.Sim(req.config(), device=self.device, stream=stream)
         x, p = initial if initial is not None else initial_conditions(req)
         sim.set_particles(x, p)
+        if self.tuning is not None:
+            sim.autotune(cache=self.tuning)
         act = _Active(req, sim, stream, admitted=now)
         return act
 
@@ -218,6 +223,19 @@ class Server:
         pool.shutdown()
         self.stats["makespan"] = now()
         return [results[r.rid] for r in sorted(requests, key=lambda r: r.rid)]
+
+
+def tune_sizes(sizes, cache=None, m22=2.5, box=2.0):
+    """Autotuner results for (particles per side, mesh) pairs of the request
+    mix, measured on one sample simulation each; returns the cache."""
+    cache = pm.TuningCache() if cache is None else cache
+    for n_side, n_mesh in sizes:
+        req = Request(-1, n_side, n_mesh, box, m22, 0)
+        sim = pm.Sim(req.config())
+        sim.set_particles(*initial_conditions(req))
+        sim.autotune(cache=cache)
+        sim.close()
+    return cache
 
 
 def initial_conditions(req):
