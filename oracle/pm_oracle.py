@@ -140,7 +140,7 @@ def half_point(a0, a1, cfg: Config) -> float:
 
 
 # --------------------------------------------------------------------------
-# (S0) cell keys and order
+# cell keys and order
 # --------------------------------------------------------------------------
 def cell_index(x, cfg: Config):
     """Integer cell (ix, iy, iz) = floor(x/dx) per dimension, periodic."""

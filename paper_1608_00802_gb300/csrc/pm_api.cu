@@ -133,6 +133,9 @@ bool valid_config(const pm_config* c, std::string* why) {
   return true;
 }
 
+// digit histograms and tile counters of a sort
+constexpr size_t hist_bytes() { return (3 * (size_t(1) << RS_MAX_BITS) + 4) * 4; }
+
 Layout make_layout(const pm_config& c, size_t work_bytes) {
   Layout L;
   const size_t n = size_t(c.n_part), N = size_t(c.n_mesh), n3 = N * N * N;
@@ -155,7 +158,7 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   for (int k = 0; k < 2; ++k) L.mom[k] = take(n * recsz);
   for (int k = 0; k < 4; ++k) L.keys[k] = take(n * 4);
   for (int k = 0; k < 3; ++k) L.vals[k] = take(n * 4);
-  L.tile_cnt = take((size_t(L.ntiles) + 2) * 4);  // movers per tile, then (stayers, movers)
+  L.tile_cnt = take(16);  // (stayers, movers) of the last re-sort
   L.row_start = take((N * N + 1) * 4);
   L.rho = take(n3 * rsz);
   L.phi = take(n3 * rsz);
@@ -165,8 +168,9 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   size_t stage = 6 * n * 8;
   if (n3 * 8 > stage) stage = n3 * 8;
   L.staging = take(stage);
-  // digit histograms of all passes (radix_max stride) + one tile counter per pass
-  L.hist = take((3 * (size_t(1) << RS_MAX_BITS) + 4) * 4);
+  // digit histograms of all passes (radix_max stride), one tile counter per pass
+  // (+ the partition's), then the partition's status word per tile
+  L.hist = take(hist_bytes() + size_t(L.ntiles) * 8);
   L.status = take((size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8);
   size_t nkb = size_t(kick_blocks(int64_t(n), KICK_MIN_THREADS));
   size_t npart = 4 * nkb;
@@ -223,6 +227,7 @@ struct pm_sim {
   uint32_t* keys_tmp[2];
   bool keys_marked = false;  // a drift has flagged the movers in `keys` since the last sort
   Tuning tune;                // launch shapes
+  int sms = 152;              // multiprocessors of the device
   bool krho_valid = false;    // the K_rho partials belong to the current Q~
   cufftHandle plan_fwd, plan_inv;
   bool have_particles, sorted, fields_valid;
@@ -331,21 +336,18 @@ pm_status resort_movers(pm_sim* s) {
   uint32_t* hist = s->at<uint32_t>(L.hist);
   uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
   uint64_t* status = s->at<uint64_t>(L.status);
-  uint32_t* tcnt = s->at<uint32_t>(L.tile_cnt);
-  uint32_t* counts = tcnt + L.ntiles;
+  uint32_t* counts = s->at<uint32_t>(L.tile_cnt);
+  uint64_t* pstatus = reinterpret_cast<uint64_t*>(s->arena + L.hist + hist_bytes());
   uint32_t* sk = s->keys_tmp[0];
   uint32_t* sv = s->at<uint32_t>(L.vals[0]);
   uint32_t* mk[2] = {s->keys_tmp[1], s->at<uint32_t>(L.keys[3])};
   uint32_t* mv[2] = {s->at<uint32_t>(L.vals[1]), s->at<uint32_t>(L.vals[2])};
-  CU(s, cudaMemsetAsync(hist, 0, (3 * (size_t(1) << RS_MAX_BITS) + 4) * 4, s->stream));
+  // histograms, tile counters and the partition's status words start at zero
+  CU(s, cudaMemsetAsync(hist, 0, hist_bytes() + size_t(L.ntiles) * 8, s->stream));
   {
     PROF(s, PM_STAGE_SORT_PARTITION);
-    CU(s, launch_mover_partition(s->keys, n, tcnt, counts, sk, sv, mk[0], mv[0], s->stream));
-  }
-  {
-    PROF(s, PM_STAGE_SORT_HISTOGRAM);
-    CU(s, launch_sort_histogram(mk[0], n, L.passes, L.digit_bits, L.key_bits, hist, s->errword() + 1, s->stream,
-                                counts + 1));
+    CU(s, launch_mover_partition(s->keys, n, pstatus, counters + 3, sk, sv, mk[0], mv[0], counts, hist, L.passes,
+                                 L.digit_bits, L.key_bits, s->errword() + 1, s->errword(), s->stream));
   }
   int b = 0;
   for (int p = 0; p < L.passes; ++p) {
@@ -379,7 +381,7 @@ pm_status sort_particles(pm_sim* s) {
   uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
   uint64_t* status = s->at<uint64_t>(L.status);
   uint32_t* vals[2] = {s->at<uint32_t>(L.vals[0]), s->at<uint32_t>(L.vals[1])};
-  CU(s, cudaMemsetAsync(hist, 0, (3 * (size_t(1) << RS_MAX_BITS) + 4) * 4, s->stream));
+  CU(s, cudaMemsetAsync(hist, 0, hist_bytes(), s->stream));
   {
     PROF(s, PM_STAGE_SORT_HISTOGRAM);
     CU(s, launch_sort_histogram(s->keys, n, L.passes, L.digit_bits, L.key_bits, hist, s->errword() + 1, s->stream));
@@ -775,6 +777,12 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
   s->keys_tmp[1] = s->at<uint32_t>(L.keys[2]);
   s->have_particles = s->sorted = s->fields_valid = false;
   s->tune = default_tuning(N);
+  {
+    int dev = 0, sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sm > 0)
+      s->sms = sm;
+  }
   cufftType fwd = c->precision == PM_FP64 ? CUFFT_D2Z : CUFFT_R2C;
   cufftType inv = c->precision == PM_FP64 ? CUFFT_Z2D : CUFFT_C2R;
   cufftHandle* plans[2] = {&s->plan_fwd, &s->plan_inv};

@@ -100,14 +100,15 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
                              const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
                              const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
                              cudaStream_t s, const uint32_t* n_dev = nullptr);
-// incremental re-sort after a drift (keys carry KEY_MOVER): per-tile mover
-// counts + their scan (counts[0] = stayers, counts[1] = movers), stable
-// partition into stayers (s_keys, s_vals) and movers (m_keys, m_vals), and
-// the merge of stayers with the sorted movers that gathers the records and
-// writes the row starts
-cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint32_t* tile_cnt, uint32_t* counts,
+// incremental re-sort after a drift (keys carry KEY_MOVER): stable partition
+// into stayers (s_keys, s_vals) and movers (m_keys, m_vals) in one pass with
+// the movers' digit histograms (pstatus: one cleared word per tile; counts[0]
+// = stayers, counts[1] = movers), then the merge of stayers with the sorted
+// movers that gathers the records and writes the row starts
+cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint64_t* pstatus, uint32_t* tile_counter,
                                    uint32_t* s_keys, uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals,
-                                   cudaStream_t s);
+                                   uint32_t* counts, uint32_t* hist, int passes, int digit_bits, int key_bits,
+                                   uint32_t* sort_epoch, uint32_t* err, cudaStream_t s);
 template <typename R>
 cudaError_t launch_merge_gather(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
                                 const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,

@@ -212,7 +212,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* part, i
   }
 }
 
-// ---------------------------------------------------------------- S0: load + keys
+// ---------------------------------------------------------------- load + cell keys
 template <typename R>
 __global__ void k_init_particles(const double* __restrict__ x, const double* __restrict__ p, int64_t n, Mesh m,
                                  double inv_dx, typename VT<R>::v4* pos, typename VT<R>::v4* mom,
@@ -247,7 +247,7 @@ __global__ void k_init_particles(const double* __restrict__ x, const double* __r
   keys[i] = cell;
 }
 
-// ---------------------------------------------------------------- S1: deposit
+// ---------------------------------------------------------------- cloud-in-cell deposit
 // rho_n = norm * sum_i W(x_n - q_i): Eq. (rhodis) with the cloud-in-cell
 // tent, no floating-point atomics.  One warp owns one mesh row (z, y) and
 // keeps it in shared memory (N + 1 slots, slot N = node 0 seen from cell
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
   for (int i = lane; i < n; i += 32) out[i] = acc[i] * norm;
 }
 
-// ---------------------------------------------------------------- S3: Green's function
+// ---------------------------------------------------------------- Green's function
 __device__ __forceinline__ float sinpi_sq(float t) {
   float s = sinpif(t);
   return s * s;
@@ -334,8 +334,56 @@ __device__ __forceinline__ double sinpi_sq(double t) {
 // inverse-FFT normalisation folded in; k = 0 set to zero.  Also accumulates
 // sum_n rho_n phi_n = sum_k w_k G_k |rho^_k|^2 (Parseval over the half spectrum,
 // w = 1 on the x = 0 and x = N/2 planes, 2 elsewhere) for W_g.
+// e / d for every 32-bit e, by the multiply-high method for invariant divisors
+// (Granlund & Montgomery 1994): mul = 2^32 (2^l - d) / d + 1, l = ceil(log2 d)
+struct DivU32 {
+  uint32_t mul;
+  int l;
+};
+inline DivU32 divu32_make(uint32_t d) {
+  int l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  DivU32 r;
+  r.mul = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+  r.l = l;
+  return r;
+}
+__device__ __forceinline__ uint32_t divu32(uint32_t e, DivU32 dv) {
+  if (dv.l == 0) return e;
+  const uint32_t t = __umulhi(dv.mul, e);
+  return (t + ((e - t) >> 1)) >> (dv.l - 1);
+}
+
+// phi^ = -(3/2) Omega_m rho^ / kappa^2 in place over the half spectrum, with
+// kappa^2 = (4/dx^2) sum_d sin^2(k_d dx/2) the exact symbol of the seven-point
+// Laplacian (the comoving Poisson equation of Sec. II), and the Parseval
+// partial of W_g.  Flat over the n^2 (n/2+1) complex values: every lane busy,
+// four independent loads in flight per thread.
 template <typename R>
-__global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef,
+__device__ __forceinline__ void green_one(typename VT<R>::cplx& v, uint32_t e, uint32_t nh, DivU32 dv, const Mesh& m,
+                                          const R* s2, R coef, R& wsum) {
+  const uint32_t n = uint32_t(m.n);
+  const uint32_t row = divu32(e, dv), jx = e - row * nh;
+  uint32_t jz, jy;
+  if (m.log2n >= 0) {
+    jz = row >> m.log2n;
+    jy = row & (n - 1u);
+  } else {
+    jz = row / n;
+    jy = row - jz * n;
+  }
+  const R syz = s2[jy] + s2[jz];
+  const R s = syz + s2[jx];
+  const R g = (row == 0 && jx == 0) ? R(0) : coef / s;
+  const R re = v.x, im = v.y;
+  const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
+  wsum += w * g * (re * re + im * im);
+  v.x = re * g;
+  v.y = im * g;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef, DivU32 dv,
                                                         double* part) {
   extern __shared__ __align__(16) unsigned char green_smem[];
   R* s2 = reinterpret_cast<R*>(green_smem);  // sin^2(pi j / N), j = 0..N-1
@@ -343,31 +391,29 @@ __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* sp
   const R inv_n = R(1) / R(n);
   for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) s2[j] = sinpi_sq(R(j) * inv_n);
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = blockDim.x >> 5;
   R wsum = R(0);
-  // one (jz, jy) row of the half spectrum per warp, jx over lanes
-  for (uint32_t row = blockIdx.x * warps + (threadIdx.x >> 5); row < m.n2; row += gridDim.x * warps) {
-    const uint32_t jz = row / n, jy = row - jz * n;
-    const R syz = s2[jy] + s2[jz];
-    typename VT<R>::cplx* line = spec + size_t(row) * nh;
-    for (uint32_t jx = lane; jx < nh; jx += 32) {
-      const R s = syz + s2[jx];
-      auto v = line[jx];
-      const R g = (row == 0 && jx == 0) ? R(0) : coef / s;
-      const R re = v.x, im = v.y;
-      const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
-      wsum += w * g * (re * re + im * im);
-      v.x = re * g;
-      v.y = im * g;
-      line[jx] = v;
+  const uint32_t total = m.n2 * nh, stride = gridDim.x * blockDim.x;
+  uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < total; e += 4 * stride) {
+    typename VT<R>::cplx v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = spec[e + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      green_one<R>(v[k], e + k * stride, nh, dv, m, s2, coef, wsum);
+      spec[e + k * stride] = v[k];
     }
+  }
+  for (; e < total; e += stride) {
+    typename VT<R>::cplx v = spec[e];
+    green_one<R>(v, e, nh, dv, m, s2, coef, wsum);
+    spec[e] = v;
   }
   R acc[1] = {wsum};
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
-// ---------------------------------------------------------------- S5: quantum stencil
+// ---------------------------------------------------------------- quantum-pressure stencil
 // Q~_n = qcoef * sum_d [(s_{n+e_d} - s_n) + (s_{n-e_d} - s_n)] / s_n with
 // s = sqrt(max(rho, floor)) and neighbours at +-step (Eq. quantumpressure with
 // the seven-point Laplacian; comoving 1/a^2 applied by the kick weights).
@@ -861,7 +907,7 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
   }
 }
 
-// ---------------------------------------------------------------- S6: interpolate + kick + drift
+// ---------------------------------------------------------------- interpolate + kick + drift
 // Gradient of a mesh potential at the particle, in one of two forms:
 //   central : sum_c w_c (f[c+e] - f[c-e]) / 2dx over the 8 cloud-in-cell corners c
 //   kernel  : grad_q sum_c f_c w_c  (Eq. equationofmotion; 8 corner values)
@@ -1175,7 +1221,8 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s) {
   using C = typename VT<R>::cplx;
-  k_green<R><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>((C*)spec, m, R(coef), part);
+  k_green<R><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>((C*)spec, m, R(coef),
+                                                                divu32_make(uint32_t(m.n / 2 + 1)), part);
   return cudaGetLastError();
 }
 

@@ -22,13 +22,14 @@ cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint32_t* tile_cnt, uint32_t* counts,
+cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint64_t* pstatus, uint32_t* tile_counter,
                                    uint32_t* s_keys, uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals,
-                                   cudaStream_t s) {
+                                   uint32_t* counts, uint32_t* hist, int passes, int digit_bits, int key_bits,
+                                   uint32_t* sort_epoch, uint32_t* err, cudaStream_t s) {
   const int ntiles = int((n + RS_TILE - 1) / RS_TILE);
-  k_mover_count<<<unsigned(ntiles), RS_THREADS, 0, s>>>(keys, n, tile_cnt);
-  k_mover_scan<<<1, RS_THREADS, 0, s>>>(tile_cnt, ntiles, n, counts);
-  k_mover_scatter<<<unsigned(ntiles), RS_THREADS, 0, s>>>(keys, n, tile_cnt, s_keys, s_vals, m_keys, m_vals);
+  k_mover_partition<<<unsigned(ntiles), RS_THREADS, 0, s>>>(keys, n, pstatus, tile_counter, s_keys, s_vals, m_keys,
+                                                             m_vals, counts, hist, passes, digit_bits, key_bits,
+                                                             sort_epoch, err);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 constexpr uint64_t RS_FLAG_AGG = 1ull << 32;
 constexpr uint64_t RS_FLAG_PREFIX = 2ull << 32;
 constexpr int RS_SPIN_LIMIT = 1 << 18;
+constexpr int RS_LOOKBACK = 8;  // predecessors read per look-back round
 
 __device__ __forceinline__ uint64_t rs_word(uint32_t epoch, uint64_t flag, uint32_t v) {
   return (uint64_t(epoch) << 48) | flag | uint64_t(v);
@@ -200,18 +201,34 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
   for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
     uint32_t excl = 0;
     if (tile > 0) {
+      // the status words of up to RS_LOOKBACK predecessors are read at once and
+      // consumed in order (nearest first) up to the first one not yet published
       int64_t t = int64_t(tile) - 1;
       int polls = 0;
-      while (t >= 0) {
-        const uint64_t w = __ldcv(reinterpret_cast<const unsigned long long*>(status + size_t(t) * radix + d));
-        if (uint32_t(w >> 48) == epoch && (w & (RS_FLAG_AGG | RS_FLAG_PREFIX))) {
-          excl += uint32_t(w);
-          if (w & RS_FLAG_PREFIX) break;
-          --t;
-        } else if (++polls > RS_SPIN_LIMIT) {
-          atomicOr(err, ERR_TIMEOUT);
-          break;
-        } else {
+      bool done = false;
+      while (!done && t >= 0) {
+        uint64_t w[RS_LOOKBACK];
+#pragma unroll
+        for (int k = 0; k < RS_LOOKBACK; ++k)
+          w[k] = t - k >= 0 ? __ldcv(reinterpret_cast<const unsigned long long*>(status + size_t(t - k) * radix + d))
+                            : 0ull;
+        int used = 0;
+#pragma unroll
+        for (int k = 0; k < RS_LOOKBACK; ++k) {
+          if (done || used < k || t - k < 0) continue;  // stop at the first gap
+          if (uint32_t(w[k] >> 48) == epoch && (w[k] & (RS_FLAG_AGG | RS_FLAG_PREFIX))) {
+            excl += uint32_t(w[k]);
+            used = k + 1;
+            if (w[k] & RS_FLAG_PREFIX) done = true;
+          }
+        }
+        t -= used;
+        if (done || t < 0) break;
+        if (used == 0) {
+          if (++polls > RS_SPIN_LIMIT) {
+            atomicOr(err, ERR_TIMEOUT);
+            break;
+          }
           __nanosleep(32);
         }
       }
@@ -307,69 +324,33 @@ static __global__ void k_reduce(const double* __restrict__ part, int nblocks, do
 // stayers and movers, radix-sort the movers (usually a few per cent), and merge
 // the two sequences by (key, previous slot) while gathering the records.  The
 // result is identical to the full sort.
-// movers per tile of RS_TILE slots
-static __global__ void __launch_bounds__(RS_THREADS) k_mover_count(const uint32_t* __restrict__ keys, int64_t n,
-                                                                   uint32_t* __restrict__ tile_cnt) {
-  __shared__ uint32_t warp_sum[RS_WARPS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t base = int64_t(blockIdx.x) * RS_TILE;
-  uint32_t c = 0;
-#pragma unroll
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int64_t i = base + r * RS_THREADS + threadIdx.x;
-    const bool mv = i < n && (__ldg(keys + i) & KEY_MOVER);
-    c += __popc(__ballot_sync(0xffffffffu, mv));
-  }
-  if (lane == 0) warp_sum[warp] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < RS_WARPS; ++w) t += warp_sum[w];
-    tile_cnt[blockIdx.x] = t;
-  }
-}
-
-// exclusive scan of the per-tile mover counts (one block); counts[0] = stayers,
-// counts[1] = movers
-static __global__ void __launch_bounds__(RS_THREADS) k_mover_scan(uint32_t* tile_cnt, int ntiles, int64_t n,
-                                                                  uint32_t* counts) {
-  __shared__ uint32_t scratch[64];
-  uint32_t carry = 0;
-  for (int base = 0; base < ntiles; base += RS_THREADS * 4) {
-    uint32_t v[4], sum = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int t = base + threadIdx.x * 4 + k;
-      v[k] = t < ntiles ? tile_cnt[t] : 0u;
-      sum += v[k];
-    }
-    uint32_t total;
-    uint32_t off = block_excl_scan(sum, scratch, total) + carry;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int t = base + threadIdx.x * 4 + k;
-      if (t < ntiles) tile_cnt[t] = off;
-      off += v[k];
-    }
-    carry += total;
-  }
-  if (threadIdx.x == 0) {
-    counts[0] = uint32_t(n) - carry;
-    counts[1] = carry;
-  }
-}
-
-// stable partition: stayers to (s_keys, s_vals), movers (flag cleared) to
-// (m_keys, m_vals); values are the previous slots
-static __global__ void __launch_bounds__(RS_THREADS) k_mover_scatter(const uint32_t* __restrict__ keys, int64_t n,
-                                                                     const uint32_t* __restrict__ tile_off,
-                                                                     uint32_t* __restrict__ s_keys,
-                                                                     uint32_t* __restrict__ s_vals,
-                                                                     uint32_t* __restrict__ m_keys,
-                                                                     uint32_t* __restrict__ m_vals) {
+// Stable partition in one pass: tiles of RS_TILE slots are taken in order
+// (dynamic tile ids); each counts its movers, publishes the count at once and
+// finds the movers of all earlier tiles by decoupled look-back over one status
+// word per tile (flag | count; the words are cleared before the launch), then
+// writes its stayers to (s_keys, s_vals) and its movers, flag cleared, to
+// (m_keys, m_vals); values are the previous slots.  It also accumulates the
+// digit histograms of the movers' keys for every radix pass (hist[p*radix_max
+// + d], cleared before), advances the sort epoch for those passes (as the
+// histogram kernel does for a full sort) and, in the last tile, stores
+// counts[0] = stayers, counts[1] = movers.
+static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
+    const uint32_t* __restrict__ keys, int64_t n, uint64_t* pstatus, uint32_t* tile_counter,
+    uint32_t* __restrict__ s_keys, uint32_t* __restrict__ s_vals, uint32_t* __restrict__ m_keys,
+    uint32_t* __restrict__ m_vals, uint32_t* __restrict__ counts, uint32_t* __restrict__ hist, int passes,
+    int digit_bits, int key_bits, uint32_t* __restrict__ sort_epoch, uint32_t* err) {
+  __shared__ uint32_t sh_hist[3 << RS_MAX_BITS];
   __shared__ uint32_t wm[RS_WARPS];
+  __shared__ uint32_t s_tile, s_excl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t tile_base = int64_t(blockIdx.x) * RS_TILE;
+  const int radix = 1 << digit_bits;
+  const int ntiles = int((n + RS_TILE - 1) / RS_TILE);
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+  for (int d = threadIdx.x; d < passes * radix; d += RS_THREADS) sh_hist[d] = 0u;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile == 0 && threadIdx.x == 0) *sort_epoch = (*sort_epoch + uint32_t(passes)) % 65530u + 1u;
+  const int64_t tile_base = int64_t(tile) * RS_TILE;
   const uint32_t lt = lanemask_lt();
   // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32
   uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
@@ -383,25 +364,84 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_scatter(const uint3
   }
   if (lane == 0) wm[warp] = mcount;
   __syncthreads();
+  // publish this tile's mover count, then sum the earlier tiles' (warp 0: its
+  // lanes read 32 predecessors' words at once, nearest in lane 0)
+  if (warp == 0) {
+    uint32_t total = 0;
+    for (int w = 0; w < RS_WARPS; ++w) total += wm[w];
+    uint32_t excl = 0;
+    if (tile == 0) {
+      if (lane == 0) __stcg(reinterpret_cast<unsigned long long*>(pstatus), RS_FLAG_PREFIX | uint64_t(total));
+    } else {
+      if (lane == 0) __stcg(reinterpret_cast<unsigned long long*>(pstatus + tile), RS_FLAG_AGG | uint64_t(total));
+      int64_t t = int64_t(tile) - 1;  // nearest predecessor not yet summed
+      int polls = 0;
+      while (t >= 0) {
+        const int64_t tl = t - lane;
+        const uint64_t w = tl >= 0 ? __ldcv(reinterpret_cast<const unsigned long long*>(pstatus + tl)) : 0ull;
+        const bool valid = tl >= 0 && (w & (RS_FLAG_AGG | RS_FLAG_PREFIX));
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        const uint32_t pmask = __ballot_sync(0xffffffffu, valid && (w & RS_FLAG_PREFIX));
+        // lanes usable: the leading run of published words, up to the first prefix
+        const int run = vmask == 0xffffffffu ? 32 : __ffs(~vmask) - 1;
+        const int pl = pmask ? __ffs(pmask) - 1 : 32;
+        const int take = pl < run ? pl + 1 : run;
+        uint32_t v = lane < take ? uint32_t(w) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pl < run) break;  // reached a prefix
+        t -= take;
+        if (take == 0) {
+          if (++polls > RS_SPIN_LIMIT) {
+            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      if (lane == 0)
+        __stcg(reinterpret_cast<unsigned long long*>(pstatus + tile), RS_FLAG_PREFIX | uint64_t(excl + total));
+    }
+    if (lane == 0) {
+      s_excl = excl;
+      if (int(tile) == ntiles - 1) {
+        counts[0] = uint32_t(n) - (excl + total);
+        counts[1] = excl + total;
+      }
+    }
+  }
+  __syncthreads();
   // movers in the earlier warps of the tile: lane w < warp contributes wm[w]
   uint32_t mbase = lane < warp ? wm[lane] : 0u;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mbase += __shfl_xor_sync(0xffffffffu, mbase, o);
-  mbase += tile_off[blockIdx.x];
+  mbase += s_excl;
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
     if (i < n) {
       const uint32_t before = mbase + rank[r];  // movers before slot i
       if (key[r] & KEY_MOVER) {
-        m_keys[before] = key[r] & ~KEY_MOVER;
-        m_vals[before] = uint32_t(i);
-      } else {
+        const uint32_t k = key[r] & ~KEY_MOVER;
+        if (before < uint32_t(n)) {  // only false after a timed-out look-back
+          m_keys[before] = k;
+          m_vals[before] = uint32_t(i);
+        }
+        for (int p = 0; p < passes; ++p) {
+          const int shift = p * digit_bits;
+          const int bits = min(digit_bits, key_bits - shift);
+          atomicAdd(&sh_hist[p * radix + ((k >> shift) & ((1u << bits) - 1u))], 1u);
+        }
+      } else if (uint32_t(i) >= before) {
         s_keys[uint32_t(i) - before] = key[r];
         s_vals[uint32_t(i) - before] = uint32_t(i);
       }
     }
   }
+  __syncthreads();
+  for (int d = threadIdx.x; d < passes * radix; d += RS_THREADS)
+    if (sh_hist[d]) atomicAdd(hist + (d / radix) * (1 << RS_MAX_BITS) + (d % radix), sh_hist[d]);
 }
 
 __device__ __forceinline__ bool kv_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {

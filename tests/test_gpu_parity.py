@@ -58,7 +58,7 @@ def oracle_order(xg, ocfg, prev_ids):
     return keys, order
 
 
-# ------------------------------------------------------------------ S0 sort
+# ------------------------------------------------------------------ sort
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("n_side,n_mesh,box", [(32, 64, 1.0), (20, 40, 1.0), (64, 128, 2.0)])
 def test_initial_sort_is_bit_exact(pm, precision, n_side, n_mesh, box):
@@ -153,7 +153,7 @@ def test_resort_at_bench_size(pm):
     assert max(moved) > 0.0
 
 
-# ------------------------------------------------------------------ S1 deposit
+# ------------------------------------------------------------------ deposit
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
 @pytest.mark.parametrize("n_side,n_mesh,box", [(32, 64, 1.0), (24, 48, 1.5), (128, 256, 2.0)])
 def test_deposit_matches_oracle(pm, precision, tol, n_side, n_mesh, box):
@@ -165,7 +165,7 @@ def test_deposit_matches_oracle(pm, precision, tol, n_side, n_mesh, box):
     assert rho.sum() == pytest.approx(n_mesh ** 3, rel=1e-6 if precision == "fp32" else 1e-12)
 
 
-# ------------------------------------------------------------------ S2-S5 mesh stages
+# ------------------------------------------------------------------ mesh stages
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-6), ("fp64", 1e-12)])
 @pytest.mark.parametrize("lap", [0, 1])
 def test_potential_and_quantum_pressure_match_oracle(pm, precision, tol, lap):
@@ -203,7 +203,7 @@ def test_gaussian_quantum_pressure_closed_form_on_gpu(pm):
     np.testing.assert_allclose(q[inner], expect[inner], rtol=1e-9, atol=1e-12 * np.abs(expect).max())
 
 
-# ------------------------------------------------------------------ S6 forces
+# ------------------------------------------------------------------ forces
 @pytest.mark.parametrize("mode", ["meshgrad", "hybrid", "lagrangian"])
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-10)])
 def test_one_step_accelerations_match_oracle(pm, mode, precision, tol):
@@ -287,7 +287,7 @@ def test_runs_are_bitwise_reproducible(pm):
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
 
 
-# ------------------------------------------------------------------ S7 energies
+# ------------------------------------------------------------------ energies
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-11)])
 @pytest.mark.parametrize("lap", [0, 1])
 def test_energies_match_oracle(pm, precision, tol, lap):
