@@ -8,8 +8,11 @@ no code with the CUDA path and imports nothing from the package.
 It follows Veltmaat & Niemeyer, "Cosmological particle-in-cell simulations with
 ultralight axion dark matter" (arXiv:1608.00802), Sec. II.A:
 
-  * density by a kernel estimate, Eq. (rhodis), with the cloud-in-cell kernel
-    (a tensor tent of width dx) in place of the cubic spline;
+  * density by a kernel estimate, Eq. (rhodis): the cloud-in-cell kernel (a
+    tensor tent of width dx), or the paper's cubic spline W(r, h) of
+    Sec. II.A (h = 3.5 dx in its cosmological runs) applied as a mesh
+    convolution of the cloud-in-cell density with the spline sampled at the
+    nodes; the force side then uses the same convolution (its transpose);
   * quantum pressure Q = -(hbar^2/2m^2) lap(sqrt rho)/sqrt rho,
     Eq. (quantumpressure), in comoving form Eq. (comquantumpressure), with the
     seven-point Laplacian named after Eq. (equationofmotion);
@@ -50,6 +53,8 @@ HYBRID = 1       # gravity as MESHGRAD; Q by Eq. (equationofmotion) (the paper's
 LAGRANGIAN = 2   # gravity and Q both by the kernel-gradient form (fully energy-conserving)
 LAP_COMPACT = 0
 LAP_WIDE = 1
+KERNEL_CIC = 0     # cloud-in-cell assignment only
+KERNEL_SPLINE = 1  # cloud-in-cell assignment convolved with the node-sampled cubic spline
 
 
 def hbar_over_m(m22: float, h: float) -> float:
@@ -88,6 +93,8 @@ class Config:
     lap: int = LAP_COMPACT
     cosmological: bool = True
     rho_floor: float = 1e-6
+    kernel: int = KERNEL_CIC
+    smooth_h: float = 3.5          # spline smoothing length in mesh cells
 
     @property
     def dx(self) -> float:
@@ -198,6 +205,50 @@ def cic_deposit(x, cfg: Config, mass=None):
                 idx = (iz * n + iy) * n + ix
                 rho += np.bincount(idx, weights=mass * wx * wy * wz, minlength=n ** 3)
     return rho.reshape(n, n, n) / cfg.dx ** 3
+
+
+# --------------------------------------------------------------------------
+# the cubic spline of Sec. II.A and the smoothed density
+# --------------------------------------------------------------------------
+def spline_w(r, h):
+    """W(r, h) = 8/(pi h^3) * {1 - 6u^2 + 6u^3 for u <= 1/2; 2(1-u)^3 for
+    1/2 < u <= 1; 0 beyond}, u = r/h (the kernel chosen in Sec. II.A)."""
+    u = np.asarray(r, dtype=np.float64) / h
+    inner = 1.0 - 6.0 * u ** 2 + 6.0 * u ** 3
+    outer = 2.0 * (1.0 - u) ** 3
+    return 8.0 / (math.pi * h ** 3) * np.where(u <= 0.5, inner, np.where(u <= 1.0, outer, 0.0))
+
+
+def spline_node_weights(cfg: Config):
+    """w_n = W(|x_n|, h) dx^3 at every node offset of the periodic mesh
+    (minimum image), divided by their sum so that mass is kept exactly."""
+    n = cfg.n_mesh
+    d = np.fft.fftfreq(n, d=1.0 / n)  # 0, 1, .., n/2-1, -n/2, .., -1 (in cells)
+    dz, dy, dx_ = np.meshgrid(d, d, d, indexing="ij")
+    r = np.sqrt(dx_ ** 2 + dy ** 2 + dz ** 2) * cfg.dx
+    w = spline_w(r, cfg.smooth_h * cfg.dx) * cfg.dx ** 3
+    return w / w.sum()
+
+
+def smoothing_symbol(cfg: Config):
+    """DFT of the node weights (real: the weights are even in every axis)."""
+    return np.real(np.fft.fftn(spline_node_weights(cfg)))
+
+
+def smooth(field, cfg: Config):
+    """Periodic convolution of a mesh field with the node weights (a symmetric
+    operator, its own transpose)."""
+    return np.real(np.fft.ifftn(np.fft.fftn(field) * smoothing_symbol(cfg)))
+
+
+def density(x, cfg: Config):
+    """The density of Eq. (rhodis) on the mesh: cloud-in-cell, then (spline
+    kernel) the convolution with the node weights.  For a particle on a node
+    this is exactly sum_i m_i W(|x_n - q_i|, h) up to the weights' normalisation."""
+    rho = cic_deposit(x, cfg)
+    if cfg.kernel == KERNEL_SPLINE:
+        rho = smooth(rho, cfg)
+    return rho
 
 
 # --------------------------------------------------------------------------
@@ -319,10 +370,19 @@ def cic_interpolate_gradient(field, x, cfg: Config):
 # forces: steps (i)-(iii)
 # --------------------------------------------------------------------------
 def mesh_fields(x, cfg: Config):
-    """Steps (i) and (ii) plus the gravity solve: rho, phi~, Q~ (Q~ = 0 for CDM)."""
-    rho = cic_deposit(x, cfg)
+    """Steps (i) and (ii) plus the gravity solve: rho, and the potentials the
+    particles feel, phi~ and Q~ (Q~ = 0 for CDM).  With the spline kernel both
+    potentials are convolved with the node weights once more: the density is
+    S rho_cic, so the force, the derivative of the energy with respect to a
+    particle position, goes through the transpose S (= S) back to the
+    cloud-in-cell interpolant."""
+    rho = density(x, cfg)
     phi = poisson_phi(rho, cfg)
     q = quantum_potential(rho, cfg) if cfg.quantum else np.zeros_like(rho)
+    if cfg.kernel == KERNEL_SPLINE:
+        phi = smooth(phi, cfg)
+        if cfg.quantum:
+            q = smooth(q, cfg)
     return rho, phi, q
 
 
@@ -434,7 +494,8 @@ def energies(x, p, a, cfg: Config):
     npart = x.shape[0]
     mp = cfg.box ** 3 / npart
     kv = 0.5 * mp * float(np.sum(p * p)) / (aa * aa)
-    rho, phi, _ = mesh_fields(x, cfg)
+    rho = density(x, cfg)
+    phi = poisson_phi(rho, cfg)
     wg = 0.5 / aa * float(np.sum((rho - 1.0) * phi)) * cfg.dx ** 3
     krho = 0.0
     if cfg.quantum:

@@ -488,3 +488,119 @@ def test_layzer_irvine_holds_for_lagrangian_cosmology():
     h = np.array(hist)
     assert abs(h[-1, 2]) > 20 * abs(h[1, 2])           # structure did grow
     assert np.abs(eps).max() < 1e-2
+
+
+# ---------------------------------------------------------------- cubic spline kernel (Sec. II.A)
+def test_spline_kernel_closed_form_properties():
+    """W of Sec. II.A: unit integral over space, continuous value and slope at
+    r = h/2, zero at and beyond r = h, W(0) = 8/(pi h^3)."""
+    from scipy.integrate import quad
+    h = 0.37
+    total = quad(lambda r: 4 * math.pi * r * r * float(O.spline_w(r, h)), 0, h, points=[h / 2],
+                 epsabs=0, epsrel=1e-13)[0]
+    assert total == pytest.approx(1.0, rel=1e-12)
+    c = 8 / (math.pi * h ** 3)
+    assert float(O.spline_w(0.0, h)) == pytest.approx(c, rel=1e-15)
+    eps = 1e-7 * h
+    lo, mid, hi = (float(O.spline_w(h / 2 + d, h)) for d in (-eps, 0.0, eps))
+    assert mid == pytest.approx(c / 4, rel=1e-14)                 # both branches give 1/4 there
+    assert (mid - lo) / eps == pytest.approx((hi - mid) / eps, rel=1e-5)   # same slope on both sides:
+    assert (mid - lo) / eps == pytest.approx(-1.5 * c / h, rel=1e-5)       # -12u + 18u^2 = -6(1-u)^2 = -3/2
+    assert float(O.spline_w(h, h)) == 0.0 and float(O.spline_w(1.5 * h, h)) == 0.0
+
+
+def test_spline_node_weights_sum_and_symbol():
+    cfg = O.Config(n_mesh=16, box=1.0, kernel=O.KERNEL_SPLINE, smooth_h=3.5)
+    w = O.spline_node_weights(cfg)
+    assert w.sum() == pytest.approx(1.0, rel=1e-14)
+    # the raw node sum of W dx^3 is a Riemann sum of a unit integral
+    d = np.fft.fftfreq(16, d=1 / 16)
+    dz, dy, dx_ = np.meshgrid(d, d, d, indexing="ij")
+    raw = O.spline_w(np.sqrt(dx_ ** 2 + dy ** 2 + dz ** 2) * cfg.dx, 3.5 * cfg.dx).sum() * cfg.dx ** 3
+    assert raw == pytest.approx(1.0, abs=2e-3)
+    sym = O.smoothing_symbol(cfg)
+    assert sym[0, 0, 0] == pytest.approx(1.0, rel=1e-14)
+    assert np.abs(np.fft.fftn(w).imag).max() < 1e-14                   # even weights: real symbol
+    assert np.all(np.abs(sym) <= 1.0 + 1e-14)
+
+
+def test_spline_density_on_nodes_is_the_direct_kernel_sum():
+    """Eq. (rhodis) by brute force for particles sitting on nodes: sum over
+    particles of m W(|x_n - q_i|, h) at every node (minimum image), divided by
+    the weights' normalisation."""
+    rng = np.random.default_rng(21)
+    n, box, h = 12, 1.5, 3.5
+    cfg = O.Config(n_mesh=n, box=box, kernel=O.KERNEL_SPLINE, smooth_h=h)
+    dx = box / n
+    cells = rng.integers(0, n, size=(7, 3))
+    x = cells * dx
+    rho = O.density(x, cfg)
+    mp = box ** 3 / len(x)
+    d = np.fft.fftfreq(n, d=1 / n)
+    dz, dy, dx_ = np.meshgrid(d, d, d, indexing="ij")
+    raw = O.spline_w(np.sqrt(dx_ ** 2 + dy ** 2 + dz ** 2) * dx, h * dx).sum() * dx ** 3
+    direct = np.zeros((n, n, n))
+    grid = np.arange(n)
+    for c in cells:
+        ox = (grid - c[0] + n // 2) % n - n // 2
+        oy = (grid - c[1] + n // 2) % n - n // 2
+        oz = (grid - c[2] + n // 2) % n - n // 2
+        r = np.sqrt(oz[:, None, None] ** 2 + oy[None, :, None] ** 2 + ox[None, None, :] ** 2) * dx
+        direct += mp * O.spline_w(r, h * dx)
+    np.testing.assert_allclose(rho, direct / raw, rtol=1e-11, atol=1e-12 * direct.max())
+
+
+def test_spline_density_is_the_weights_convolved_with_cic():
+    """Off-node particles: rho_n = sum_m w_{n-m} rho_cic_m, brute-force double sum."""
+    rng = np.random.default_rng(22)
+    n = 8
+    cfg = O.Config(n_mesh=n, box=1.0, kernel=O.KERNEL_SPLINE, smooth_h=2.5)
+    x = rng.uniform(0, 1, size=(5, 3))
+    rc = O.cic_deposit(x, O.Config(n_mesh=n, box=1.0))
+    w = O.spline_node_weights(cfg)
+    ref = np.zeros((n, n, n))
+    for mz in range(n):
+        for my in range(n):
+            for mx in range(n):
+                if rc[mz, my, mx] != 0.0:
+                    ref += rc[mz, my, mx] * np.roll(w, (mz, my, mx), axis=(0, 1, 2))
+    np.testing.assert_allclose(O.density(x, cfg), ref, rtol=1e-12, atol=1e-13)
+    assert O.density(x, cfg).sum() * cfg.dx ** 3 == pytest.approx(1.0, rel=1e-13)   # mass kept
+
+
+def test_spline_lagrangian_forces_are_minus_energy_gradients():
+    """With the spline kernel the LAGRANGIAN forces stay the derivatives of the
+    discrete energies: Q force vs -dK_rho/dq and gravity vs -dW_g/dq (static,
+    a = 1), by central finite differences in one particle's position."""
+    rng = np.random.default_rng(23)
+    cfg = O.Config(n_mesh=8, box=1.0, omega_m=0.3, cosmological=False, force_mode=O.LAGRANGIAN,
+                   m22=0.01, kernel=O.KERNEL_SPLINE, smooth_h=2.0)
+    x, _ = ics.lattice(4, 8, 1.0)
+    x = np.mod(x + 0.03 * rng.standard_normal(x.shape), 1.0)
+    p = np.zeros_like(x)
+    gphi, gq = O.force_parts(x, cfg)
+    mp = 1.0 / len(x)
+    for i in (0, 17, 41):
+        for d in range(3):
+            eps = 1e-6
+            xp, xm = x.copy(), x.copy()
+            xp[i, d] += eps
+            xm[i, d] -= eps
+            ep, em = O.energies(xp, p, 1.0, cfg), O.energies(xm, p, 1.0, cfg)
+            fq = -(ep[2] - em[2]) / (2 * eps)
+            fg = -(ep[1] - em[1]) / (2 * eps)
+            assert mp * gq[i, d] == pytest.approx(fq, rel=1e-5, abs=1e-8 * abs(fq) + 1e-16)
+            assert mp * gphi[i, d] == pytest.approx(fg, rel=1e-5, abs=1e-8 * abs(fg) + 1e-16)
+
+
+def test_spline_gravity_conserves_momentum():
+    """The spline-smoothed mesh-gradient gravity (MESHGRAD, HYBRID) keeps the
+    PM pair symmetry: the forces sum to zero.  (The kernel-gradient forms are
+    derivatives of mesh energies, not pair forces, and conserve momentum only
+    approximately, with cloud-in-cell as with the spline.)"""
+    rng = np.random.default_rng(24)
+    for fm in (O.MESHGRAD, O.HYBRID):
+        cfg = O.Config(n_mesh=16, box=1.0, force_mode=fm, kernel=O.KERNEL_SPLINE)
+        x = rng.uniform(0, 1, size=(300, 3))
+        gphi, _ = O.force_parts(x, cfg)
+        assert np.abs(gphi.sum(axis=0)).max() < 1e-12 * np.abs(gphi).sum()
