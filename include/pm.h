@@ -61,6 +61,12 @@ enum {
   PM_LAP_WIDE = 1          /* neighbours at +-2dx; pairs with the central differences of Eq. diskpoten */
 };
 enum { PM_FP32 = 0, PM_FP64 = 1 };
+/* Density kernel of Eq. rhodis.  SPLINE: the cubic spline W(r, h) of Sec. II.A
+ * (h = smooth_h mesh cells), applied as the periodic convolution of the
+ * cloud-in-cell density with W sampled at the nodes (normalised to unit sum);
+ * the potentials the particles feel are convolved once more (the transpose),
+ * so the kernel-gradient forces stay the derivatives of the discrete energies. */
+enum { PM_KERNEL_CIC = 0, PM_KERNEL_SPLINE = 1 };
 enum { PM_FIELD_RHO = 0, PM_FIELD_PHI = 1, PM_FIELD_Q = 2 };
 
 typedef struct {
@@ -81,13 +87,18 @@ typedef struct {
                           undefined where rho = 0 (Sec. II.A) */
   double rho_fp64;     /* PM_FP32 only: nodes with rho below this evaluate sqrt(rho) and Q
                           in fp64 (ill-conditioned ratio); 0 disables */
+  int32_t kernel;      /* PM_KERNEL_* */
+  int32_t reserved;    /* 0 */
+  double smooth_h;     /* PM_KERNEL_SPLINE: smoothing length h in mesh cells, 1 .. n_mesh/4
+                          (the paper's cosmological runs: 3.5) */
 } pm_config;
 
 typedef struct pm_sim pm_sim;
 
 /* Fills a configuration with defaults (fp32, MESHGRAD, compact, quantum on,
  * cosmological, Omega_m 0.3, Omega_L 0.7, h 0.7, m22 2.5, floor 1e-6,
- * fp64 branch below 1e-2).  n_part, n_mesh and box are left 0. */
+ * fp64 branch below 1e-2, cloud-in-cell kernel, smooth_h 3.5).  n_part,
+ * n_mesh and box are left 0. */
 void pm_config_default(pm_config* cfg);
 
 /* hbar/m in code units (Mpc/h)^2 H0 for the configuration's m22 and h. */

@@ -35,6 +35,7 @@ Mesh node n sits at n * dx.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass
 
@@ -232,7 +233,13 @@ def spline_node_weights(cfg: Config):
 
 def smoothing_symbol(cfg: Config):
     """DFT of the node weights (real: the weights are even in every axis)."""
-    return np.real(np.fft.fftn(spline_node_weights(cfg)))
+    return _symbol(cfg.n_mesh, cfg.box, cfg.smooth_h).copy()
+
+
+@functools.lru_cache(maxsize=8)
+def _symbol(n, box, smooth_h):
+    # memo of the symbol per mesh (the weights depend only on n, box and h)
+    return np.real(np.fft.fftn(spline_node_weights(Config(n_mesh=n, box=box, smooth_h=smooth_h))))
 
 
 def smooth(field, cfg: Config):

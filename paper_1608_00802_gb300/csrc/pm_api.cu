@@ -88,7 +88,7 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[4], vals[3], tile_cnt, row_start, rho, phi, q, spec, work, staging, hist, status,
+  size_t pos[2], mom[2], keys[4], vals[3], tile_cnt, row_start, rho, phi, q, spec, what, spec2, work, staging, hist, status,
       st_list, st_count, part, part_aux, red, err, ktab, total;
   int key_bits, passes, digit_bits, ntiles;
 };
@@ -130,6 +130,14 @@ bool valid_config(const pm_config* c, std::string* why) {
     *why = "rho_floor must be positive";
     return false;
   }
+  if (c->kernel != PM_KERNEL_CIC && c->kernel != PM_KERNEL_SPLINE) {
+    *why = "kernel must be PM_KERNEL_CIC or PM_KERNEL_SPLINE";
+    return false;
+  }
+  if (c->kernel == PM_KERNEL_SPLINE && !(c->smooth_h >= 1.0 && c->smooth_h <= 0.25 * c->n_mesh)) {
+    *why = "smooth_h must be in [1, n_mesh/4] mesh cells";
+    return false;
+  }
   return true;
 }
 
@@ -164,6 +172,10 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   L.phi = take(n3 * rsz);
   L.q = take(n3 * rsz);
   L.spec = take(N * N * (N / 2 + 1) * 2 * rsz);
+  // spline kernel: its real symbol over the half spectrum and a second spectrum
+  const bool spline = c.kernel == PM_KERNEL_SPLINE;
+  L.what = take(spline ? N * N * (N / 2 + 1) * rsz : 0);
+  L.spec2 = take(spline ? N * N * (N / 2 + 1) * 2 * rsz : 0);
   L.work = take(work_bytes);
   size_t stage = 6 * n * 8;
   if (n3 * 8 > stage) stage = n3 * 8;
@@ -446,37 +458,109 @@ pm_status stencil_stage(pm_sim* s, bool diag = false) {
   return PM_OK;
 }
 
+// forward and inverse transforms between a real mesh field and a spectrum
+template <typename R>
+pm_status fft_r2c(pm_sim* s, void* in, void* out) {
+  PROF(s, PM_STAGE_FFT_R2C);
+  if (s->fp64()) {
+    CF(s, cufftExecD2Z(s->plan_fwd, (cufftDoubleReal*)in, (cufftDoubleComplex*)out));
+  } else {
+    CF(s, cufftExecR2C(s->plan_fwd, (cufftReal*)in, (cufftComplex*)out));
+  }
+  return PM_OK;
+}
+
+template <typename R>
+pm_status fft_c2r(pm_sim* s, void* in, void* out) {
+  PROF(s, PM_STAGE_FFT_C2R);
+  if (s->fp64()) {
+    CF(s, cufftExecZ2D(s->plan_inv, (cufftDoubleComplex*)in, (cufftDoubleReal*)out));
+  } else {
+    CF(s, cufftExecC2R(s->plan_inv, (cufftComplex*)in, (cufftReal*)out));
+  }
+  return PM_OK;
+}
+
+#define PMST(expr)                  \
+  do {                              \
+    pm_status st_ = (expr);         \
+    if (st_ != PM_OK) return st_;   \
+  } while (0)
+
+bool spline(const pm_sim* s) { return s->cfg.kernel == PM_KERNEL_SPLINE; }
+
+// a mesh field convolved in place with the spline's node weights
+template <typename R>
+pm_status smooth_field(pm_sim* s, size_t field) {
+  PMST(fft_r2c<R>(s, s->arena + field, s->arena + s->L.spec));
+  {
+    PROF(s, PM_STAGE_GREEN);
+    CU(s, launch_smooth_spec<R>(s->arena + s->L.spec, s->arena + s->L.what, s->mesh, s->stream));
+  }
+  return fft_c2r<R>(s, s->arena + s->L.spec, s->arena + field);
+}
+
+double green_coef(const pm_sim* s) {
+  const double N = s->cfg.n_mesh;
+  return -1.5 * s->cfg.omega_m * s->dx * s->dx / (4.0 * N * N * N);
+}
+
+// Q~ from the density in `rho`, smoothed with the spline kernel (the transpose
+// of the density's smoothing)
+template <typename R>
+pm_status quantum_stage(pm_sim* s) {
+  if (!s->cfg.quantum) return PM_OK;
+  PMST(stencil_stage<R>(s));
+  if (spline(s)) PMST(smooth_field<R>(s, s->L.q));
+  return PM_OK;
+}
+
+// phi~ and Q~ from the density in `rho` (cloud-in-cell kernel: the deposit;
+// spline kernel: the already smoothed density, whose force potential is
+// smoothed once more)
 template <typename R>
 pm_status mesh_from_density(pm_sim* s) {
   const Layout& L = s->L;
-  R* rho = s->at<R>(L.rho);
-  {
-    PROF(s, PM_STAGE_FFT_R2C);
-    if (s->fp64()) {
-      CF(s, cufftExecD2Z(s->plan_fwd, (cufftDoubleReal*)rho, (cufftDoubleComplex*)(s->arena + L.spec)));
-    } else {
-      CF(s, cufftExecR2C(s->plan_fwd, (cufftReal*)rho, (cufftComplex*)(s->arena + L.spec)));
-    }
-  }
-  const double N = s->cfg.n_mesh;
-  const double coef = -1.5 * s->cfg.omega_m * s->dx * s->dx / (4.0 * N * N * N);
+  PMST(fft_r2c<R>(s, s->arena + L.rho, s->arena + L.spec));
   {
     PROF(s, PM_STAGE_GREEN);
-    CU(s, launch_green<R>(s->arena + L.spec, s->mesh, coef, wg_part(s), s->stream));
+    if (spline(s))
+      CU(s, launch_green_spline<R>(s->arena + L.spec, nullptr, s->arena + L.what, s->mesh, green_coef(s), wg_part(s),
+                                   s->stream));
+    else
+      CU(s, launch_green<R>(s->arena + L.spec, s->mesh, green_coef(s), wg_part(s), s->stream));
   }
-  {
-    PROF(s, PM_STAGE_FFT_C2R);
-    if (s->fp64()) {
-      CF(s, cufftExecZ2D(s->plan_inv, (cufftDoubleComplex*)(s->arena + L.spec), (cufftDoubleReal*)(s->arena + L.phi)));
-    } else {
-      CF(s, cufftExecC2R(s->plan_inv, (cufftComplex*)(s->arena + L.spec), (cufftReal*)(s->arena + L.phi)));
-    }
-  }
-  if (s->cfg.quantum) {
-    pm_status st = stencil_stage<R>(s);
-    if (st != PM_OK) return st;
-  }
+  PMST(fft_c2r<R>(s, s->arena + L.spec, s->arena + L.phi));
+  PMST(quantum_stage<R>(s));
   s->fields_valid = true;
+  return PM_OK;
+}
+
+// spline kernel from the cloud-in-cell density in `rho`: one forward transform
+// gives both the smoothed density (back into `rho`) and the force potential
+template <typename R>
+pm_status spline_fields(pm_sim* s) {
+  const Layout& L = s->L;
+  PMST(fft_r2c<R>(s, s->arena + L.rho, s->arena + L.spec));
+  {
+    PROF(s, PM_STAGE_GREEN);
+    CU(s, launch_green_spline<R>(s->arena + L.spec, s->arena + L.spec2, s->arena + L.what, s->mesh, green_coef(s),
+                                 wg_part(s), s->stream));
+  }
+  PMST(fft_c2r<R>(s, s->arena + L.spec2, s->arena + L.rho));
+  PMST(fft_c2r<R>(s, s->arena + L.spec, s->arena + L.phi));
+  PMST(quantum_stage<R>(s));
+  s->fields_valid = true;
+  return PM_OK;
+}
+
+// the normalised symbol of the spline's node weights (once, at creation)
+template <typename R>
+pm_status spline_symbol(pm_sim* s) {
+  const Layout& L = s->L;
+  CU(s, launch_spline_weights<R>(s->arena + L.rho, s->mesh, s->cfg.smooth_h, s->stream));
+  PMST(fft_r2c<R>(s, s->arena + L.rho, s->arena + L.spec));
+  CU(s, launch_spline_symbol<R>(s->arena + L.spec, s->arena + L.what, s->mesh, s->stream));
   return PM_OK;
 }
 
@@ -496,7 +580,16 @@ template <typename R>
 pm_status compute_fields(pm_sim* s) {
   pm_status st = deposit<R>(s);
   if (st != PM_OK) return st;
-  return mesh_from_density<R>(s);
+  return spline(s) ? spline_fields<R>(s) : mesh_from_density<R>(s);
+}
+
+// the density of Eq. (rhodis) in `rho` (fields left invalid)
+template <typename R>
+pm_status density(pm_sim* s) {
+  PMST(deposit<R>(s));
+  if (spline(s)) PMST(smooth_field<R>(s, s->L.rho));
+  s->fields_valid = false;
+  return PM_OK;
 }
 
 KickParams base_kick(const pm_sim* s) {
@@ -724,6 +817,8 @@ void pm_config_default(pm_config* c) {
   c->cosmological = 1;
   c->rho_floor = 1e-6;
   c->rho_fp64 = 1e-2;
+  c->kernel = PM_KERNEL_CIC;
+  c->smooth_h = 3.5;
 }
 
 double pm_hbar_over_m(const pm_config* c) { return c ? hbar_over_m(c->m22, c->h) : 0.0; }
@@ -809,6 +904,17 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     delete s;
     return fail(nullptr, PM_ERR_CUDA, "stream setup failed");
   }
+  if (s->cfg.kernel == PM_KERNEL_SPLINE) {
+    pm_status st = DISPATCH(s, spline_symbol, s);
+    if (st == PM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) st = PM_ERR_CUDA;
+    if (st != PM_OK) {
+      const std::string msg = s->err;
+      cufftDestroy(s->plan_fwd);
+      cufftDestroy(s->plan_inv);
+      delete s;
+      return fail(nullptr, st, "spline kernel setup failed: %s", msg.c_str());
+    }
+  }
   *out = s;
   return PM_OK;
 }
@@ -867,9 +973,8 @@ pm_status pm_get_particles(pm_sim* s, double* x, double* p) {
 pm_status pm_deposit(pm_sim* s, double* rho_host) {
   pm_status st = check(s);
   if (st != PM_OK) return st;
-  st = DISPATCH(s, deposit, s);
+  st = DISPATCH(s, density, s);  // phi and Q no longer match rho until the mesh stages run
   if (st != PM_OK) return st;
-  s->fields_valid = false;  // phi and Q no longer match rho until the mesh stages run
   if (rho_host) return pm_get_field(s, PM_FIELD_RHO, rho_host);
   return PM_OK;
 }
@@ -1045,7 +1150,13 @@ pm_status pm_power_spectrum(pm_sim* s, int32_t nbins, double* k, double* P, int6
   if (st != PM_OK) return st;
   if (nbins < 1 || nbins > s->cfg.n_mesh / 2 || nbins > PK_MAX_BINS || !k || !P || !nmodes)
     return fail(s, PM_ERR_INVALID_ARG, "nbins must be in [1, N/2] with non-null outputs");
-  st = ensure_fields(s);
+  if (spline(s)) {
+    // P(k) of the particles' cloud-in-cell density (the mesh holds the smoothed one)
+    st = DISPATCH(s, deposit, s);
+    s->fields_valid = false;
+  } else {
+    st = ensure_fields(s);
+  }
   if (st != PM_OK) return st;
   const Layout& L = s->L;
   if (s->fp64()) {

@@ -14,6 +14,10 @@
                                               void*, void*, uint32_t, uint32_t*, cudaStream_t);                   \
   template cudaError_t launch_deposit<R>(const void*, const uint32_t*, int64_t, Mesh, double, R*, cudaStream_t, int);           \
   template cudaError_t launch_green<R>(void*, Mesh, double, double*, cudaStream_t);                               \
+  template cudaError_t launch_spline_weights<R>(void*, Mesh, double, cudaStream_t);                               \
+  template cudaError_t launch_spline_symbol<R>(const void*, void*, Mesh, cudaStream_t);                           \
+  template cudaError_t launch_green_spline<R>(void*, void*, const void*, Mesh, double, double*, cudaStream_t);    \
+  template cudaError_t launch_smooth_spec<R>(void*, const void*, Mesh, cudaStream_t);                             \
   template cudaError_t launch_stencil<R>(const R*, Mesh, StencilParams, R*, double*, uint32_t*, uint32_t*,       \
                                           uint32_t*, cudaStream_t);               \
   template cudaError_t launch_kick<R>(void*, void*, uint32_t*, int64_t, const R*, const R*, Mesh, KickParams,     \

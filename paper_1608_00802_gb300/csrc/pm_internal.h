@@ -122,6 +122,18 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
                            cudaStream_t s, int warps = 8);
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
+// cubic spline kernel: node weights, their normalised real symbol, the Green
+// multiplication with the symbol (spec2 null: spec already holds rho_W^) and
+// the smoothing of a transformed field
+template <typename R>
+cudaError_t launch_spline_weights(void* w, Mesh m, double hc, cudaStream_t s);
+template <typename R>
+cudaError_t launch_spline_symbol(const void* spec, void* what, Mesh m, cudaStream_t s);
+template <typename R>
+cudaError_t launch_green_spline(void* spec, void* spec2, const void* what, Mesh m, double coef, double* part,
+                                cudaStream_t s);
+template <typename R>
+cudaError_t launch_smooth_spec(void* spec, const void* what, Mesh m, cudaStream_t s);
 template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
                            uint32_t* list_count, uint32_t* err, cudaStream_t s);

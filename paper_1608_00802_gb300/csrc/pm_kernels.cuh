@@ -413,6 +413,97 @@ __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* sp
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
+// ---------------------------------------------------------------- cubic spline kernel
+// The cubic spline W(r, h) of Sec. II.A on the mesh: its weights W(|x_n|, h) dx^3
+// at the node offsets (periodic minimum image; with h = hc dx they are
+// 8/(pi hc^3) f(r/hc), r in cells), their transform's real part divided by its
+// k = 0 value (unit sum), and the multiplications by that symbol.
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_spline_weights(R* __restrict__ w, Mesh m, double hc) {
+  const int n = m.n;
+  const double c = 8.0 / (M_PI * hc * hc * hc);
+  for (uint32_t node = blockIdx.x * blockDim.x + threadIdx.x; node < m.n3; node += gridDim.x * blockDim.x) {
+    int x, y, z;
+    split_cell(node, m, x, y, z);
+    const double dx = x <= n / 2 ? x : x - n, dy = y <= n / 2 ? y : y - n, dz = z <= n / 2 ? z : z - n;
+    const double u = sqrt(dx * dx + dy * dy + dz * dz) / hc;
+    const double f = u <= 0.5 ? 1.0 - 6.0 * u * u + 6.0 * u * u * u : (u <= 1.0 ? 2.0 * (1.0 - u) * (1.0 - u) * (1.0 - u) : 0.0);
+    w[node] = R(c * f);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_spline_symbol(const typename VT<R>::cplx* __restrict__ spec,
+                                                                R* __restrict__ what, uint32_t total) {
+  const R w0 = spec[0].x;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x)
+    what[e] = spec[e].x / w0;
+}
+
+// The Green multiplication with the spline: spec holds rho^ (cloud-in-cell,
+// with spec2 given) or rho_W^ (spec2 null).  rho_W^ = W^ rho^ goes to spec2
+// (normalised for the inverse transform), the force potential
+// phi_S^ = W^ G rho_W^ replaces spec, and the W_g partial sums G |rho_W^|^2.
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_green_spline(typename VT<R>::cplx* spec,
+                                                               typename VT<R>::cplx* spec2,
+                                                               const R* __restrict__ what, Mesh m, R coef, R inv_n3,
+                                                               DivU32 dv, double* part) {
+  extern __shared__ __align__(16) unsigned char gs_smem[];
+  R* s2 = reinterpret_cast<R*>(gs_smem);
+  const uint32_t n = uint32_t(m.n), nh = n / 2 + 1;
+  const R inv_n = R(1) / R(n);
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) s2[j] = sinpi_sq(R(j) * inv_n);
+  __syncthreads();
+  R wsum = R(0);
+  const uint32_t total = m.n2 * nh, stride = gridDim.x * blockDim.x;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const uint32_t row = divu32(e, dv), jx = e - row * nh;
+    uint32_t jz, jy;
+    if (m.log2n >= 0) {
+      jz = row >> m.log2n;
+      jy = row & (n - 1u);
+    } else {
+      jz = row / n;
+      jy = row - jz * n;
+    }
+    const R syz = s2[jy] + s2[jz];
+    const R sk = syz + s2[jx];
+    const R g = (row == 0 && jx == 0) ? R(0) : coef / sk;
+    const R wk = what[e];
+    auto v = spec[e];
+    if (spec2) {
+      v.x *= wk;
+      v.y *= wk;
+      auto u = v;
+      u.x *= inv_n3;
+      u.y *= inv_n3;
+      spec2[e] = u;
+    }
+    const R w = (jx == 0 || jx == n / 2) ? R(1) : R(2);
+    wsum += w * g * (v.x * v.x + v.y * v.y);
+    const R f = g * wk;
+    v.x *= f;
+    v.y *= f;
+    spec[e] = v;
+  }
+  R acc[1] = {wsum};
+  block_sum_store<1>(acc, part, gridDim.x);
+}
+
+// spec *= W^ / N^3 (the smoothing of a transformed field, ready for the inverse transform)
+template <typename R>
+__global__ void __launch_bounds__(MESH_THREADS) k_smooth_spec(typename VT<R>::cplx* spec, const R* __restrict__ what,
+                                                              uint32_t total, R inv_n3) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    auto v = spec[e];
+    const R f = what[e] * inv_n3;
+    v.x *= f;
+    v.y *= f;
+    spec[e] = v;
+  }
+}
+
 // ---------------------------------------------------------------- quantum-pressure stencil
 // Q~_n = qcoef * sum_d [(s_{n+e_d} - s_n) + (s_{n-e_d} - s_n)] / s_n with
 // s = sqrt(max(rho, floor)) and neighbours at +-step (Eq. quantumpressure with
@@ -1215,6 +1306,36 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
   }
   const unsigned blocks = (m.n2 + warps - 1) / warps;
   k_deposit<R><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_spline_weights(void* w, Mesh m, double hc, cudaStream_t s) {
+  k_spline_weights<R><<<MESH_GRID, MESH_THREADS, 0, s>>>((R*)w, m, hc);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_spline_symbol(const void* spec, void* what, Mesh m, cudaStream_t s) {
+  using C = typename VT<R>::cplx;
+  k_spline_symbol<R><<<MESH_GRID, MESH_THREADS, 0, s>>>((const C*)spec, (R*)what, m.n2 * uint32_t(m.n / 2 + 1));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_green_spline(void* spec, void* spec2, const void* what, Mesh m, double coef, double* part,
+                                cudaStream_t s) {
+  using C = typename VT<R>::cplx;
+  k_green_spline<R><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>(
+      (C*)spec, (C*)spec2, (const R*)what, m, R(coef), R(1.0 / double(m.n3)), divu32_make(uint32_t(m.n / 2 + 1)), part);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_smooth_spec(void* spec, const void* what, Mesh m, cudaStream_t s) {
+  using C = typename VT<R>::cplx;
+  k_smooth_spec<R><<<MESH_GRID, MESH_THREADS, 0, s>>>((C*)spec, (const R*)what, m.n2 * uint32_t(m.n / 2 + 1),
+                                                      R(1.0 / double(m.n3)));
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_NO_MEMORY", 3: "PM_ERR
 FORCE_MESHGRAD, FORCE_HYBRID, FORCE_LAGRANGIAN = 0, 1, 2
 LAP_COMPACT, LAP_WIDE = 0, 1
 FP32, FP64 = 0, 1
+KERNEL_CIC, KERNEL_SPLINE = 0, 1
 FIELD_RHO, FIELD_PHI, FIELD_Q = 0, 1, 2
 
 # every entry point declared in include/pm.h
@@ -41,7 +42,8 @@ class pm_config(C.Structure):
                 ("box", C.c_double), ("omega_m", C.c_double), ("omega_l", C.c_double),
                 ("h", C.c_double), ("m22", C.c_double), ("quantum", C.c_int32),
                 ("force_mode", C.c_int32), ("lap", C.c_int32), ("cosmological", C.c_int32),
-                ("rho_floor", C.c_double), ("rho_fp64", C.c_double)]
+                ("rho_floor", C.c_double), ("rho_fp64", C.c_double), ("kernel", C.c_int32),
+                ("reserved", C.c_int32), ("smooth_h", C.c_double)]
 
 
 class pm_tuning(C.Structure):
@@ -126,7 +128,7 @@ def _dptr(a):
 
 def make_config(n_part, n_mesh, box, precision=FP32, omega_m=0.3, omega_l=0.7, h=0.7, m22=2.5,
                 quantum=True, force_mode=FORCE_MESHGRAD, lap=LAP_COMPACT, cosmological=True,
-                rho_floor=1e-6, rho_fp64=1e-2) -> pm_config:
+                rho_floor=1e-6, rho_fp64=1e-2, kernel=KERNEL_CIC, smooth_h=3.5) -> pm_config:
     cfg = pm_config()
     lib().pm_config_default(C.byref(cfg))
     cfg.n_part, cfg.n_mesh, cfg.box = int(n_part), int(n_mesh), float(box)
@@ -135,6 +137,7 @@ def make_config(n_part, n_mesh, box, precision=FP32, omega_m=0.3, omega_l=0.7, h
     cfg.quantum, cfg.force_mode, cfg.lap = int(bool(quantum)), int(force_mode), int(lap)
     cfg.cosmological = int(bool(cosmological))
     cfg.rho_floor, cfg.rho_fp64 = float(rho_floor), float(rho_fp64)
+    cfg.kernel, cfg.smooth_h = int(kernel), float(smooth_h)
     return cfg
 
 
@@ -144,7 +147,8 @@ def arena_bytes(cfg: pm_config) -> int:
 
 def tuning_key(cfg: pm_config) -> str:
     """Configurations with the same key share launch shapes."""
-    return "n%d_N%d_p%d_q%d_f%d_l%d" % (cfg.n_part, cfg.n_mesh, cfg.precision, cfg.quantum, cfg.force_mode, cfg.lap)
+    return "n%d_N%d_p%d_q%d_f%d_l%d_k%d" % (cfg.n_part, cfg.n_mesh, cfg.precision, cfg.quantum, cfg.force_mode,
+                                           cfg.lap, cfg.kernel)
 
 
 class TuningCache(dict):
