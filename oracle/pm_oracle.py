@@ -483,6 +483,56 @@ def run(x, p, a_start, a_end, nsteps, cfg: Config, energy_every=0):
     return x, p, hist
 
 
+def next_scale_factor(p_sync, parts, a0, a_end, cfg: Config, cfl):
+    """Adaptive step (Sec. II.A: the quantum acceleration enters the condition
+    that no particle moves farther than dx in one step).  The step's drift is
+    bounded by
+        (max|p_sync| + K_g(a0, a_h) max|g_phi| + K_q(a0, a_h) max|g_Q|) D(a0, a1)
+    (the opening half kick, then the drift with the kicked momentum); the
+    step ends at the largest a1 <= a_end that keeps the bound within cfl*dx,
+    found by bisection in ln a (static runs: in t)."""
+    gphi, gq = parts
+    pmax = float(np.max(np.sqrt(np.sum(p_sync * p_sync, axis=1)))) if len(p_sync) else 0.0
+    gmax = float(np.max(np.sqrt(np.sum(gphi * gphi, axis=1)))) if len(gphi) else 0.0
+    qmax = float(np.max(np.sqrt(np.sum(gq * gq, axis=1)))) if len(gq) else 0.0
+    limit = cfl * cfg.dx
+
+    def bound(a1):
+        ah = half_point(a0, a1, cfg)
+        return (pmax + kick_factor(a0, ah, cfg) * gmax + drift_factor(a0, ah, cfg) * qmax) * drift_factor(a0, a1, cfg)
+
+    if bound(a_end) <= limit:
+        return a_end
+    lo, hi = 0.0, 1.0  # fraction of the interval in ln a (or t)
+
+    def at(f):
+        if cfg.cosmological:
+            return a0 * (a_end / a0) ** f
+        return a0 + (a_end - a0) * f
+
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if bound(at(mid)) <= limit:
+            lo = mid
+        else:
+            hi = mid
+    return at(lo)
+
+
+def run_adaptive(x, p, a_start, a_end, cfg: Config, cfl=0.5, max_steps=100000):
+    """KDK steps from a_start to a_end with the adaptive step above; returns
+    (x, p, the step boundaries)."""
+    a = a_start
+    parts = force_parts(x, cfg)
+    bounds = [a]
+    while a < a_end and len(bounds) <= max_steps:
+        a1 = next_scale_factor(p, parts, a, a_end, cfg, cfl)
+        x, p, parts = kdk_step(x, p, a, a1, cfg, parts)
+        a = a1
+        bounds.append(a)
+    return x, p, np.array(bounds)
+
+
 # --------------------------------------------------------------------------
 # energies, Eq. (diskkinen) and Eq. (diskpoten)
 # --------------------------------------------------------------------------

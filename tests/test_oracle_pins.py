@@ -604,3 +604,59 @@ def test_spline_gravity_conserves_momentum():
         x = rng.uniform(0, 1, size=(300, 3))
         gphi, _ = O.force_parts(x, cfg)
         assert np.abs(gphi.sum(axis=0)).max() < 1e-12 * np.abs(gphi).sum()
+
+
+# ---------------------------------------------------------------- adaptive step (Sec. II.A)
+def _min_image(d, box):
+    return d - box * np.round(d / box)
+
+
+def test_adaptive_step_bounds_every_displacement():
+    """Every particle moves at most cfl*dx per step, and a step that stops
+    before a_end sits on the bound (the bisection finds its edge)."""
+    rng = np.random.default_rng(31)
+    cfg = O.Config(n_mesh=16, box=1.0, force_mode=O.HYBRID, m22=2.5)
+    x, p = ics.zeldovich(8, 16, 1.0, 1 / 101.0, 5, amplitude=6.0)
+    p = p * 3.0 + 0.02 * rng.standard_normal(p.shape)
+    cfl = 0.4
+    parts = O.force_parts(x, cfg)
+    a0, a_end = 1 / 101.0, 1 / 20.0
+    a1 = O.next_scale_factor(p, parts, a0, a_end, cfg, cfl)
+    assert a0 < a1 < a_end
+    gphi, gq = parts
+    ah = O.half_point(a0, a1, cfg)
+    b = (np.linalg.norm(p, axis=1).max() + O.kick_factor(a0, ah, cfg) * np.linalg.norm(gphi, axis=1).max()
+         + O.drift_factor(a0, ah, cfg) * np.linalg.norm(gq, axis=1).max()) * O.drift_factor(a0, a1, cfg)
+    assert b == pytest.approx(cfl * cfg.dx, rel=1e-9)
+    xs, ps, bounds = O.run_adaptive(x, p, a0, 1 / 60.0, cfg, cfl=cfl)
+    assert bounds[-1] == 1 / 60.0 and len(bounds) > 3
+    # replay the steps and check each one's displacement
+    xi, pi, parts = x, p, O.force_parts(x, cfg)
+    for k in range(len(bounds) - 1):
+        xn, pi, parts = O.kdk_step(xi, pi, bounds[k], bounds[k + 1], cfg, parts)
+        assert np.linalg.norm(_min_image(xn - xi, cfg.box), axis=1).max() <= cfl * cfg.dx * (1 + 1e-12)
+        xi = xn
+    np.testing.assert_allclose(xi, xs, rtol=0, atol=1e-14)
+
+
+def test_adaptive_step_free_streaming_count():
+    """No forces, static box, speed v: steps of exactly cfl*dx/v, so a span T
+    takes ceil(T v / (cfl dx)) steps."""
+    cfg = O.Config(n_mesh=16, box=1.0, omega_m=0.0, quantum=False, cosmological=False)
+    x, _ = ics.lattice(4, 16, 1.0)
+    v = 0.37
+    p = np.zeros_like(x)
+    p[:, 0] = v
+    p[:, 1] = -v * 0.5
+    speed = v * math.sqrt(1.25)
+    cfl, T = 0.5, 0.9
+    _, _, bounds = O.run_adaptive(x, p, 0.0, T, cfg, cfl=cfl)
+    assert len(bounds) - 1 == math.ceil(T * speed / (cfl * cfg.dx))
+    np.testing.assert_allclose(np.diff(bounds)[:-1], cfl * cfg.dx / speed, rtol=1e-12)
+
+
+def test_adaptive_step_at_rest_takes_one_step():
+    cfg = O.Config(n_mesh=8, box=1.0, omega_m=0.3, quantum=True, cosmological=False)
+    x, _ = ics.lattice(4, 8, 1.0)      # uniform density: no force
+    _, _, bounds = O.run_adaptive(x, np.zeros_like(x), 0.0, 2.0, cfg)
+    assert len(bounds) == 2
