@@ -152,6 +152,20 @@ pm_status pm_step(pm_sim* sim, double a0, double a1);
 #define PM_RUN_GRAPH_MAX_STEPS 4096
 pm_status pm_run(pm_sim* sim, int32_t nsteps, double a_start, double a_end);
 
+/* Leapfrog from a_start to a_end with adaptive steps (Sec. II.A: the time
+ * step keeps every particle within one cell width per step, the quantum
+ * acceleration included).  Each step first finds max|p_sync|, max|grad phi~|
+ * and max|grad Q~| over the particles, then ends at the largest a1 <= a_end
+ * for which (max|p_sync| + K_g(a, a_h) max|grad phi~| + K_q(a, a_h) max|grad Q~|)
+ * D(a, a1) <= cfl * dx, an upper bound of every particle's drift (a_h the
+ * half point, K and D the kick and drift weights); cfl in (0, 1].  Stops at
+ * a_end or after max_steps steps; the momenta are synchronised at the end.
+ * a_steps (nullable, max_steps + 1 doubles) receives the step boundaries,
+ * steps_taken (nullable) their number.  Static runs step in t.  Sync (one
+ * small device-to-host read per step). */
+pm_status pm_run_adaptive(pm_sim* sim, double a_start, double a_end, double cfl, int32_t max_steps,
+                          double* a_steps, int32_t* steps_taken);
+
 /* Energies at scale factor a for the current particles (momenta synchronised):
  * out = {K_v (Eq. diskkinen), W_g = (1/2a) sum (rho-1) phi dx^3,
  *        K_rho (Eq. diskpoten; forward differences for the compact Laplacian,

@@ -1014,6 +1014,80 @@ pm_status pm_step(pm_sim* s, double a0, double a1) {
   return pass(s, time_weights(s->cfg, ah, a1), zero, 0.0, true);
 }
 
+pm_status pm_run_adaptive(pm_sim* s, double a_start, double a_end, double cfl, int32_t max_steps, double* a_steps,
+                          int32_t* steps_taken) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (max_steps < 1) return fail(s, PM_ERR_INVALID_ARG, "max_steps must be >= 1");
+  if (!(cfl > 0.0 && cfl <= 1.0)) return fail(s, PM_ERR_INVALID_ARG, "cfl must be in (0, 1]");
+  if (!(a_end > a_start)) return fail(s, PM_ERR_INVALID_ARG, "a_end must exceed a_start");
+  if (s->cfg.cosmological && !(a_start > 0)) return fail(s, PM_ERR_INVALID_ARG, "a must be positive");
+  st = ensure_fields(s);
+  if (st != PM_OK) return st;
+  const pm_config& c = s->cfg;
+  const double limit = cfl * s->dx;
+  const int nkb = kick_blocks(s->n(), s->tune.kick_threads);
+  Weights pending = {0.0, 0.0};  // closing half kick of the previous step
+  double a = a_start;
+  int32_t done = 0;
+  if (a_steps) a_steps[0] = a;
+  while (a < a_end && done < max_steps) {
+    // the bound's inputs: max |p_sync|, max |grad phi~|, max |grad Q~| (one read-only particle pass)
+    KickParams km = base_kick(s);
+    km.cg1 = pending.kg;
+    km.cq1 = pending.kq;
+    km.maxima = 1;
+    st = DISPATCH(s, kick, s, km, nullptr);
+    if (st != PM_OK) return st;
+    double mx[3];
+    CU(s, launch_reduce_max(s->part(), nkb, 3, s->red(), s->stream));
+    CU(s, cudaMemcpyAsync(mx, s->red(), sizeof mx, cudaMemcpyDeviceToHost, s->stream));
+    CU(s, cudaStreamSynchronize(s->stream));
+    const double pmax = sqrt(mx[0]), gmax = sqrt(mx[1]), qmax = sqrt(mx[2]);
+    // the drift of the step, (max|p_sync| + K_g(a, a_h) g + K_q(a, a_h) q) D(a, a1), within cfl*dx:
+    // the largest a1 <= a_end, by bisection in ln a (static: in t)
+    auto bound = [&](double a1) {
+      const Weights wh = time_weights(c, a, half_point(c, a, a1));
+      return (pmax + wh.kg * gmax + wh.kq * qmax) * time_weights(c, a, a1).kq;
+    };
+    auto at = [&](double f) { return c.cosmological ? a * pow(a_end / a, f) : a + (a_end - a) * f; };
+    double a1 = a_end;
+    if (!(bound(a_end) <= limit)) {
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (bound(at(mid)) <= limit)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      a1 = at(lo);
+      if (!(a1 > a)) return fail(s, PM_ERR_NONFINITE, "adaptive step collapsed at a = %g", a);
+    }
+    // the step: closing half kick of the previous step + opening half kick + drift, then the forces at a1
+    const double ah = half_point(c, a, a1);
+    const Weights wo = time_weights(c, a, ah);
+    KickParams kp = base_kick(s);
+    kp.cg1 = pending.kg;
+    kp.cq1 = pending.kq;
+    kp.cg2 = wo.kg;
+    kp.cq2 = wo.kq;
+    kp.drift = time_weights(c, a, a1).kq / s->dx;
+    st = DISPATCH(s, kick, s, kp, nullptr);
+    if (st != PM_OK) return st;
+    st = ensure_fields(s);
+    if (st != PM_OK) return st;
+    pending = time_weights(c, ah, a1);
+    a = a1;
+    ++done;
+    if (a_steps) a_steps[done] = a;
+  }
+  st = pass(s, pending, Weights{0.0, 0.0}, 0.0, true);  // closing half kick: synchronised momenta
+  if (st != PM_OK) return st;
+  if (steps_taken) *steps_taken = done;
+  return device_errors(s);
+}
+
 pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
   pm_status st = check(s);
   if (st != PM_OK) return st;

@@ -42,6 +42,7 @@ struct KickParams {
   int quantum;        // Q force on/off
   int diag;           // accumulate sum p_sync^2 and sum p_sync per block
   int accel_out;      // write -(cg1 grad phi + cq1 grad Q) to acc[id] and leave the state
+  int maxima;         // leave the state; per-block maxima of |p_sync|^2, |grad phi|^2, |grad Q|^2
 };
 
 struct StencilParams {
@@ -152,6 +153,8 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R
 template <typename R>
 cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);
+// out[v] = max_b part[v*nblocks + b]
+cudaError_t launch_reduce_max(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);
 template <typename R>
 cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Mesh m, double dx, double* x,
                                  double* p, cudaStream_t s);

@@ -1099,8 +1099,35 @@ __device__ __forceinline__ int carry(R& o) {
   return c;
 }
 
+// Per-block maxima of NV fp32 values (thread 0 writes part[k*nblocks + bid]).
+template <int NV>
+__device__ __forceinline__ void block_max_store(const float (&v)[NV], double* part, int nblocks, int bid) {
+  __shared__ float shm[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float m[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    m[k] = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m[k] = fmaxf(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
+    if (lane == 0) shm[warp][k] = m[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float r = 0.0f;
+      for (int w = 0; w < nw; ++w) r = fmaxf(r, shm[w][k]);
+      part[k * nblocks + bid] = double(r);
+    }
+  }
+}
+
 // MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync; 2: write
-// the accelerations only.  Separate instantiations keep the common pass lean.
+// the accelerations only; 3: leave the state and write the per-block maxima of
+// |p_sync|^2, |grad phi|^2 and |grad Q|^2 (the adaptive step's bound).
+// Separate instantiations keep the common pass lean.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(KICK_THREADS, 4) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
                                                        uint32_t* keys, int64_t n, const R* __restrict__ phi,
@@ -1142,7 +1169,12 @@ __global__ void __launch_bounds__(KICK_THREADS, 4) k_kick(typename VT<R>::v4* po
     }
     const R cg1 = R(kp.cg1), cq1 = R(kp.cq1);
     R d1[3] = {cg1 * gp[0] + cq1 * gq[0], cg1 * gp[1] + cq1 * gq[1], cg1 * gp[2] + cq1 * gq[2]};
-    if (MODE == 2) {
+    if (MODE == 3) {
+      const R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
+      dg[0] = px * px + py * py + pz * pz;
+      dg[1] = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+      dg[2] = gq[0] * gq[0] + gq[1] * gq[1] + gq[2] * gq[2];
+    } else if (MODE == 2) {
       const uint32_t id = rec_id(mo);
       acc_out[3 * size_t(id) + 0] = -double(d1[0]);
       acc_out[3 * size_t(id) + 1] = -double(d1[1]);
@@ -1191,6 +1223,10 @@ __global__ void __launch_bounds__(KICK_THREADS, 4) k_kick(typename VT<R>::v4* po
     }
   }
   if (MODE == 1) block_sum_store<4>(dg, part, gridDim.x);
+  if (MODE == 3) {
+    const float mx[3] = {float(dg[0]), float(dg[1]), float(dg[2])};
+    block_max_store<3>(mx, part, gridDim.x, blockIdx.x);
+  }
 }
 
 // ---------------------------------------------------------------- power spectrum
@@ -1417,7 +1453,9 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R
   using V4 = typename VT<R>::v4;
   if (threads != 128 && threads != 256) threads = KICK_THREADS;
   const unsigned g = kick_blocks(n, threads);
-  if (kp.accel_out)
+  if (kp.maxima)
+    k_kick<R, 3><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+  else if (kp.accel_out)
     k_kick<R, 2><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if (kp.diag)
     k_kick<R, 1><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);

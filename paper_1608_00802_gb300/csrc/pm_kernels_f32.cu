@@ -82,6 +82,12 @@ Tuning default_tuning(int n) {
   return t;
 }
 
+cudaError_t launch_reduce_max(const double* part, int nblocks, int nvals, double* out, cudaStream_t s) {
+  if (nvals <= 0) return cudaSuccess;
+  k_reduce_max<<<nvals, 256, 0, s>>>(part, nblocks, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s) {
   if (nvals <= 0) return cudaSuccess;
   k_reduce<<<nvals, 256, 0, s>>>(part, nblocks, out);

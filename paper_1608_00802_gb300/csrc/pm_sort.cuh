@@ -316,6 +316,21 @@ static __global__ void k_reduce(const double* __restrict__ part, int nblocks, do
   if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
+// Maximum of per-block partials: out[v] = max_b part[v*nblocks + b].
+static __global__ void k_reduce_max(const double* __restrict__ part, int nblocks, double* out) {
+  __shared__ double sh[256];
+  const double* row = part + size_t(blockIdx.x) * nblocks;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s = fmax(s, row[b]);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
 // ---------------------------------------------------------------- incremental re-sort
 // After a drift the kick marks particles whose cell changed ("movers") by
 // setting bit 31 of their new key.  The others ("stayers") keep their key, so

@@ -29,7 +29,7 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
            "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error",
            "pm_batch_arena_bytes", "pm_batch_create", "pm_batch_destroy", "pm_batch_member", "pm_batch_run",
-           "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune"]
+           "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_run_adaptive"]
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
@@ -86,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_forces": (C.c_int, [vp, C.c_double, dp]),
         "pm_step": (C.c_int, [vp, C.c_double, C.c_double]),
         "pm_run": (C.c_int, [vp, C.c_int32, C.c_double, C.c_double]),
+        "pm_run_adaptive": (C.c_int, [vp, C.c_double, C.c_double, C.c_double, C.c_int32, dp,
+                                      C.POINTER(C.c_int32)]),
         "pm_energy": (C.c_int, [vp, C.c_double, dp]),
         "pm_power_spectrum": (C.c_int, [vp, C.c_int32, dp, dp, C.POINTER(C.c_int64)]),
         "pm_get_field": (C.c_int, [vp, C.c_int32, dp]),
@@ -257,6 +259,14 @@ class Sim:
 
     def run(self, nsteps, a_start, a_end):
         self._check(lib().pm_run(self.handle, int(nsteps), float(a_start), float(a_end)))
+
+    def run_adaptive(self, a_start, a_end, cfl=0.5, max_steps=100000):
+        """Adaptive leapfrog to a_end; returns the step boundaries (a or t)."""
+        bounds = np.empty(int(max_steps) + 1)
+        done = C.c_int32(0)
+        self._check(lib().pm_run_adaptive(self.handle, float(a_start), float(a_end), float(cfl), int(max_steps),
+                                          _dptr(bounds), C.byref(done)))
+        return bounds[:done.value + 1].copy()
 
     def energy(self, a):
         out = np.empty(6)
