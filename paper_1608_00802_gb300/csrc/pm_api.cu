@@ -1166,7 +1166,9 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
     cufftSetStream(s->plan_inv, user);
     if (st != PM_OK) return st;
     if (ec != cudaSuccess) return fail(s, PM_ERR_CUDA, "captured steps: %s", cudaGetErrorString(ec));
-    // the replays leave the state as it was before them (two sorts per graph)
+    // the replays leave the state as it was before them (two sorts per graph),
+    // except that their stencils skipped the K_rho partials
+    s->krho_valid = false;
     CU(s, cudaEventRecord(s->ev_out, s->cap));
     CU(s, cudaStreamWaitEvent(s->stream, s->ev_out, 0));
   } else {
@@ -1595,6 +1597,7 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     }
     cudaGraphExecDestroy(exec);
     if (ec != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ec));
+    for (int i = 0; i < n; ++i) b->sims[i]->krho_valid = false;  // the replayed stencils skipped K_rho
   }
   // an odd last step, then the closing half kicks, on the member streams
   BCU(cudaEventRecord(b->fork, b->cap));

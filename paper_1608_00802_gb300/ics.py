@@ -136,3 +136,86 @@ def lattice(n_part_side, n_mesh, box):
     iz, iy, ix = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     x = np.stack([(ix * r + 0.5) * dxm, (iy * r + 0.5) * dxm, (iz * r + 0.5) * dxm], axis=-1).reshape(-1, 3)
     return x, np.zeros_like(x)
+
+
+# --------------------------------------------------------------------------
+# solitonic core: the spherically symmetric ground state of the
+# Schroedinger-Poisson equations (the initial profile of the paper's static
+# soliton test, Sec. II.B, after Guzman & Urena-Lopez 2004)
+# --------------------------------------------------------------------------
+def _sp_rhs(r, y):
+    # units hbar/m = 1, 4 pi G = 1, psi(0) = 1; u = V - eps
+    psi, dpsi, u, du = y
+    if r == 0.0:
+        return [dpsi, 2.0 * u * psi / 3.0, du, psi * psi / 3.0]
+    return [dpsi, 2.0 * u * psi - 2.0 * dpsi / r, du, psi * psi - 2.0 * du / r]
+
+
+def _sp_shoot(u0, rmax=20.0):
+    from scipy.integrate import solve_ivp
+
+    def crosses(r, y):
+        return y[0]
+    crosses.terminal, crosses.direction = True, -1
+
+    def turns_up(r, y):
+        return y[1]
+    turns_up.terminal, turns_up.direction = True, 1
+    return solve_ivp(_sp_rhs, [0.0, rmax], [1.0, 0.0, u0, 0.0], rtol=1e-12, atol=1e-15,
+                     events=[crosses, turns_up], dense_output=True)
+
+
+def soliton_ground_state(npts=4000):
+    """(r, psi, u0) of the nodeless stationary state in units hbar/m = 1,
+    4 pi G = 1, psi(0) = 1 (rho = psi^2): psi'' + 2psi'/r = 2(V - eps) psi,
+    V'' + 2V'/r = psi^2.  The central value u0 = V(0) - eps is found by
+    bisection between solutions that cross zero and ones that turn up; psi is
+    cut where the bracketing solutions part (psi ~ 1e-6 of its centre)."""
+    lo, hi = -1.0, -0.25   # lo: crosses zero, hi: turns up
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        s = _sp_shoot(mid)
+        if len(s.t_events[0]):
+            lo = mid
+        else:
+            hi = mid
+    s_lo, s_hi = _sp_shoot(lo), _sp_shoot(hi)
+    r_end = min(s_lo.t[-1], s_hi.t[-1])
+    r = np.linspace(0.0, r_end, npts)
+    a, b = s_lo.sol(r)[0], s_hi.sol(r)[0]
+    psi = 0.5 * (a + b)
+    cut = np.argmax(np.abs(a - b) > 1e-6) if np.any(np.abs(a - b) > 1e-6) else npts
+    psi[cut:] = 0.0
+    return r, np.clip(psi, 0.0, None), 0.5 * (lo + hi)
+
+
+def soliton_particles(n_part, box, n_mesh, r95_cells, hbm, seed=0, center=None):
+    """n_part particles (mass box^3 / n_part each, so the mean density is 1)
+    drawn from the ground-state profile scaled to enclose 95 % of the mass
+    within r95_cells mesh cells, at rest.  The scaling symmetry of the SP
+    equations fixes the coupling: with hbar/m = hbm the profile of total mass
+    box^3 and that radius needs 4 pi G = gamma, returned as omega_m =
+    gamma / 1.5 for a static run (4 pi G rho_bar = 1.5 omega_m, rho_bar = 1).
+    Returns (x, p, omega_m, info)."""
+    r_d, psi, u0 = soliton_ground_state()
+    rho_d = psi * psi
+    dr = r_d[1] - r_d[0]
+    shell = 4.0 * np.pi * r_d * r_d * rho_d
+    m_cum = np.concatenate([[0.0], np.cumsum(0.5 * (shell[1:] + shell[:-1]) * dr)])
+    m_d = m_cum[-1]
+    r95_d = float(np.interp(0.95 * m_d, m_cum, r_d))
+    alpha = r95_cells * (box / n_mesh) / r95_d      # length scale
+    mass = box ** 3
+    gamma = hbm * hbm * m_d / (alpha * mass)        # 4 pi G
+    rng = np.random.Generator(np.random.Philox(seed))
+    u = rng.uniform(size=(n_part, 3))
+    rr = alpha * np.interp(u[:, 0] * m_d, m_cum, r_d)
+    cz = 2.0 * u[:, 1] - 1.0
+    ph = 2.0 * np.pi * u[:, 2]
+    sz = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
+    c = np.full(3, 0.5 * box) if center is None else np.asarray(center, dtype=np.float64)
+    x = np.stack([rr * sz * np.cos(ph), rr * sz * np.sin(ph), rr * cz], axis=1) + c
+    x = np.mod(x, box)
+    info = {"alpha": alpha, "gamma": gamma, "rho_c": hbm * hbm / (alpha ** 4 * gamma), "t_unit": alpha * alpha / hbm,
+            "r95": r95_cells * box / n_mesh, "u0": u0, "mass_dimless": m_d, "r95_dimless": r95_d}
+    return x, np.zeros_like(x), gamma / 1.5, info

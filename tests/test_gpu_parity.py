@@ -439,3 +439,18 @@ def test_largest_configuration_256_on_512(pm):
     gphi, gq = O.force_parts(xg[sample], ocfg, fields=fields)
     ref_acc = gphi / a + gq / (a * a)
     assert rel_rms(acc[sample], ref_acc) < 1e-5
+
+
+def test_energies_after_replayed_graph_steps(pm):
+    """pm_run replays its captured steps on later calls; the energies after such
+    a call must describe the new state (the replayed stencils skip the K_rho
+    sums, so pm_energy has to redo them), as for a fresh simulation there."""
+    sim, ocfg = make(pm, 24, 48, 1.0, "fp64", mode="lagrangian", amplitude=4.0)
+    a = np.geomspace(1 / 101.0, 1 / 60.0, 9)
+    sim.run(4, a[0], a[4])
+    sim.energy(a[4])
+    sim.run(4, a[4], a[8])                      # the graphs of the first call are reused
+    e = sim.energy(a[8])
+    x, p = sim.get_particles()
+    ref = O.energies(x, p, a[8], ocfg)
+    np.testing.assert_allclose(e[:3], ref[:3], rtol=1e-9)
