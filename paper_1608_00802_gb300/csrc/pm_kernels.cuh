@@ -260,17 +260,32 @@ __global__ void k_init_particles(const double* __restrict__ x, const double* __r
 // particle order, so the result is reproducible.
 constexpr int DEP_WARPS = 8;
 
+// Both halves of a batch's x-weights in one segmented scan: the particles of
+// a lane's cell t (sorted, so cells form runs of lanes) sum their f_x shares
+// (for node t+1) and 1 - f_x shares (for node t); the last lane of each run
+// adds them, first every run's f_x sum, then every run's 1 - f_x sum (the
+// same order, and the same bits, as two separate scans).  Lanes with `valid`
+// false carry unique targets past the row.
 template <typename R>
-__device__ __forceinline__ void seg_add(R v, int t, bool valid, R* acc) {
+__device__ __forceinline__ void seg_add2(R lo, R hi, int t, bool valid, R* acc) {
   const int lane = threadIdx.x & 31;
+  const int tp = __shfl_up_sync(0xffffffffu, t, 1);
+  const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || tp != t);
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    const R u = __shfl_up_sync(0xffffffffu, v, off);
-    const int tu = __shfl_up_sync(0xffffffffu, t, off);
-    if (lane >= off && tu == t) v += u;
+    const R ulo = __shfl_up_sync(0xffffffffu, lo, off);
+    const R uhi = __shfl_up_sync(0xffffffffu, hi, off);
+    // lane - off is in this lane's run iff no run starts in (lane - off, lane]
+    const uint32_t span = lane >= off ? ((2u << lane) - 1u) & ~((2u << (lane - off)) - 1u) : 0u;
+    if (lane >= off && !(heads & span)) {
+      lo += ulo;
+      hi += uhi;
+    }
   }
-  const int tn = __shfl_down_sync(0xffffffffu, t, 1);
-  if (valid && (lane == 31 || tn != t)) acc[t] += v;
+  const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  if (valid && last) acc[t + 1] += hi;
+  __syncwarp();
+  if (valid && last) acc[t] += lo;
   __syncwarp();
 }
 
@@ -308,8 +323,8 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
           hi = r.y * wyz;
           lo = (R(1) - r.y) * wyz;
         }
-        seg_add(hi, valid ? c + 1 : c, valid, acc);  // f_x to the node above (slot N = node 0)
-        seg_add(lo, c, valid, acc);                  // 1 - f_x to the node of the cell
+        // f_x to the node above (slot N = node 0), 1 - f_x to the node of the cell
+        seg_add2(lo, hi, c, valid, acc);
       }
     }
   }
