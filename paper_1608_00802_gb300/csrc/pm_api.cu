@@ -130,6 +130,10 @@ bool valid_config(const pm_config* c, std::string* why) {
     *why = "rho_floor must be positive";
     return false;
   }
+  if (c->fft_jit != 0 && c->fft_jit != 1) {
+    *why = "fft_jit must be 0 or 1";
+    return false;
+  }
   if (c->kernel != PM_KERNEL_CIC && c->kernel != PM_KERNEL_SPLINE) {
     *why = "kernel must be PM_KERNEL_CIC or PM_KERNEL_SPLINE";
     return false;
@@ -211,6 +215,7 @@ bool fft_work_bytes(const pm_config& c, size_t* out, std::string* why) {
       return false;
     }
     cufftSetAutoAllocation(h, 0);
+    if (c.fft_jit) cufftSetPlanPropertyInt64(h, NVFFT_PLAN_PROPERTY_INT64_PATIENT_JIT, 1);
     cufftResult r = cufftMakePlan3d(h, c.n_mesh, c.n_mesh, c.n_mesh, types[k], &ws[k]);
     cufftDestroy(h);
     if (r != CUFFT_SUCCESS) {
@@ -886,6 +891,8 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     size_t w = 0;
     cufftResult r = cufftCreate(plans[k]);
     if (r == CUFFT_SUCCESS) r = cufftSetAutoAllocation(*plans[k], 0);
+    if (r == CUFFT_SUCCESS && c->fft_jit)
+      r = cufftSetPlanPropertyInt64(*plans[k], NVFFT_PLAN_PROPERTY_INT64_PATIENT_JIT, 1);
     if (r == CUFFT_SUCCESS) r = cufftMakePlan3d(*plans[k], N, N, N, types[k], &w);
     if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(*plans[k], s->arena + L.work);
     if (r == CUFFT_SUCCESS) r = cufftSetStream(*plans[k], s->stream);
