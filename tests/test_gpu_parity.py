@@ -454,3 +454,16 @@ def test_energies_after_replayed_graph_steps(pm):
     x, p = sim.get_particles()
     ref = O.energies(x, p, a[8], ocfg)
     np.testing.assert_allclose(e[:3], ref[:3], rtol=1e-9)
+
+
+def test_patient_jit_plans_keep_parity(pm):
+    """Simulations planned in cuFFT's patient JIT mode (fft_jit) compute the same
+    accelerations within the fp32 bar."""
+    x, p = ics.zeldovich(32, 64, 1.0, 1 / 101.0, 42, amplitude=4.0)
+    cfg = pm.make_config(len(x), 64, 1.0, force_mode=pm.FORCE_HYBRID, fft_jit=True)
+    sim = pm.Sim(cfg)
+    sim.set_particles(x, p)
+    acc = sim.forces(1 / 101.0)
+    xg, _ = sim.get_particles()
+    ref = O.accelerations(xg, 1 / 101.0, O.Config(n_mesh=64, box=1.0, force_mode=O.HYBRID))
+    assert rel_rms(acc, ref) < 1e-5
