@@ -4,7 +4,8 @@
  * Method: Veltmaat & Niemeyer, "Cosmological particle-in-cell simulations with
  * ultralight axion dark matter", arXiv:1608.00802, Sec. II.A and Sec. III.
  * Each step (i) deposits the particle density on a periodic mesh with a
- * kernel estimate (Eq. rhodis; here the cloud-in-cell kernel), (ii) solves
+ * kernel estimate (Eq. rhodis: the cloud-in-cell kernel, or the paper's cubic
+ * spline of Sec. II.A through PM_KERNEL_SPLINE), (ii) solves
  * the gravity potential and evaluates the quantum pressure
  * Q = -(hbar^2/2m^2) lap(sqrt rho)/sqrt rho (Eq. quantumpressure, comoving
  * form Eq. comquantumpressure) with a seven-point Laplacian, (iii) turns both
