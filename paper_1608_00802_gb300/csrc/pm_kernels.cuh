@@ -1139,12 +1139,17 @@ __device__ __forceinline__ void block_max_store(const float (&v)[NV], double* pa
   }
 }
 
+// resident 256-thread blocks per SM the kick's register budget is cut for
+#ifndef PM_KICK_MINB
+#define PM_KICK_MINB 4
+#endif
+
 // MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync; 2: write
 // the accelerations only; 3: leave the state and write the per-block maxima of
 // |p_sync|^2, |grad phi|^2 and |grad Q|^2 (the adaptive step's bound).
 // Separate instantiations keep the common pass lean.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(KICK_THREADS, 4) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
+__global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
                                                        uint32_t* keys, int64_t n, const R* __restrict__ phi,
                                                        const R* __restrict__ qf, Mesh m, KickParams kp_arg,
                                                        const KickParams* __restrict__ kp_tab,
