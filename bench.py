@@ -410,6 +410,28 @@ def run_gpu(args):
                 "steps": K64, "ms_per_step": t64 / K64}
         s64.close()
 
+    # the same workload with the paper's cubic spline kernel (h = 3.5 dx): three more transforms per step
+    spline = None
+    if not args.no_spline:
+        cfgs = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP32, m22=w["m22"],
+                              force_mode=pm.FORCE_HYBRID, kernel=pm.KERNEL_SPLINE, smooth_h=3.5, fft_jit=True)
+        torch.cuda.empty_cache()
+        ssp = pm.Sim(cfgs, stream=stream)
+        ssp.set_particles(x, p)
+        ssp.autotune(reps=3)
+        with torch.cuda.stream(stream):
+            ssp.run(W, a[0], a[W])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ssp.run(K, a[W], a[W + K])
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ts = max_over_ranks(dist, e0.elapsed_time(e1))
+        spline = {"value": sum_over_ranks(dist, n * K) / (ts / 1e3), "unit": "particle-steps/s", "steps": K,
+                  "ms_per_step": ts / K, "kernel": "cubic spline, h = 3.5 dx (Sec. II.A)"}
+        ssp.close()
+
     batched = None
     if not args.no_batch:
         torch.cuda.empty_cache()
@@ -437,7 +459,8 @@ def run_gpu(args):
             "roofline": roofline, "step_roofline": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches,
             "launch_shapes": tuning,
-            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "batched": batched, "served": served,
+            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "spline_kernel": spline,
+            "batched": batched, "served": served,
             "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None}
     print(json.dumps(line))
     return 0
@@ -525,6 +548,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-spline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--tuning", default=None, help="launch shapes (pm_tuning fields as JSON) instead of the "
                     "autotuner's, for the single simulation")
