@@ -85,9 +85,11 @@ typedef struct {
   int32_t lap;         /* PM_LAP_* */
   int32_t cosmological;/* 1: comoving equations with a(t); 0: static, a = 1 */
   double rho_floor;    /* sqrt(rho) uses max(rho, rho_floor) (units of the mean); Q is
-                          undefined where rho = 0 (Sec. II.A) */
-  double rho_fp64;     /* PM_FP32 only: nodes with rho below this evaluate sqrt(rho) and Q
-                          in fp64 (ill-conditioned ratio); 0 disables */
+                          undefined where rho = 0 (Sec. II.A).  > 0; with PM_FP32 >= 1e-30 */
+  double rho_fp64;     /* PM_FP32 only: near-empty nodes (rho below this) whose fp32 Laplacian
+                          of sqrt(rho) is ill-conditioned (the sum of the seven sqrt values
+                          above 4 |Laplacian|) evaluate sqrt(rho) and Q in float-float
+                          (~48-bit significand) instead of fp32; 0 disables */
   int32_t kernel;      /* PM_KERNEL_* */
   int32_t reserved;    /* 0 */
   double smooth_h;     /* PM_KERNEL_SPLINE: smoothing length h in mesh cells, 1 .. n_mesh/4

@@ -126,8 +126,8 @@ bool valid_config(const pm_config* c, std::string* why) {
     *why = "cosmological run needs omega_m >= 0 and omega_m + omega_l > 0";
     return false;
   }
-  if (!(c->rho_floor > 0)) {
-    *why = "rho_floor must be positive";
+  if (!(c->rho_floor > 0) || (c->precision == PM_FP32 && !(c->rho_floor >= 1e-30))) {
+    *why = "rho_floor must be positive (at least 1e-30 with PM_FP32: a normal fp32 number)";
     return false;
   }
   if (c->fft_jit != 0 && c->fft_jit != 1) {

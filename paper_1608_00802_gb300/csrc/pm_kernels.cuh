@@ -97,23 +97,38 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   float e = fmaf(a.hi, b, -p);
   return fast_two_sum(p, fmaf(a.lo, b, e));
 }
-// sqrt and quotient start from the hardware approximations (a few ulp) and are
+// Hardware approximations of 1/sqrt(x) and 1/x (a few ulp) with subnormal
+// inputs and results flushed to zero; the stencils call them only on floored
+// densities (normal fp32 numbers, rho_floor >= 1e-30) and their square roots.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The square root starts from the hardware approximation (a few ulp) and is
 // refined by one Newton step whose residual is formed exactly with fma, which
-// brings them to float-float accuracy.
-__device__ __forceinline__ ff ff_sqrt(float x) {  // x > 0
-  const float rs = rsqrtf(x);
+// brings it to float-float accuracy.
+__device__ __forceinline__ ff ff_sqrt(float x) {  // x > 0, normal
+  const float rs = rsqrt_ftz(x);
   const float s = x * rs;
   const float r = fmaf(-s, s, x);  // x - s^2, exact
   return fast_two_sum(s, r * (0.5f * rs));
 }
-__device__ __forceinline__ ff ff_div(ff a, ff b) {
-  const float inv = __frcp_rn(b.hi);
+// fp32 quotient of two float-float numbers: the fp32 quotient from the
+// hardware reciprocal, refined by one Newton correction whose residual
+// a - q b is formed in float-float.  The result is rounded to fp32, and one
+// correction already brings it to about that rounding.
+__device__ __forceinline__ float ff_quot(ff a, ff b) {
+  const float inv = rcp_ftz(b.hi);
   const float q1 = a.hi * inv;
   const ff r = ff_sub(a, ff_mul_f(b, q1));
-  const float q2 = r.hi * inv;
-  const ff q = fast_two_sum(q1, q2);
-  const ff r2 = ff_sub(a, ff_add(ff_mul_f(b, q.hi), ff_mul_f(b, q.lo)));
-  return ff_add(q, {r2.hi * inv, 0.0f});
+  return fmaf(r.hi, inv, q1);
 }
 __device__ __forceinline__ ff ff_shfl_down(ff v, int o) {
   return {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
@@ -531,17 +546,37 @@ __device__ __forceinline__ R sfloor(R rho, R fl) {
   return r_sqrt(rho > fl ? rho : fl);
 }
 
-// Extended-precision evaluation of Q~ at one near-empty node (float-float:
-// sqrt, neighbour differences, sum and ratio).
+// Extended-precision evaluation of Q~ at one near-empty node: the seven
+// square roots in float-float, the Laplacian as (sum of the six neighbours)
+// - 6 s_0 in float-float, so that the cancellation between neighbours of
+// nearly equal density costs no digits, and the ratio to s_0 to fp32
+// rounding.
 static __device__ __forceinline__ float q_ext(float r0, float rxp, float rxm, float ryp, float rym, float rzp, float rzm,
                                            float fl, float qcoef) {
   const ff t0 = ff_sqrt(fmaxf(r0, fl));
-  const ff d[6] = {ff_sub(ff_sqrt(fmaxf(rxp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rxm, fl)), t0),
-                   ff_sub(ff_sqrt(fmaxf(ryp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rym, fl)), t0),
-                   ff_sub(ff_sqrt(fmaxf(rzp, fl)), t0), ff_sub(ff_sqrt(fmaxf(rzm, fl)), t0)};
-  const ff l = ff_add(ff_add(ff_add(d[0], d[1]), ff_add(d[2], d[3])), ff_add(d[4], d[5]));
-  const ff r = ff_div(l, t0);
-  return r.hi * qcoef + r.lo * qcoef;
+  const ff sx = ff_add(ff_sqrt(fmaxf(rxp, fl)), ff_sqrt(fmaxf(rxm, fl)));
+  const ff sy = ff_add(ff_sqrt(fmaxf(ryp, fl)), ff_sqrt(fmaxf(rym, fl)));
+  const ff sz = ff_add(ff_sqrt(fmaxf(rzp, fl)), ff_sqrt(fmaxf(rzm, fl)));
+  const ff l = ff_sub(ff_add(ff_add(sx, sy), sz), ff_mul_f(t0, 6.0f));
+  return ff_quot(l, t0) * qcoef;
+}
+
+// Which fp32 nodes are redone by q_ext.  A near-empty node (s_0 < slim) whose
+// fp32 Q~ may miss by more than ~2e-6: each s is within 2^-22 of sqrt(rho)
+// and the sums round at 2^-24, so the fp32 Laplacian is within ~2^-21 mag of
+// the exact one, mag = the sum of the seven s; its relative error is thus at
+// most 2^-21 mag / |lap|, and nodes with mag > ST_KAPPA |lap| are redone
+// (ST_KAPPA = 4: at most 1.9e-6 elsewhere).  Seven equal values give lap = 0
+// exactly in both evaluations and are kept.  Explicitly rounded operations,
+// so that every kernel takes the same decision on the same values.
+constexpr float ST_KAPPA = 4.0f;
+__device__ __forceinline__ bool q_needs_ext(float s0, float sxp, float sxm, float syp, float sym, float szp, float szm,
+                                            float lap, float slim) {
+  if (!(s0 < slim)) return false;
+  if ((sxp == s0) & (sxm == s0) & (syp == s0) & (sym == s0) & (szp == s0) & (szm == s0)) return false;
+  const float mag = __fadd_rn(__fadd_rn(__fadd_rn(sxp, sxm), __fadd_rn(syp, sym)),
+                              __fmaf_rn(6.0f, s0, __fadd_rn(szp, szm)));
+  return mag > __fmul_rn(ST_KAPPA, fabsf(lap));
 }
 
 template <typename R>
@@ -551,7 +586,7 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
   R ksum = R(0);
   const R fl = R(sp.rho_floor);
   const R qc = R(sp.qcoef);
-  const R lim64 = sizeof(R) == 4 ? R(sp.rho_fp64) : R(-1);
+  const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;  // fp32 only
   for (uint32_t node = blockIdx.x * blockDim.x + threadIdx.x; node < m.n3; node += gridDim.x * blockDim.x) {
     int x, y, z;
     split_cell(node, m, x, y, z);
@@ -570,8 +605,10 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
     R szp = sfloor(rzp, fl), szm = sfloor(rzm, fl);
     R lap = ((sxp - s0) + (sxm - s0)) + ((syp - s0) + (sym - s0)) + ((szp - s0) + (szm - s0));
     R qv = qc * lap / s0;
-    if (r0 < lim64) qv = R(q_ext(float(r0), float(rxp), float(rxm), float(ryp), float(rym), float(rzp), float(rzm),
-                                 float(sp.rho_floor), float(sp.qcoef)));
+    if (sizeof(R) == 4 && q_needs_ext(float(s0), float(sxp), float(sxm), float(syp), float(sym), float(szp),
+                                      float(szm), float(lap), slim))
+      qv = R(q_ext(float(r0), float(rxp), float(rxm), float(ryp), float(rym), float(rzp), float(rzm),
+                   float(sp.rho_floor), float(sp.qcoef)));
     q[node] = qv;
     if (st == 1) {
       R a = sxp - s0, b = syp - s0, c = szp - s0;
@@ -600,9 +637,10 @@ __global__ void __launch_bounds__(MESH_THREADS) k_stencil(const R* __restrict__ 
 // warp shuffles (the two edge lanes load theirs), y-neighbours from a
 // shared-memory copy of plane z (two warps also load the halo rows).  Each
 // density is read about once and its square root taken about once, at ~35
-// instructions per node.  Nodes with rho < rho_fp64 are collected in the
-// block's region of `list` (shared-memory counter) and recomputed in
-// float-float by the same block after its sweep.
+// instructions per node.  Near-empty nodes whose fp32 value is
+// ill-conditioned (q_needs_ext) are collected in the block's region of `list`
+// (shared-memory counter) and recomputed in float-float by the same block
+// after its sweep.
 #ifndef PM_ST_TY
 #define PM_ST_TY 16
 #endif
@@ -613,7 +651,7 @@ constexpr int ST_X = 32, ST_TY = PM_ST_TY, ST_Y = ST_TY, ST_ZCH = PM_ST_ZCH;
 
 __device__ __forceinline__ float s_of(float r, float fl) {
   const float x = fmaxf(r, fl);
-  return x * rsqrtf(x);
+  return x * rsqrt_ftz(x);
 }
 
 // the seven densities of a node: centre, x+, x-, y+, y-, z+, z-
@@ -721,14 +759,10 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
       const float dxp = sxp - sc, dyp = syp - sc, dzp = sp - sc;
       const float lap = (dxp + (sxm - sc)) + (dyp + (sym - sc)) + (dzp + (sm - sc));
       const uint32_t node = uint32_t(z) * m.n2 + col;
-      q[node] = __fdividef(qc * lap, sc);
+      q[node] = (qc * lap) * rcp_ftz(sc);
       if (diag) ff_accumulate(ksum, krho_term(dxp, dyp, dzp));
-      // near-empty: redone in float-float unless all seven values are equal
-      // (then the Laplacian is exactly zero either way)
-      if (sc < slim) {
-        if (!((sxp == sc) & (sxm == sc) & (syp == sc) & (sym == sc) & (sp == sc) & (sm == sc)))
-          my_list[atomicAdd(&s_cnt, 1u)] = node;
-      }
+      // near-empty and ill-conditioned: redone in float-float
+      if (q_needs_ext(sc, sxp, sxm, syp, sym, sp, sm, lap, slim)) my_list[atomicAdd(&s_cnt, 1u)] = node;
     }
     __syncthreads();  // S is rewritten next
     sm = sc;
@@ -757,8 +791,8 @@ static __global__ void __launch_bounds__(ST_X * ST_TY) k_stencil_tiled(const flo
 // planes are in flight while the threads work.  When a plane arrives its
 // s = sqrt(max(rho, floor)) is taken once into a ring of three s planes; Q~ of
 // plane z then reads s of z-1, z, z+1 from shared memory in float4 groups
-// along x.  Near-empty nodes go to a per-plane list and are redone in
-// float-float from the densities still in the ring.  Per node the arithmetic
+// along x.  Ill-conditioned near-empty nodes (q_needs_ext) go to a per-plane
+// list and are redone in float-float from the densities still in the ring.  Per node the arithmetic
 // is that of k_stencil_tiled, so both kernels give the same bits.
 constexpr int SB_THREADS = 256;
 constexpr uint32_t SB_WAIT_LIMIT = 1u << 20;
@@ -778,6 +812,11 @@ inline bool stencil_tile_shape_ok(int n, int ty, int tz) {
   if (n % 4 || !(ty == 1 || ty == 2 || ty == 4 || ty == 8) || n % ty) return false;
   if (tz < 2 || tz > 16 || tz > n) return false;
   return stencil_tile_smem(n, ty, tz) <= SB_SMEM_MAX;
+}
+
+// the fp32 compact stencil runs as one-shot tiles with these parameters
+inline bool stencil_tile_path(int n, const StencilParams& sp, bool fp32) {
+  return fp32 && sp.step == 1 && sp.ty > 0 && sp.stages == 0 && stencil_tile_shape_ok(n, sp.ty, sp.zlen);
 }
 
 inline bool stencil_bulk_shape_ok(int n, int ty, int zlen, int stages) {
@@ -871,13 +910,10 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_bulk(const float*
         const float sxm = k ? sc[k - 1] : xl, sxp = k < 3 ? sc[k + 1] : xr;
         const float dxp = sxp - sc[k], dyp = syp[k] - sc[k], dzp = szp[k] - sc[k];
         const float lap = (dxp + (sxm - sc[k])) + (dyp + (sym[k] - sc[k])) + (dzp + (szm[k] - sc[k]));
-        qv[k] = __fdividef(qc * lap, sc[k]);
+        qv[k] = (qc * lap) * rcp_ftz(sc[k]);
         if (diag) ff_accumulate(ksum, krho_term(dxp, dyp, dzp));
-        if (sc[k] < slim) {
-          if (!((sxp == sc[k]) & (sxm == sc[k]) & (syp[k] == sc[k]) & (sym[k] == sc[k]) & (szp[k] == sc[k]) &
-                (szm[k] == sc[k])))
-            list[atomicAdd(&s_cnt, 1u)] = uint16_t(e + k);
-        }
+        if (q_needs_ext(sc[k], sxp, sxm, syp[k], sym[k], szp[k], szm[k], lap, slim))
+          list[atomicAdd(&s_cnt, 1u)] = uint16_t(e + k);
       }
       *reinterpret_cast<float4*>(q + size_t(z) * m.n2 + size_t(y0) * n + e) = make_float4(qv[0], qv[1], qv[2], qv[3]);
     }
@@ -911,12 +947,16 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_bulk(const float*
 }
 
 // fp32 compact stencil, one tile per block with no sweep: a block owns `ty`
-// whole rows of `tz` planes and requests its whole input tile at once (the
-// (ty+2) x (tz+2) rows with halos, three bulk copies per plane, one mbarrier),
-// takes s in place, then evaluates Q~ of the interior from shared memory.  The
-// input of several resident blocks is in flight together and nothing waits
-// on a plane-by-plane chain.  Near-empty nodes go to the block's region of a
-// global list and are redone in float-float (densities reread through L2).
+// whole rows of `tz` planes and requests its whole input tile at once (one
+// mbarrier): the ty+2 rows (with the y halo) of each of its planes, and the
+// ty interior rows of the two halo planes; the four corner rows of the
+// (ty+2) x (tz+2) frame are no neighbour of any node in a seven-point
+// stencil, so they are neither copied nor used.  The block takes s in place,
+// then evaluates Q~ of the interior from shared memory.  The input of several
+// resident blocks is in flight together and nothing waits on a plane-by-plane
+// chain.  Ill-conditioned near-empty nodes (q_needs_ext) go to the block's
+// region of a global list and are redone in float-float (densities reread
+// through L2).
 // Per node the arithmetic is that of k_stencil_tiled (same bits).
 static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float* __restrict__ rho, Mesh m, float fl,
                                                                     float qc, float slim, int ty, int tz,
@@ -940,13 +980,15 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
     mbar_init_fence();
     s_cnt = 0;
     s_ok = 1;
-    mbar_arrive_expect(bar, uint32_t(nz + 2) * uint32_t(ty + 2) * row_bytes);
+    mbar_arrive_expect(bar, uint32_t(nz * (ty + 2) + 2 * ty) * row_bytes);
     for (int j = 0; j < nz + 2; ++j) {
       const float* pl = rho + size_t(wrap(z0 - 1 + j, n)) * m.n2;
       float* dst = S + size_t(j) * plane;
-      bulk_load(dst, pl + size_t(wrap(y0 - 1, n)) * n, row_bytes, bar);
       bulk_load(dst + row, pl + size_t(y0) * n, uint32_t(ty) * row_bytes, bar);
-      bulk_load(dst + size_t(ty + 1) * row, pl + size_t(wrap(y0 + ty, n)) * n, row_bytes, bar);
+      if (j > 0 && j <= nz) {  // the y halo rows of the tile's own planes
+        bulk_load(dst, pl + size_t(wrap(y0 - 1, n)) * n, row_bytes, bar);
+        bulk_load(dst + size_t(ty + 1) * row, pl + size_t(wrap(y0 + ty, n)) * n, row_bytes, bar);
+      }
     }
   }
   __syncthreads();
@@ -961,12 +1003,16 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
     if (tid == 0) mbar_wait(bar, 0, SB_WAIT_LIMIT);
     return;
   }
-  // s in place
+  // s in place: all rows of planes 1..nz (one contiguous span), then the
+  // interior rows of halo planes 0 and nz+1
   float4* S4 = reinterpret_cast<float4*>(S);
-  const int all4 = (nz + 2) * plane / 4;
-  for (int g = tid; g < all4; g += SB_THREADS) {
-    const float4 r = S4[g];
-    S4[g] = make_float4(s_of(r.x, fl), s_of(r.y, fl), s_of(r.z, fl), s_of(r.w, fl));
+  const int mid4 = nz * plane / 4, halo4 = ty * row / 4;
+  for (int g = tid; g < mid4 + 2 * halo4; g += SB_THREADS) {
+    const int h = g - mid4;
+    float4* at = h < 0 ? S4 + plane / 4 + g
+                       : (h < halo4 ? S4 + row / 4 + h : S4 + (nz + 1) * plane / 4 + row / 4 + (h - halo4));
+    const float4 r = *at;
+    *at = make_float4(s_of(r.x, fl), s_of(r.y, fl), s_of(r.z, fl), s_of(r.w, fl));
   }
   __syncthreads();
   ff ksum = {0.0f, 0.0f};
@@ -995,13 +1041,10 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float*
       const float sxm = k ? sc[k - 1] : xl, sxp = k < 3 ? sc[k + 1] : xr;
       const float dxp = sxp - sc[k], dyp = syp[k] - sc[k], dzp = szp[k] - sc[k];
       const float lap = (dxp + (sxm - sc[k])) + (dyp + (sym[k] - sc[k])) + (dzp + (szm[k] - sc[k]));
-      qv[k] = __fdividef(qc * lap, sc[k]);
+      qv[k] = (qc * lap) * rcp_ftz(sc[k]);
       if (diag) ff_accumulate(ksum, krho_term(dxp, dyp, dzp));
-      if (sc[k] < slim) {
-        if (!((sxp == sc[k]) & (sxm == sc[k]) & (syp[k] == sc[k]) & (sym[k] == sc[k]) & (szp[k] == sc[k]) &
-              (szm[k] == sc[k])))
-          my_list[atomicAdd(&s_cnt, 1u)] = node0 + k;
-      }
+      if (q_needs_ext(sc[k], sxp, sxm, syp[k], sym[k], szp[k], szm[k], lap, slim))
+        my_list[atomicAdd(&s_cnt, 1u)] = node0 + k;
     }
     *reinterpret_cast<float4*>(q + node0) = make_float4(qv[0], qv[1], qv[2], qv[3]);
   }
@@ -1421,9 +1464,9 @@ template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
                            uint32_t* list_count, uint32_t* err, cudaStream_t s) {
   if (sizeof(R) == 4 && sp.step == 1) {
-    // fp32 compact path: shared-memory tiles, near-empty nodes redone in float-float
+    // fp32 compact path: shared-memory tiles, ill-conditioned near-empty nodes redone in float-float
     const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;
-    if (sp.ty > 0 && sp.stages == 0 && stencil_tile_shape_ok(m.n, sp.ty, sp.zlen)) {
+    if (stencil_tile_path(m.n, sp, true)) {
       static bool done[64];
       int dev = 0;
       cudaGetDevice(&dev);

@@ -134,11 +134,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t epoch = *epoch_base + uint32_t(pass);
   if (threadIdx.x == 0) scratch[63] = atomicAdd(tile_counter, 1u);
-  for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
   __syncthreads();
   const uint32_t tile = scratch[63];
   const int64_t tile_base = int64_t(tile) * RS_TILE;
   if (tile_base >= n) return;  // whole block: tile ids past the data (grid sized for the largest count)
+  // (cleared counters are first read after the barriers of the digit scan below)
+  for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
   const int64_t rem = n - tile_base;
   const int tile_n = rem < RS_TILE ? int(rem) : RS_TILE;
   const int per = (radix + RS_THREADS - 1) / RS_THREADS;  // <= 4

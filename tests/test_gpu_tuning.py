@@ -84,6 +84,36 @@ def test_bulk_stencil_matches_oracle_near_empty(pm):
     assert np.all(np.abs(q - ref) <= 1e-6 * scale)
 
 
+def _q_rel_rms(pm, rho, rho_fp64, shape=None):
+    n = rho.shape[0]
+    cfg = pm.make_config((n // 2) ** 3, n, 1.0, m22=2.5, force_mode=pm.FORCE_HYBRID, rho_fp64=rho_fp64)
+    sim = pm.Sim(cfg)
+    if shape is not None:
+        sim.set_tuning(dict(sim.get_tuning(), **shape))
+    sim.set_density(rho)
+    q = sim.get_field(pm.FIELD_Q)
+    sim.close()
+    ref = O.quantum_potential(rho.astype(np.float32).astype(np.float64), O.Config(n_mesh=n, box=1.0, m22=2.5))
+    return float(np.sqrt(np.mean((q - ref) ** 2) / np.mean(ref ** 2)))
+
+
+@pytest.mark.parametrize("shape", [None, dict(stencil_rows=0), dict(stencil_rows=4, stencil_planes=8, stencil_stages=4)],
+                         ids=["tiles", "register-columns", "sweep"])
+def test_near_empty_branch_keeps_the_digits_fp32_loses(pm, shape):
+    """A smooth low-density field (all nodes below rho_fp64): the seven-point
+    Laplacian of s cancels to ~1e-5 of s (condition number ~1e5), so the fp32
+    formula keeps only a few digits of Q~; the extended-precision branch keeps
+    it to about fp32 rounding of Q~ itself.  The one-shot tile kernel
+    (default), the register-column kernel and the sweeping tile kernel."""
+    n = 32
+    z, y, x = np.indices((n, n, n)) * (2 * np.pi / n)
+    rho = 1e-3 * (1.0 + 1e-3 * (np.sin(x) + np.cos(2 * y + 0.4) + np.sin(z + 0.3)))
+    extended = _q_rel_rms(pm, rho, 1e-2, shape)
+    plain = _q_rel_rms(pm, rho, 0.0, shape)
+    assert extended < 1e-6
+    assert plain > 100 * extended    # the control: the same field without the branch
+
+
 def test_kick_and_deposit_shapes_give_identical_states(pm):
     ref = None
     for kt, dw in [(256, 8), (128, 2), (128, 8), (256, 1)]:
