@@ -339,7 +339,7 @@ def run_gpu(args):
     dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
     d = per_stage[dom]
     achieved = d["GBps"]
-    kernel_names = {"kick": "k_kick", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
+    kernel_names = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
                     "sort_pass": "k_sort_pass", "sort_histogram": "k_sort_histogram",
                     "row_start": "k_row_start", "sort_partition": "k_mover_scatter",
                     "sort_merge": "k_merge_gather"}

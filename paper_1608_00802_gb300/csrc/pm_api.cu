@@ -911,6 +911,7 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     delete s;
     return fail(nullptr, PM_ERR_CUDA, "stream setup failed");
   }
+  if (c->precision == PM_FP32) kick_stream_prepare();
   if (s->cfg.kernel == PM_KERNEL_SPLINE) {
     pm_status st = DISPATCH(s, spline_symbol, s);
     if (st == PM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) st = PM_ERR_CUDA;

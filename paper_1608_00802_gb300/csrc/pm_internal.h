@@ -146,6 +146,9 @@ int stencil_launch_blocks(int n, int ty, int zlen);
 int stencil_max_blocks(int n);
 bool stencil_shape_ok(int n, int ty, int zlen, int stages);
 Tuning default_tuning(int n);
+// sizes the fp32 streaming kick's grid for this device (an occupancy query;
+// call outside any stream capture, before the first kick)
+void kick_stream_prepare();
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
                         KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,

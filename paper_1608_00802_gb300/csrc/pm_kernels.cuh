@@ -1187,10 +1187,97 @@ __device__ __forceinline__ void block_max_store(const float (&v)[NV], double* pa
 #define PM_KICK_MINB 4
 #endif
 
-// MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync; 2: write
-// the accelerations only; 3: leave the state and write the per-block maxima of
-// |p_sync|^2, |grad phi|^2 and |grad Q|^2 (the adaptive step's bound).
-// Separate instantiations keep the common pass lean.
+// One particle of a kick pass: gradients at the particle, kick, drift, new
+// key.  MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync
+// (dg); 2: write the accelerations only; 3: leave the state and write
+// |p_sync|^2, |grad phi|^2 and |grad Q|^2 to dg (the adaptive step's bound).
+template <typename R, int MODE>
+__device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, typename VT<R>::v4 mo,
+                                              typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys,
+                                              const R* __restrict__ phi, const R* __restrict__ qf, const Mesh& m,
+                                              const KickParams& kp, double* acc_out, uint32_t* err, R (&dg)[4]) {
+  const uint32_t cell = rec_cell(ps);
+  int cx, cy, cz;
+  split_cell(cell, m, cx, cy, cz);
+  const int nn = m.n;
+  Stencil s;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    s.xi[k] = uint32_t(wrap(cx + k - 1, nn));
+    s.yi[k] = uint32_t(wrap(cy + k - 1, nn)) * uint32_t(nn);
+    s.zi[k] = uint32_t(wrap(cz + k - 1, nn)) * m.n2;
+  }
+  const R wx[2] = {R(1) - ps.y, ps.y}, wy[2] = {R(1) - ps.z, ps.z}, wz[2] = {R(1) - ps.w, ps.w};
+  const R inv_dx = R(kp.inv_dx);
+  R gp[3], gq[3] = {R(0), R(0), R(0)};
+  if (kp.grav_kernel)
+    grad_kernel(phi, s, wx, wy, wz, inv_dx, gp);
+  else
+    grad_central(phi, s, wx, wy, wz, inv_dx, gp);
+  if (kp.quantum) {
+    if (kp.q_kernel)
+      grad_kernel(qf, s, wx, wy, wz, inv_dx, gq);
+    else
+      grad_central(qf, s, wx, wy, wz, inv_dx, gq);
+  }
+  const R cg1 = R(kp.cg1), cq1 = R(kp.cq1);
+  R d1[3] = {cg1 * gp[0] + cq1 * gq[0], cg1 * gp[1] + cq1 * gq[1], cg1 * gp[2] + cq1 * gq[2]};
+  if (MODE == 3) {
+    const R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
+    dg[0] = px * px + py * py + pz * pz;
+    dg[1] = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+    dg[2] = gq[0] * gq[0] + gq[1] * gq[1] + gq[2] * gq[2];
+  } else if (MODE == 2) {
+    const uint32_t id = rec_id(mo);
+    acc_out[3 * size_t(id) + 0] = -double(d1[0]);
+    acc_out[3 * size_t(id) + 1] = -double(d1[1]);
+    acc_out[3 * size_t(id) + 2] = -double(d1[2]);
+  } else {
+    R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
+    if (MODE == 1) {
+      dg[0] = px * px + py * py + pz * pz;
+      dg[1] = px;
+      dg[2] = py;
+      dg[3] = pz;
+    }
+    const R cg2 = R(kp.cg2), cq2 = R(kp.cq2);
+    px -= cg2 * gp[0] + cq2 * gq[0];
+    py -= cg2 * gp[1] + cq2 * gq[1];
+    pz -= cg2 * gp[2] + cq2 * gq[2];
+    uint32_t ncell = cell;
+    R fx = ps.y, fy = ps.z, fz = ps.w;
+    if (kp.drift != 0.0) {
+      const R dr = R(kp.drift);
+      fx += px * dr;
+      fy += py * dr;
+      fz += pz * dr;
+      if (!finite3(fx, fy, fz) || !finite3(px, py, pz)) {
+        atomicOr(err, ERR_NONFINITE);
+        fx = ps.y;
+        fy = ps.z;
+        fz = ps.w;
+      }
+      int ccx = carry(fx), ccy = carry(fy), ccz = carry(fz);
+      if (ccx | ccy | ccz) {
+        int64_t ix = (int64_t(cx) + ccx) % nn, iy = (int64_t(cy) + ccy) % nn, iz = (int64_t(cz) + ccz) % nn;
+        ix += ix < 0 ? nn : 0;
+        iy += iy < 0 ? nn : 0;
+        iz += iz < 0 ? nn : 0;
+        ncell = (uint32_t(iz) * uint32_t(nn) + uint32_t(iy)) * uint32_t(nn) + uint32_t(ix);
+      }
+    } else if (!finite3(px, py, pz)) {
+      atomicOr(err, ERR_NONFINITE);
+    }
+    pos[i] = make_pos(ncell, fx, fy, fz);
+    mom[i] = make_mom(px, py, pz, rec_id(mo));
+    // the drift marks the particles that changed cell for the incremental re-sort;
+    // without a drift the keys (marked or not) stay as they are
+    if (kp.drift != 0.0) keys[i] = ncell | (ncell != cell ? KEY_MOVER : 0u);
+  }
+}
+
+// One particle per thread, every mode (separate instantiations keep the
+// common pass lean); MODE 1 and 3 write one partial per block.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
                                                        uint32_t* keys, int64_t n, const R* __restrict__ phi,
@@ -1198,97 +1285,50 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT
                                                        const KickParams* __restrict__ kp_tab,
                                                        const uint32_t* __restrict__ step, double* part,
                                                        double* acc_out, uint32_t* err) {
-  using V4 = typename VT<R>::v4;
   // weights by value, or (graph replay) from a per-step table indexed by a device step counter
   const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   R dg[4] = {R(0), R(0), R(0), R(0)};
-  if (i < n) {
-    V4 ps = pos[i];
-    V4 mo = mom[i];
-    const uint32_t cell = rec_cell(ps);
-    int cx, cy, cz;
-    split_cell(cell, m, cx, cy, cz);
-    const int nn = m.n;
-    Stencil s;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      s.xi[k] = uint32_t(wrap(cx + k - 1, nn));
-      s.yi[k] = uint32_t(wrap(cy + k - 1, nn)) * uint32_t(nn);
-      s.zi[k] = uint32_t(wrap(cz + k - 1, nn)) * m.n2;
-    }
-    const R wx[2] = {R(1) - ps.y, ps.y}, wy[2] = {R(1) - ps.z, ps.z}, wz[2] = {R(1) - ps.w, ps.w};
-    const R inv_dx = R(kp.inv_dx);
-    R gp[3], gq[3] = {R(0), R(0), R(0)};
-    if (kp.grav_kernel)
-      grad_kernel(phi, s, wx, wy, wz, inv_dx, gp);
-    else
-      grad_central(phi, s, wx, wy, wz, inv_dx, gp);
-    if (kp.quantum) {
-      if (kp.q_kernel)
-        grad_kernel(qf, s, wx, wy, wz, inv_dx, gq);
-      else
-        grad_central(qf, s, wx, wy, wz, inv_dx, gq);
-    }
-    const R cg1 = R(kp.cg1), cq1 = R(kp.cq1);
-    R d1[3] = {cg1 * gp[0] + cq1 * gq[0], cg1 * gp[1] + cq1 * gq[1], cg1 * gp[2] + cq1 * gq[2]};
-    if (MODE == 3) {
-      const R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
-      dg[0] = px * px + py * py + pz * pz;
-      dg[1] = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
-      dg[2] = gq[0] * gq[0] + gq[1] * gq[1] + gq[2] * gq[2];
-    } else if (MODE == 2) {
-      const uint32_t id = rec_id(mo);
-      acc_out[3 * size_t(id) + 0] = -double(d1[0]);
-      acc_out[3 * size_t(id) + 1] = -double(d1[1]);
-      acc_out[3 * size_t(id) + 2] = -double(d1[2]);
-    } else {
-      R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
-      if (MODE == 1) {
-        dg[0] = px * px + py * py + pz * pz;
-        dg[1] = px;
-        dg[2] = py;
-        dg[3] = pz;
-      }
-      const R cg2 = R(kp.cg2), cq2 = R(kp.cq2);
-      px -= cg2 * gp[0] + cq2 * gq[0];
-      py -= cg2 * gp[1] + cq2 * gq[1];
-      pz -= cg2 * gp[2] + cq2 * gq[2];
-      uint32_t ncell = cell;
-      R fx = ps.y, fy = ps.z, fz = ps.w;
-      if (kp.drift != 0.0) {
-        const R dr = R(kp.drift);
-        fx += px * dr;
-        fy += py * dr;
-        fz += pz * dr;
-        if (!finite3(fx, fy, fz) || !finite3(px, py, pz)) {
-          atomicOr(err, ERR_NONFINITE);
-          fx = ps.y;
-          fy = ps.z;
-          fz = ps.w;
-        }
-        int ccx = carry(fx), ccy = carry(fy), ccz = carry(fz);
-        if (ccx | ccy | ccz) {
-          int64_t ix = (int64_t(cx) + ccx) % nn, iy = (int64_t(cy) + ccy) % nn, iz = (int64_t(cz) + ccz) % nn;
-          ix += ix < 0 ? nn : 0;
-          iy += iy < 0 ? nn : 0;
-          iz += iz < 0 ? nn : 0;
-          ncell = (uint32_t(iz) * uint32_t(nn) + uint32_t(iy)) * uint32_t(nn) + uint32_t(ix);
-        }
-      } else if (!finite3(px, py, pz)) {
-        atomicOr(err, ERR_NONFINITE);
-      }
-      pos[i] = make_pos(ncell, fx, fy, fz);
-      mom[i] = make_mom(px, py, pz, rec_id(mo));
-      // the drift marks the particles that changed cell for the incremental re-sort;
-      // without a drift the keys (marked or not) stay as they are
-      if (kp.drift != 0.0) keys[i] = ncell | (ncell != cell ? KEY_MOVER : 0u);
-    }
-  }
+  if (i < n) kick_particle<R, MODE>(i, pos[i], mom[i], pos, mom, keys, phi, qf, m, kp, acc_out, err, dg);
   if (MODE == 1) block_sum_store<4>(dg, part, gridDim.x);
   if (MODE == 3) {
     const float mx[3] = {float(dg[0]), float(dg[1]), float(dg[2])};
     block_max_store<3>(mx, part, gridDim.x, blockIdx.x);
+  }
+}
+
+// The common pass (MODE 0) as a grid-stride loop over a grid of resident
+// blocks: each thread loads the records of its next particle before it works
+// on the current one, so that the record loads of one particle overlap the
+// mesh gathers of the previous one instead of adding a second dependent
+// memory latency per particle.
+#ifndef PM_KICK_STREAM_MINB
+#define PM_KICK_STREAM_MINB 3  // the prefetched records need registers beyond k_kick's cap
+#endif
+template <typename R>
+__global__ void __launch_bounds__(KICK_THREADS, PM_KICK_STREAM_MINB) k_kick_stream(
+    typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys, int64_t n, const R* __restrict__ phi,
+    const R* __restrict__ qf, Mesh m, KickParams kp_arg, const KickParams* __restrict__ kp_tab,
+    const uint32_t* __restrict__ step, uint32_t* err) {
+  using V4 = typename VT<R>::v4;
+  const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  V4 ps = pos[i], mo = mom[i];
+  R dg[4];
+  for (;;) {
+    const int64_t j = i + stride;
+    V4 nps = ps, nmo = mo;
+    if (j < n) {
+      nps = pos[j];
+      nmo = mom[j];
+    }
+    kick_particle<R, 0>(i, ps, mo, pos, mom, keys, phi, qf, m, kp, nullptr, err, dg);
+    if (j >= n) break;
+    i = j;
+    ps = nps;
+    mo = nmo;
   }
 }
 
@@ -1508,6 +1548,30 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
   return cudaGetLastError();
 }
 
+// resident blocks of k_kick_stream on the whole GPU for a block size, queried
+// once per device and block size (pm_create asks first, outside any capture);
+// if the query fails, one particle per thread
+template <typename R>
+int kick_stream_resident(int threads) {
+  static int cache[64][2];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int t = threads == 128 ? 0 : 1;
+  if (dev >= 0 && dev < 64 && cache[dev][t] > 0) return cache[dev][t];
+  int per_sm = 0, sms = 0, r = 1 << 30;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kick_stream<R>, threads, 0) == cudaSuccess &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && per_sm > 0 && sms > 0)
+    r = per_sm * sms;
+  else
+    cudaGetLastError();
+  if (dev >= 0 && dev < 64) cache[dev][t] = r;
+  return r;
+}
+inline unsigned kick_stream_blocks(int64_t n, int threads, int resident) {
+  const int64_t need = (n + threads - 1) / threads;
+  return unsigned(need < resident ? need : resident);
+}
+
 template <typename R>
 cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
                         KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
@@ -1522,6 +1586,9 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R
     k_kick<R, 2><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if (kp.diag)
     k_kick<R, 1><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+  else if constexpr (sizeof(R) == 4)  // the fp64 records would spill in the streaming loop
+    k_kick_stream<R><<<kick_stream_blocks(n, threads, kick_stream_resident<R>(threads)), threads, 0, s>>>(
+        (V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, err);
   else
     k_kick<R, 0><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   return cudaGetLastError();

@@ -40,6 +40,11 @@ cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, u
 
 size_t stencil_list_entries(int n) { return stencil_list_len(n); }
 
+void kick_stream_prepare() {
+  kick_stream_resident<float>(128);
+  kick_stream_resident<float>(256);
+}
+
 int stencil_launch_blocks(int n, int ty, int zlen) {
   if (ty <= 0) return stencil_blocks(n);
   return (n / ty) * ((n + zlen - 1) / zlen);
