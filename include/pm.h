@@ -87,8 +87,8 @@ typedef struct {
   double rho_floor;    /* sqrt(rho) uses max(rho, rho_floor) (units of the mean); Q is
                           undefined where rho = 0 (Sec. II.A).  > 0; with PM_FP32 >= 1e-30 */
   double rho_fp64;     /* PM_FP32 only: near-empty nodes (rho below this) whose fp32 Laplacian
-                          of sqrt(rho) is ill-conditioned (the sum of the seven sqrt values
-                          above 4 |Laplacian|) evaluate sqrt(rho) and Q in float-float
+                          of sqrt(rho) is ill-conditioned (the six neighbours' sqrt values
+                          plus 6 sqrt(rho) above 4 |Laplacian|) evaluate sqrt(rho) and Q in float-float
                           (~48-bit significand) instead of fp32; 0 disables */
   int32_t kernel;      /* PM_KERNEL_* */
   int32_t reserved;    /* 0 */

@@ -564,7 +564,8 @@ static __device__ __forceinline__ float q_ext(float r0, float rxp, float rxm, fl
 // Which fp32 nodes are redone by q_ext.  A near-empty node (s_0 < slim) whose
 // fp32 Q~ may miss by more than ~2e-6: each s is within 2^-22 of sqrt(rho)
 // and the sums round at 2^-24, so the fp32 Laplacian is within ~2^-21 mag of
-// the exact one, mag = the sum of the seven s; its relative error is thus at
+// the exact one, mag = sum of the six neighbours' s + 6 s_0 (the absolute
+// terms of the Laplacian); its relative error is thus at
 // most 2^-21 mag / |lap|, and nodes with mag > ST_KAPPA |lap| are redone
 // (ST_KAPPA = 4: at most 1.9e-6 elsewhere).  Seven equal values give lap = 0
 // exactly in both evaluations and are kept.  Explicitly rounded operations,
