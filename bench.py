@@ -341,7 +341,7 @@ def run_gpu(args):
     achieved = d["GBps"]
     kernel_names = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
                     "sort_pass": "k_sort_pass", "sort_histogram": "k_sort_histogram",
-                    "row_start": "k_row_start", "sort_partition": "k_mover_scatter",
+                    "row_start": "k_row_start", "sort_partition": "k_mover_partition",
                     "sort_merge": "k_merge_gather"}
     roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak if achieved else None,
