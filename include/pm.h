@@ -239,6 +239,10 @@ enum {
   PM_STAGE_SORT_PARTITION = 9, PM_STAGE_SORT_MERGE = 10, PM_STAGE_OTHER = 11, PM_NSTAGES = 12
 };
 
+/* Incremental re-sorts since pm_create (one per drift of the particles) and
+ * the particles they moved to another cell, summed on the device.  Sync. */
+pm_status pm_sort_stats(pm_sim* sim, int64_t* resorts, int64_t* movers);
+
 /* Starts recording a CUDA-event pair around every launch of this handle, for
  * up to `capacity` launches (events are created here, before any timed work).
  * Async. */
@@ -292,26 +296,33 @@ const char* pm_batch_last_error(const pm_batch* b);
  *
  * pm_deposit_noalloc computes the same cloud-in-cell density as pm_deposit
  * (step (i); fp32 path: cell + offset positions, stable radix sort by cell,
- * deterministic gather) from n_part positions x_dev (device memory, n_part x 3
- * doubles in [0, box), wrapped periodically otherwise) into rho_dev (device
- * memory, n_mesh^3 floats, [z][y][x], mean 1), enqueued on the cudaStream_t
- * `stream` (NULL = legacy default stream); async.  It calls no cudaMalloc,
- * cudaFree or allocating library routine: all temporaries live in one
- * file-scope static device array of PM_NOALLOC_SCRATCH_BYTES, which every GPU
- * that loads the library holds until the process exits.  Limits:
+ * deterministic gather; the same bits as pm_deposit on the same positions)
+ * from n_part positions x_dev (device memory, n_part x 3 doubles in [0, box),
+ * wrapped periodically otherwise) into rho_dev (device memory, n_mesh^3
+ * floats, [z][y][x], mean 1), enqueued on the cudaStream_t `stream` (NULL =
+ * legacy default stream); async.  err_dev (nullable; device memory or mapped
+ * pinned host memory) receives, in stream order after the deposit, the
+ * call's device error bits: 0 = ok, bit 0 (1) = a non-finite position was
+ * placed at 0, bit 1 (2) = a bounded wait of the sort gave up and rho_dev is
+ * invalid.  The host return value cannot report these without a
+ * synchronisation, which this entry point does not make.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: all temporaries live
+ * in one file-scope static device array of PM_NOALLOC_SCRATCH_BYTES, which
+ * every GPU that loads the library holds until the process exits.  Limits:
  * 1 <= n_part <= PM_NOALLOC_MAX_PARTICLES and n_mesh even in
  * [8, PM_NOALLOC_MAX_MESH]; larger sizes return PM_ERR_INVALID_ARG and
  * pm_last_error(NULL) says which limit was exceeded.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call
- * reuses the same array and clears what must start at zero, so calls that
- * overlap on the GPU (other streams, other host threads) race: serialise them.
- * Non-finite positions are placed at 0. */
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) after it.  Every call reuses the same array and clears
+ * what must start at zero, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them. */
 #define PM_NOALLOC_MAX_PARTICLES 65536
 #define PM_NOALLOC_MAX_MESH 128
 #define PM_NOALLOC_SCRATCH_BYTES (8u << 20)
 pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh, double box, float* rho_dev,
-                             void* stream);
+                             uint32_t* err_dev, void* stream);
 
 /* Message of the last failure on this handle (or of the last pm_create
  * failure when sim is NULL). */

@@ -88,8 +88,8 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[4], vals[3], tile_cnt, row_start, rho, phi, q, spec, what, spec2, work, staging, hist, status,
-      st_list, st_count, part, part_aux, red, err, ktab, total;
+  size_t pos[2], mom[2], keys[4], vals[3], src, tcount, tile_cnt, row_start, rho, phi, q, spec, what, spec2, work, staging,
+      hist, status, st_list, st_count, part, part_aux, red, err, ktab, total;
   int key_bits, passes, digit_bits, ntiles;
 };
 
@@ -170,6 +170,8 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   for (int k = 0; k < 2; ++k) L.mom[k] = take(n * recsz);
   for (int k = 0; k < 4; ++k) L.keys[k] = take(n * 4);
   for (int k = 0; k < 3; ++k) L.vals[k] = take(n * 4);
+  L.src = take(n * 4);                              // slot of every sorted index
+  L.tcount = take(size_t(mover_count_words(int64_t(n))) * 4);  // movers per tile and group
   L.tile_cnt = take(16);  // (stayers, movers) of the last re-sort
   L.row_start = take((N * N + 1) * 4);
   L.rho = take(n3 * rsz);
@@ -185,8 +187,7 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   if (n3 * 8 > stage) stage = n3 * 8;
   L.staging = take(stage);
   // digit histograms of all passes (radix_max stride), one tile counter per pass
-  // (+ the partition's), then the partition's status word per tile
-  L.hist = take(hist_bytes() + size_t(L.ntiles) * 8);
+  L.hist = take(hist_bytes());
   L.status = take((size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8);
   size_t nkb = size_t(kick_blocks(int64_t(n), KICK_MIN_THREADS));
   size_t npart = 4 * nkb;
@@ -277,9 +278,14 @@ struct pm_sim {
   }
   void* pos() const { return arena + L.pos[cur]; }
   void* mom() const { return arena + L.mom[cur]; }
+  // slot of every sorted index in pos()/mom() (written by every sort)
+  uint32_t* src() const { return at<uint32_t>(L.src); }
   bool fp64() const { return cfg.precision == PM_FP64; }
   int64_t n() const { return cfg.n_part; }
+  // err region: [0] error bits, [1] sort epoch, [2] device step counter; at byte 64 two
+  // 64-bit counters of the incremental re-sorts and of the particles they moved
   uint32_t* errword() const { return at<uint32_t>(L.err); }
+  unsigned long long* sort_stats() const { return reinterpret_cast<unsigned long long*>(arena + L.err + 64); }
   double* part() const { return at<double>(L.part); }
   double* red() const { return at<double>(L.red); }
   double* staging() const { return at<double>(L.staging); }
@@ -342,10 +348,11 @@ int kr_blocks(const pm_sim* s) {
 }
 
 // Incremental re-sort after a drift: the stayers are still in order, so the
-// movers are split off (stable partition), radix-sorted by (key, previous
-// slot) with their count known only on the device, and merged back; the merge
-// gathers the records into the other buffer and writes the row starts.  Same
-// order as the full sort.
+// movers are split off (stable partition, with the drift's per-tile mover
+// counts), radix-sorted by (key, previous slot) with their count known only on
+// the device, and merged back; the merge writes the sorted keys, the slot of
+// every sorted index and the row starts.  The records stay where the drift
+// wrote them.  Same order as the full sort.
 template <typename R>
 pm_status resort_movers(pm_sim* s) {
   const Layout& L = s->L;
@@ -354,17 +361,16 @@ pm_status resort_movers(pm_sim* s) {
   uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
   uint64_t* status = s->at<uint64_t>(L.status);
   uint32_t* counts = s->at<uint32_t>(L.tile_cnt);
-  uint64_t* pstatus = reinterpret_cast<uint64_t*>(s->arena + L.hist + hist_bytes());
   uint32_t* sk = s->keys_tmp[0];
   uint32_t* sv = s->at<uint32_t>(L.vals[0]);
   uint32_t* mk[2] = {s->keys_tmp[1], s->at<uint32_t>(L.keys[3])};
   uint32_t* mv[2] = {s->at<uint32_t>(L.vals[1]), s->at<uint32_t>(L.vals[2])};
-  // histograms, tile counters and the partition's status words start at zero
-  CU(s, cudaMemsetAsync(hist, 0, hist_bytes() + size_t(L.ntiles) * 8, s->stream));
+  // histograms and tile counters start at zero
+  CU(s, cudaMemsetAsync(hist, 0, hist_bytes(), s->stream));
   {
     PROF(s, PM_STAGE_SORT_PARTITION);
-    CU(s, launch_mover_partition(s->keys, n, pstatus, counters + 3, sk, sv, mk[0], mv[0], counts, hist, L.passes,
-                                 L.digit_bits, L.key_bits, s->errword() + 1, s->errword(), s->stream));
+    CU(s, launch_mover_partition(s->keys, n, s->at<uint32_t>(L.tcount), sk, sv, mk[0], mv[0], counts, hist,
+                                 L.passes, L.digit_bits, L.key_bits, s->errword() + 1, s->sort_stats(), s->stream));
   }
   int b = 0;
   for (int p = 0; p < L.passes; ++p) {
@@ -376,14 +382,11 @@ pm_status resort_movers(pm_sim* s) {
                               nullptr, nullptr, s->errword(), s->stream, counts + 1));
     b ^= 1;
   }
-  const int nxt = s->cur ^ 1;
   {
     PROF(s, PM_STAGE_SORT_MERGE);
-    CU(s, launch_merge_gather<R>(sk, sv, mk[b], mv[b], counts, n, s->keys, s->pos(), s->mom(),
-                                 s->arena + L.pos[nxt], s->arena + L.mom[nxt], uint32_t(s->cfg.n_mesh),
-                                 s->at<uint32_t>(L.row_start), s->stream));
+    CU(s, launch_merge(sk, sv, mk[b], mv[b], counts, n, s->keys, s->src(), uint32_t(s->cfg.n_mesh),
+                       s->at<uint32_t>(L.row_start), s->stream));
   }
-  s->cur = nxt;
   s->keys_marked = false;
   s->sorted = true;
   return PM_OK;
@@ -437,7 +440,8 @@ pm_status sort_particles(pm_sim* s) {
   }
   {
     PROF(s, PM_STAGE_ROW_START);
-    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->stream));
+    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->src(),
+                           s->stream));
   }
   s->sorted = true;
   return PM_OK;
@@ -520,6 +524,16 @@ pm_status quantum_stage(pm_sim* s) {
   return PM_OK;
 }
 
+// the K_rho partials of the current density (the steps skip them): Q~ again
+// with the sums, and, with the spline kernel, smoothed again as the step
+// smoothed it, so that the field the next kick reads is the same
+template <typename R>
+pm_status krho_stage(pm_sim* s) {
+  PMST(stencil_stage<R>(s, true));
+  if (spline(s)) PMST(smooth_field<R>(s, s->L.q));
+  return PM_OK;
+}
+
 // phi~ and Q~ from the density in `rho` (cloud-in-cell kernel: the deposit;
 // spline kernel: the already smoothed density, whose force potential is
 // smoothed once more)
@@ -576,8 +590,8 @@ pm_status deposit(pm_sim* s) {
     if (st != PM_OK) return st;
   }
   PROF(s, PM_STAGE_DEPOSIT);
-  CU(s, launch_deposit<R>(s->pos(), s->at<uint32_t>(s->L.row_start), s->n(), s->mesh, s->norm, s->at<R>(s->L.rho),
-                          s->stream, s->tune.dep_warps));
+  CU(s, launch_deposit<R>(s->pos(), s->src(), s->at<uint32_t>(s->L.row_start), s->n(), s->mesh, s->norm,
+                          s->at<R>(s->L.rho), s->stream, s->tune.dep_warps));
   return PM_OK;
 }
 
@@ -611,16 +625,23 @@ template <typename R>
 pm_status kick(pm_sim* s, const KickParams& kp, double* acc, const KickParams* kp_tab = nullptr,
                const uint32_t* step = nullptr) {
   const Layout& L = s->L;
-  if (kp.drift != 0.0 && !s->sorted) {  // movers are marked against the sorted cells
+  const bool drift = kp.drift != 0.0;
+  if (drift && !s->sorted) {  // movers are marked against the sorted cells
     pm_status st = sort_particles<R>(s);
     if (st != PM_OK) return st;
   }
+  // a drift writes the records in sorted order to the other buffer and counts its movers
+  const int nxt = s->cur ^ 1;
+  if (drift)
+    CU(s, cudaMemsetAsync(s->at<uint32_t>(L.tcount), 0, size_t(mover_count_words(s->n())) * 4, s->stream));
   {
     PROF(s, PM_STAGE_KICK);
-    CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, kp_tab,
-                         step, s->part(), acc, s->errword(), s->tune.kick_threads, s->stream));
+    CU(s, launch_kick<R>(s->pos(), s->mom(), s->src(), s->arena + L.pos[nxt], s->arena + L.mom[nxt], s->keys,
+                         s->at<uint32_t>(L.tcount), s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, kp_tab, step,
+                         s->part(), acc, s->errword(), s->tune.kick_threads, s->stream));
   }
-  if (kp.drift != 0.0) {
+  if (drift) {
+    s->cur = nxt;
     s->sorted = false;
     s->fields_valid = false;
     s->keys_marked = true;
@@ -902,7 +923,7 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
       return fail(nullptr, PM_ERR_CUFFT, "cuFFT plan setup failed (%d)", int(r));
     }
   }
-  if (cudaMemsetAsync(s->errword(), 0, 8, s->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(s->errword(), 0, 256, s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->arena + L.status, 0, (size_t(1) << L.digit_bits) * size_t(L.ntiles) * 8, s->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(s->stream) != cudaSuccess) {
@@ -1201,7 +1222,7 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   st = pass(s, Weights{0.0, 0.0}, Weights{0.0, 0.0}, 0.0, true);
   if (st != PM_OK) return st;
   if (s->cfg.quantum && !s->krho_valid) {  // the steps skip the K_rho sums: Q~ again, with them
-    st = DISPATCH(s, stencil_stage, s, true);
+    st = DISPATCH(s, krho_stage, s);
     if (st != PM_OK) return st;
   }
   const int nkb = kick_blocks(s->n(), s->tune.kick_threads);
@@ -1352,10 +1373,20 @@ pm_status pm_get_order(pm_sim* s, uint32_t* cell, uint32_t* id) {
     if (st != PM_OK) return st;
   }
   uint32_t* d = reinterpret_cast<uint32_t*>(s->staging());
-  CU(s, DISPATCH(s, launch_get_order, s->pos(), s->mom(), s->n(), d, d + s->n(), s->stream));
+  CU(s, DISPATCH(s, launch_get_order, s->pos(), s->mom(), s->src(), s->n(), d, d + s->n(), s->stream));
   CU(s, cudaMemcpyAsync(cell, d, size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
   CU(s, cudaMemcpyAsync(id, d + s->n(), size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
   return device_errors(s);
+}
+
+pm_status pm_sort_stats(pm_sim* s, int64_t* resorts, int64_t* movers) {
+  if (!s || !resorts || !movers) return PM_ERR_INVALID_ARG;
+  unsigned long long h[2];
+  CU(s, cudaMemcpyAsync(h, s->sort_stats(), sizeof h, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  *resorts = int64_t(h[0]);
+  *movers = int64_t(h[1]);
+  return PM_OK;
 }
 
 pm_status pm_profile_begin(pm_sim* s, int32_t capacity) {

@@ -73,6 +73,14 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_TILE_SHIFT = 11;
+static_assert(RS_TILE == (1 << RS_TILE_SHIFT), "RS_TILE is 2^RS_TILE_SHIFT");
+// the drift counts its movers per tile and per group of 2^RS_GROUP_SHIFT tiles
+constexpr int RS_GROUP_SHIFT = 6;
+inline int64_t mover_count_words(int64_t n) {
+  const int64_t tiles = (n + RS_TILE - 1) >> RS_TILE_SHIFT;
+  return tiles + ((tiles + (1 << RS_GROUP_SHIFT) - 1) >> RS_GROUP_SHIFT);
+}
 constexpr int RS_MAX_BITS = 10;
 // set in a sort key by the drift when the particle's cell changed (keys use at most 30 bits)
 constexpr uint32_t KEY_MOVER = 0x80000000u;
@@ -101,26 +109,28 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
                              const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
                              const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
                              cudaStream_t s, const uint32_t* n_dev = nullptr);
-// incremental re-sort after a drift (keys carry KEY_MOVER): stable partition
+// incremental re-sort after a drift (keys carry KEY_MOVER; tcount holds the
+// drift's mover counts per tile and per group of tiles): stable partition
 // into stayers (s_keys, s_vals) and movers (m_keys, m_vals) in one pass with
-// the movers' digit histograms (pstatus: one cleared word per tile; counts[0]
-// = stayers, counts[1] = movers), then the merge of stayers with the sorted
-// movers that gathers the records and writes the row starts
-cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, uint64_t* pstatus, uint32_t* tile_counter,
-                                   uint32_t* s_keys, uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals,
-                                   uint32_t* counts, uint32_t* hist, int passes, int digit_bits, int key_bits,
-                                   uint32_t* sort_epoch, uint32_t* err, cudaStream_t s);
-template <typename R>
-cudaError_t launch_merge_gather(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
-                                const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,
-                                const void* pos_in, const void* mom_in, void* pos_out, void* mom_out,
-                                uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);
+// the movers' digit histograms (counts[0] = stayers, counts[1] = movers),
+// then the merge of stayers with the sorted movers by (key, previous slot),
+// which writes the sorted keys, the slot of every sorted index (src) and the
+// row starts; the records stay where the drift wrote them
+cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, const uint32_t* tcount, uint32_t* s_keys,
+                                   uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals, uint32_t* counts,
+                                   uint32_t* hist, int passes, int digit_bits, int key_bits, uint32_t* sort_epoch,
+                                   unsigned long long* stats, cudaStream_t s);
+cudaError_t launch_merge(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
+                         const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,
+                         uint32_t* src_out, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);
 cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s);
-cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start,
+// row starts of sorted keys; src (nullable) receives the identity order
+cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, uint32_t* src,
                              cudaStream_t s);
+// src (nullable): slot of each sorted index (null: records in sorted order)
 template <typename R>
-cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
-                           cudaStream_t s, int warps = 8);
+cudaError_t launch_deposit(const void* pos, const uint32_t* src, const uint32_t* row_start, int64_t n, Mesh m,
+                           double norm, R* rho, cudaStream_t s, int warps = 8);
 template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
 // cubic spline kernel: node weights, their normalised real symbol, the Green
@@ -149,10 +159,14 @@ Tuning default_tuning(int n);
 // sizes the fp32 streaming kick's grid for this device (an occupancy query;
 // call outside any stream capture, before the first kick)
 void kick_stream_prepare();
+// reads the records of sorted index i at slot src[i] (src nullable) of (pos,
+// mom); with a drift writes them to (pos_out, mom_out)[i], the keys and the
+// mover counts tcount (cleared before), otherwise updates them in place
 template <typename R>
-cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
-                        KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
-                        uint32_t* err, int threads, cudaStream_t s);
+cudaError_t launch_kick(void* pos, void* mom, const uint32_t* src, void* pos_out, void* mom_out, uint32_t* keys,
+                        uint32_t* tcount, int64_t n, const R* phi, const R* q, Mesh m, KickParams kp,
+                        const KickParams* kp_tab, const uint32_t* step, double* part, double* acc, uint32_t* err,
+                        int threads, cudaStream_t s);
 template <typename R>
 cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);
@@ -162,8 +176,8 @@ template <typename R>
 cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Mesh m, double dx, double* x,
                                  double* p, cudaStream_t s);
 template <typename R>
-cudaError_t launch_get_order(const void* pos, const void* mom, int64_t n, uint32_t* cell, uint32_t* id,
-                             cudaStream_t s);
+cudaError_t launch_get_order(const void* pos, const void* mom, const uint32_t* src, int64_t n, uint32_t* cell,
+                             uint32_t* id, cudaStream_t s);
 template <typename R>
 cudaError_t launch_to_double(const R* f, int64_t n, double* out, cudaStream_t s);
 template <typename R>

@@ -45,6 +45,13 @@ __device__ __forceinline__ D4 make_mom(double px, double py, double pz, uint32_t
   r.w = __longlong_as_double((long long)id);
   return r;
 }
+// Records of the particle at sorted index i: slot src[i] of the record
+// buffers (src null: slot i).  The incremental re-sort leaves the records
+// where the last drift wrote them and gives their sorted order as src.
+__device__ __forceinline__ int64_t rec_slot(const uint32_t* __restrict__ src, int64_t i) {
+  return src ? int64_t(__ldg(src + i)) : i;
+}
+
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) {
   return __ldg(p);
@@ -258,7 +265,9 @@ __global__ void k_init_particles(const double* __restrict__ x, const double* __r
   }
   uint32_t cell = (uint32_t(c[2]) * uint32_t(m.n) + uint32_t(c[1])) * uint32_t(m.n) + uint32_t(c[0]);
   pos[i] = make_pos(cell, f[0], f[1], f[2]);
-  mom[i] = make_mom(R(p[3 * i]), R(p[3 * i + 1]), R(p[3 * i + 2]), uint32_t(i));
+  // p null: particles at rest (the allocation-free deposit needs no momenta)
+  mom[i] = p ? make_mom(R(p[3 * i]), R(p[3 * i + 1]), R(p[3 * i + 2]), uint32_t(i))
+             : make_mom(R(0), R(0), R(0), uint32_t(i));
   keys[i] = cell;
 }
 
@@ -281,13 +290,19 @@ constexpr int DEP_WARPS = 8;
 // adds them, first every run's f_x sum, then every run's 1 - f_x sum (the
 // same order, and the same bits, as two separate scans).  Lanes with `valid`
 // false carry unique targets past the row.
+// The scan stops after the steps the longest run needs (a batch of distinct
+// cells, the common case on a mesh of several cells per particle, takes none);
+// the steps it skips would add nothing, so the sums are the same bits.
 template <typename R>
 __device__ __forceinline__ void seg_add2(R lo, R hi, int t, bool valid, R* acc) {
   const int lane = threadIdx.x & 31;
   const int tp = __shfl_up_sync(0xffffffffu, t, 1);
   const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || tp != t);
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
+  // length of the run that starts at this lane (0 elsewhere), and the longest
+  const uint32_t above = heads & ~((2u << lane) - 1u);
+  const int len = ((heads >> lane) & 1u) ? (above ? __ffs(above) - 1 : 32) - lane : 0;
+  const int longest = int(__reduce_max_sync(0xffffffffu, uint32_t(len)));
+  for (int off = 1; off < longest; off <<= 1) {
     const R ulo = __shfl_up_sync(0xffffffffu, lo, off);
     const R uhi = __shfl_up_sync(0xffffffffu, hi, off);
     // lane - off is in this lane's run iff no run starts in (lane - off, lane]
@@ -306,6 +321,7 @@ __device__ __forceinline__ void seg_add2(R lo, R hi, int t, bool valid, R* acc) 
 
 template <typename R>
 __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
+                                                            const uint32_t* __restrict__ src,
                                                             const uint32_t* __restrict__ row_start, uint32_t np,
                                                             Mesh m, R norm, R* __restrict__ rho) {
   using V4 = typename VT<R>::v4;
@@ -328,12 +344,16 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
       const uint32_t e = min(__ldg(row_start + srow + 1), np);
       for (uint32_t j0 = b; j0 < e; j0 += 32) {
         const uint32_t j = j0 + lane;
-        const bool valid = j < e;
+        bool valid = j < e;
         R lo = R(0), hi = R(0);
         int c = n + 1 + lane;  // invalid lanes: unique targets past the row
         if (valid) {
-          const V4 r = ldg(pos + j);
-          c = int(rec_cell(r) - base_cell);
+          const V4 r = ldg(pos + rec_slot(src, j));
+          const uint32_t cx = rec_cell(r) - base_cell;
+          // a record outside this row (only after a sort whose look-back timed
+          // out, which the error word reports) is skipped, not written out of bounds
+          valid = cx < uint32_t(n);
+          c = valid ? int(cx) : c;
           const R wyz = (dy ? r.z : R(1) - r.z) * (dz ? r.w : R(1) - r.w);
           hi = r.y * wyz;
           lo = (R(1) - r.y) * wyz;
@@ -1192,9 +1212,17 @@ __device__ __forceinline__ void block_max_store(const float (&v)[NV], double* pa
 // key.  MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync
 // (dg); 2: write the accelerations only; 3: leave the state and write
 // |p_sync|^2, |grad phi|^2 and |grad Q|^2 to dg (the adaptive step's bound).
+// The particle has sorted index i and its records (ps, mo) came from `slot`.
+// With a drift the new records go to (pos_out, mom_out)[i], in sorted order
+// (the other buffer), the new key to keys[i], and a particle that changed
+// cell adds one to the mover count of its tile of RS_TILE sorted indices and
+// of its group of RS_TILE_GROUP tiles (tcount: tiles, then groups).  Without
+// a drift the records are updated in place at `slot`.
 template <typename R, int MODE>
-__device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, typename VT<R>::v4 mo,
-                                              typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys,
+__device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename VT<R>::v4 ps, typename VT<R>::v4 mo,
+                                              typename VT<R>::v4* pos, typename VT<R>::v4* mom,
+                                              typename VT<R>::v4* pos_out, typename VT<R>::v4* mom_out,
+                                              uint32_t* keys, uint32_t* tcount, uint32_t ntiles,
                                               const R* __restrict__ phi, const R* __restrict__ qf, const Mesh& m,
                                               const KickParams& kp, double* acc_out, uint32_t* err, R (&dg)[4]) {
   const uint32_t cell = rec_cell(ps);
@@ -1269,11 +1297,20 @@ __device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, 
     } else if (!finite3(px, py, pz)) {
       atomicOr(err, ERR_NONFINITE);
     }
-    pos[i] = make_pos(ncell, fx, fy, fz);
-    mom[i] = make_mom(px, py, pz, rec_id(mo));
     // the drift marks the particles that changed cell for the incremental re-sort;
     // without a drift the keys (marked or not) stay as they are
-    if (kp.drift != 0.0) keys[i] = ncell | (ncell != cell ? KEY_MOVER : 0u);
+    if (kp.drift != 0.0) {
+      pos_out[i] = make_pos(ncell, fx, fy, fz);
+      mom_out[i] = make_mom(px, py, pz, rec_id(mo));
+      keys[i] = ncell | (ncell != cell ? KEY_MOVER : 0u);
+      if (ncell != cell) {
+        atomicAdd(tcount + (i >> RS_TILE_SHIFT), 1u);
+        atomicAdd(tcount + ntiles + (i >> (RS_TILE_SHIFT + RS_GROUP_SHIFT)), 1u);
+      }
+    } else {
+      pos[slot] = make_pos(ncell, fx, fy, fz);
+      mom[slot] = make_mom(px, py, pz, rec_id(mo));
+    }
   }
 }
 
@@ -1281,7 +1318,9 @@ __device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, 
 // common pass lean); MODE 1 and 3 write one partial per block.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
-                                                       uint32_t* keys, int64_t n, const R* __restrict__ phi,
+                                                       const uint32_t* __restrict__ src, typename VT<R>::v4* pos_out,
+                                                       typename VT<R>::v4* mom_out, uint32_t* keys, uint32_t* tcount,
+                                                       int64_t n, const R* __restrict__ phi,
                                                        const R* __restrict__ qf, Mesh m, KickParams kp_arg,
                                                        const KickParams* __restrict__ kp_tab,
                                                        const uint32_t* __restrict__ step, double* part,
@@ -1289,8 +1328,13 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT
   // weights by value, or (graph replay) from a per-step table indexed by a device step counter
   const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint32_t ntiles = uint32_t((n + RS_TILE - 1) >> RS_TILE_SHIFT);
   R dg[4] = {R(0), R(0), R(0), R(0)};
-  if (i < n) kick_particle<R, MODE>(i, pos[i], mom[i], pos, mom, keys, phi, qf, m, kp, acc_out, err, dg);
+  if (i < n) {
+    const int64_t slot = rec_slot(src, i);
+    kick_particle<R, MODE>(i, slot, pos[slot], mom[slot], pos, mom, pos_out, mom_out, keys, tcount, ntiles, phi,
+                           qf, m, kp, acc_out, err, dg);
+  }
   if (MODE == 1) block_sum_store<4>(dg, part, gridDim.x);
   if (MODE == 3) {
     const float mx[3] = {float(dg[0]), float(dg[1]), float(dg[2])};
@@ -1308,26 +1352,33 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT
 #endif
 template <typename R>
 __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_STREAM_MINB) k_kick_stream(
-    typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys, int64_t n, const R* __restrict__ phi,
+    typename VT<R>::v4* pos, typename VT<R>::v4* mom, const uint32_t* __restrict__ src, typename VT<R>::v4* pos_out,
+    typename VT<R>::v4* mom_out, uint32_t* keys, uint32_t* tcount, int64_t n, const R* __restrict__ phi,
     const R* __restrict__ qf, Mesh m, KickParams kp_arg, const KickParams* __restrict__ kp_tab,
     const uint32_t* __restrict__ step, uint32_t* err) {
   using V4 = typename VT<R>::v4;
   const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const uint32_t ntiles = uint32_t((n + RS_TILE - 1) >> RS_TILE_SHIFT);
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  V4 ps = pos[i], mo = mom[i];
+  int64_t slot = rec_slot(src, i);
+  V4 ps = pos[slot], mo = mom[slot];
   R dg[4];
   for (;;) {
     const int64_t j = i + stride;
+    int64_t nslot = slot;
     V4 nps = ps, nmo = mo;
     if (j < n) {
-      nps = pos[j];
-      nmo = mom[j];
+      nslot = rec_slot(src, j);
+      nps = pos[nslot];
+      nmo = mom[nslot];
     }
-    kick_particle<R, 0>(i, ps, mo, pos, mom, keys, phi, qf, m, kp, nullptr, err, dg);
+    kick_particle<R, 0>(i, slot, ps, mo, pos, mom, pos_out, mom_out, keys, tcount, ntiles, phi, qf, m, kp, nullptr,
+                        err, dg);
     if (j >= n) break;
     i = j;
+    slot = nslot;
     ps = nps;
     mo = nmo;
   }
@@ -1396,11 +1447,12 @@ __global__ void k_get_particles(const typename VT<R>::v4* __restrict__ pos, cons
 
 template <typename R>
 __global__ void k_get_order(const typename VT<R>::v4* __restrict__ pos, const typename VT<R>::v4* __restrict__ mom,
-                            int64_t n, uint32_t* cell, uint32_t* id) {
+                            const uint32_t* __restrict__ src, int64_t n, uint32_t* cell, uint32_t* id) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  cell[i] = rec_cell(pos[i]);
-  id[i] = rec_id(mom[i]);
+  const int64_t slot = rec_slot(src, i);
+  cell[i] = rec_cell(pos[slot]);
+  id[i] = rec_id(mom[slot]);
 }
 
 template <typename R>
@@ -1427,8 +1479,8 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
 }
 
 template <typename R>
-cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
-                           cudaStream_t s, int warps) {
+cudaError_t launch_deposit(const void* pos, const uint32_t* src, const uint32_t* row_start, int64_t n, Mesh m,
+                           double norm, R* rho, cudaStream_t s, int warps) {
   using V4 = typename VT<R>::v4;
   if (warps < 1 || warps > DEP_WARPS) warps = DEP_WARPS;
   const size_t smem = size_t(warps) * (m.n + 1) * sizeof(R);
@@ -1445,7 +1497,7 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
     }
   }
   const unsigned blocks = (m.n2 + warps - 1) / warps;
-  k_deposit<R><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho);
+  k_deposit<R><<<blocks, warps * 32, smem, s>>>((const V4*)pos, src, row_start, uint32_t(n), m, R(norm), rho);
   return cudaGetLastError();
 }
 
@@ -1574,24 +1626,30 @@ inline unsigned kick_stream_blocks(int64_t n, int threads, int resident) {
 }
 
 template <typename R>
-cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, int64_t n, const R* phi, const R* q, Mesh m,
-                        KickParams kp, const KickParams* kp_tab, const uint32_t* step, double* part, double* acc,
-                        uint32_t* err, int threads, cudaStream_t s) {
+cudaError_t launch_kick(void* pos, void* mom, const uint32_t* src, void* pos_out, void* mom_out, uint32_t* keys,
+                        uint32_t* tcount, int64_t n, const R* phi, const R* q, Mesh m, KickParams kp,
+                        const KickParams* kp_tab, const uint32_t* step, double* part, double* acc, uint32_t* err,
+                        int threads, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   using V4 = typename VT<R>::v4;
   if (threads != 128 && threads != 256) threads = KICK_THREADS;
   const unsigned g = kick_blocks(n, threads);
+  V4 *p = (V4*)pos, *mo = (V4*)mom, *po = (V4*)pos_out, *moo = (V4*)mom_out;
   if (kp.maxima)
-    k_kick<R, 3><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 3><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
+                                        err);
   else if (kp.accel_out)
-    k_kick<R, 2><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 2><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
+                                        err);
   else if (kp.diag)
-    k_kick<R, 1><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 1><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
+                                        err);
   else if constexpr (sizeof(R) == 4)  // the fp64 records would spill in the streaming loop
     k_kick_stream<R><<<kick_stream_blocks(n, threads, kick_stream_resident<R>(threads)), threads, 0, s>>>(
-        (V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, err);
+        p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, err);
   else
-    k_kick<R, 0><<<g, threads, 0, s>>>((V4*)pos, (V4*)mom, keys, n, phi, q, m, kp, kp_tab, step, part, acc, err);
+    k_kick<R, 0><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
+                                        err);
   return cudaGetLastError();
 }
 
@@ -1612,11 +1670,11 @@ cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Me
 }
 
 template <typename R>
-cudaError_t launch_get_order(const void* pos, const void* mom, int64_t n, uint32_t* cell, uint32_t* id,
-                             cudaStream_t s) {
+cudaError_t launch_get_order(const void* pos, const void* mom, const uint32_t* src, int64_t n, uint32_t* cell,
+                             uint32_t* id, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   using V4 = typename VT<R>::v4;
-  k_get_order<R><<<unsigned((n + 255) / 256), 256, 0, s>>>((const V4*)pos, (const V4*)mom, n, cell, id);
+  k_get_order<R><<<unsigned((n + 255) / 256), 256, 0, s>>>((const V4*)pos, (const V4*)mom, src, n, cell, id);
   return cudaGetLastError();
 }
 

@@ -39,8 +39,7 @@ constexpr size_t kKeys1 = kKeys0 + align256(kMaxPart * 4);
 constexpr size_t kKeys2 = kKeys1 + align256(kMaxPart * 4);
 constexpr size_t kVals0 = kKeys2 + align256(kMaxPart * 4);
 constexpr size_t kVals1 = kVals0 + align256(kMaxPart * 4);
-constexpr size_t kZeroP = kVals1 + align256(kMaxPart * 4);  // zero momenta (3 doubles per particle)
-constexpr size_t kHist = kZeroP + align256(kMaxPart * 24);   // 3 histograms + 4 tile counters
+constexpr size_t kHist = kVals1 + align256(kMaxPart * 4);  // 3 histograms + 4 tile counters
 constexpr size_t kStatus = kHist + align256((3 * kRadixMax + 4) * 4);
 constexpr size_t kRows = kStatus + align256(size_t(kMaxTiles) * kRadixMax * 8);
 constexpr size_t kErr = kRows + align256((size_t(kMaxMesh) * kMaxMesh + 1) * 4);
@@ -56,6 +55,9 @@ void* g_addr[64];
 bool g_ready[64];
 
 thread_local char g_msg[256];
+
+// the call's error bits to the caller's word (device or mapped host memory)
+__global__ void k_copy_error(const uint32_t* err, uint32_t* out) { *out = *err; }
 
 // the message goes where pm_last_error(NULL) reads it
 pm_status nfail(pm_status st, const char* msg) {
@@ -86,7 +88,7 @@ pm_status scratch_address(unsigned char** out) {
 extern "C" {
 
 pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh, double box, float* rho_dev,
-                             void* stream) {
+                             uint32_t* err_dev, void* stream) {
   if (n_part < 1 || n_part > kMaxPart) {
     snprintf(g_msg, sizeof g_msg, "n_part = %lld is outside [1, %lld], the static scratch limit", (long long)n_part,
              (long long)kMaxPart);
@@ -123,7 +125,6 @@ pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh
   uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(base + kVals0), reinterpret_cast<uint32_t*>(base + kVals1)};
   void* pos[2] = {base + kPos0, base + kPos1};
   void* mom[2] = {base + kMom0, base + kMom1};
-  double* zero_p = reinterpret_cast<double*>(base + kZeroP);
 
 #define NA_CU(expr)                                                                             \
   do {                                                                                          \
@@ -137,8 +138,8 @@ pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh
   NA_CU(cudaMemsetAsync(hist, 0, (3 * kRadixMax + 4) * 4, s));
   NA_CU(cudaMemsetAsync(status, 0, size_t(ntiles) * (size_t(1) << digit_bits) * 8, s));
   NA_CU(cudaMemsetAsync(err, 0, 8, s));  // error word and sort epoch word
-  NA_CU(cudaMemsetAsync(zero_p, 0, size_t(n) * 24, s));
-  NA_CU(launch_init_particles<float>(x_dev, zero_p, n, m, double(n_mesh) / box, pos[0], mom[0], keys[0], err, s));
+  // positions to cell + offset as pm_set_particles converts them (1/dx with dx = box/N), at rest
+  NA_CU(launch_init_particles<float>(x_dev, nullptr, n, m, 1.0 / (box / n_mesh), pos[0], mom[0], keys[0], err, s));
   NA_CU(launch_sort_histogram(keys[0], n, passes, digit_bits, bits, hist, err + 1, s));
   const uint32_t* kin = keys[0];
   const uint32_t* vin = nullptr;
@@ -162,8 +163,12 @@ pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh
     }
   }
   uint32_t* rows = reinterpret_cast<uint32_t*>(base + kRows);
-  NA_CU(launch_row_start(sorted_keys, n, uint32_t(n_mesh), rows, s));
-  NA_CU(launch_deposit<float>(pos[1], rows, n, m, double(m.n3) / double(n), rho_dev, s));
+  NA_CU(launch_row_start(sorted_keys, n, uint32_t(n_mesh), rows, nullptr, s));
+  NA_CU(launch_deposit<float>(pos[1], nullptr, rows, n, m, double(m.n3) / double(n), rho_dev, s));
+  if (err_dev) {
+    k_copy_error<<<1, 1, 0, s>>>(err, err_dev);
+    NA_CU(cudaGetLastError());
+  }
 #undef NA_CU
   return PM_OK;
 }

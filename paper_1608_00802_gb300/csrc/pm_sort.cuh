@@ -292,13 +292,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
 // row_start[r] = first sorted slot whose mesh row (key / N = z*N + y) is >= r,
 // for r = 0..N^2.  Each slot i fills the rows between the row of slot i-1 and
 // its own (rows are rarely empty, so almost every thread writes once or not
-// at all).
+// at all).  Rows are clamped to N^2: a key outside the mesh (a slot left
+// unwritten by a sort whose look-back timed out) writes nothing past the table.
 static __global__ void k_row_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_mesh, uint32_t nrows,
-                                   uint32_t* row_start) {
+                                   uint32_t* row_start, uint32_t* src) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i > n) return;
-  const int64_t prev = i == 0 ? -1 : int64_t(__ldg(keys + i - 1) / n_mesh);
-  const int64_t cur = i == n ? int64_t(nrows) : int64_t(__ldg(keys + i) / n_mesh);
+  if (src && i < n) src[i] = uint32_t(i);  // the records are in sorted order
+  const int64_t prev = i == 0 ? -1 : min(int64_t(__ldg(keys + i - 1) / n_mesh), int64_t(nrows));
+  const int64_t cur = i == n ? int64_t(nrows) : min(int64_t(__ldg(keys + i) / n_mesh), int64_t(nrows));
   for (int64_t r = prev + 1; r <= cur; ++r) row_start[r] = uint32_t(i);
 }
 
@@ -340,34 +342,40 @@ static __global__ void k_reduce_max(const double* __restrict__ part, int nblocks
 // stayers and movers, radix-sort the movers (usually a few per cent), and merge
 // the two sequences by (key, previous slot) while gathering the records.  The
 // result is identical to the full sort.
-// Stable partition in one pass: tiles of RS_TILE slots are taken in order
-// (dynamic tile ids); each counts its movers, publishes the count at once and
-// finds the movers of all earlier tiles by decoupled look-back over one status
-// word per tile (flag | count; the words are cleared before the launch), then
-// writes its stayers to (s_keys, s_vals) and its movers, flag cleared, to
-// (m_keys, m_vals); values are the previous slots.  It also accumulates the
-// digit histograms of the movers' keys for every radix pass (hist[p*radix_max
-// + d], cleared before), advances the sort epoch for those passes (as the
-// histogram kernel does for a full sort) and, in the last tile, stores
-// counts[0] = stayers, counts[1] = movers.
+// Stable partition in one pass: block t takes tile t of RS_TILE slots.  The
+// drift has already counted the movers of every tile and of every group of
+// 2^RS_GROUP_SHIFT tiles (tcount), so a block finds the movers of all earlier
+// tiles by summing at most one group's tile counts and the earlier groups'
+// counts, with no wait on other blocks.  It writes its stayers to (s_keys,
+// s_vals) and its movers, flag cleared, to (m_keys, m_vals); values are the
+// previous slots.  It also accumulates the digit histograms of the movers'
+// keys for every radix pass (hist[p*radix_max + d], cleared before), advances
+// the sort epoch for those passes (as the histogram kernel does for a full
+// sort) and, in the last tile, stores counts[0] = stayers, counts[1] = movers
+// and adds one re-sort and the movers to stats (nullable).
 static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
-    const uint32_t* __restrict__ keys, int64_t n, uint64_t* pstatus, uint32_t* tile_counter,
+    const uint32_t* __restrict__ keys, int64_t n, const uint32_t* __restrict__ tcount,
     uint32_t* __restrict__ s_keys, uint32_t* __restrict__ s_vals, uint32_t* __restrict__ m_keys,
     uint32_t* __restrict__ m_vals, uint32_t* __restrict__ counts, uint32_t* __restrict__ hist, int passes,
-    int digit_bits, int key_bits, uint32_t* __restrict__ sort_epoch, uint32_t* err) {
+    int digit_bits, int key_bits, uint32_t* __restrict__ sort_epoch, unsigned long long* __restrict__ stats) {
   __shared__ uint32_t sh_hist[3 << RS_MAX_BITS];
-  __shared__ uint32_t wm[RS_WARPS];
-  __shared__ uint32_t s_tile, s_excl;
+  __shared__ uint32_t wm[RS_WARPS], wsum[RS_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int radix = 1 << digit_bits;
-  const int ntiles = int((n + RS_TILE - 1) / RS_TILE);
-  if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+  const uint32_t ntiles = uint32_t((n + RS_TILE - 1) >> RS_TILE_SHIFT);
+  const uint32_t tile = blockIdx.x;
   for (int d = threadIdx.x; d < passes * radix; d += RS_THREADS) sh_hist[d] = 0u;
-  __syncthreads();
-  const uint32_t tile = s_tile;
   if (tile == 0 && threadIdx.x == 0) *sort_epoch = (*sort_epoch + uint32_t(passes)) % 65530u + 1u;
   const int64_t tile_base = int64_t(tile) * RS_TILE;
   const uint32_t lt = lanemask_lt();
+  // movers before this tile: the earlier groups' counts, then the earlier tiles of this group
+  const uint32_t grp = tile >> RS_GROUP_SHIFT, first = grp << RS_GROUP_SHIFT;
+  uint32_t e = 0;
+  for (uint32_t g = threadIdx.x; g < grp; g += RS_THREADS) e += __ldg(tcount + ntiles + g);
+  for (uint32_t t = first + threadIdx.x; t < tile; t += RS_THREADS) e += __ldg(tcount + t);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if (lane == 0) wsum[warp] = e;
   // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32
   uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
 #pragma unroll
@@ -380,59 +388,25 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
   }
   if (lane == 0) wm[warp] = mcount;
   __syncthreads();
-  // publish this tile's mover count, then sum the earlier tiles' (warp 0: its
-  // lanes read 32 predecessors' words at once, nearest in lane 0)
-  if (warp == 0) {
-    uint32_t total = 0;
-    for (int w = 0; w < RS_WARPS; ++w) total += wm[w];
-    uint32_t excl = 0;
-    if (tile == 0) {
-      if (lane == 0) __stcg(reinterpret_cast<unsigned long long*>(pstatus), RS_FLAG_PREFIX | uint64_t(total));
-    } else {
-      if (lane == 0) __stcg(reinterpret_cast<unsigned long long*>(pstatus + tile), RS_FLAG_AGG | uint64_t(total));
-      int64_t t = int64_t(tile) - 1;  // nearest predecessor not yet summed
-      int polls = 0;
-      while (t >= 0) {
-        const int64_t tl = t - lane;
-        const uint64_t w = tl >= 0 ? __ldcv(reinterpret_cast<const unsigned long long*>(pstatus + tl)) : 0ull;
-        const bool valid = tl >= 0 && (w & (RS_FLAG_AGG | RS_FLAG_PREFIX));
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        const uint32_t pmask = __ballot_sync(0xffffffffu, valid && (w & RS_FLAG_PREFIX));
-        // lanes usable: the leading run of published words, up to the first prefix
-        const int run = vmask == 0xffffffffu ? 32 : __ffs(~vmask) - 1;
-        const int pl = pmask ? __ffs(pmask) - 1 : 32;
-        const int take = pl < run ? pl + 1 : run;
-        uint32_t v = lane < take ? uint32_t(w) : 0u;
+  uint32_t excl = 0, total = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        excl += v;
-        if (pl < run) break;  // reached a prefix
-        t -= take;
-        if (take == 0) {
-          if (++polls > RS_SPIN_LIMIT) {
-            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
-      if (lane == 0)
-        __stcg(reinterpret_cast<unsigned long long*>(pstatus + tile), RS_FLAG_PREFIX | uint64_t(excl + total));
-    }
-    if (lane == 0) {
-      s_excl = excl;
-      if (int(tile) == ntiles - 1) {
-        counts[0] = uint32_t(n) - (excl + total);
-        counts[1] = excl + total;
-      }
+  for (int w = 0; w < RS_WARPS; ++w) {
+    excl += wsum[w];
+    total += wm[w];
+  }
+  if (tile == ntiles - 1 && threadIdx.x == 0) {
+    counts[0] = uint32_t(n) - (excl + total);
+    counts[1] = excl + total;
+    if (stats) {  // re-sorts and moved particles so far (a diagnostic)
+      stats[0] += 1ull;
+      stats[1] += (unsigned long long)(excl + total);
     }
   }
-  __syncthreads();
   // movers in the earlier warps of the tile: lane w < warp contributes wm[w]
   uint32_t mbase = lane < warp ? wm[lane] : 0u;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mbase += __shfl_xor_sync(0xffffffffu, mbase, o);
-  mbase += s_excl;
+  mbase += excl;
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
@@ -440,7 +414,7 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
       const uint32_t before = mbase + rank[r];  // movers before slot i
       if (key[r] & KEY_MOVER) {
         const uint32_t k = key[r] & ~KEY_MOVER;
-        if (before < uint32_t(n)) {  // only false after a timed-out look-back
+        if (before < uint32_t(n)) {  // always (the counts bound the movers)
           m_keys[before] = k;
           m_vals[before] = uint32_t(i);
         }
@@ -523,15 +497,14 @@ __device__ __forceinline__ void merge_split_block(const uint32_t* sk, const uint
 }
 
 // merge of the stayers with the sorted movers, by (key, previous slot); writes
-// the sorted keys, gathers the records of the previous slots and fills the
-// row starts (row_start[r] = first slot whose key is in row r or above;
-// row_start[N^2] = n)
-template <typename V4>
-__global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
+// the sorted keys, the previous slot of every sorted index (src: the records
+// stay where the drift wrote them, and the deposit and the next kick read
+// them through src) and the row starts (row_start[r] = first slot whose key
+// is in row r or above; row_start[N^2] = n)
+static __global__ void __launch_bounds__(RS_THREADS) k_merge(
     const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ mk,
     const uint32_t* __restrict__ mv, const uint32_t* __restrict__ counts, int64_t n, uint32_t* __restrict__ keys_out,
-    const V4* __restrict__ pos_in, const V4* __restrict__ mom_in, V4* __restrict__ pos_out,
-    V4* __restrict__ mom_out, uint32_t n_mesh, uint32_t* __restrict__ row_start) {
+    uint32_t* __restrict__ src_out, uint32_t n_mesh, uint32_t* __restrict__ row_start) {
   extern __shared__ uint32_t msm[];
   uint32_t* a_k = msm;               // stayers of this tile
   uint32_t* a_v = a_k + MG_TILE;
@@ -548,13 +521,48 @@ __global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
   const uint32_t a0 = lo_s[0], a1 = lo_s[1];
   const uint32_t b0 = d0 - a0, b1 = d1 - a1;
   const uint32_t na = a1 - a0, nb = b1 - b0;
-  for (uint32_t t = threadIdx.x; t < na; t += RS_THREADS) {
-    a_k[t] = sk[a0 + t];
-    a_v[t] = sv[a0 + t];
-  }
-  for (uint32_t t = threadIdx.x; t < nb; t += RS_THREADS) {
-    b_k[t] = mk[b0 + t];
-    b_v[t] = mv[b0 + t];
+  const uint32_t tn = d1 - d0;
+  if (nb == 0) {
+    // no mover falls in this tile (the common case): the stayers pass through
+    for (uint32_t q = threadIdx.x; q < tn; q += RS_THREADS) {
+      const uint32_t k = __ldg(sk + a0 + q);
+      keys_out[d0 + q] = k;
+      src_out[d0 + q] = __ldg(sv + a0 + q);
+      o_k[q] = k;
+    }
+  } else {
+    for (uint32_t t = threadIdx.x; t < na; t += RS_THREADS) {
+      a_k[t] = sk[a0 + t];
+      a_v[t] = sv[a0 + t];
+    }
+    for (uint32_t t = threadIdx.x; t < nb; t += RS_THREADS) {
+      b_k[t] = mk[b0 + t];
+      b_v[t] = mv[b0 + t];
+    }
+    __syncthreads();
+    // each thread merges RS_ITEMS consecutive outputs of the tile
+    const uint32_t q0 = min(uint32_t(threadIdx.x) * RS_ITEMS, tn), q1 = min(q0 + RS_ITEMS, tn);
+    if (q0 < q1) {
+      uint32_t ia = merge_split(a_k, a_v, na, b_k, b_v, nb, q0);
+      uint32_t ib = q0 - ia;
+      for (uint32_t q = q0; q < q1; ++q) {
+        const bool take_a = ib >= nb || (ia < na && kv_less(a_k[ia], a_v[ia], b_k[ib], b_v[ib]));
+        if (take_a) {
+          o_k[q] = a_k[ia];
+          o_v[q] = a_v[ia];
+          ++ia;
+        } else {
+          o_k[q] = b_k[ib];
+          o_v[q] = b_v[ib];
+          ++ib;
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < tn; q += RS_THREADS) {
+      keys_out[d0 + q] = o_k[q];
+      src_out[d0 + q] = o_v[q];
+    }
   }
   if (threadIdx.x == 0 && d0 > 0) {
     // the key at output d0-1: the larger of the last stayer and the last mover before this tile
@@ -569,62 +577,32 @@ __global__ void __launch_bounds__(RS_THREADS) k_merge_gather(
     prev_key = k;
   }
   __syncthreads();
-  // each thread merges RS_ITEMS consecutive outputs of the tile
-  const uint32_t tn = d1 - d0;
-  const uint32_t q0 = min(uint32_t(threadIdx.x) * RS_ITEMS, tn), q1 = min(q0 + RS_ITEMS, tn);
-  if (q0 < q1) {
-    uint32_t ia = merge_split(a_k, a_v, na, b_k, b_v, nb, q0);
-    uint32_t ib = q0 - ia;
-    for (uint32_t q = q0; q < q1; ++q) {
-      const bool take_a = ib >= nb || (ia < na && kv_less(a_k[ia], a_v[ia], b_k[ib], b_v[ib]));
-      if (take_a) {
-        o_k[q] = a_k[ia];
-        o_v[q] = a_v[ia];
-        ++ia;
-      } else {
-        o_k[q] = b_k[ib];
-        o_v[q] = b_v[ib];
-        ++ib;
-      }
-    }
-  }
-  __syncthreads();
+  // rows (row of output i-1, row of output i] start at i (rows clamped to N^2, as in k_row_start)
+  const int64_t nrows = int64_t(n_mesh) * n_mesh;
   for (uint32_t q = threadIdx.x; q <= tn; q += RS_THREADS) {
     const uint32_t i = d0 + q;
-    if (q < tn) {
-      const uint32_t src = o_v[q];
-      keys_out[i] = o_k[q];
-      pos_out[i] = pos_in[src];
-      mom_out[i] = mom_in[src];
-    } else if (i != uint32_t(n)) {
-      break;  // output n (the closing row starts) belongs to the last block
-    }
-    // rows (row of output i-1, row of output i] start at i
-    const int64_t prev = i == 0 ? -1 : int64_t((q ? o_k[q - 1] : prev_key) / n_mesh);
-    const int64_t cur = i == uint32_t(n) ? int64_t(n_mesh) * n_mesh : int64_t(o_k[q] / n_mesh);
+    if (q == tn && i != uint32_t(n)) break;  // output n (the closing row starts) belongs to the last block
+    const int64_t prev = i == 0 ? -1 : min(int64_t((q ? o_k[q - 1] : prev_key) / n_mesh), nrows);
+    const int64_t cur = i == uint32_t(n) ? nrows : min(int64_t(o_k[q] / n_mesh), nrows);
     for (int64_t r = prev + 1; r <= cur; ++r) row_start[r] = i;
   }
 }
 
-template <typename R>
-cudaError_t launch_merge_gather(const uint32_t* sk, const uint32_t* sv, const uint32_t* mk, const uint32_t* mv,
-                                const uint32_t* counts, int64_t n, uint32_t* keys_out, const void* pos_in,
-                                const void* mom_in, void* pos_out, void* mom_out, uint32_t n_mesh,
-                                uint32_t* row_start, cudaStream_t s) {
-  using V4 = typename VT<R>::v4;
+inline cudaError_t launch_merge_impl(const uint32_t* sk, const uint32_t* sv, const uint32_t* mk, const uint32_t* mv,
+                                     const uint32_t* counts, int64_t n, uint32_t* keys_out, uint32_t* src_out,
+                                     uint32_t n_mesh, uint32_t* row_start, cudaStream_t s) {
   static bool done[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_merge_gather<V4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(merge_smem_bytes()));
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = true;
   }
   const unsigned blocks = unsigned((n + MG_TILE - 1) / MG_TILE);
-  k_merge_gather<V4><<<blocks, RS_THREADS, merge_smem_bytes(), s>>>(sk, sv, mk, mv, counts, n, keys_out,
-                                                                    (const V4*)pos_in, (const V4*)mom_in,
-                                                                    (V4*)pos_out, (V4*)mom_out, n_mesh, row_start);
+  k_merge<<<blocks, RS_THREADS, merge_smem_bytes(), s>>>(sk, sv, mk, mv, counts, n, keys_out, src_out, n_mesh,
+                                                          row_start);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_energy", "pm_power_spectrum", "pm_get_field", "pm_set_density", "pm_get_order",
            "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error",
            "pm_batch_arena_bytes", "pm_batch_create", "pm_batch_destroy", "pm_batch_member", "pm_batch_run",
-           "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_run_adaptive"]
+           "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_run_adaptive",
+           "pm_sort_stats"]
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
@@ -94,9 +95,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_get_field": (C.c_int, [vp, C.c_int32, dp]),
         "pm_set_density": (C.c_int, [vp, dp]),
         "pm_get_order": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+        "pm_sort_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "pm_profile_begin": (C.c_int, [vp, C.c_int32]),
         "pm_profile_end": (C.c_int, [vp, dp, C.POINTER(C.c_int64)]),
-        "pm_deposit_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, C.c_double, vp, vp]),
+        "pm_deposit_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, C.c_double, vp, vp, vp]),
         "pm_last_error": (C.c_char_p, [vp]),
         "pm_batch_arena_bytes": (C.c_size_t, [cfgp, C.c_int32]),
         "pm_batch_create": (C.c_int, [cfgp, C.c_int32, vp, C.c_size_t, vp, C.POINTER(vp)]),
@@ -324,6 +326,12 @@ class Sim:
             cache[key] = t.as_dict()
         return t.as_dict()
 
+    def sort_stats(self):
+        """(incremental re-sorts, particles they moved) since creation."""
+        r, m = C.c_int64(0), C.c_int64(0)
+        self._check(lib().pm_sort_stats(self.handle, C.byref(r), C.byref(m)))
+        return int(r.value), int(m.value)
+
     def profile_begin(self, capacity):
         self._check(lib().pm_profile_begin(self.handle, int(capacity)))
 
@@ -335,16 +343,22 @@ class Sim:
         return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(STAGES)}
 
 
-def deposit_noalloc(x_dev, n_mesh, box, rho_dev, stream=None):
+def deposit_noalloc(x_dev, n_mesh, box, rho_dev, stream=None, err_dev=None):
     """pm_deposit_noalloc on torch CUDA tensors: x_dev float64 (n, 3), rho_dev
-    float32 (N, N, N); enqueued on `stream` (default: the current stream)."""
+    float32 (N, N, N); enqueued on `stream` (default: the current stream).
+    err_dev (optional): a one-element int32 CUDA tensor that receives the
+    call's device error bits in stream order (0 = ok)."""
     import torch
     assert x_dev.is_cuda and x_dev.dtype == torch.float64 and x_dev.is_contiguous() and x_dev.shape[1] == 3
     assert rho_dev.is_cuda and rho_dev.dtype == torch.float32 and rho_dev.is_contiguous()
     assert rho_dev.numel() == n_mesh ** 3
+    err_ptr = None
+    if err_dev is not None:
+        assert err_dev.is_cuda and err_dev.dtype == torch.int32 and err_dev.numel() >= 1
+        err_ptr = C.c_void_p(err_dev.data_ptr())
     st_obj = stream if stream is not None else torch.cuda.current_stream(x_dev.device)
     st = lib().pm_deposit_noalloc(C.c_void_p(x_dev.data_ptr()), int(x_dev.shape[0]), int(n_mesh), float(box),
-                                  C.c_void_p(rho_dev.data_ptr()), C.c_void_p(st_obj.cuda_stream))
+                                  C.c_void_p(rho_dev.data_ptr()), err_ptr, C.c_void_p(st_obj.cuda_stream))
     if st != PM_OK:
         raise PMError(st, lib().pm_last_error(None).decode())
 

@@ -24,8 +24,13 @@ def pm():
     return _pm
 
 
-def _full_run(pm, precision, mode, kernel=0, quantum=True, chunks=20, nsteps=500):
+def _full_run(pm, precision, mode, kernel=0, quantum=True, chunks=20, nsteps=500, ulp_shift=False):
     x, p = ics.zeldovich(128, 256, 2.0, 1 / 101.0, 42, m22=2.5)
+    if ulp_shift:
+        # every input position moved by one fp32 ulp (alternating sign): the
+        # run's sensitivity to rounding, measured in fp64
+        ulp = np.spacing(x.astype(np.float32)).astype(np.float64)
+        x = np.mod(x + np.where(np.arange(x.size).reshape(x.shape) % 2 == 0, ulp, -ulp), 2.0)
     cfg = pm.make_config(len(x), 256, 2.0, m22=2.5, precision=precision, force_mode=mode, kernel=kernel,
                          quantum=quantum)
     sim = pm.Sim(cfg)
@@ -43,13 +48,18 @@ def _full_run(pm, precision, mode, kernel=0, quantum=True, chunks=20, nsteps=500
     return k, pk, np.array(hist)
 
 
+OCFG = O.Config(n_mesh=256, box=2.0, m22=2.5)
+
+
+def _dp(k, pa, pb):
+    sel = k <= 0.5 * math.pi * 256 / 2.0  # k <= k_Nyq / 2
+    return np.abs(pa[sel] / pb[sel] - 1).max()
+
+
 def _compare(pm, **kw):
     k, p32, h32 = _full_run(pm, pm.FP32, **kw)
     _, p64, h64 = _full_run(pm, pm.FP64, **kw)
-    sel = k <= 0.5 * math.pi * 256 / 2.0
-    ocfg = O.Config(n_mesh=256, box=2.0, m22=2.5)
-    return (np.abs(p32[sel] / p64[sel] - 1).max(), O.layzer_irvine_residual(h32, ocfg),
-            O.layzer_irvine_residual(h64, ocfg))
+    return (_dp(k, p32, p64), O.layzer_irvine_residual(h32, OCFG), O.layzer_irvine_residual(h64, OCFG))
 
 
 def test_pressureless_bench_workload_fp32_matches_fp64(pm):
@@ -62,13 +72,33 @@ def test_pressureless_bench_workload_fp32_matches_fp64(pm):
 @pytest.mark.parametrize("mode", ["hybrid", "lagrangian"])
 def test_spline_bench_workload_fp32_matches_fp64(pm, mode):
     """With the quantum force and the paper's spline kernel (h = 3.5 dx): P(k)
-    within 3e-3 (the sensitivity of the nonlinear evolution to rounding; the
-    pressureless run stays within 1e-5), energy budget closed to 1e-2 by both
-    paths, alike to 1e-3.  (With cloud-in-cell at this resolution the quantum
-    pressure acts on the particle shot noise and the budget does not close;
-    the design notes give the numbers.)"""
+    within 1e-3 after the full run (the accuracy bar for full runs; the fp64
+    run moved by one fp32 ulp per position stays within ~1e-4 of itself, so
+    the bar is not below the problem's own rounding sensitivity), the energy
+    budget closed to 1e-2 by both paths and alike to 1e-3."""
     fm = pm.FORCE_HYBRID if mode == "hybrid" else pm.FORCE_LAGRANGIAN
     dp, li32, li64 = _compare(pm, mode=fm, kernel=pm.KERNEL_SPLINE)
-    assert dp < 3e-3
+    assert dp < 1e-3
     assert np.abs(li32).max() < 1e-2 and np.abs(li64).max() < 1e-2
     assert np.abs(li32 - li64).max() < 1e-3
+
+
+def test_cloud_in_cell_quantum_bench_workload_fp32_within_the_rounding_floor(pm):
+    """The benchmarked cloud-in-cell run with the quantum force (HYBRID).  On a
+    mesh of eight cells per particle the quantum pressure acts on the particles'
+    shot noise and the run is chaotic: the fp64 run against itself with every
+    input position moved by one fp32 ulp already differs by several per cent in
+    P(k) (measured here, not assumed), so a 1e-3 bar cannot hold for any
+    precision.  The fp32 path must stay within twice that floor, and its
+    Layzer-Irvine residual (which does not close for this scheme at this
+    resolution, in fp64 either) within twice the floor's change of it."""
+    k, p64, h64 = _full_run(pm, pm.FP64, mode=pm.FORCE_HYBRID)
+    _, p64b, h64b = _full_run(pm, pm.FP64, mode=pm.FORCE_HYBRID, ulp_shift=True)
+    _, p32, h32 = _full_run(pm, pm.FP32, mode=pm.FORCE_HYBRID)
+    floor = _dp(k, p64b, p64)
+    assert floor > 1e-3  # the bar of 1e-3 is below this run's own rounding sensitivity
+    assert _dp(k, p32, p64) < 2 * floor
+    li64 = np.abs(O.layzer_irvine_residual(h64, OCFG)).max()
+    li64b = np.abs(O.layzer_irvine_residual(h64b, OCFG)).max()
+    li32 = np.abs(O.layzer_irvine_residual(h32, OCFG)).max()
+    assert abs(li32 - li64) < 2 * abs(li64b - li64) + 1e-3 * li64

@@ -116,3 +116,24 @@ def test_spline_config_validation(pm):
         assert pm.arena_bytes(cfg) == 0
     cfg = pm.make_config(base["n_part"], base["n_mesh"], base["box"], kernel=7)
     assert pm.arena_bytes(cfg) == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_energy_calls_leave_the_trajectory_unchanged(pm, precision):
+    """pm_energy recomputes Q~ with the K_rho sums; with the spline kernel the
+    field the particles feel is the smoothed one, so the recomputation must
+    smooth it again: a run with energy calls between its parts ends on the
+    same bits as the same run without them."""
+    a0, a1 = 1 / 101.0, 1 / 20.0
+    am = math.sqrt(a0 * a1)
+    finals = []
+    for with_energy in (False, True):
+        sim, _ = make(pm, 16, 32, 1.0, precision, mode="hybrid")
+        sim.run(8, a0, am)
+        if with_energy:
+            sim.energy(am)
+        sim.run(8, am, a1)
+        finals.append(sim.get_particles())
+        sim.close()
+    np.testing.assert_array_equal(finals[0][0], finals[1][0])
+    np.testing.assert_array_equal(finals[0][1], finals[1][1])
