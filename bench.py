@@ -1,20 +1,25 @@
 """Throughput of the GB300 particle-mesh step with quantum pressure.
 
-Workload: one simulation of 128^3 particles on a 256^3 periodic mesh,
-L = 2 Mpc/h, m = 2.5e-22 eV, Omega_m = 0.3, Omega_L = 0.7, h = 0.7, fp32
-(int32 cell + fp32 offset positions, fp32 mesh and cuFFT), Zel'dovich initial
-conditions at z = 100 from the seed-42 Gaussian field with
+Headline workload: one simulation of 128^3 particles on a 256^3 periodic
+mesh, L = 2 Mpc/h, m = 2.5e-22 eV, Omega_m = 0.3, Omega_L = 0.7, h = 0.7,
+fp32 (int32 cell + fp32 offset positions, fp32 mesh and cuFFT), Zel'dovich
+initial conditions at z = 100 from the seed-42 Gaussian field with
 P ~ k^0.96 T_BBKS^2 T_FDM^2, 500 leapfrog steps (uniform in ln a) to z = 3.
-A step is one pass of the whole path: interpolate + kick + drift, radix sort
-by cell, row starts, deterministic CIC deposit, R2C FFT, Green's function,
-C2R FFT, quantum-pressure stencil.  The timed steps are W..W+K of that
-schedule.  Each step touches ~0.5 GB (> the 126 MB L2), so no L2 flush is
-inserted between steps.
+A step is one pass of the whole path: interpolate + kick + drift, re-sort by
+cell, deterministic CIC deposit, R2C FFT, Green's function, C2R FFT,
+quantum-pressure stencil.  The timed steps are W..W+K of that schedule.  Each
+step touches ~0.5 GB (> the 126 MB L2), so no L2 flush is inserted between
+steps.  Beside it, on the same line: the same workload with the paper's cubic
+spline kernel (the configuration that meets the full-run accuracy bar), the
+plain fp64 path, the large single simulation (256^3 on 512^3), the small
+plain-fp64 configuration (32^3 on 64^3, a full 200-step run), the
+48-simulation batch and the served request stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 (torchrun): independent replicas, one per GPU, no data-path collective.
---impl reference times the FP64 CPU oracle on the host cores instead.
+--impl reference times the FP64 CPU oracle on the host cores instead (on one
+core, and as one independent copy per core).
 """
 from __future__ import annotations
 
@@ -36,6 +41,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="single sim 128^3 particles on 256^3 mesh, L=2 Mpc/h, m22=2.5, z=100->3 in 500 steps",
                 n_side=128, n_mesh=256, box=2.0, m22=2.5, z_start=100.0, z_end=3.0, nsteps=500, seed=42)
+LARGE = dict(name="large single sim 256^3 particles on 512^3 mesh, L=10 Mpc/h, m22=1, z=100->3 in 1000 steps",
+             n_side=256, n_mesh=512, box=10.0, m22=1.0, z_start=100.0, z_end=3.0, nsteps=1000, seed=42)
+SMALL = dict(name="plain fp64 32^3 particles on 64^3 mesh, L=1 Mpc/h, m22=2.5, z=100->3 in 200 steps",
+             n_side=32, n_mesh=64, box=1.0, m22=2.5, z_start=100.0, z_end=3.0, nsteps=200, seed=42)
 METRIC = "particle-steps/s"
 PROFILES = os.path.join(ROOT, "profiles")
 
@@ -45,29 +54,35 @@ def schedule(w):
     return a0 * (a1 / a0) ** (np.arange(w["nsteps"] + 1) / w["nsteps"])
 
 
-def algorithmic_bytes(stage, n, n_mesh, rsz=4):
-    """Minimal DRAM bytes of one launch of each kernel (fp32 path)."""
+def algorithmic_bytes(stage, n, n_mesh, rsz=4, movers=None, spline=False):
+    """Minimal DRAM bytes of one launch of each kernel.  `movers`: particles
+    that changed cell per step (the radix passes over the movers see only
+    those); `spline`: the Green stage then alternates the spline's Green pass
+    (spectrum read, spectrum and smoothed-density spectrum written, symbol
+    read) with the smoothing of Q (spectrum read and written, symbol read)."""
     n3 = n_mesh ** 3
-    spec = n_mesh * n_mesh * (n_mesh // 2 + 1) * 2 * rsz
+    half = n_mesh * n_mesh * (n_mesh // 2 + 1)
+    spec = half * 2 * rsz
     rec = 4 * rsz
+    green = (2 * spec) if not spline else ((3 * spec + half * rsz) + (2 * spec + half * rsz)) / 2
     return {
-        # pos + mom read and written, new key written; phi~ and Q~ read once
+        # pos + mom read and written in place, new key written; phi~ and Q~ read once
         "kick": n * (4 * rec + 4) + 2 * n3 * rsz,
-        # particle positions read once, row starts read once, rho written
+        # position record read once per particle, row starts read once, rho written
         "deposit": n * rec + n_mesh * n_mesh * 4 + n3 * rsz,
         # rho read, Q~ written
         "stencil": 2 * n3 * rsz,
-        # half spectrum read and written
-        "green": 2 * spec,
+        "green": green,
         "fft_r2c": n3 * rsz + spec,
         "fft_c2r": spec + n3 * rsz,
-        # re-sort after a drift: keys read twice (count, scatter), stayer keys + previous slots written
-        "sort_partition": n * 16,
-        # stayers (key, slot) read, sorted keys written, records gathered (read) and written
-        "sort_merge": n * (8 + 4 + 4 * rec),
-        # the histogram and radix passes see only the movers, a data-dependent count
+        # re-sort after a drift: keys read, stayer keys + previous slots written (movers alike)
+        "sort_partition": n * 12,
+        # the rows: per-row counts read twice, stayer/mover/total row offsets written; the movers read and
+        # written to their row's bucket
+        "sort_pass": n_mesh * n_mesh * 28 + (movers or 0) * 16,
+        # the placement: every (key, slot) read, key written, records read at the slot and written in order
+        "sort_merge": n * (8 + 4 + 2 * 2 * rec) + n_mesh * n_mesh * 12,
         "sort_histogram": None,
-        "sort_pass": None,
         "row_start": n * 4 + n_mesh * n_mesh * 4,
     }.get(stage)
 
@@ -202,26 +217,48 @@ def sum_over_ranks(dist, v):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_step_rate(w, budget_s=30.0):
-    """Times the FP64 CPU oracle on a bounded sample of the workload: the same
-    recipe, one step, on the full problem if one step fits the budget, else on
-    a proportionally smaller box (the mesh/particle ratio kept)."""
+def _oracle_steps(w, nsteps, first=0, x=None, p=None):
+    """nsteps KDK steps of the FP64 CPU oracle on workload w (steps first ..
+    first + nsteps - 1 of its schedule); returns (seconds, x, p)."""
     from oracle import pm_oracle as O
     from paper_1608_00802_gb300 import ics
-    n_side, n_mesh, box = w["n_side"], w["n_mesh"], w["box"]
-    # per-step cost is ~13 s for 128^3 on 256^3 on one core; shrink by 2 per dimension until it fits
-    est = 13.0 * (n_side / 128.0) ** 3
-    while est > budget_s and n_side > 16:
-        n_side, n_mesh, box, est = n_side // 2, n_mesh // 2, box / 2, est / 8
     a = schedule(w)
-    x, p = ics.zeldovich(n_side, n_mesh, box, a[0], w["seed"], m22=w["m22"])
-    cfg = O.Config(n_mesh=n_mesh, box=box, m22=w["m22"], force_mode=O.HYBRID)
+    if x is None:
+        x, p = ics.zeldovich(w["n_side"], w["n_mesh"], w["box"], a[0], w["seed"], m22=w["m22"])
+    cfg = O.Config(n_mesh=w["n_mesh"], box=w["box"], m22=w["m22"], force_mode=O.HYBRID)
     parts = O.force_parts(x, cfg)
     t0 = time.perf_counter()
-    O.kdk_step(x, p, a[0], a[1], cfg, parts)
-    dt = time.perf_counter() - t0
-    sample = "1 KDK step (one force evaluation) of %d^3 particles on %d^3 mesh, L=%g" % (n_side, n_mesh, box)
-    return n_side ** 3 / dt, dt, sample
+    for i in range(first, first + nsteps):
+        x, p, parts = O.kdk_step(x, p, a[i], a[i + 1], cfg, parts)
+    return time.perf_counter() - t0, x, p
+
+
+def _oracle_replica(args):
+    w, nsteps = args
+    dt, _, _ = _oracle_steps(w, nsteps)
+    return dt
+
+
+def oracle_parallel_rate(w, nsteps=1):
+    """The oracle as it stands (one thread per copy) run as one independent copy
+    per host core, all at once: aggregate particle-steps/s and the copies run.
+    Started with `spawn` (no state shared with a CUDA context)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        # every copy times its own steps (after its set-up); the slowest one bounds the aggregate
+        dts = pool.map(_oracle_replica, [(w, nsteps)] * cores)
+    wall = max(dts)
+    return cores * w["n_side"] ** 3 * nsteps / wall, cores, wall
+
+
+def oracle_step_rate(w):
+    """The FP64 CPU oracle on one host core: one full-size KDK step of the
+    workload (one force evaluation per step, as on the GPU)."""
+    dt, _, _ = _oracle_steps(w, 1)
+    sample = "1 KDK step (one force evaluation) of %d^3 particles on %d^3 mesh, L=%g (the full workload)" % (
+        w["n_side"], w["n_mesh"], w["box"])
+    return w["n_side"] ** 3 / dt, dt, sample
 
 
 def cpu_cores_used():
@@ -231,43 +268,113 @@ def cpu_cores_used():
 
 
 def run_reference(args):
+    """The FP64 CPU oracle on the headline workload at full size: W untimed and
+    K timed KDK steps on one core, then one step per core as independent copies
+    (reported beside it)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     w = WORKLOAD
-    total = args.steps + args.warmup
-    budget = max(2.0, 150.0 / max(total, 1))
-    from oracle import pm_oracle as O
-    from paper_1608_00802_gb300 import ics
-    n_side, n_mesh, box = w["n_side"], w["n_mesh"], w["box"]
-    est = 13.0
-    while est > budget and n_side > 16:
-        n_side, n_mesh, box, est = n_side // 2, n_mesh // 2, box / 2, est / 8
-    a = schedule(w)
-    x, p = ics.zeldovich(n_side, n_mesh, box, a[0], w["seed"], m22=w["m22"])
-    cfg = O.Config(n_mesh=n_mesh, box=box, m22=w["m22"], force_mode=O.HYBRID)
-    parts = None
-    for i in range(args.warmup):
-        x, p, parts = O.kdk_step(x, p, a[i], a[i + 1], cfg, parts)
-    t0 = time.perf_counter()
-    for i in range(args.warmup, args.warmup + args.steps):
-        x, p, parts = O.kdk_step(x, p, a[i], a[i + 1], cfg, parts)
-    dt = time.perf_counter() - t0
-    value = n_side ** 3 * args.steps / dt
-    sample = "%d KDK steps of %d^3 particles on %d^3 mesh, L=%g (bounded sample of the workload)" % (
-        args.steps, n_side, n_mesh, box)
+    _, x, p = _oracle_steps(w, args.warmup)
+    dt, _, _ = _oracle_steps(w, args.steps, first=args.warmup, x=x, p=p)
+    value = w["n_side"] ** 3 * args.steps / dt
+    sample = "%d KDK steps of %d^3 particles on %d^3 mesh, L=%g (the full workload, steps %d..%d)" % (
+        args.steps, w["n_side"], w["n_mesh"], w["box"], args.warmup, args.warmup + args.steps - 1)
+    par = None
+    if not args.no_parallel_oracle:
+        v, cores, wall = oracle_parallel_rate(w)
+        par = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+               "sample": "one full-size KDK step per core, %d independent copies at once" % cores,
+               "wall_s": wall}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w["name"], "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
+            "cpu_parallel": par,
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
 # ---------------------------------------------------------------- GPU arm
+KERNEL_NAMES = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
+                "sort_pass": "k_row_scan+k_bucket_movers", "sort_histogram": "k_sort_histogram",
+                "row_start": "k_row_start", "sort_partition": "k_mover_partition", "sort_merge": "k_place_rows"}
+
+
+def measure(pm, sim, w, K, W, stream, rsz=4, spline=False, tuning=None, peak=None, workload_key=None):
+    """W untimed steps, K graph-replayed steps timed with CUDA events on the
+    simulation's stream, then the next K steps again with an event pair
+    around every launch (per-stage times) and the movers they re-sorted.
+    Returns the throughput, the stage table, the dominant kernel's roofline
+    and the whole step against the copy bandwidth."""
+    import torch
+    a = schedule(w)
+    n, nm = w["n_side"] ** 3, w["n_mesh"]
+    with torch.cuda.stream(stream):
+        if W > 0:
+            sim.run(W, a[0], a[W])
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with Clocks(torch.cuda.current_device()) as clk:
+            ev0.record(stream)
+            sim.run(K, a[W], a[W + K])
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        t_ms = ev0.elapsed_time(ev1)
+        r0, m0 = sim.sort_stats()
+        sim.profile_begin(64 * (K + 2))
+        sim.run(K, a[W + K], a[W + 2 * K])
+        stages = sim.profile_end()
+        r1, m1 = sim.sort_stats()
+    movers = (m1 - m0) / max(r1 - r0, 1)
+    per_stage = {}
+    for name, (ms, cnt) in stages.items():
+        if cnt == 0:
+            continue
+        b = algorithmic_bytes(name, n, nm, rsz, movers=movers, spline=spline)
+        avg = ms / cnt
+        per_stage[name] = {"ms_per_step": ms / K, "launches": cnt, "avg_launch_ms": avg,
+                           "bytes_per_launch": b, "GBps": (b / (avg / 1e3) / 1e9) if b else None}
+    ours = {k: v for k, v in per_stage.items() if k not in pm.CUFFT_STAGES and v["GBps"] is not None}
+    dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
+    d = per_stage[dom]
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES.get(dom, dom), "achieved": d["GBps"], "peak": peak,
+                "unit": "GB/s", "frac": d["GBps"] / peak if d["GBps"] else None,
+                "traffic": ncu_traffic(KERNEL_NAMES.get(dom, dom), workload_key) if workload_key else None,
+                "algorithmic_bytes_per_launch": d["bytes_per_launch"]}
+    step_bytes = step_bytes_fft = fft_ms = 0.0
+    for name, (ms, cnt) in stages.items():
+        b = algorithmic_bytes(name, n, nm, rsz, movers=movers, spline=spline)
+        if cnt and b:
+            step_bytes += b * cnt / K
+            if name in pm.CUFFT_STAGES:
+                step_bytes_fft += b * cnt / K
+                fft_ms += ms / K
+    t_step = t_ms / K
+    step_roofline = {"bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (t_step / 1e3) / 1e9,
+                     "frac": step_bytes / (t_step / 1e3) / 1e9 / peak,
+                     "frac_excl_cufft": ((step_bytes - step_bytes_fft) / (max(t_step - fft_ms, 1e-9) / 1e3) / 1e9
+                                         / peak),
+                     "note": "cuFFT time taken from the profiled pass; peak as in roofline"}
+    # our kernels per timed region: the profiled pass launches the same kernels one by one; the replayed
+    # graph adds one step-counter kernel per step
+    launches = sum(v["launches"] for k, v in per_stage.items() if k not in pm.CUFFT_STAGES) + K
+    return {"value": n * K / (t_ms / 1e3), "t_ms": t_ms, "ms_per_step": t_step, "stages": per_stage,
+            "roofline": roofline, "step_roofline": step_roofline, "launches": launches,
+            "movers_per_step": movers, "clocks": clk.summary(), "launch_shapes": tuning}
+
+
+def flush_l2():
+    import torch
+    buf = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    buf.fill_(1.0)
+    del buf
+
+
 def run_gpu(args):
     import torch
 
@@ -286,6 +393,7 @@ def run_gpu(args):
     K, W = args.steps, args.warmup
     if W + 2 * K > w["nsteps"]:
         raise SystemExit("warmup + 2 * steps must be <= %d" % w["nsteps"])
+    peak, peak_kind = read_peaks()
     x, p = ics.zeldovich(w["n_side"], w["n_mesh"], w["box"], a[0], w["seed"] + rank, m22=w["m22"])
     n = len(x)
     cfg = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP32, m22=w["m22"],
@@ -299,101 +407,60 @@ def run_gpu(args):
         tuning = sim.get_tuning()
     else:
         tuning = sim.autotune(reps=5)
-    # warm-up steps (untimed): the first W steps of the schedule
-    with torch.cuda.stream(stream):
-        if W > 0:
-            sim.run(W, a[0], a[W])
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with Clocks(local) as clk:
-            ev0.record(stream)
-            sim.run(K, a[W], a[W + K])
-            ev1.record(stream)
-            torch.cuda.synchronize()
-        t_ms = ev0.elapsed_time(ev1)
-        # per-kernel durations: the next K steps again, launched one by one with an
-        # event pair around every launch (kernel times do not depend on graph replay)
-        sim.profile_begin(64 * (K + 2))
-        sim.run(K, a[W + K], a[W + 2 * K])
-        stages = sim.profile_end()
     if dist is not None:
         dist.barrier()
-    t_max = max_over_ranks(dist, t_ms)
+    head = measure(pm, sim, w, K, W, stream, tuning=tuning, peak=peak, workload_key="c2")
+    t_max = max_over_ranks(dist, head["t_ms"])
     units = sum_over_ranks(dist, n * K)
     value = units / (t_max / 1e3)
-
-    # per-kernel roofline (ours only; cuFFT reported beside)
-    peak, peak_kind = read_peaks()
-    per_stage = {}
-    for name, (ms, cnt) in stages.items():  # ms over the K profiled steps
-        if cnt == 0:
-            continue
-        b = algorithmic_bytes(name, n, w["n_mesh"])
-        avg = ms / cnt
-        per_stage[name] = {"ms_per_step": ms / K, "launches": cnt, "avg_launch_ms": avg,
-                           "GBps": (b / (avg / 1e3) / 1e9) if b else None}
-    ours = {k: v for k, v in per_stage.items() if k not in pm.CUFFT_STAGES and v["GBps"] is not None}
-    dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
-    d = per_stage[dom]
-    achieved = d["GBps"]
-    kernel_names = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
-                    "sort_pass": "k_sort_pass", "sort_histogram": "k_sort_histogram",
-                    "row_start": "k_row_start", "sort_partition": "k_mover_partition",
-                    "sort_merge": "k_merge_gather"}
-    roofline = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak if achieved else None,
-                "traffic": ncu_traffic(kernel_names.get(dom, dom), "c2"), "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": algorithmic_bytes(dom, n, w["n_mesh"])}
-    # our kernels per timed region: the profiled pass launches the same kernels one by one; the replayed
-    # graph adds one step-counter kernel per step
-    launches = sum(v["launches"] for k, v in per_stage.items() if k not in pm.CUFFT_STAGES) + K
-    # the whole step against the copy bandwidth: algorithmic bytes of every stage with a fixed count
-    # (the radix passes over the movers are left out) over the graph-timed step, with and without cuFFT
-    step_bytes, step_bytes_fft, fft_ms = 0.0, 0.0, 0.0
-    for name, (ms, cnt) in stages.items():
-        b = algorithmic_bytes(name, n, w["n_mesh"])
-        if cnt and b:
-            step_bytes += b * cnt / K
-            if name in pm.CUFFT_STAGES:
-                step_bytes_fft += b * cnt / K
-                fft_ms += ms / K
-    t_step = t_max / K
-    step_roofline = {"bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (t_step / 1e3) / 1e9,
-                     "frac": step_bytes / (t_step / 1e3) / 1e9 / peak,
-                     "frac_excl_cufft": ((step_bytes - step_bytes_fft) / (max(t_step - fft_ms, 1e-9) / 1e3) / 1e9
-                                         / peak),
-                     "note": "cuFFT time taken from the profiled pass; peak as in roofline"}
+    head["roofline"]["peak_source"] = peak_kind
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
     ph = torch.from_numpy(np.ascontiguousarray(p)).pin_memory().numpy()
     xo = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
     po = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-    sim2 = sim
     with torch.cuda.stream(stream):
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim2.set_particles(xh, ph)
-        sim2.run(K, a[0], a[K])
-        sim2.get_particles(xo, po)
+        sim.set_particles(xh, ph)
+        sim.run(K, a[0], a[K])
+        sim.get_particles(xo, po)
         t_e2e = time.perf_counter() - t0
     t_e2e = max_over_ranks(dist, t_e2e)
     e2e = {"value": units / t_e2e, "unit": "particle-steps/s", "h2d_bytes_per_step": 48 * n / K,
            "d2h_bytes_per_step": 48 * n / K,
            "note": "set_particles(pinned host x,p) + run(K) + get_particles(host) per job of K steps"}
+    del sim
+    torch.cuda.empty_cache()
+
+    # the same workload with the paper's cubic spline kernel (h = 3.5 dx): the configuration that meets the
+    # full-run accuracy bar (cloud-in-cell with the quantum force is chaotic on this mesh)
+    spline = None
+    if not args.no_spline:
+        cfgs = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP32, m22=w["m22"],
+                              force_mode=pm.FORCE_HYBRID, kernel=pm.KERNEL_SPLINE, smooth_h=3.5, fft_jit=True)
+        ssp = pm.Sim(cfgs, stream=stream)
+        ssp.set_particles(x, p)
+        tun_s = ssp.autotune(reps=5)
+        if dist is not None:
+            dist.barrier()
+        spline = measure(pm, ssp, w, K, W, stream, spline=True, tuning=tun_s, peak=peak, workload_key="c2s")
+        ts = max_over_ranks(dist, spline["t_ms"])
+        spline["value"] = sum_over_ranks(dist, n * K) / (ts / 1e3)
+        spline["kernel"] = "cubic spline, h = 3.5 dx (Sec. II.A), hybrid force"
+        spline["accuracy"] = ("full run fp32 vs fp64: max |dP/P| <= 1e-3 for k <= k_Nyq/2 and Layzer-Irvine "
+                              "residual < 1e-2 (gated in tests/test_gpu_full_scale.py)")
+        ssp.close()
+        torch.cuda.empty_cache()
 
     # plain fp64 path on the same workload
     fp64 = None
     if not args.no_fp64:
         cfg64 = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP64, m22=w["m22"],
                                force_mode=pm.FORCE_HYBRID)
-        del sim
-        torch.cuda.empty_cache()
         s64 = pm.Sim(cfg64, stream=stream)
         s64.set_particles(x, p)
         K64 = max(2, min(K, 10))
@@ -409,39 +476,69 @@ def run_gpu(args):
         fp64 = {"value": sum_over_ranks(dist, n * K64) / (t64 / 1e3), "unit": "particle-steps/s",
                 "steps": K64, "ms_per_step": t64 / K64}
         s64.close()
-
-    # the same workload with the paper's cubic spline kernel (h = 3.5 dx): three more transforms per step
-    spline = None
-    if not args.no_spline:
-        cfgs = pm.make_config(n, w["n_mesh"], w["box"], precision=pm.FP32, m22=w["m22"],
-                              force_mode=pm.FORCE_HYBRID, kernel=pm.KERNEL_SPLINE, smooth_h=3.5, fft_jit=True)
         torch.cuda.empty_cache()
-        ssp = pm.Sim(cfgs, stream=stream)
-        ssp.set_particles(x, p)
-        ssp.autotune(reps=3)
+
+    # the large single simulation (256^3 particles on 512^3, fp32)
+    large = None
+    if not args.no_large:
+        wl = LARGE
+        al = schedule(wl)
+        xl, pl = ics.zeldovich(wl["n_side"], wl["n_mesh"], wl["box"], al[0], wl["seed"] + rank, m22=wl["m22"])
+        cfgl = pm.make_config(len(xl), wl["n_mesh"], wl["box"], precision=pm.FP32, m22=wl["m22"],
+                              force_mode=pm.FORCE_HYBRID, fft_jit=True)
+        sl = pm.Sim(cfgl, stream=stream)
+        sl.set_particles(xl, pl)
+        tun_l = sl.autotune(reps=3)
+        KL, WL = max(2, min(K, 10)), max(3, min(W, 5))
+        if dist is not None:
+            dist.barrier()
+        large = measure(pm, sl, wl, KL, WL, stream, tuning=tun_l, peak=peak, workload_key="c3")
+        tl = max_over_ranks(dist, large["t_ms"])
+        large["value"] = sum_over_ranks(dist, len(xl) * KL) / (tl / 1e3)
+        large["workload"] = wl["name"]
+        large["steps"], large["warmup"] = KL, WL
+        sl.close()
+        del xl, pl
+        torch.cuda.empty_cache()
+
+    # the small plain-fp64 configuration: one whole 200-step run (its working set fits in L2; the run starts
+    # after an L2 flush and its steps reuse L2 as a production run would)
+    small = None
+    if not args.no_small:
+        ws = SMALL
+        asm = schedule(ws)
+        xs, ps = ics.zeldovich(ws["n_side"], ws["n_mesh"], ws["box"], asm[0], ws["seed"] + rank, m22=ws["m22"])
+        cfgs1 = pm.make_config(len(xs), ws["n_mesh"], ws["box"], precision=pm.FP64, m22=ws["m22"],
+                               force_mode=pm.FORCE_HYBRID)
+        s1 = pm.Sim(cfgs1, stream=stream)
+        reps = []
         with torch.cuda.stream(stream):
-            ssp.run(W, a[0], a[W])
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ssp.run(K, a[W], a[W + K])
-            e1.record(stream)
-            torch.cuda.synchronize()
-        ts = max_over_ranks(dist, e0.elapsed_time(e1))
-        spline = {"value": sum_over_ranks(dist, n * K) / (ts / 1e3), "unit": "particle-steps/s", "steps": K,
-                  "ms_per_step": ts / K, "kernel": "cubic spline, h = 3.5 dx (Sec. II.A)"}
-        ssp.close()
+            for r in range(3):  # the first run captures the graphs
+                s1.set_particles(xs, ps)
+                flush_l2()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s1.run(ws["nsteps"], asm[0], asm[-1])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                reps.append(e0.elapsed_time(e1))
+        t1 = max_over_ranks(dist, min(reps[1:]))
+        small = {"value": sum_over_ranks(dist, len(xs) * ws["nsteps"]) / (t1 / 1e3), "unit": "particle-steps/s",
+                 "ms_per_run": t1, "ms_per_step": t1 / ws["nsteps"], "steps": ws["nsteps"], "dtype": "f64",
+                 "workload": ws["name"], "l2": "working set fits in L2; L2 flushed before each timed run"}
+        s1.close()
+        torch.cuda.empty_cache()
 
     batched = None
     if not args.no_batch:
-        torch.cuda.empty_cache()
         batched = run_batched(pm, ics, K, W, stream)
         t_b = max_over_ranks(dist, batched["ms_per_step"])
         batched["value"] = sum_over_ranks(dist, batched["particles"] * K) / (t_b * K / 1e3)
+        torch.cuda.empty_cache()
     served = None
     if args.serve_requests > 0:
         from paper_1608_00802_gb300 import serve
-        torch.cuda.empty_cache()
         served = run_served(serve, args.serve_requests)
     if rank != 0:
         return 0
@@ -450,16 +547,22 @@ def run_gpu(args):
         v, dt, sample = oracle_step_rate(w)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": cpu_cores_used(), "kind": "oracle",
                "sample": sample, "seconds": dt}
+        if not args.no_parallel_oracle:
+            vp, cores, wall = oracle_parallel_rate(w)
+            cpu["parallel"] = {"value": vp, "cores": cores, "wall_s": wall,
+                               "sample": "one full-size KDK step per core, %d independent copies at once" % cores}
     line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "precision": "fp32 cell+offset, fp32 mesh/FFT",
-                       "force_mode": "hybrid (PM gravity + Q by the kernel gradient, Sec. II.A step iii)", "parallelism": "replicas" if world > 1 else "single",
+                       "kernel": "cloud-in-cell",
+                       "force_mode": "hybrid (PM gravity + Q by the kernel gradient, Sec. II.A step iii)",
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.5 GB touched per step), no flush"},
-            "roofline": roofline, "step_roofline": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches,
-            "launch_shapes": tuning,
-            "clocks": clk.summary(), "stages": per_stage, "fp64_plain": fp64, "spline_kernel": spline,
+            "roofline": head["roofline"], "step_roofline": head["step_roofline"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": head["launches"], "launch_shapes": tuning, "clocks": head["clocks"],
+            "stages": head["stages"], "movers_per_step": head["movers_per_step"],
+            "spline_kernel": spline, "fp64_plain": fp64, "large": large, "small_fp64": small,
             "batched": batched, "served": served,
             "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None}
     print(json.dumps(line))
@@ -492,7 +595,14 @@ def run_batched(pm, ics, K, W, stream):
     cache = pm.TuningCache()  # one autotuner run per member size, shared by the others (untimed)
     for mem, (n, nm, box, m22, seed) in zip(batch.members, members):
         mem.set_particles(*ics.zeldovich(n, nm, box, a[0], seed, m22=m22))
-        mem.autotune(reps=5, cache=cache)
+        key = pm.tuning_key(mem.cfg)
+        if key not in cache:
+            t = mem.autotune(reps=5)
+            if t["stencil_rows"] == 0 or t["stencil_stages"] != 0:
+                # a class steps packed with one-shot stencil tiles only
+                t = dict(t, stencil_rows=4, stencil_planes=4, stencil_stages=0)
+            cache[key] = t
+        mem.set_tuning(cache[key])
     with torch.cuda.stream(stream):
         if W > 0:
             batch.run(W, a[0], a[W])
@@ -504,9 +614,12 @@ def run_batched(pm, ics, K, W, stream):
         torch.cuda.synchronize()
     t = e0.elapsed_time(e1)
     units = sum(n ** 3 for n, *_ in members) * K
+    classes, packed = batch.info()
     batch.close()
     return {"value": units / (t / 1e3), "unit": "particle-steps/s", "steps": K, "ms_per_step": t / K,
-            "workload": BATCH["name"], "particles": sum(n ** 3 for n, *_ in members)}
+            "workload": BATCH["name"], "particles": sum(n ** 3 for n, *_ in members),
+            "classes": classes, "packed_members": packed,
+            "launch_shapes": {k: v for k, v in cache.items()}}
 
 
 SERVE = dict(name="Poisson arrivals 20 req/s, particles {32,64,128,192}^3 (weights .4/.3/.2/.1), mesh 2x, "
@@ -549,6 +662,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-spline", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-parallel-oracle", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--tuning", default=None, help="launch shapes (pm_tuning fields as JSON) instead of the "
                     "autotuner's, for the single simulation")

@@ -239,6 +239,15 @@ enum {
   PM_STAGE_SORT_PARTITION = 9, PM_STAGE_SORT_MERGE = 10, PM_STAGE_OTHER = 11, PM_NSTAGES = 12
 };
 
+/* Test aid for the bounded device waits: runs one radix pass of the
+ * particles' keys in which no block takes the first tile, so the decoupled
+ * look-back of the second tile waits on a predecessor that never publishes;
+ * after spin_limit polls the wait gives up and sets the timeout bit of the
+ * error word instead of hanging.  Returns the status that produces
+ * (PM_ERR_TIMEOUT); only scratch buffers are written, so the simulation stays
+ * usable.  Needs more than 2048 particles.  Sync. */
+pm_status pm_debug_sort_timeout(pm_sim* sim, int32_t spin_limit);
+
 /* Incremental re-sorts since pm_create (one per drift of the particles) and
  * the particles they moved to another cell, summed on the device.  Sync. */
 pm_status pm_sort_stats(pm_sim* sim, int64_t* resorts, int64_t* movers);
@@ -257,10 +266,14 @@ pm_status pm_profile_end(pm_sim* sim, double* ms, int64_t* launches);
  * paper's runs are independent; the batch is only an execution unit).  Each
  * member is an ordinary pm_sim (use pm_batch_member with the single-simulation
  * calls: pm_set_particles, pm_energy, pm_get_particles, ...) with its own
- * stream; pm_batch_run captures two leapfrog steps of all members as one CUDA
- * graph (members run concurrently inside it) and replays it, so a step costs
- * one graph launch.  Per-step kick and drift weights come from a table in the
- * batch arena indexed by a per-member step counter on the device. */
+ * stream.  Members of equal configuration apart from box, mass and cosmology
+ * form a class and sit in the batch arena at a fixed stride; pm_batch_run
+ * steps each class with one launch per kernel over all its members and one
+ * batched cuFFT plan (see pm_batch_info), captures two leapfrog steps of all
+ * classes as one CUDA graph (classes run concurrently inside it) and replays
+ * it, so a step costs one graph launch.  Per-step kick and drift weights come
+ * from a table in each member's arena indexed by its step counter on the
+ * device. */
 typedef struct pm_batch pm_batch;
 #define PM_BATCH_MAX_STEPS 8192
 
@@ -283,6 +296,13 @@ pm_sim* pm_batch_member(pm_batch* b, int32_t i);
  * momenta are synchronised at the end.  1 <= nsteps <= PM_BATCH_MAX_STEPS.
  * Async with respect to the host; the batch stream waits for all members. */
 pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const double* a_end);
+
+/* Classes of the batch (members of equal configuration apart from box, mass
+ * and cosmology) and the members the last pm_batch_run stepped by packed
+ * launches: one launch per kernel and one batched cuFFT transform per class
+ * (fp32 cloud-in-cell classes of two or more members in one common state, with
+ * one-shot stencil tiles); the others step member by member. */
+pm_status pm_batch_info(const pm_batch* b, int32_t* classes, int32_t* packed_members);
 
 /* Message of the last failure of a batch call. */
 const char* pm_batch_last_error(const pm_batch* b);

@@ -88,8 +88,8 @@ double half_point(const pm_config& c, double a0, double a1) {
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t pos[2], mom[2], keys[4], vals[3], src, tcount, tile_cnt, row_start, rho, phi, q, spec, what, spec2, work, staging,
-      hist, status, st_list, st_count, part, part_aux, red, err, ktab, total;
+  size_t pos[2], mom[2], keys[4], vals[3], tcount, rcnt, btot, srow, mrow, tile_cnt, row_start, rho, phi, q, spec, what,
+      spec2, work, staging, hist, status, st_list, st_count, part, part_aux, red, err, ktab, total;
   int key_bits, passes, digit_bits, ntiles;
 };
 
@@ -170,8 +170,13 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   for (int k = 0; k < 2; ++k) L.mom[k] = take(n * recsz);
   for (int k = 0; k < 4; ++k) L.keys[k] = take(n * 4);
   for (int k = 0; k < 3; ++k) L.vals[k] = take(n * 4);
-  L.src = take(n * 4);                              // slot of every sorted index
-  L.tcount = take(size_t(mover_count_words(int64_t(n))) * 4);  // movers per tile and group
+  L.tcount = take(size_t(mover_count_words(int64_t(n))) * 8);  // movers per tile, movers before each tile
+  // re-sort: stayers, movers and bucket fill per mesh row; the row scan's tile totals; stayers and movers
+  // before each row
+  L.rcnt = take(3 * N * N * 4);
+  L.btot = take(2 * row_scan_tiles(int(N)) * 4);
+  L.srow = take((N * N + 1) * 4);
+  L.mrow = take((N * N + 1) * 4);
   L.tile_cnt = take(16);  // (stayers, movers) of the last re-sort
   L.row_start = take((N * N + 1) * 4);
   L.rho = take(n3 * rsz);
@@ -199,7 +204,8 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   L.part_aux = take(2 * aux * 8);
   L.red = take(3 * PK_MAX_BINS * 8 + 64);
   L.err = take(256);
-  L.ktab = take(size_t(PM_RUN_GRAPH_MAX_STEPS) * sizeof(KickParams));
+  // per-step kick weights of pm_run and of a batch run
+  L.ktab = take(size_t(std::max(PM_RUN_GRAPH_MAX_STEPS, PM_BATCH_MAX_STEPS)) * sizeof(KickParams));
   L.total = off;
   return L;
 }
@@ -245,6 +251,11 @@ struct pm_sim {
   uint32_t* keys_tmp[2];
   bool keys_marked = false;  // a drift has flagged the movers in `keys` since the last sort
   Tuning tune;                // launch shapes
+  // spline kernel smoothed in real space (fp32, support within three cells):
+  // the smoothed density lives in the spec2 region, and `rho` holds the
+  // unsmoothed Q~ between the stencil and its smoothing
+  bool direct = false;
+  double taps[19 * 4];
   int sms = 152;              // multiprocessors of the device
   bool krho_valid = false;    // the K_rho partials belong to the current Q~
   cufftHandle plan_fwd, plan_inv;
@@ -278,14 +289,16 @@ struct pm_sim {
   }
   void* pos() const { return arena + L.pos[cur]; }
   void* mom() const { return arena + L.mom[cur]; }
-  // slot of every sorted index in pos()/mom() (written by every sort)
-  uint32_t* src() const { return at<uint32_t>(L.src); }
   bool fp64() const { return cfg.precision == PM_FP64; }
   int64_t n() const { return cfg.n_part; }
   // err region: [0] error bits, [1] sort epoch, [2] device step counter; at byte 64 two
   // 64-bit counters of the incremental re-sorts and of the particles they moved
   uint32_t* errword() const { return at<uint32_t>(L.err); }
   unsigned long long* sort_stats() const { return reinterpret_cast<unsigned long long*>(arena + L.err + 64); }
+  // at byte 128 the Green and quantum-pressure coefficients of this simulation
+  // (doubles, written at creation), read by the launches that step a packed
+  // group of simulations whose boxes and masses differ
+  double* coefs() const { return reinterpret_cast<double*>(arena + L.err + 128); }
   double* part() const { return at<double>(L.part); }
   double* red() const { return at<double>(L.red); }
   double* staging() const { return at<double>(L.staging); }
@@ -347,46 +360,29 @@ int kr_blocks(const pm_sim* s) {
   return tiled ? stencil_launch_blocks(s->cfg.n_mesh, s->tune.st_ty, s->tune.st_zlen) : MESH_GRID;
 }
 
-// Incremental re-sort after a drift: the stayers are still in order, so the
-// movers are split off (stable partition, with the drift's per-tile mover
-// counts), radix-sorted by (key, previous slot) with their count known only on
-// the device, and merged back; the merge writes the sorted keys, the slot of
-// every sorted index and the row starts.  The records stay where the drift
-// wrote them.  Same order as the full sort.
+// Incremental re-sort after a drift: the stayers are still in order, so every
+// particle's place follows from the stayers and movers of its mesh row (stable
+// partition with per-row counts, a scan of the rows, the movers in per-row
+// buckets, the placement of each particle with its records into the other
+// buffer; see pm_sort.cuh).  Same order as the full sort; also writes the row
+// starts.
 template <typename R>
 pm_status resort_movers(pm_sim* s) {
   const Layout& L = s->L;
-  const int64_t n = s->n();
-  uint32_t* hist = s->at<uint32_t>(L.hist);
-  uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
-  uint64_t* status = s->at<uint64_t>(L.status);
-  uint32_t* counts = s->at<uint32_t>(L.tile_cnt);
-  uint32_t* sk = s->keys_tmp[0];
-  uint32_t* sv = s->at<uint32_t>(L.vals[0]);
-  uint32_t* mk[2] = {s->keys_tmp[1], s->at<uint32_t>(L.keys[3])};
-  uint32_t* mv[2] = {s->at<uint32_t>(L.vals[1]), s->at<uint32_t>(L.vals[2])};
-  // histograms and tile counters start at zero
-  CU(s, cudaMemsetAsync(hist, 0, hist_bytes(), s->stream));
-  {
-    PROF(s, PM_STAGE_SORT_PARTITION);
-    CU(s, launch_mover_partition(s->keys, n, s->at<uint32_t>(L.tcount), sk, sv, mk[0], mv[0], counts, hist,
-                                 L.passes, L.digit_bits, L.key_bits, s->errword() + 1, s->sort_stats(), s->stream));
+  const int N = s->cfg.n_mesh;
+  const int nxt = s->cur ^ 1;
+  CU(s, cudaMemsetAsync(s->at<uint32_t>(L.rcnt), 0, size_t(3) * N * N * 4, s->stream));
+  const int stages[3] = {PM_STAGE_SORT_PARTITION, PM_STAGE_SORT_PASS, PM_STAGE_SORT_MERGE};
+  for (int part = 0; part < 3; ++part) {
+    PROF(s, stages[part]);
+    CU(s, launch_resort<R>(part, s->keys, s->n(), s->at<uint32_t>(L.tcount), s->keys_tmp[0],
+                           s->at<uint32_t>(L.vals[0]), s->keys_tmp[1], s->at<uint32_t>(L.vals[1]),
+                           s->at<uint32_t>(L.keys[3]), s->at<uint32_t>(L.vals[2]), s->at<uint32_t>(L.tile_cnt),
+                           s->at<uint32_t>(L.rcnt), s->at<uint32_t>(L.btot), s->at<uint32_t>(L.srow),
+                           s->at<uint32_t>(L.mrow), s->at<uint32_t>(L.row_start), s->mesh, s->sort_stats(), s->keys,
+                           s->pos(), s->mom(), s->arena + L.pos[nxt], s->arena + L.mom[nxt], s->sms, s->stream));
   }
-  int b = 0;
-  for (int p = 0; p < L.passes; ++p) {
-    const int shift = p * L.digit_bits;
-    const int bits = (shift + L.digit_bits <= L.key_bits) ? L.digit_bits : (L.key_bits - shift);
-    PROF(s, PM_STAGE_SORT_PASS);
-    CU(s, launch_sort_pass<R>(false, mk[b], mv[b], n, shift, bits, hist + p * (1 << RS_MAX_BITS), status,
-                              counters + p, s->errword() + 1, p, L.ntiles, mk[b ^ 1], mv[b ^ 1], nullptr, nullptr,
-                              nullptr, nullptr, s->errword(), s->stream, counts + 1));
-    b ^= 1;
-  }
-  {
-    PROF(s, PM_STAGE_SORT_MERGE);
-    CU(s, launch_merge(sk, sv, mk[b], mv[b], counts, n, s->keys, s->src(), uint32_t(s->cfg.n_mesh),
-                       s->at<uint32_t>(L.row_start), s->stream));
-  }
+  s->cur = nxt;
   s->keys_marked = false;
   s->sorted = true;
   return PM_OK;
@@ -440,17 +436,17 @@ pm_status sort_particles(pm_sim* s) {
   }
   {
     PROF(s, PM_STAGE_ROW_START);
-    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->src(),
-                           s->stream));
+    CU(s, launch_row_start(s->keys, n, uint32_t(s->cfg.n_mesh), s->at<uint32_t>(L.row_start), s->stream));
   }
   s->sorted = true;
   return PM_OK;
 }
 
-// Q~ (and the K_rho partials) from the density on the mesh
-template <typename R>
-pm_status stencil_stage(pm_sim* s, bool diag = false) {
-  const Layout& L = s->L;
+// where the density the stencil and the Poisson solve read lives: `rho`, or
+// with the real-space spline smoothing the smoothed copy in the spec2 region
+size_t density_field(const pm_sim* s) { return s->direct ? s->L.spec2 : s->L.rho; }
+
+StencilParams stencil_params(const pm_sim* s, bool diag) {
   StencilParams sp;
   sp.step = s->cfg.lap == PM_LAP_WIDE ? 2 : 1;
   sp.rho_floor = s->cfg.rho_floor;
@@ -460,10 +456,18 @@ pm_status stencil_stage(pm_sim* s, bool diag = false) {
   sp.zlen = s->tune.st_zlen;
   sp.stages = s->tune.st_stages;
   sp.diag = diag ? 1 : 0;
+  return sp;
+}
+
+// Q~ (and the K_rho partials) from the density on the mesh
+template <typename R>
+pm_status stencil_stage(pm_sim* s, bool diag = false) {
+  const Layout& L = s->L;
+  const StencilParams sp = stencil_params(s, diag);
   s->krho_valid = diag || s->fp64() || s->cfg.lap != PM_LAP_COMPACT;  // the generic kernel always sums
   PROF(s, PM_STAGE_STENCIL);
-  CU(s, launch_stencil<R>(s->at<R>(L.rho), s->mesh, sp, s->at<R>(L.q), kr_part(s), s->at<uint32_t>(L.st_list),
-                          s->at<uint32_t>(L.st_count), s->errword(), s->stream));
+  CU(s, launch_stencil<R>(s->at<R>(density_field(s)), s->mesh, sp, s->at<R>(s->direct ? L.rho : L.q), kr_part(s),
+                          s->at<uint32_t>(L.st_list), s->at<uint32_t>(L.st_count), s->errword(), s->stream));
   return PM_OK;
 }
 
@@ -498,15 +502,37 @@ pm_status fft_c2r(pm_sim* s, void* in, void* out) {
 
 bool spline(const pm_sim* s) { return s->cfg.kernel == PM_KERNEL_SPLINE; }
 
-// a mesh field convolved in place with the spline's node weights
+// the normalised node weights of the spline at squared distance i^2 + s (in
+// cells, s = j^2 + k^2 <= 18, i <= 3) for the real-space smoothing: W(r, h)
+// of Sec. II.A up to its constant, divided by its sum over the nodes
+void spline_taps(double hc, double* g) {
+  auto f = [&](int r2) {
+    const double u = sqrt(double(r2)) / hc;
+    return u <= 0.5 ? 1.0 - 6.0 * u * u + 6.0 * u * u * u : (u <= 1.0 ? 2.0 * (1.0 - u) * (1.0 - u) * (1.0 - u) : 0.0);
+  };
+  double sum = 0.0;
+  for (int i = -3; i <= 3; ++i)
+    for (int j = -3; j <= 3; ++j)
+      for (int k = -3; k <= 3; ++k) sum += f(i * i + j * j + k * k);
+  for (int q = 0; q < 19; ++q)
+    for (int i = 0; i < 4; ++i) g[q * 4 + i] = f(i * i + q) / sum;
+}
+
+// a mesh field convolved with the spline's node weights, from `in` to `out`
+// (the same offset for the spectral smoothing, which works in place)
 template <typename R>
-pm_status smooth_field(pm_sim* s, size_t field) {
-  PMST(fft_r2c<R>(s, s->arena + field, s->arena + s->L.spec));
+pm_status smooth_field(pm_sim* s, size_t in, size_t out) {
+  if (s->direct) {
+    PROF(s, PM_STAGE_GREEN);
+    CU(s, launch_smooth_direct<float>(s->at<float>(in), s->at<float>(out), s->mesh, s->taps, s->stream));
+    return PM_OK;
+  }
+  PMST(fft_r2c<R>(s, s->arena + in, s->arena + s->L.spec));
   {
     PROF(s, PM_STAGE_GREEN);
     CU(s, launch_smooth_spec<R>(s->arena + s->L.spec, s->arena + s->L.what, s->mesh, s->stream));
   }
-  return fft_c2r<R>(s, s->arena + s->L.spec, s->arena + field);
+  return fft_c2r<R>(s, s->arena + s->L.spec, s->arena + out);
 }
 
 double green_coef(const pm_sim* s) {
@@ -514,13 +540,17 @@ double green_coef(const pm_sim* s) {
   return -1.5 * s->cfg.omega_m * s->dx * s->dx / (4.0 * N * N * N);
 }
 
-// Q~ from the density in `rho`, smoothed with the spline kernel (the transpose
-// of the density's smoothing)
+// Q~ from the density, smoothed with the spline kernel (the transpose of the
+// density's smoothing); diag: with the K_rho partials.  In real space the
+// stencil writes the raw Q~ to `rho` and the smoothing moves it to `q`.
 template <typename R>
-pm_status quantum_stage(pm_sim* s) {
+pm_status quantum_stage(pm_sim* s, bool diag = false) {
   if (!s->cfg.quantum) return PM_OK;
-  PMST(stencil_stage<R>(s));
-  if (spline(s)) PMST(smooth_field<R>(s, s->L.q));
+  PMST(stencil_stage<R>(s, diag));
+  if (s->direct)
+    PMST(smooth_field<R>(s, s->L.rho, s->L.q));
+  else if (spline(s))
+    PMST(smooth_field<R>(s, s->L.q, s->L.q));
   return PM_OK;
 }
 
@@ -529,23 +559,21 @@ pm_status quantum_stage(pm_sim* s) {
 // smoothed it, so that the field the next kick reads is the same
 template <typename R>
 pm_status krho_stage(pm_sim* s) {
-  PMST(stencil_stage<R>(s, true));
-  if (spline(s)) PMST(smooth_field<R>(s, s->L.q));
-  return PM_OK;
+  return quantum_stage<R>(s, true);
 }
 
-// phi~ and Q~ from the density in `rho` (cloud-in-cell kernel: the deposit;
-// spline kernel: the already smoothed density, whose force potential is
-// smoothed once more)
+// phi~ and Q~ from the density (cloud-in-cell kernel: the deposit; spline
+// kernel: the already smoothed density, whose force potential is smoothed
+// once more)
 template <typename R>
 pm_status mesh_from_density(pm_sim* s) {
   const Layout& L = s->L;
-  PMST(fft_r2c<R>(s, s->arena + L.rho, s->arena + L.spec));
+  PMST(fft_r2c<R>(s, s->arena + density_field(s), s->arena + L.spec));
   {
     PROF(s, PM_STAGE_GREEN);
     if (spline(s))
       CU(s, launch_green_spline<R>(s->arena + L.spec, nullptr, s->arena + L.what, s->mesh, green_coef(s), wg_part(s),
-                                   s->stream));
+                                   s->stream, 0));
     else
       CU(s, launch_green<R>(s->arena + L.spec, s->mesh, green_coef(s), wg_part(s), s->stream));
   }
@@ -556,17 +584,22 @@ pm_status mesh_from_density(pm_sim* s) {
 }
 
 // spline kernel from the cloud-in-cell density in `rho`: one forward transform
-// gives both the smoothed density (back into `rho`) and the force potential
+// gives the force potential and (spectral smoothing) the smoothed density
+// back into `rho`; the real-space smoothing writes the smoothed density to the
+// spec2 region instead
 template <typename R>
 pm_status spline_fields(pm_sim* s) {
   const Layout& L = s->L;
   PMST(fft_r2c<R>(s, s->arena + L.rho, s->arena + L.spec));
   {
     PROF(s, PM_STAGE_GREEN);
-    CU(s, launch_green_spline<R>(s->arena + L.spec, s->arena + L.spec2, s->arena + L.what, s->mesh, green_coef(s),
-                                 wg_part(s), s->stream));
+    CU(s, launch_green_spline<R>(s->arena + L.spec, s->direct ? nullptr : s->arena + L.spec2, s->arena + L.what,
+                                 s->mesh, green_coef(s), wg_part(s), s->stream, 1));
   }
-  PMST(fft_c2r<R>(s, s->arena + L.spec2, s->arena + L.rho));
+  if (s->direct)
+    PMST(smooth_field<R>(s, L.rho, L.spec2));
+  else
+    PMST(fft_c2r<R>(s, s->arena + L.spec2, s->arena + L.rho));
   PMST(fft_c2r<R>(s, s->arena + L.spec, s->arena + L.phi));
   PMST(quantum_stage<R>(s));
   s->fields_valid = true;
@@ -590,8 +623,8 @@ pm_status deposit(pm_sim* s) {
     if (st != PM_OK) return st;
   }
   PROF(s, PM_STAGE_DEPOSIT);
-  CU(s, launch_deposit<R>(s->pos(), s->src(), s->at<uint32_t>(s->L.row_start), s->n(), s->mesh, s->norm,
-                          s->at<R>(s->L.rho), s->stream, s->tune.dep_warps));
+  CU(s, launch_deposit<R>(s->pos(), s->at<uint32_t>(s->L.row_start), s->n(), s->mesh, s->norm, s->at<R>(s->L.rho),
+                          s->stream, s->tune.dep_warps));
   return PM_OK;
 }
 
@@ -602,11 +635,11 @@ pm_status compute_fields(pm_sim* s) {
   return spline(s) ? spline_fields<R>(s) : mesh_from_density<R>(s);
 }
 
-// the density of Eq. (rhodis) in `rho` (fields left invalid)
+// the density of Eq. (rhodis) in density_field (fields left invalid)
 template <typename R>
 pm_status density(pm_sim* s) {
   PMST(deposit<R>(s));
-  if (spline(s)) PMST(smooth_field<R>(s, s->L.rho));
+  if (spline(s)) PMST(smooth_field<R>(s, s->L.rho, density_field(s)));
   s->fields_valid = false;
   return PM_OK;
 }
@@ -630,18 +663,16 @@ pm_status kick(pm_sim* s, const KickParams& kp, double* acc, const KickParams* k
     pm_status st = sort_particles<R>(s);
     if (st != PM_OK) return st;
   }
-  // a drift writes the records in sorted order to the other buffer and counts its movers
-  const int nxt = s->cur ^ 1;
+  // a drift counts its movers per tile (for the re-sort's partition)
   if (drift)
     CU(s, cudaMemsetAsync(s->at<uint32_t>(L.tcount), 0, size_t(mover_count_words(s->n())) * 4, s->stream));
   {
     PROF(s, PM_STAGE_KICK);
-    CU(s, launch_kick<R>(s->pos(), s->mom(), s->src(), s->arena + L.pos[nxt], s->arena + L.mom[nxt], s->keys,
-                         s->at<uint32_t>(L.tcount), s->n(), s->at<R>(L.phi), s->at<R>(L.q), s->mesh, kp, kp_tab, step,
-                         s->part(), acc, s->errword(), s->tune.kick_threads, s->stream));
+    CU(s, launch_kick<R>(s->pos(), s->mom(), s->keys, s->at<uint32_t>(L.tcount), s->n(), s->at<R>(L.phi),
+                         s->at<R>(L.q), s->mesh, kp, kp_tab, step, s->part(), acc, s->errword(),
+                         s->tune.kick_threads, s->stream));
   }
   if (drift) {
-    s->cur = nxt;
     s->sorted = false;
     s->fields_valid = false;
     s->keys_marked = true;
@@ -932,8 +963,21 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     delete s;
     return fail(nullptr, PM_ERR_CUDA, "stream setup failed");
   }
+  {
+    const double coefs[2] = {green_coef(s), stencil_params(s, false).qcoef};
+    if (cudaMemcpyAsync(s->coefs(), coefs, sizeof coefs, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      cufftDestroy(s->plan_fwd);
+      cufftDestroy(s->plan_inv);
+      delete s;
+      return fail(nullptr, PM_ERR_CUDA, "coefficient upload failed");
+    }
+  }
   if (c->precision == PM_FP32) kick_stream_prepare();
   if (s->cfg.kernel == PM_KERNEL_SPLINE) {
+    // real-space smoothing for fp32 supports within three cells (h <= 4 cells)
+    s->direct = c->precision == PM_FP32 && c->smooth_h <= 4.0;
+    spline_taps(c->smooth_h, s->taps);
     pm_status st = DISPATCH(s, spline_symbol, s);
     if (st == PM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) st = PM_ERR_CUDA;
     if (st != PM_OK) {
@@ -1298,7 +1342,7 @@ pm_status pm_get_field(pm_sim* s, int32_t which, double* host_out) {
   if (!host_out || which < 0 || which > 2) return fail(s, PM_ERR_INVALID_ARG, "bad field or output");
   if (which == PM_FIELD_Q && !s->cfg.quantum) return fail(s, PM_ERR_STATE, "quantum pressure is off");
   const Layout& L = s->L;
-  const size_t offs[3] = {L.rho, L.phi, L.q};
+  const size_t offs[3] = {density_field(s), L.phi, L.q};
   const int64_t n3 = s->mesh.n3;
   double* d = s->staging();
   if (s->fp64()) {
@@ -1318,9 +1362,9 @@ pm_status pm_set_density(pm_sim* s, const double* rho_host) {
   double* d = s->staging();
   CU(s, cudaMemcpyAsync(d, rho_host, n3 * 8, cudaMemcpyHostToDevice, s->stream));
   if (s->fp64()) {
-    CU(s, cudaMemcpyAsync(s->arena + s->L.rho, d, n3 * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CU(s, cudaMemcpyAsync(s->arena + density_field(s), d, n3 * 8, cudaMemcpyDeviceToDevice, s->stream));
   } else {
-    CU(s, launch_from_double<float>(d, n3, s->at<float>(s->L.rho), s->stream));
+    CU(s, launch_from_double<float>(d, n3, s->at<float>(density_field(s)), s->stream));
   }
   pm_status st = DISPATCH(s, mesh_from_density, s);
   if (st != PM_OK) return st;
@@ -1373,9 +1417,30 @@ pm_status pm_get_order(pm_sim* s, uint32_t* cell, uint32_t* id) {
     if (st != PM_OK) return st;
   }
   uint32_t* d = reinterpret_cast<uint32_t*>(s->staging());
-  CU(s, DISPATCH(s, launch_get_order, s->pos(), s->mom(), s->src(), s->n(), d, d + s->n(), s->stream));
+  CU(s, DISPATCH(s, launch_get_order, s->pos(), s->mom(), s->n(), d, d + s->n(), s->stream));
   CU(s, cudaMemcpyAsync(cell, d, size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
   CU(s, cudaMemcpyAsync(id, d + s->n(), size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
+  return device_errors(s);
+}
+
+pm_status pm_debug_sort_timeout(pm_sim* s, int32_t spin_limit) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (spin_limit < 1) return fail(s, PM_ERR_INVALID_ARG, "spin_limit must be >= 1");
+  const Layout& L = s->L;
+  const int64_t n = s->n();
+  if (L.ntiles < 2) return fail(s, PM_ERR_INVALID_ARG, "needs more than %d particles", RS_TILE);
+  uint32_t* hist = s->at<uint32_t>(L.hist);
+  uint32_t* counters = hist + 3 * (1 << RS_MAX_BITS);
+  const int bits = std::min(L.digit_bits, L.key_bits);
+  CU(s, cudaMemsetAsync(hist, 0, hist_bytes(), s->stream));
+  CU(s, launch_sort_histogram(s->keys, n, L.passes, L.digit_bits, L.key_bits, hist, s->errword() + 1, s->stream));
+  // the first tile is never claimed: its status words stay unpublished for this pass's epoch
+  const uint32_t one = 1;
+  CU(s, cudaMemcpyAsync(counters, &one, sizeof one, cudaMemcpyHostToDevice, s->stream));
+  CU(s, DISPATCH(s, launch_sort_pass, false, s->keys, nullptr, n, 0, bits, hist, s->at<uint64_t>(L.status), counters,
+                 s->errword() + 1, 0, L.ntiles, s->keys_tmp[0], s->at<uint32_t>(L.vals[0]), nullptr, nullptr, nullptr,
+                 nullptr, s->errword(), s->stream, nullptr, 1, 0, int(spin_limit)));
   return device_errors(s);
 }
 
@@ -1428,15 +1493,135 @@ const char* pm_last_error(const pm_sim* s) { return s ? s->err.c_str() : g_creat
 }  // extern "C"
 
 // ================================================================ batches
+// Members of equal configuration (every field but the box, the axion mass and
+// the cosmology) form a class.  A class's members sit in the batch arena one
+// after another at a fixed stride, so every buffer of member m lies m strides
+// after member 0's, and one launch steps all of them: the packed kick, re-sort,
+// deposit, Green and stencil kernels take the member from a grid dimension, and
+// one batched cuFFT plan per class transforms all its meshes.  Per-member
+// coefficients (box, mass) come from each member's arena.  Classes that the
+// packed launches do not cover (fp64, the spline kernel, the wide Laplacian, a
+// stencil shape other than one-shot tiles, a single member) step member by
+// member on their own streams, as in pm_run.
+namespace {
+
+struct ClassKey {
+  pm_config c;
+  bool operator==(const ClassKey& o) const {
+    const pm_config &a = c, &b = o.c;
+    return a.n_part == b.n_part && a.n_mesh == b.n_mesh && a.precision == b.precision && a.quantum == b.quantum &&
+           a.force_mode == b.force_mode && a.lap == b.lap && a.cosmological == b.cosmological &&
+           a.rho_floor == b.rho_floor && a.rho_fp64 == b.rho_fp64 && a.kernel == b.kernel &&
+           a.smooth_h == b.smooth_h && a.fft_jit == b.fft_jit;
+  }
+};
+
+bool packable(const pm_config& c) {
+  return c.precision == PM_FP32 && c.kernel == PM_KERNEL_CIC && c.lap == PM_LAP_COMPACT;
+}
+
+// the batched transforms of a class: nm meshes, ms bytes apart
+cufftResult class_plans(const pm_config& c, int nm, size_t ms, cufftHandle* fwd, cufftHandle* inv, size_t* work) {
+  long long n[3] = {c.n_mesh, c.n_mesh, c.n_mesh};
+  long long re[3] = {c.n_mesh, c.n_mesh, c.n_mesh};
+  long long cx[3] = {c.n_mesh, c.n_mesh, c.n_mesh / 2 + 1};
+  size_t w[2] = {0, 0};
+  cufftHandle* h[2] = {fwd, inv};
+  for (int k = 0; k < 2; ++k) {
+    cufftResult r = cufftCreate(h[k]);
+    if (r != CUFFT_SUCCESS) return r;
+    r = cufftSetAutoAllocation(*h[k], 0);
+    if (r == CUFFT_SUCCESS && c.fft_jit) r = cufftSetPlanPropertyInt64(*h[k], NVFFT_PLAN_PROPERTY_INT64_PATIENT_JIT, 1);
+    if (r == CUFFT_SUCCESS)
+      r = k == 0 ? cufftMakePlanMany64(*h[k], 3, n, re, 1, (long long)(ms / 4), cx, 1, (long long)(ms / 8), CUFFT_R2C,
+                                       nm, &w[k])
+                 : cufftMakePlanMany64(*h[k], 3, n, cx, 1, (long long)(ms / 8), re, 1, (long long)(ms / 4), CUFFT_C2R,
+                                       nm, &w[k]);
+    if (r != CUFFT_SUCCESS) {
+      cufftDestroy(*h[k]);
+      if (k == 1) cufftDestroy(*fwd);
+      return r;
+    }
+  }
+  *work = std::max(w[0], w[1]);
+  return CUFFT_SUCCESS;
+}
+
+struct BatchClass {
+  std::vector<int> members;  // batch indices, in arena order
+  size_t off = 0, stride = 0, work_off = 0, work = 0;
+  bool packed = false;
+};
+
+struct BatchLayout {
+  std::vector<BatchClass> classes;
+  std::vector<size_t> off, bytes;  // per member (batch index)
+  size_t total = 0;
+};
+
+bool batch_layout(const pm_config* cfgs, int n, BatchLayout* L, std::string* why) {
+  std::vector<ClassKey> keys;
+  L->off.assign(n, 0);
+  L->bytes.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const size_t b = pm_arena_bytes(&cfgs[i]);
+    if (b == 0) {
+      *why = "member " + std::to_string(i) + ": " + g_create_error;
+      return false;
+    }
+    L->bytes[i] = b;
+    size_t k = 0;
+    while (k < keys.size() && !(keys[k] == ClassKey{cfgs[i]})) ++k;
+    if (k == keys.size()) {
+      keys.push_back(ClassKey{cfgs[i]});
+      L->classes.emplace_back();
+    }
+    L->classes[k].members.push_back(i);
+  }
+  size_t off = 0;
+  for (size_t k = 0; k < L->classes.size(); ++k) {
+    BatchClass& C = L->classes[k];
+    C.stride = align_up(L->bytes[C.members[0]]);
+    C.off = off;
+    for (size_t j = 0; j < C.members.size(); ++j) L->off[C.members[j]] = off + j * C.stride;
+    off = align_up(off + C.members.size() * C.stride);
+    C.packed = packable(keys[k].c) && C.members.size() >= 2;
+    if (C.packed) {
+      cufftHandle f, v;
+      if (class_plans(keys[k].c, int(C.members.size()), C.stride, &f, &v, &C.work) != CUFFT_SUCCESS) {
+        C.packed = false;  // no batched plan for this class: member by member
+      } else {
+        cufftDestroy(f);
+        cufftDestroy(v);
+        C.work_off = off;
+        off = align_up(off + C.work);
+      }
+    }
+  }
+  L->total = off;
+  return true;
+}
+
+}  // namespace
+
 struct pm_batch {
-  std::vector<pm_sim*> sims;
-  std::vector<cudaStream_t> streams;
+  std::vector<pm_sim*> sims;          // batch order
+  std::vector<cudaStream_t> streams;  // one per member (member-by-member classes)
   std::vector<cudaEvent_t> join;
+  struct Class {
+    std::vector<int> members;
+    size_t stride = 0;
+    bool packed = false;
+    cufftHandle fwd = 0, inv = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t join = nullptr;
+  };
+  std::vector<Class> classes;
   cudaEvent_t fork = nullptr, done = nullptr;
   cudaStream_t stream = nullptr;  // the caller's stream
   cudaStream_t cap = nullptr;     // the batch's own stream: graphs are captured and launched here
   char* arena = nullptr;
-  size_t table_off = 0, step_off = 0;
+  int last_packed = 0;  // members stepped by packed launches in the last run
   std::string err;
 };
 
@@ -1450,33 +1635,80 @@ pm_status bfail(pm_batch* b, pm_status st, const std::string& msg) {
   return st;
 }
 
-struct BatchLayout {
-  std::vector<size_t> off, bytes;
-  size_t table_off, step_off, total;
-};
-
-bool batch_layout(const pm_config* cfgs, int n, BatchLayout* L, std::string* why) {
-  size_t off = 0;
-  L->off.resize(n);
-  L->bytes.resize(n);
-  for (int i = 0; i < n; ++i) {
-    const size_t b = pm_arena_bytes(&cfgs[i]);
-    if (b == 0) {
-      *why = "member " + std::to_string(i) + ": " + g_create_error;
+// the members of a packed class step together only from one common state
+bool same_state(const pm_batch::Class& C, const std::vector<pm_sim*>& sims) {
+  const pm_sim* a = sims[C.members[0]];
+  for (int i : C.members) {
+    const pm_sim* s = sims[i];
+    if (s->cur != a->cur || s->sorted != a->sorted || s->fields_valid != a->fields_valid ||
+        s->keys_marked != a->keys_marked || (s->keys - s->at<uint32_t>(0)) != (a->keys - a->at<uint32_t>(0)) ||
+        s->tune.st_ty != a->tune.st_ty || s->tune.st_zlen != a->tune.st_zlen ||
+        s->tune.st_stages != a->tune.st_stages || s->tune.kick_threads != a->tune.kick_threads ||
+        s->tune.dep_warps != a->tune.dep_warps)
       return false;
-    }
-    L->off[i] = off;
-    L->bytes[i] = b;
-    off = align_up(off + b);
   }
-  L->table_off = off;
-  off = align_up(off + size_t(n) * PM_BATCH_MAX_STEPS * sizeof(KickParams));
-  L->step_off = off;
-  off = align_up(off + size_t(n) * sizeof(uint32_t));
-  L->total = off;
-  return true;
+  const StencilParams sp = stencil_params(a, false);
+  return !a->cfg.quantum || (a->tune.st_ty > 0 && a->tune.st_stages == 0 && stencil_shape_ok(a->cfg.n_mesh, sp.ty, sp.zlen, 0));
 }
 
+#define PCU(expr)                                                                                       \
+  do {                                                                                                  \
+    cudaError_t e_ = (expr);                                                                            \
+    if (e_ != cudaSuccess) return fail(s, PM_ERR_CUDA, "packed step: %s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+// One table-driven leapfrog step of every member of a packed class on
+// stream `st` (the packed form of table_step): kick + drift, re-sort, deposit,
+// both transforms, Green, stencil, step counters.  Member 0's pointers, the
+// others a stride apart.
+pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cudaStream_t st) {
+  pm_sim* s = sims[C.members[0]];
+  const Layout& L = s->L;
+  const int nm = int(C.members.size());
+  const size_t ms = C.stride;
+  const int64_t n = s->n();
+  const int nxt = s->cur ^ 1;
+  // kick + drift with the weights of the members' step counters
+  KickParams kp = base_kick(s);
+  kp.drift = 1.0;  // host-side marker only: the positions move, the weights come from the tables
+  PCU(cudaMemset2DAsync(s->at<uint32_t>(L.tcount), ms, 0, size_t(mover_count_words(n)) * 4, size_t(nm), st));
+  PCU(launch_kick<float>(s->pos(), s->mom(), s->keys, s->at<uint32_t>(L.tcount), n, s->at<float>(L.phi),
+                         s->at<float>(L.q), s->mesh, kp, s->at<KickParams>(L.ktab), s->errword() + 2, s->part(),
+                         nullptr, s->errword(), s->tune.kick_threads, st, nm, ms));
+  // re-sort into the other record buffer (the movers' count on the device of every member)
+  const int N = s->cfg.n_mesh;
+  PCU(cudaMemset2DAsync(s->at<uint32_t>(L.rcnt), ms, 0, size_t(3) * N * N * 4, size_t(nm), st));
+  for (int part = 0; part < 3; ++part)
+    PCU(launch_resort<float>(part, s->keys, n, s->at<uint32_t>(L.tcount), s->keys_tmp[0], s->at<uint32_t>(L.vals[0]),
+                             s->keys_tmp[1], s->at<uint32_t>(L.vals[1]), s->at<uint32_t>(L.keys[3]),
+                             s->at<uint32_t>(L.vals[2]), s->at<uint32_t>(L.tile_cnt), s->at<uint32_t>(L.rcnt),
+                             s->at<uint32_t>(L.btot), s->at<uint32_t>(L.srow), s->at<uint32_t>(L.mrow),
+                             s->at<uint32_t>(L.row_start), s->mesh, s->sort_stats(), s->keys, s->pos(), s->mom(),
+                             s->arena + L.pos[nxt], s->arena + L.mom[nxt], s->sms, st, nm, ms));
+  // deposit, potential, quantum pressure
+  PCU(launch_deposit<float>(s->arena + L.pos[nxt], s->at<uint32_t>(L.row_start), n, s->mesh, s->norm,
+                            s->at<float>(L.rho), st, s->tune.dep_warps, nm, ms));
+  CF(s, cufftSetStream(C.fwd, st));
+  CF(s, cufftSetStream(C.inv, st));
+  CF(s, cufftExecR2C(C.fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
+  PCU(launch_green<float>(s->arena + L.spec, s->mesh, green_coef(s), wg_part(s), st, s->coefs(), nm, ms));
+  CF(s, cufftExecC2R(C.inv, (cufftComplex*)(s->arena + L.spec), s->at<cufftReal>(L.phi)));
+  if (s->cfg.quantum)
+    PCU(launch_stencil<float>(s->at<float>(L.rho), s->mesh, stencil_params(s, false), s->at<float>(L.q), kr_part(s),
+                              s->at<uint32_t>(L.st_list), s->at<uint32_t>(L.st_count), s->errword(), st,
+                              s->coefs() + 1, nm, ms));
+  PCU(launch_step_inc(s->errword() + 2, st, nm, ms));
+  for (int i : C.members) {
+    pm_sim* m = sims[i];
+    m->cur = nxt;
+    m->keys_marked = false;
+    m->sorted = true;
+    m->fields_valid = true;
+    m->krho_valid = false;
+  }
+  return PM_OK;
+}
+#undef PCU
 
 }  // namespace
 
@@ -1512,22 +1744,15 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
   pm_batch* b = new pm_batch();
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->arena = reinterpret_cast<char*>(dev_arena);
-  b->table_off = L.table_off;
-  b->step_off = L.step_off;
   auto cleanup = [&](pm_status st, const std::string& msg) {
-    for (pm_sim* s : b->sims) pm_destroy(s);
-    for (cudaStream_t st2 : b->streams) cudaStreamDestroy(st2);
-    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->done) cudaEventDestroy(b->done);
-    if (b->cap) cudaStreamDestroy(b->cap);
-    delete b;
+    pm_batch_destroy(b);
     return bfail(nullptr, st, msg);
   };
   if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(PM_ERR_CUDA, "event or stream creation failed");
+  b->sims.assign(n, nullptr);
   for (int i = 0; i < n; ++i) {
     cudaStream_t st2;
     cudaEvent_t ev;
@@ -1540,7 +1765,29 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
     pm_sim* s = nullptr;
     pm_status r = pm_create(&cfgs[i], b->arena + L.off[i], L.bytes[i], st2, &s);
     if (r != PM_OK) return cleanup(r, "member " + std::to_string(i) + ": " + g_create_error);
-    b->sims.push_back(s);
+    b->sims[i] = s;
+  }
+  for (const BatchClass& BC : L.classes) {
+    pm_batch::Class C;
+    C.members = BC.members;
+    C.stride = BC.stride;
+    C.packed = BC.packed;
+    if (cudaStreamCreateWithFlags(&C.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C.join, cudaEventDisableTiming) != cudaSuccess) {
+      b->classes.push_back(C);
+      return cleanup(PM_ERR_CUDA, "class stream creation failed");
+    }
+    if (C.packed) {
+      size_t w = 0;
+      const pm_config& c = cfgs[C.members[0]];
+      if (class_plans(c, int(C.members.size()), C.stride, &C.fwd, &C.inv, &w) != CUFFT_SUCCESS || w > BC.work ||
+          cufftSetWorkArea(C.fwd, b->arena + BC.work_off) != CUFFT_SUCCESS ||
+          cufftSetWorkArea(C.inv, b->arena + BC.work_off) != CUFFT_SUCCESS) {
+        b->classes.push_back(C);
+        return cleanup(PM_ERR_CUFFT, "batched transforms of a class could not be planned");
+      }
+    }
+    b->classes.push_back(C);
   }
   *out = b;
   return PM_OK;
@@ -1548,9 +1795,16 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
 
 pm_status pm_batch_destroy(pm_batch* b) {
   if (!b) return PM_ERR_INVALID_ARG;
-  for (pm_sim* s : b->sims) pm_destroy(s);
+  for (pm_sim* s : b->sims)
+    if (s) pm_destroy(s);
   for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  for (auto& C : b->classes) {
+    if (C.fwd) cufftDestroy(C.fwd);
+    if (C.inv) cufftDestroy(C.inv);
+    if (C.stream) cudaStreamDestroy(C.stream);
+    if (C.join) cudaEventDestroy(C.join);
+  }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->done) cudaEventDestroy(b->done);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -1581,22 +1835,21 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     cudaError_t e_ = (expr);                                                                       \
     if (e_ != cudaSuccess) return bfail(b, PM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
-  // per-member weights of every step, and the closing half kicks
-  std::vector<KickParams> tab(size_t(n) * nsteps);
+  // per-member weights of every step (into each member's own table), and the closing half kicks
+  std::vector<KickParams> tab(nsteps);
   std::vector<Weights> closing(n);
-  for (int i = 0; i < n; ++i) {
-    Weights pending = {0.0, 0.0};
-    for (int k = 0; k < nsteps; ++k)
-      tab[size_t(i) * nsteps + k] = step_params(b->sims[i], k, nsteps, a_start[i], a_end[i], &pending);
-    closing[i] = pending;
-  }
-  // the batch's own stream follows the caller's stream (the legacy default stream cannot be captured)
   BCU(cudaEventRecord(b->done, b->stream));
   BCU(cudaStreamWaitEvent(b->cap, b->done, 0));
-  KickParams* tab_dev = reinterpret_cast<KickParams*>(b->arena + b->table_off);
-  uint32_t* steps_dev = reinterpret_cast<uint32_t*>(b->arena + b->step_off);
-  BCU(cudaMemcpyAsync(tab_dev, tab.data(), tab.size() * sizeof(KickParams), cudaMemcpyHostToDevice, b->cap));
-  BCU(cudaMemsetAsync(steps_dev, 0, size_t(n) * sizeof(uint32_t), b->cap));
+  for (int i = 0; i < n; ++i) {
+    pm_sim* s = b->sims[i];
+    Weights pending = {0.0, 0.0};
+    for (int k = 0; k < nsteps; ++k) tab[k] = step_params(s, k, nsteps, a_start[i], a_end[i], &pending);
+    closing[i] = pending;
+    // a pageable copy returns once the table is staged, so `tab` can be refilled
+    BCU(cudaMemcpyAsync(s->at<KickParams>(s->L.ktab), tab.data(), size_t(nsteps) * sizeof(KickParams),
+                        cudaMemcpyHostToDevice, b->cap));
+    BCU(cudaMemsetAsync(s->errword() + 2, 0, sizeof(uint32_t), b->cap));
+  }
   BCU(cudaEventRecord(b->fork, b->cap));
   // forces at the start of every member (outside the graph), on the member streams
   for (int i = 0; i < n; ++i) {
@@ -1604,6 +1857,13 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     if (ensure_fields(b->sims[i]) != PM_OK) return member_error(i);
     BCU(cudaEventRecord(b->join[i], b->streams[i]));
     BCU(cudaStreamWaitEvent(b->cap, b->join[i], 0));
+  }
+  // which classes step packed this time (a common state is needed)
+  std::vector<bool> packed(b->classes.size());
+  b->last_packed = 0;
+  for (size_t k = 0; k < b->classes.size(); ++k) {
+    packed[k] = b->classes[k].packed && same_state(b->classes[k], b->sims);
+    if (packed[k] && nsteps >= 2) b->last_packed += int(b->classes[k].members.size());
   }
   const int pairs = nsteps / 2;
   if (pairs > 0) {
@@ -1613,13 +1873,27 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     pm_status st = PM_OK;
     if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) st = PM_ERR_CUDA;
-    for (int i = 0; i < n && st == PM_OK; ++i) {
-      pm_sim* s = b->sims[i];
-      if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) st = PM_ERR_CUDA;
-      for (int r = 0; r < 2 && st == PM_OK; ++r) st = table_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i);
-      if (st == PM_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) st = PM_ERR_CUDA;
-      if (st == PM_OK && cudaStreamWaitEvent(b->cap, b->join[i], 0) != cudaSuccess) st = PM_ERR_CUDA;
-      if (st != PM_OK) b->err = "capture of member " + std::to_string(i) + " failed: " + s->err;
+    for (size_t k = 0; k < b->classes.size() && st == PM_OK; ++k) {
+      pm_batch::Class& C = b->classes[k];
+      if (packed[k]) {
+        if (cudaStreamWaitEvent(C.stream, b->fork, 0) != cudaSuccess) st = PM_ERR_CUDA;
+        for (int r = 0; r < 2 && st == PM_OK; ++r) st = packed_step(C, b->sims, C.stream);
+        if (st == PM_OK && cudaEventRecord(C.join, C.stream) != cudaSuccess) st = PM_ERR_CUDA;
+        if (st == PM_OK && cudaStreamWaitEvent(b->cap, C.join, 0) != cudaSuccess) st = PM_ERR_CUDA;
+        if (st != PM_OK) b->err = "capture of a packed class failed: " + b->sims[C.members[0]]->err;
+        continue;
+      }
+      for (int i : C.members) {
+        pm_sim* s = b->sims[i];
+        if (st == PM_OK && cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) st = PM_ERR_CUDA;
+        for (int r = 0; r < 2 && st == PM_OK; ++r) st = table_step(s, s->at<KickParams>(s->L.ktab), s->errword() + 2);
+        if (st == PM_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) st = PM_ERR_CUDA;
+        if (st == PM_OK && cudaStreamWaitEvent(b->cap, b->join[i], 0) != cudaSuccess) st = PM_ERR_CUDA;
+        if (st != PM_OK) {
+          b->err = "capture of member " + std::to_string(i) + " failed: " + s->err;
+          break;
+        }
+      }
     }
     cudaError_t ec = cudaStreamEndCapture(b->cap, &graph);
     if (st != PM_OK) {
@@ -1644,7 +1918,7 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
     pm_sim* s = b->sims[i];
     BCU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
     if (nsteps & 1) {
-      if (table_step(s, tab_dev + size_t(i) * nsteps, steps_dev + i) != PM_OK) return member_error(i);
+      if (table_step(s, s->at<KickParams>(s->L.ktab), s->errword() + 2) != PM_OK) return member_error(i);
     }
     if (pass(s, closing[i], Weights{0.0, 0.0}, 0.0, true) != PM_OK) return member_error(i);
     BCU(cudaEventRecord(b->join[i], b->streams[i]));
@@ -1654,6 +1928,13 @@ pm_status pm_batch_run(pm_batch* b, int32_t nsteps, const double* a_start, const
   BCU(cudaEventRecord(b->done, b->cap));
   BCU(cudaStreamWaitEvent(b->stream, b->done, 0));
 #undef BCU
+  return PM_OK;
+}
+
+pm_status pm_batch_info(const pm_batch* b, int32_t* classes, int32_t* packed_members) {
+  if (!b || !classes || !packed_members) return PM_ERR_INVALID_ARG;
+  *classes = int32_t(b->classes.size());
+  *packed_members = b->last_packed;
   return PM_OK;
 }
 

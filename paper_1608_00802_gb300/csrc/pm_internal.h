@@ -66,6 +66,16 @@ struct Tuning {
 };
 constexpr int KICK_MIN_THREADS = 128;
 
+// Packed groups of simulations: member m of a group of equal configurations
+// has every buffer at the same offset of its own arena, the arenas `ms` bytes
+// apart, so a pointer of member 0 becomes member m's by moff(p, m * ms).
+// Kernels that step a whole group take the member from a grid dimension
+// (ms = 0 and one member for a single simulation).
+template <typename T>
+__host__ __device__ __forceinline__ T* moff(T* p, size_t off) {
+  return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + off) : p;
+}
+
 // error bits of the device error word
 enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
@@ -75,12 +85,9 @@ constexpr int RS_ITEMS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_TILE_SHIFT = 11;
 static_assert(RS_TILE == (1 << RS_TILE_SHIFT), "RS_TILE is 2^RS_TILE_SHIFT");
-// the drift counts its movers per tile and per group of 2^RS_GROUP_SHIFT tiles
-constexpr int RS_GROUP_SHIFT = 6;
-inline int64_t mover_count_words(int64_t n) {
-  const int64_t tiles = (n + RS_TILE - 1) >> RS_TILE_SHIFT;
-  return tiles + ((tiles + (1 << RS_GROUP_SHIFT) - 1) >> RS_GROUP_SHIFT);
-}
+// the drift counts its movers per tile (one word per tile), and the re-sort
+// scans those counts into the movers before each tile (one more word per tile)
+inline int64_t mover_count_words(int64_t n) { return (n + RS_TILE - 1) >> RS_TILE_SHIFT; }
 constexpr int RS_MAX_BITS = 10;
 // set in a sort key by the drift when the particle's cell changed (keys use at most 30 bits)
 constexpr uint32_t KEY_MOVER = 0x80000000u;
@@ -108,31 +115,36 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
                              int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
                              const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
                              const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
-                             cudaStream_t s, const uint32_t* n_dev = nullptr);
+                             cudaStream_t s, const uint32_t* n_dev = nullptr, int nm = 1, size_t ms = 0,
+                             int spin_limit = 0);  // polls of a look-back wait before it gives up (0: default)
 // incremental re-sort after a drift (keys carry KEY_MOVER; tcount holds the
 // drift's mover counts per tile and per group of tiles): stable partition
-// into stayers (s_keys, s_vals) and movers (m_keys, m_vals) in one pass with
-// the movers' digit histograms (counts[0] = stayers, counts[1] = movers),
-// then the merge of stayers with the sorted movers by (key, previous slot),
-// which writes the sorted keys, the slot of every sorted index (src) and the
-// row starts; the records stay where the drift wrote them
-cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, const uint32_t* tcount, uint32_t* s_keys,
-                                   uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals, uint32_t* counts,
-                                   uint32_t* hist, int passes, int digit_bits, int key_bits, uint32_t* sort_epoch,
-                                   unsigned long long* stats, cudaStream_t s);
-cudaError_t launch_merge(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
-                         const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,
-                         uint32_t* src_out, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);
-cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s);
-// row starts of sorted keys; src (nullable) receives the identity order
-cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, uint32_t* src,
-                             cudaStream_t s);
-// src (nullable): slot of each sorted index (null: records in sorted order)
+// into stayers (sk, sv) and movers (mk, mv) with per-row counts (rcnt: 3 N^2
+// words, cleared before: stayers, movers, bucket fill), a scan of the row
+// counts (btot: 2 ceil(N^2 / 4096) words; srow, mrow, row_start: N^2 + 1
+// words), the movers in per-row buckets (bk, bv) and the placement of every
+// particle: sorted keys to keys_out, records from (pos_in, mom_in) to
+// (pos_out, mom_out) in sorted order.  stats (nullable): re-sorts and movers.
+// part 0: the partition; 1: the rows (scan, buckets, movers' placement); 2:
+// the stayers' placement (launched in this order).
 template <typename R>
-cudaError_t launch_deposit(const void* pos, const uint32_t* src, const uint32_t* row_start, int64_t n, Mesh m,
-                           double norm, R* rho, cudaStream_t s, int warps = 8);
+cudaError_t launch_resort(int part, const uint32_t* keys, int64_t n, const uint32_t* tcount, uint32_t* sk, uint32_t* sv,
+                          uint32_t* mk, uint32_t* mv, uint32_t* bk, uint32_t* bv, uint32_t* counts, uint32_t* rcnt,
+                          uint32_t* btot, uint32_t* srow, uint32_t* mrow, uint32_t* row_start, Mesh m,
+                          unsigned long long* stats, uint32_t* keys_out, const void* pos_in, const void* mom_in,
+                          void* pos_out, void* mom_out, int sms, cudaStream_t s, int nm = 1, size_t ms = 0);
+inline size_t row_scan_tiles(int n_mesh) { return (size_t(n_mesh) * n_mesh + 4095) / 4096; }
+cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s, int nm = 1, size_t ms = 0);
+// row starts of sorted keys
+cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);
+// (nm, ms: a packed group of nm members, ms bytes apart; coefp/qcp: member
+// 0's coefficient in device memory, read per member)
 template <typename R>
-cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s);
+cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
+                           cudaStream_t s, int warps = 8, int nm = 1, size_t ms = 0);
+template <typename R>
+cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s,
+                         const double* coefp = nullptr, int nm = 1, size_t ms = 0);
 // cubic spline kernel: node weights, their normalised real symbol, the Green
 // multiplication with the symbol (spec2 null: spec already holds rho_W^) and
 // the smoothing of a transformed field
@@ -142,12 +154,17 @@ template <typename R>
 cudaError_t launch_spline_symbol(const void* spec, void* what, Mesh m, cudaStream_t s);
 template <typename R>
 cudaError_t launch_green_spline(void* spec, void* spec2, const void* what, Mesh m, double coef, double* part,
-                                cudaStream_t s);
+                                cudaStream_t s, int smooth_in);
+// the spline smoothing in real space for supports within three cells (fp32):
+// g[s*4 + i] = normalised node weight at squared distance i^2 + s (s <= 18)
+template <typename R>
+cudaError_t launch_smooth_direct(const R* in, R* out, Mesh m, const double* g, cudaStream_t s);
 template <typename R>
 cudaError_t launch_smooth_spec(void* spec, const void* what, Mesh m, cudaStream_t s);
 template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
-                           uint32_t* list_count, uint32_t* err, cudaStream_t s);
+                           uint32_t* list_count, uint32_t* err, cudaStream_t s, const double* qcp = nullptr,
+                           int nm = 1, size_t ms = 0);
 // fp32 stencil tiling (defined with the kernels): list length of the
 // register-column kernel, blocks (= K_rho partials) of a shape and the most
 // over every valid shape, shape validity and the default shape
@@ -159,14 +176,13 @@ Tuning default_tuning(int n);
 // sizes the fp32 streaming kick's grid for this device (an occupancy query;
 // call outside any stream capture, before the first kick)
 void kick_stream_prepare();
-// reads the records of sorted index i at slot src[i] (src nullable) of (pos,
-// mom); with a drift writes them to (pos_out, mom_out)[i], the keys and the
-// mover counts tcount (cleared before), otherwise updates them in place
+// updates the records in place; with a drift also the keys and the mover
+// counts tcount (cleared before)
 template <typename R>
-cudaError_t launch_kick(void* pos, void* mom, const uint32_t* src, void* pos_out, void* mom_out, uint32_t* keys,
-                        uint32_t* tcount, int64_t n, const R* phi, const R* q, Mesh m, KickParams kp,
+cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, uint32_t* tcount, int64_t n, const R* phi, const R* q,
+                        Mesh m, KickParams kp,
                         const KickParams* kp_tab, const uint32_t* step, double* part, double* acc, uint32_t* err,
-                        int threads, cudaStream_t s);
+                        int threads, cudaStream_t s, int nm = 1, size_t ms = 0);
 template <typename R>
 cudaError_t launch_power(const void* spec, Mesh m, int nbins, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* out, cudaStream_t s);
@@ -176,8 +192,8 @@ template <typename R>
 cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Mesh m, double dx, double* x,
                                  double* p, cudaStream_t s);
 template <typename R>
-cudaError_t launch_get_order(const void* pos, const void* mom, const uint32_t* src, int64_t n, uint32_t* cell,
-                             uint32_t* id, cudaStream_t s);
+cudaError_t launch_get_order(const void* pos, const void* mom, int64_t n, uint32_t* cell, uint32_t* id,
+                             cudaStream_t s);
 template <typename R>
 cudaError_t launch_to_double(const R* f, int64_t n, double* out, cudaStream_t s);
 template <typename R>

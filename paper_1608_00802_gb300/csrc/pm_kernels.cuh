@@ -45,13 +45,6 @@ __device__ __forceinline__ D4 make_mom(double px, double py, double pz, uint32_t
   r.w = __longlong_as_double((long long)id);
   return r;
 }
-// Records of the particle at sorted index i: slot src[i] of the record
-// buffers (src null: slot i).  The incremental re-sort leaves the records
-// where the last drift wrote them and gives their sorted order as src.
-__device__ __forceinline__ int64_t rec_slot(const uint32_t* __restrict__ src, int64_t i) {
-  return src ? int64_t(__ldg(src + i)) : i;
-}
-
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) {
   return __ldg(p);
@@ -321,10 +314,13 @@ __device__ __forceinline__ void seg_add2(R lo, R hi, int t, bool valid, R* acc) 
 
 template <typename R>
 __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
-                                                            const uint32_t* __restrict__ src,
                                                             const uint32_t* __restrict__ row_start, uint32_t np,
-                                                            Mesh m, R norm, R* __restrict__ rho) {
+                                                            Mesh m, R norm, R* __restrict__ rho, size_t ms) {
   using V4 = typename VT<R>::v4;
+  if (ms) {  // member blockIdx.y of a packed group
+    const size_t o = size_t(blockIdx.y) * ms;
+    pos = moff(pos, o), row_start = moff(row_start, o), rho = moff(rho, o);
+  }
   extern __shared__ __align__(16) unsigned char dep_smem[];
   const int n = m.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -348,7 +344,7 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
         R lo = R(0), hi = R(0);
         int c = n + 1 + lane;  // invalid lanes: unique targets past the row
         if (valid) {
-          const V4 r = ldg(pos + rec_slot(src, j));
+          const V4 r = ldg(pos + j);
           const uint32_t cx = rec_cell(r) - base_cell;
           // a record outside this row (only after a sort whose look-back timed
           // out, which the error word reports) is skipped, not written out of bounds
@@ -432,9 +428,16 @@ __device__ __forceinline__ void green_one(typename VT<R>::cplx& v, uint32_t e, u
   v.y = im * g;
 }
 
+// coefp (nullable): the coefficient in device memory (member 0's, ms bytes
+// apart), used instead of coef by the packed groups, whose members differ in box
 template <typename R>
 __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef, DivU32 dv,
-                                                        double* part) {
+                                                        double* part, const double* coefp, size_t ms) {
+  if (coefp) {  // member blockIdx.y of a packed group
+    const size_t o = size_t(blockIdx.y) * ms;
+    spec = moff(spec, o), part = moff(part, o);
+    coef = R(*moff(coefp, o));
+  }
   extern __shared__ __align__(16) unsigned char green_smem[];
   R* s2 = reinterpret_cast<R*>(green_smem);  // sin^2(pi j / N), j = 0..N-1
   const uint32_t n = uint32_t(m.n), nh = n / 2 + 1;
@@ -491,14 +494,14 @@ __global__ void __launch_bounds__(MESH_THREADS) k_spline_symbol(const typename V
 }
 
 // The Green multiplication with the spline: spec holds rho^ (cloud-in-cell,
-// with spec2 given) or rho_W^ (spec2 null).  rho_W^ = W^ rho^ goes to spec2
-// (normalised for the inverse transform), the force potential
+// smooth_in = 1) or rho_W^ (smooth_in = 0).  rho_W^ = W^ rho^ goes to spec2
+// if given (normalised for the inverse transform), the force potential
 // phi_S^ = W^ G rho_W^ replaces spec, and the W_g partial sums G |rho_W^|^2.
 template <typename R>
 __global__ void __launch_bounds__(MESH_THREADS) k_green_spline(typename VT<R>::cplx* spec,
                                                                typename VT<R>::cplx* spec2,
                                                                const R* __restrict__ what, Mesh m, R coef, R inv_n3,
-                                                               DivU32 dv, double* part) {
+                                                               DivU32 dv, double* part, int smooth_in) {
   extern __shared__ __align__(16) unsigned char gs_smem[];
   R* s2 = reinterpret_cast<R*>(gs_smem);
   const uint32_t n = uint32_t(m.n), nh = n / 2 + 1;
@@ -522,9 +525,11 @@ __global__ void __launch_bounds__(MESH_THREADS) k_green_spline(typename VT<R>::c
     const R g = (row == 0 && jx == 0) ? R(0) : coef / sk;
     const R wk = what[e];
     auto v = spec[e];
-    if (spec2) {
+    if (smooth_in) {
       v.x *= wk;
       v.y *= wk;
+    }
+    if (spec2) {
       auto u = v;
       u.x *= inv_n3;
       u.y *= inv_n3;
@@ -551,6 +556,81 @@ __global__ void __launch_bounds__(MESH_THREADS) k_smooth_spec(typename VT<R>::cp
     v.x *= f;
     v.y *= f;
     spec[e] = v;
+  }
+}
+
+// The same smoothing in real space, for spline kernels whose support ends
+// within three cells (h <= 4 mesh cells; the paper's runs use 3.5 and 4):
+// out_n = sum_o w_o in_{n+o} over the periodic mesh with the node weights w
+// (normalised to unit sum), which is the operator whose symbol the spectral
+// smoothing multiplies by.  Summed in real space every output is a positive
+// combination of nearby values, so it keeps their relative precision (the
+// transforms' rounding is relative to the whole field's norm instead, which a
+// near-empty region cannot afford).  The weight of offset (i, j, k) depends on
+// s = j^2 + k^2 and i^2 only, so with g[s][i] = w(i^2 + s) the sum is
+//   out(x) = T_0(x) + sum_{i=1..3} (T_i(x - i) + T_i(x + i)),
+//   T_i(x) = sum_s g[s][i] R_s(x),  R_s(x) = sum_{j^2 + k^2 = s} in(x, y+j, z+k):
+// one block per y row (all x) and a run of z planes; each thread keeps the
+// 7 x 7 (j, k) window of its column in registers while it steps along z and
+// loads one value per j for the next plane; the T_i of the row are exchanged
+// through shared memory (periodic in x).
+constexpr int SP_S = 19;  // s = j^2 + k^2 <= 18
+template <typename R>
+struct SplineTaps {
+  R g[SP_S][4];  // g[s][i] = w(i^2 + s), 0 beyond the support
+};
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_smooth_direct(const R* __restrict__ in, R* __restrict__ out, Mesh m,
+                                                        SplineTaps<R> tp, int zc) {
+  extern __shared__ __align__(16) unsigned char sd_smem[];
+  R* T = reinterpret_cast<R*>(sd_smem);  // T_1, T_2, T_3 of the row
+  const int n = m.n, x = threadIdx.x, y = blockIdx.x;
+  const int z0 = blockIdx.y * zc, z1 = min(z0 + zc, n);
+  uint32_t row[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) row[j] = uint32_t(wrap(y + j - 3, n)) * uint32_t(n) + uint32_t(x);
+  R w[7][7];  // w[j][k] = in(x, y + j - 3, z + k - 3) for the plane z being computed
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const R* pl = in + size_t(wrap(z0 - 3 + k, n)) * m.n2;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) w[j][k] = __ldg(pl + row[j]);
+  }
+  const int xm1 = wrap(x - 1, n), xp1 = wrap(x + 1, n), xm2 = wrap(x - 2, n), xp2 = wrap(x + 2, n);
+  const int xm3 = wrap(x - 3, n), xp3 = wrap(x + 3, n);
+  for (int z = z0; z < z1; ++z) {
+    const R* pl = in + size_t(wrap(z + 3, n)) * m.n2;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) w[j][6] = __ldg(pl + row[j]);
+    R rs[SP_S];
+#pragma unroll
+    for (int q = 0; q < SP_S; ++q) rs[q] = R(0);
+#pragma unroll
+    for (int j = 0; j < 7; ++j)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) rs[(j - 3) * (j - 3) + (k - 3) * (k - 3)] += w[j][k];
+    R t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      R a = R(0);
+#pragma unroll
+      for (int q = 0; q < SP_S; ++q)
+        if (q == 0 || q == 1 || q == 2 || q == 4 || q == 5 || q == 8 || q == 9 || q == 10 || q == 13 || q == 18)
+          a += tp.g[q][i] * rs[q];
+      t[i] = a;
+    }
+    T[x] = t[1];
+    T[n + x] = t[2];
+    T[2 * n + x] = t[3];
+    __syncthreads();
+    const R o = t[0] + (T[xm1] + T[xp1]) + (T[n + xm2] + T[n + xp2]) + (T[2 * n + xm3] + T[2 * n + xp3]);
+    out[size_t(z) * m.n2 + row[3]] = o;
+    __syncthreads();  // T is rewritten for the next plane
+#pragma unroll
+    for (int j = 0; j < 7; ++j)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) w[j][k] = w[j][k + 1];
   }
 }
 
@@ -982,7 +1062,13 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_bulk(const float*
 static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float* __restrict__ rho, Mesh m, float fl,
                                                                     float qc, float slim, int ty, int tz,
                                                                     float* __restrict__ q, uint32_t* list,
-                                                                    double* part, uint32_t* err, int diag) {
+                                                                    double* part, uint32_t* err, int diag,
+                                                                    const double* qcp, size_t ms) {
+  if (qcp) {  // member blockIdx.z of a packed group (coefficient from device memory, as in k_green)
+    const size_t o = size_t(blockIdx.z) * ms;
+    rho = moff(rho, o), q = moff(q, o), list = moff(list, o), part = moff(part, o), err = moff(err, o);
+    qc = float(*moff(qcp, o));
+  }
   extern __shared__ __align__(16) unsigned char st_smem[];
   __shared__ uint32_t s_cnt;
   __shared__ int s_ok;
@@ -1208,23 +1294,36 @@ __device__ __forceinline__ void block_max_store(const float (&v)[NV], double* pa
 #define PM_KICK_MINB 4
 #endif
 
+// The leapfrog weights of a pass in the working precision (converted once
+// per thread, so that the loop keeps no doubles live) and its switches.
+template <typename R>
+struct KickR {
+  R cg1, cq1, cg2, cq2, drift, inv_dx;
+  bool grav_kernel, q_kernel, quantum, has_drift;
+};
+template <typename R>
+__device__ __forceinline__ KickR<R> kick_r(const KickParams& kp) {
+  KickR<R> k;
+  k.cg1 = R(kp.cg1), k.cq1 = R(kp.cq1), k.cg2 = R(kp.cg2), k.cq2 = R(kp.cq2), k.drift = R(kp.drift);
+  k.inv_dx = R(kp.inv_dx);
+  k.grav_kernel = kp.grav_kernel != 0, k.q_kernel = kp.q_kernel != 0, k.quantum = kp.quantum != 0;
+  k.has_drift = kp.drift != 0.0;
+  return k;
+}
+
 // One particle of a kick pass: gradients at the particle, kick, drift, new
 // key.  MODE 0: kick (+ drift); 1: kick with the diagnostic sums of p_sync
 // (dg); 2: write the accelerations only; 3: leave the state and write
 // |p_sync|^2, |grad phi|^2 and |grad Q|^2 to dg (the adaptive step's bound).
-// The particle has sorted index i and its records (ps, mo) came from `slot`.
-// With a drift the new records go to (pos_out, mom_out)[i], in sorted order
-// (the other buffer), the new key to keys[i], and a particle that changed
-// cell adds one to the mover count of its tile of RS_TILE sorted indices and
-// of its group of RS_TILE_GROUP tiles (tcount: tiles, then groups).  Without
-// a drift the records are updated in place at `slot`.
+// The records are updated in place; with a drift the new key goes to
+// keys[i] and a particle that changed cell counts in the mover count of its
+// tile of RS_TILE slots (tcount).
 template <typename R, int MODE>
-__device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename VT<R>::v4 ps, typename VT<R>::v4 mo,
+__device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, typename VT<R>::v4 mo,
                                               typename VT<R>::v4* pos, typename VT<R>::v4* mom,
-                                              typename VT<R>::v4* pos_out, typename VT<R>::v4* mom_out,
-                                              uint32_t* keys, uint32_t* tcount, uint32_t ntiles,
+                                              uint32_t* keys, uint32_t* tcount,
                                               const R* __restrict__ phi, const R* __restrict__ qf, const Mesh& m,
-                                              const KickParams& kp, double* acc_out, uint32_t* err, R (&dg)[4]) {
+                                              const KickR<R>& kp, double* acc_out, uint32_t* err, R (&dg)[4]) {
   const uint32_t cell = rec_cell(ps);
   int cx, cy, cz;
   split_cell(cell, m, cx, cy, cz);
@@ -1237,7 +1336,7 @@ __device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename 
     s.zi[k] = uint32_t(wrap(cz + k - 1, nn)) * m.n2;
   }
   const R wx[2] = {R(1) - ps.y, ps.y}, wy[2] = {R(1) - ps.z, ps.z}, wz[2] = {R(1) - ps.w, ps.w};
-  const R inv_dx = R(kp.inv_dx);
+  const R inv_dx = kp.inv_dx;
   R gp[3], gq[3] = {R(0), R(0), R(0)};
   if (kp.grav_kernel)
     grad_kernel(phi, s, wx, wy, wz, inv_dx, gp);
@@ -1249,7 +1348,7 @@ __device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename 
     else
       grad_central(qf, s, wx, wy, wz, inv_dx, gq);
   }
-  const R cg1 = R(kp.cg1), cq1 = R(kp.cq1);
+  const R cg1 = kp.cg1, cq1 = kp.cq1;
   R d1[3] = {cg1 * gp[0] + cq1 * gq[0], cg1 * gp[1] + cq1 * gq[1], cg1 * gp[2] + cq1 * gq[2]};
   if (MODE == 3) {
     const R px = mo.x - d1[0], py = mo.y - d1[1], pz = mo.z - d1[2];
@@ -1269,14 +1368,14 @@ __device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename 
       dg[2] = py;
       dg[3] = pz;
     }
-    const R cg2 = R(kp.cg2), cq2 = R(kp.cq2);
+    const R cg2 = kp.cg2, cq2 = kp.cq2;
     px -= cg2 * gp[0] + cq2 * gq[0];
     py -= cg2 * gp[1] + cq2 * gq[1];
     pz -= cg2 * gp[2] + cq2 * gq[2];
     uint32_t ncell = cell;
     R fx = ps.y, fy = ps.z, fz = ps.w;
-    if (kp.drift != 0.0) {
-      const R dr = R(kp.drift);
+    if (kp.has_drift) {
+      const R dr = kp.drift;
       fx += px * dr;
       fy += py * dr;
       fz += pz * dr;
@@ -1297,19 +1396,22 @@ __device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename 
     } else if (!finite3(px, py, pz)) {
       atomicOr(err, ERR_NONFINITE);
     }
+    pos[i] = make_pos(ncell, fx, fy, fz);
+    mom[i] = make_mom(px, py, pz, rec_id(mo));
     // the drift marks the particles that changed cell for the incremental re-sort;
     // without a drift the keys (marked or not) stay as they are
-    if (kp.drift != 0.0) {
-      pos_out[i] = make_pos(ncell, fx, fy, fz);
-      mom_out[i] = make_mom(px, py, pz, rec_id(mo));
-      keys[i] = ncell | (ncell != cell ? KEY_MOVER : 0u);
-      if (ncell != cell) {
-        atomicAdd(tcount + (i >> RS_TILE_SHIFT), 1u);
-        atomicAdd(tcount + ntiles + (i >> (RS_TILE_SHIFT + RS_GROUP_SHIFT)), 1u);
+    if (kp.has_drift) {
+      const bool moved = ncell != cell;
+      keys[i] = ncell | (moved ? KEY_MOVER : 0u);
+      // one atomic per tile among the active lanes of the warp that moved
+      const uint32_t act = __activemask();
+      if (__ballot_sync(act, moved)) {
+        const uint32_t peers = __match_any_sync(act, uint32_t(i >> RS_TILE_SHIFT));
+        const uint32_t movers = __ballot_sync(act, moved) & peers;
+        uint32_t lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        if (movers && (peers & lt) == 0) atomicAdd(tcount + (i >> RS_TILE_SHIFT), uint32_t(__popc(movers)));
       }
-    } else {
-      pos[slot] = make_pos(ncell, fx, fy, fz);
-      mom[slot] = make_mom(px, py, pz, rec_id(mo));
     }
   }
 }
@@ -1318,23 +1420,17 @@ __device__ __forceinline__ void kick_particle(int64_t i, int64_t slot, typename 
 // common pass lean); MODE 1 and 3 write one partial per block.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT<R>::v4* pos, typename VT<R>::v4* mom,
-                                                       const uint32_t* __restrict__ src, typename VT<R>::v4* pos_out,
-                                                       typename VT<R>::v4* mom_out, uint32_t* keys, uint32_t* tcount,
+                                                       uint32_t* keys, uint32_t* tcount,
                                                        int64_t n, const R* __restrict__ phi,
                                                        const R* __restrict__ qf, Mesh m, KickParams kp_arg,
                                                        const KickParams* __restrict__ kp_tab,
                                                        const uint32_t* __restrict__ step, double* part,
                                                        double* acc_out, uint32_t* err) {
   // weights by value, or (graph replay) from a per-step table indexed by a device step counter
-  const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
+  const KickR<R> kp = kick_r<R>(kp_tab ? kp_tab[*step] : kp_arg);
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const uint32_t ntiles = uint32_t((n + RS_TILE - 1) >> RS_TILE_SHIFT);
   R dg[4] = {R(0), R(0), R(0), R(0)};
-  if (i < n) {
-    const int64_t slot = rec_slot(src, i);
-    kick_particle<R, MODE>(i, slot, pos[slot], mom[slot], pos, mom, pos_out, mom_out, keys, tcount, ntiles, phi,
-                           qf, m, kp, acc_out, err, dg);
-  }
+  if (i < n) kick_particle<R, MODE>(i, pos[i], mom[i], pos, mom, keys, tcount, phi, qf, m, kp, acc_out, err, dg);
   if (MODE == 1) block_sum_store<4>(dg, part, gridDim.x);
   if (MODE == 3) {
     const float mx[3] = {float(dg[0]), float(dg[1]), float(dg[2])};
@@ -1352,33 +1448,32 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT
 #endif
 template <typename R>
 __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_STREAM_MINB) k_kick_stream(
-    typename VT<R>::v4* pos, typename VT<R>::v4* mom, const uint32_t* __restrict__ src, typename VT<R>::v4* pos_out,
-    typename VT<R>::v4* mom_out, uint32_t* keys, uint32_t* tcount, int64_t n, const R* __restrict__ phi,
+    typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys, uint32_t* tcount, int64_t n, const R* __restrict__ phi,
     const R* __restrict__ qf, Mesh m, KickParams kp_arg, const KickParams* __restrict__ kp_tab,
-    const uint32_t* __restrict__ step, uint32_t* err) {
+    const uint32_t* __restrict__ step, uint32_t* err, size_t ms) {
   using V4 = typename VT<R>::v4;
-  const KickParams kp = kp_tab ? kp_tab[*step] : kp_arg;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  const uint32_t ntiles = uint32_t((n + RS_TILE - 1) >> RS_TILE_SHIFT);
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t slot = rec_slot(src, i);
-  V4 ps = pos[slot], mo = mom[slot];
+  if (ms) {  // member blockIdx.y of a packed group
+    const size_t o = size_t(blockIdx.y) * ms;
+    pos = moff(pos, o), mom = moff(mom, o), keys = moff(keys, o), tcount = moff(tcount, o), phi = moff(phi, o);
+    qf = moff(qf, o), kp_tab = moff(kp_tab, o), step = moff(step, o), err = moff(err, o);
+  }
+  const KickR<R> kp = kick_r<R>(kp_tab ? kp_tab[*step] : kp_arg);
+  // 32-bit indices (n < 2^31, so i + stride < 2^32) keep the loop's registers down
+  const uint32_t stride = gridDim.x * blockDim.x, nn = uint32_t(n);
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  V4 ps = pos[i], mo = mom[i];
   R dg[4];
   for (;;) {
-    const int64_t j = i + stride;
-    int64_t nslot = slot;
+    const uint32_t j = i + stride;
     V4 nps = ps, nmo = mo;
-    if (j < n) {
-      nslot = rec_slot(src, j);
-      nps = pos[nslot];
-      nmo = mom[nslot];
+    if (j < nn) {
+      nps = pos[j];
+      nmo = mom[j];
     }
-    kick_particle<R, 0>(i, slot, ps, mo, pos, mom, pos_out, mom_out, keys, tcount, ntiles, phi, qf, m, kp, nullptr,
-                        err, dg);
-    if (j >= n) break;
+    kick_particle<R, 0>(i, ps, mo, pos, mom, keys, tcount, phi, qf, m, kp, nullptr, err, dg);
+    if (j >= nn) break;
     i = j;
-    slot = nslot;
     ps = nps;
     mo = nmo;
   }
@@ -1447,12 +1542,11 @@ __global__ void k_get_particles(const typename VT<R>::v4* __restrict__ pos, cons
 
 template <typename R>
 __global__ void k_get_order(const typename VT<R>::v4* __restrict__ pos, const typename VT<R>::v4* __restrict__ mom,
-                            const uint32_t* __restrict__ src, int64_t n, uint32_t* cell, uint32_t* id) {
+                            int64_t n, uint32_t* cell, uint32_t* id) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t slot = rec_slot(src, i);
-  cell[i] = rec_cell(pos[slot]);
-  id[i] = rec_id(mom[slot]);
+  cell[i] = rec_cell(pos[i]);
+  id[i] = rec_id(mom[i]);
 }
 
 template <typename R>
@@ -1479,8 +1573,8 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
 }
 
 template <typename R>
-cudaError_t launch_deposit(const void* pos, const uint32_t* src, const uint32_t* row_start, int64_t n, Mesh m,
-                           double norm, R* rho, cudaStream_t s, int warps) {
+cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
+                           cudaStream_t s, int warps, int nm, size_t ms) {
   using V4 = typename VT<R>::v4;
   if (warps < 1 || warps > DEP_WARPS) warps = DEP_WARPS;
   const size_t smem = size_t(warps) * (m.n + 1) * sizeof(R);
@@ -1497,7 +1591,8 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* src, const uint32_t*
     }
   }
   const unsigned blocks = (m.n2 + warps - 1) / warps;
-  k_deposit<R><<<blocks, warps * 32, smem, s>>>((const V4*)pos, src, row_start, uint32_t(n), m, R(norm), rho);
+  k_deposit<R><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m,
+                                                                    R(norm), rho, nm > 1 ? ms : 0);
   return cudaGetLastError();
 }
 
@@ -1516,10 +1611,23 @@ cudaError_t launch_spline_symbol(const void* spec, void* what, Mesh m, cudaStrea
 
 template <typename R>
 cudaError_t launch_green_spline(void* spec, void* spec2, const void* what, Mesh m, double coef, double* part,
-                                cudaStream_t s) {
+                                cudaStream_t s, int smooth_in) {
   using C = typename VT<R>::cplx;
   k_green_spline<R><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>(
-      (C*)spec, (C*)spec2, (const R*)what, m, R(coef), R(1.0 / double(m.n3)), divu32_make(uint32_t(m.n / 2 + 1)), part);
+      (C*)spec, (C*)spec2, (const R*)what, m, R(coef), R(1.0 / double(m.n3)), divu32_make(uint32_t(m.n / 2 + 1)), part,
+      smooth_in);
+  return cudaGetLastError();
+}
+
+// the direct smoothing (support within three cells); zc planes per block
+template <typename R>
+cudaError_t launch_smooth_direct(const R* in, R* out, Mesh m, const double* g, cudaStream_t s) {
+  SplineTaps<R> tp;
+  for (int q = 0; q < SP_S; ++q)
+    for (int i = 0; i < 4; ++i) tp.g[q][i] = R(g[q * 4 + i]);
+  const int zc = m.n >= 64 ? 32 : m.n;
+  const dim3 grid(unsigned(m.n), unsigned((m.n + zc - 1) / zc));
+  k_smooth_direct<R><<<grid, unsigned(m.n), 3 * m.n * sizeof(R), s>>>(in, out, m, tp, zc);
   return cudaGetLastError();
 }
 
@@ -1532,10 +1640,11 @@ cudaError_t launch_smooth_spec(void* spec, const void* what, Mesh m, cudaStream_
 }
 
 template <typename R>
-cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s) {
+cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s, const double* coefp, int nm,
+                         size_t ms) {
   using C = typename VT<R>::cplx;
-  k_green<R><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>((C*)spec, m, R(coef),
-                                                                divu32_make(uint32_t(m.n / 2 + 1)), part);
+  k_green<R><<<dim3(MESH_GRID, unsigned(nm)), MESH_THREADS, m.n * sizeof(R), s>>>(
+      (C*)spec, m, R(coef), divu32_make(uint32_t(m.n / 2 + 1)), part, coefp, ms);
   return cudaGetLastError();
 }
 
@@ -1555,7 +1664,10 @@ inline int stencil_blocks(int n) {
 
 template <typename R>
 cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double* part, uint32_t* list,
-                           uint32_t* list_count, uint32_t* err, cudaStream_t s) {
+                           uint32_t* list_count, uint32_t* err, cudaStream_t s, const double* qcp, int nm,
+                           size_t ms) {
+  // a packed group steps its members in one launch of the one-shot tiles only
+  if (nm > 1 && !stencil_tile_path(m.n, sp, sizeof(R) == 4)) return cudaErrorInvalidValue;
   if (sizeof(R) == 4 && sp.step == 1) {
     // fp32 compact path: shared-memory tiles, ill-conditioned near-empty nodes redone in float-float
     const float slim = sp.rho_fp64 > 0 ? float(sqrt(sp.rho_fp64)) : 0.0f;
@@ -1569,10 +1681,10 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) done[dev] = true;
       }
-      const dim3 g(unsigned(m.n / sp.ty), unsigned((m.n + sp.zlen - 1) / sp.zlen));
+      const dim3 g(unsigned(m.n / sp.ty), unsigned((m.n + sp.zlen - 1) / sp.zlen), unsigned(nm));
       k_stencil_tile<<<g, SB_THREADS, stencil_tile_smem(m.n, sp.ty, sp.zlen), s>>>(
           (const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, sp.ty, sp.zlen, (float*)q, list, part,
-          err, sp.diag);
+          err, sp.diag, nm > 1 ? qcp : nullptr, ms);
       return cudaGetLastError();
     }
     if (sp.ty > 0 && stencil_bulk_shape_ok(m.n, sp.ty, sp.zlen, sp.stages)) {
@@ -1626,30 +1738,41 @@ inline unsigned kick_stream_blocks(int64_t n, int threads, int resident) {
 }
 
 template <typename R>
-cudaError_t launch_kick(void* pos, void* mom, const uint32_t* src, void* pos_out, void* mom_out, uint32_t* keys,
-                        uint32_t* tcount, int64_t n, const R* phi, const R* q, Mesh m, KickParams kp,
+cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, uint32_t* tcount, int64_t n, const R* phi, const R* q,
+                        Mesh m, KickParams kp,
                         const KickParams* kp_tab, const uint32_t* step, double* part, double* acc, uint32_t* err,
-                        int threads, cudaStream_t s) {
+                        int threads, cudaStream_t s, int nm, size_t ms) {
   if (n <= 0) return cudaSuccess;
+  if (nm > 1) {
+    // a packed group: the streaming pass of every member, resident blocks shared among them
+    if constexpr (sizeof(R) == 4) {
+      if (kp.maxima || kp.accel_out || kp.diag || !kp_tab) return cudaErrorInvalidValue;
+      using V4 = typename VT<R>::v4;
+      if (threads != 128 && threads != 256) threads = KICK_THREADS;
+      const int per = kick_stream_resident<R>(threads) / nm;
+      const unsigned g = kick_stream_blocks(n, threads, per > 1 ? per : 1);
+      k_kick_stream<R><<<dim3(g, unsigned(nm)), threads, 0, s>>>((V4*)pos, (V4*)mom, keys, tcount, n, phi, q, m,
+                                                                  kp, kp_tab, step, err, ms);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   using V4 = typename VT<R>::v4;
   if (threads != 128 && threads != 256) threads = KICK_THREADS;
   const unsigned g = kick_blocks(n, threads);
-  V4 *p = (V4*)pos, *mo = (V4*)mom, *po = (V4*)pos_out, *moo = (V4*)mom_out;
+  V4 *p = (V4*)pos, *mo = (V4*)mom;
   if (kp.maxima)
-    k_kick<R, 3><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
-                                        err);
+    k_kick<R, 3><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if (kp.accel_out)
-    k_kick<R, 2><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
-                                        err);
+    k_kick<R, 2><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if (kp.diag)
-    k_kick<R, 1><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
-                                        err);
+    k_kick<R, 1><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if constexpr (sizeof(R) == 4)  // the fp64 records would spill in the streaming loop
     k_kick_stream<R><<<kick_stream_blocks(n, threads, kick_stream_resident<R>(threads)), threads, 0, s>>>(
-        p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, err);
+        p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, err, 0);
   else
-    k_kick<R, 0><<<g, threads, 0, s>>>(p, mo, src, po, moo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc,
-                                        err);
+    k_kick<R, 0><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   return cudaGetLastError();
 }
 
@@ -1670,11 +1793,11 @@ cudaError_t launch_get_particles(const void* pos, const void* mom, int64_t n, Me
 }
 
 template <typename R>
-cudaError_t launch_get_order(const void* pos, const void* mom, const uint32_t* src, int64_t n, uint32_t* cell,
-                             uint32_t* id, cudaStream_t s) {
+cudaError_t launch_get_order(const void* pos, const void* mom, int64_t n, uint32_t* cell, uint32_t* id,
+                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   using V4 = typename VT<R>::v4;
-  k_get_order<R><<<unsigned((n + 255) / 256), 256, 0, s>>>((const V4*)pos, (const V4*)mom, src, n, cell, id);
+  k_get_order<R><<<unsigned((n + 255) / 256), 256, 0, s>>>((const V4*)pos, (const V4*)mom, n, cell, id);
   return cudaGetLastError();
 }
 

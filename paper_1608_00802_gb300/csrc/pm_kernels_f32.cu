@@ -5,10 +5,14 @@
 
 namespace pm {
 
-static __global__ void k_step_inc(uint32_t* step) { *step += 1u; }
+// the device step counters of nm members (ms bytes apart)
+static __global__ void k_step_inc(uint32_t* step, int nm, size_t ms) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < nm) *moff(step, size_t(m) * ms) += 1u;
+}
 
-cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s) {
-  k_step_inc<<<1, 1, 0, s>>>(step);
+cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s, int nm, size_t ms) {
+  k_step_inc<<<unsigned((nm + 255) / 256), 256, 0, s>>>(step, nm, ms);
   return cudaGetLastError();
 }
 
@@ -22,25 +26,8 @@ cudaError_t launch_sort_histogram(const uint32_t* keys, int64_t n, int passes, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_mover_partition(const uint32_t* keys, int64_t n, const uint32_t* tcount, uint32_t* s_keys,
-                                   uint32_t* s_vals, uint32_t* m_keys, uint32_t* m_vals, uint32_t* counts,
-                                   uint32_t* hist, int passes, int digit_bits, int key_bits, uint32_t* sort_epoch,
-                                   unsigned long long* stats, cudaStream_t s) {
-  const int ntiles = int((n + RS_TILE - 1) / RS_TILE);
-  k_mover_partition<<<unsigned(ntiles), RS_THREADS, 0, s>>>(keys, n, tcount, s_keys, s_vals, m_keys, m_vals, counts,
-                                                             hist, passes, digit_bits, key_bits, sort_epoch, stats);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_merge(const uint32_t* s_keys, const uint32_t* s_vals, const uint32_t* m_keys,
-                         const uint32_t* m_vals, const uint32_t* counts, int64_t n, uint32_t* keys_out,
-                         uint32_t* src_out, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s) {
-  return launch_merge_impl(s_keys, s_vals, m_keys, m_vals, counts, n, keys_out, src_out, n_mesh, row_start, s);
-}
-
-cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, uint32_t* src,
-                             cudaStream_t s) {
-  k_row_start<<<unsigned((n + 1 + 255) / 256), 256, 0, s>>>(keys, n, n_mesh, n_mesh * n_mesh, row_start, src);
+cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s) {
+  k_row_start<<<unsigned((n + 1 + 255) / 256), 256, 0, s>>>(keys, n, n_mesh, n_mesh * n_mesh, row_start);
   return cudaGetLastError();
 }
 
@@ -106,5 +93,6 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
 }
 
 PM_INSTANTIATE(float)
+template cudaError_t launch_smooth_direct<float>(const float*, float*, Mesh, const double*, cudaStream_t);
 
 }  // namespace pm

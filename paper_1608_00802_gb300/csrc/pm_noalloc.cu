@@ -163,8 +163,8 @@ pm_status pm_deposit_noalloc(const double* x_dev, int64_t n_part, int32_t n_mesh
     }
   }
   uint32_t* rows = reinterpret_cast<uint32_t*>(base + kRows);
-  NA_CU(launch_row_start(sorted_keys, n, uint32_t(n_mesh), rows, nullptr, s));
-  NA_CU(launch_deposit<float>(pos[1], nullptr, rows, n, m, double(m.n3) / double(n), rho_dev, s));
+  NA_CU(launch_row_start(sorted_keys, n, uint32_t(n_mesh), rows, s));
+  NA_CU(launch_deposit<float>(pos[1], rows, n, m, double(m.n3) / double(n), rho_dev, s));
   if (err_dev) {
     k_copy_error<<<1, 1, 0, s>>>(err, err_dev);
     NA_CU(cudaGetLastError());

@@ -36,6 +36,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 constexpr uint64_t RS_FLAG_AGG = 1ull << 32;
+constexpr int RS_PASS_BLOCKS = 1216;  // blocks of one radix pass (8 per SM on 152 SMs)
 constexpr uint64_t RS_FLAG_PREFIX = 2ull << 32;
 constexpr int RS_SPIN_LIMIT = 1 << 18;
 constexpr int RS_LOOKBACK = 8;  // predecessors read per look-back round
@@ -119,8 +120,14 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
     const uint32_t* __restrict__ epoch_base, int pass,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, const V4* __restrict__ pos_in,
     const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out, uint32_t* err,
-    const uint32_t* __restrict__ n_dev) {
+    const uint32_t* __restrict__ n_dev, size_t ms, int spin_limit) {
   extern __shared__ uint32_t smem[];
+  if (ms) {  // member blockIdx.y of a packed group (the passes over its movers)
+    const size_t o = size_t(blockIdx.y) * ms;
+    keys_in = moff(keys_in, o), vals_in = moff(vals_in, o), digit_total = moff(digit_total, o);
+    status = moff(status, o), tile_counter = moff(tile_counter, o), epoch_base = moff(epoch_base, o);
+    keys_out = moff(keys_out, o), vals_out = moff(vals_out, o), err = moff(err, o), n_dev = moff(n_dev, o);
+  }
   if (n_dev) n = *n_dev;  // element count known on the device only: surplus tiles exit below
   const int radix = 1 << bits;
   const uint32_t mask = uint32_t(radix - 1);
@@ -133,159 +140,164 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t epoch = *epoch_base + uint32_t(pass);
-  if (threadIdx.x == 0) scratch[63] = atomicAdd(tile_counter, 1u);
-  __syncthreads();
-  const uint32_t tile = scratch[63];
-  const int64_t tile_base = int64_t(tile) * RS_TILE;
-  if (tile_base >= n) return;  // whole block: tile ids past the data (grid sized for the largest count)
-  // (cleared counters are first read after the barriers of the digit scan below)
-  for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
-  const int64_t rem = n - tile_base;
-  const int tile_n = rem < RS_TILE ? int(rem) : RS_TILE;
-  const int per = (radix + RS_THREADS - 1) / RS_THREADS;  // <= 4
+  // persistent blocks: each claims tiles in order until none is left (predecessors
+  // of a claimed tile are always claimed already, so the look-back ends)
+  for (;;) {
+    if (threadIdx.x == 0) scratch[63] = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = scratch[63];
+    const int64_t tile_base = int64_t(tile) * RS_TILE;
+    if (tile_base >= n) break;  // whole block: no tile left (the grid is capped below the tile count)
+    // (cleared counters are first read after the barriers of the digit scan below)
+    for (int d = threadIdx.x; d < RS_WARPS * radix; d += RS_THREADS) warp_cnt[d] = 0;
+    const int64_t rem = n - tile_base;
+    const int tile_n = rem < RS_TILE ? int(rem) : RS_TILE;
+    const int per = (radix + RS_THREADS - 1) / RS_THREADS;  // <= 4
 
-  // exclusive scan of the pass histogram -> global start of each digit
-  {
-    uint32_t v[4], sum = 0;
+    // exclusive scan of the pass histogram -> global start of each digit
+    {
+      uint32_t v[4], sum = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int d = threadIdx.x * per + k;
-      v[k] = (k < per && d < radix) ? __ldg(digit_total + d) : 0u;
-      sum += v[k];
-    }
-    uint32_t total;
-    uint32_t off = block_excl_scan(sum, scratch, total);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int d = threadIdx.x * per + k;
-      if (k < per && d < radix) digit_base[d] = off;
-      off += v[k];
-    }
-  }
-
-  // stable rank: warp w owns items [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) in rounds of 32
-  uint32_t key[RS_ITEMS], rank[RS_ITEMS];
-  const uint32_t lt = lanemask_lt();
-  uint32_t* my_cnt = warp_cnt + warp * radix;
-#pragma unroll
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
-    key[r] = li < tile_n ? __ldg(keys_in + tile_base + li) : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
-    const bool valid = li < tile_n;
-    const uint32_t d = valid ? (key[r] >> shift) & mask : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t before = valid ? my_cnt[d] : 0u;
-    __syncwarp();
-    const uint32_t within = __popc(peers & lt);
-    if (valid && within == 0) my_cnt[d] = before + __popc(peers);
-    __syncwarp();
-    rank[r] = before + within;
-  }
-  __syncthreads();
-  // per digit: exclusive scan over warps; the tile's count, published at once
-  for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
-    uint32_t run = 0;
-    for (int w = 0; w < RS_WARPS; ++w) {
-      const uint32_t t = warp_cnt[w * radix + d];
-      warp_cnt[w * radix + d] = run;
-      run += t;
-    }
-    tile_start[d] = run;
-    __stcg(reinterpret_cast<unsigned long long*>(status + size_t(tile) * radix + d),
-           rs_word(epoch, tile == 0 ? RS_FLAG_PREFIX : RS_FLAG_AGG, run));
-  }
-  // decoupled look-back: sum the counts of the preceding tiles for each digit
-  for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
-    uint32_t excl = 0;
-    if (tile > 0) {
-      // the status words of up to RS_LOOKBACK predecessors are read at once and
-      // consumed in order (nearest first) up to the first one not yet published
-      int64_t t = int64_t(tile) - 1;
-      int polls = 0;
-      bool done = false;
-      while (!done && t >= 0) {
-        uint64_t w[RS_LOOKBACK];
-#pragma unroll
-        for (int k = 0; k < RS_LOOKBACK; ++k)
-          w[k] = t - k >= 0 ? __ldcv(reinterpret_cast<const unsigned long long*>(status + size_t(t - k) * radix + d))
-                            : 0ull;
-        int used = 0;
-#pragma unroll
-        for (int k = 0; k < RS_LOOKBACK; ++k) {
-          if (done || used < k || t - k < 0) continue;  // stop at the first gap
-          if (uint32_t(w[k] >> 48) == epoch && (w[k] & (RS_FLAG_AGG | RS_FLAG_PREFIX))) {
-            excl += uint32_t(w[k]);
-            used = k + 1;
-            if (w[k] & RS_FLAG_PREFIX) done = true;
-          }
-        }
-        t -= used;
-        if (done || t < 0) break;
-        if (used == 0) {
-          if (++polls > RS_SPIN_LIMIT) {
-            atomicOr(err, ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-        }
+      for (int k = 0; k < 4; ++k) {
+        const int d = threadIdx.x * per + k;
+        v[k] = (k < per && d < radix) ? __ldg(digit_total + d) : 0u;
+        sum += v[k];
       }
+      uint32_t total;
+      uint32_t off = block_excl_scan(sum, scratch, total);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int d = threadIdx.x * per + k;
+        if (k < per && d < radix) digit_base[d] = off;
+        off += v[k];
+      }
+    }
+
+    // stable rank: warp w owns items [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) in rounds of 32
+    uint32_t key[RS_ITEMS], rank[RS_ITEMS];
+    const uint32_t lt = lanemask_lt();
+    uint32_t* my_cnt = warp_cnt + warp * radix;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
+      key[r] = li < tile_n ? __ldg(keys_in + tile_base + li) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
+      const bool valid = li < tile_n;
+      const uint32_t d = valid ? (key[r] >> shift) & mask : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = valid ? my_cnt[d] : 0u;
+      __syncwarp();
+      const uint32_t within = __popc(peers & lt);
+      if (valid && within == 0) my_cnt[d] = before + __popc(peers);
+      __syncwarp();
+      rank[r] = before + within;
+    }
+    __syncthreads();
+    // per digit: exclusive scan over warps; the tile's count, published at once
+    for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
+      uint32_t run = 0;
+      for (int w = 0; w < RS_WARPS; ++w) {
+        const uint32_t t = warp_cnt[w * radix + d];
+        warp_cnt[w * radix + d] = run;
+        run += t;
+      }
+      tile_start[d] = run;
       __stcg(reinterpret_cast<unsigned long long*>(status + size_t(tile) * radix + d),
-             rs_word(epoch, RS_FLAG_PREFIX, excl + tile_start[d]));
+             rs_word(epoch, tile == 0 ? RS_FLAG_PREFIX : RS_FLAG_AGG, run));
     }
-    digit_base[d] += excl;
-  }
-  __syncthreads();
-  // exclusive scan of the tile counts -> start of each digit inside the tile
-  {
-    uint32_t v[4], sum = 0;
+    // decoupled look-back: sum the counts of the preceding tiles for each digit
+    for (int d = threadIdx.x; d < radix; d += RS_THREADS) {
+      uint32_t excl = 0;
+      if (tile > 0) {
+        // the status words of up to RS_LOOKBACK predecessors are read at once and
+        // consumed in order (nearest first) up to the first one not yet published
+        int64_t t = int64_t(tile) - 1;
+        int polls = 0;
+        bool done = false;
+        while (!done && t >= 0) {
+          uint64_t w[RS_LOOKBACK];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int d = threadIdx.x * per + k;
-      v[k] = (k < per && d < radix) ? tile_start[d] : 0u;
-      sum += v[k];
-    }
-    uint32_t total;
-    uint32_t off = block_excl_scan(sum, scratch, total);
+          for (int k = 0; k < RS_LOOKBACK; ++k)
+            w[k] = t - k >= 0 ? __ldcv(reinterpret_cast<const unsigned long long*>(status + size_t(t - k) * radix + d))
+                              : 0ull;
+          int used = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int d = threadIdx.x * per + k;
-      if (k < per && d < radix) tile_start[d] = off;
-      off += v[k];
+          for (int k = 0; k < RS_LOOKBACK; ++k) {
+            if (done || used < k || t - k < 0) continue;  // stop at the first gap
+            if (uint32_t(w[k] >> 48) == epoch && (w[k] & (RS_FLAG_AGG | RS_FLAG_PREFIX))) {
+              excl += uint32_t(w[k]);
+              used = k + 1;
+              if (w[k] & RS_FLAG_PREFIX) done = true;
+            }
+          }
+          t -= used;
+          if (done || t < 0) break;
+          if (used == 0) {
+            if (++polls > spin_limit) {
+              atomicOr(err, ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+        __stcg(reinterpret_cast<unsigned long long*>(status + size_t(tile) * radix + d),
+               rs_word(epoch, RS_FLAG_PREFIX, excl + tile_start[d]));
+      }
+      digit_base[d] += excl;
     }
-  }
-  __syncthreads();
-  // stage in tile-sorted order
+    __syncthreads();
+    // exclusive scan of the tile counts -> start of each digit inside the tile
+    {
+      uint32_t v[4], sum = 0;
 #pragma unroll
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
-    if (li < tile_n) {
-      const uint32_t d = (key[r] >> shift) & mask;
-      const uint32_t p = tile_start[d] + warp_cnt[warp * radix + d] + rank[r];
-      s_keys[p] = key[r];
-      s_vals[p] = vals_in ? __ldg(vals_in + tile_base + li) : uint32_t(tile_base + li);
+      for (int k = 0; k < 4; ++k) {
+        const int d = threadIdx.x * per + k;
+        v[k] = (k < per && d < radix) ? tile_start[d] : 0u;
+        sum += v[k];
+      }
+      uint32_t total;
+      uint32_t off = block_excl_scan(sum, scratch, total);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int d = threadIdx.x * per + k;
+        if (k < per && d < radix) tile_start[d] = off;
+        off += v[k];
+      }
     }
-  }
-  __syncthreads();
-  for (int li = threadIdx.x; li < tile_n; li += RS_THREADS) {
-    const uint32_t k = s_keys[li];
-    const uint32_t d = (k >> shift) & mask;
-    const uint32_t dest = digit_base[d] + uint32_t(li) - tile_start[d];
-    if (dest >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
-      atomicOr(err, ERR_TIMEOUT);
-      continue;
+    __syncthreads();
+    // stage in tile-sorted order
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+      const int li = warp * (RS_ITEMS * 32) + r * 32 + lane;
+      if (li < tile_n) {
+        const uint32_t d = (key[r] >> shift) & mask;
+        const uint32_t p = tile_start[d] + warp_cnt[warp * radix + d] + rank[r];
+        s_keys[p] = key[r];
+        s_vals[p] = vals_in ? __ldg(vals_in + tile_base + li) : uint32_t(tile_base + li);
+      }
     }
-    keys_out[dest] = k;
-    if (LAST) {
-      const uint32_t src = s_vals[li];
-      pos_out[dest] = pos_in[src];
-      mom_out[dest] = mom_in[src];
-    } else {
-      vals_out[dest] = s_vals[li];
+    __syncthreads();
+    for (int li = threadIdx.x; li < tile_n; li += RS_THREADS) {
+      const uint32_t k = s_keys[li];
+      const uint32_t d = (k >> shift) & mask;
+      const uint32_t dest = digit_base[d] + uint32_t(li) - tile_start[d];
+      if (dest >= uint32_t(n)) {  // only possible after a timed-out look-back: drop the element
+        atomicOr(err, ERR_TIMEOUT);
+        continue;
+      }
+      keys_out[dest] = k;
+      if (LAST) {
+        const uint32_t src = s_vals[li];
+        pos_out[dest] = pos_in[src];
+        mom_out[dest] = mom_in[src];
+      } else {
+        vals_out[dest] = s_vals[li];
+      }
     }
+    __syncthreads();  // shared memory is reused by the next tile
   }
 }
 
@@ -295,10 +307,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_sort_pass(
 // at all).  Rows are clamped to N^2: a key outside the mesh (a slot left
 // unwritten by a sort whose look-back timed out) writes nothing past the table.
 static __global__ void k_row_start(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_mesh, uint32_t nrows,
-                                   uint32_t* row_start, uint32_t* src) {
+                                   uint32_t* row_start) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i > n) return;
-  if (src && i < n) src[i] = uint32_t(i);  // the records are in sorted order
   const int64_t prev = i == 0 ? -1 : min(int64_t(__ldg(keys + i - 1) / n_mesh), int64_t(nrows));
   const int64_t cur = i == n ? int64_t(nrows) : min(int64_t(__ldg(keys + i) / n_mesh), int64_t(nrows));
   for (int64_t r = prev + 1; r <= cur; ++r) row_start[r] = uint32_t(i);
@@ -335,65 +346,113 @@ static __global__ void k_reduce_max(const double* __restrict__ part, int nblocks
 }
 
 // ---------------------------------------------------------------- incremental re-sort
-// After a drift the kick marks particles whose cell changed ("movers") by
-// setting bit 31 of their new key.  The others ("stayers") keep their key, so
-// in storage order they are still sorted by (key, previous slot).  The stable
-// sort by new key with ties in previous order is then: partition stably into
-// stayers and movers, radix-sort the movers (usually a few per cent), and merge
-// the two sequences by (key, previous slot) while gathering the records.  The
-// result is identical to the full sort.
-// Stable partition in one pass: block t takes tile t of RS_TILE slots.  The
-// drift has already counted the movers of every tile and of every group of
-// 2^RS_GROUP_SHIFT tiles (tcount), so a block finds the movers of all earlier
-// tiles by summing at most one group's tile counts and the earlier groups'
-// counts, with no wait on other blocks.  It writes its stayers to (s_keys,
-// s_vals) and its movers, flag cleared, to (m_keys, m_vals); values are the
-// previous slots.  It also accumulates the digit histograms of the movers'
-// keys for every radix pass (hist[p*radix_max + d], cleared before), advances
-// the sort epoch for those passes (as the histogram kernel does for a full
-// sort) and, in the last tile, stores counts[0] = stayers, counts[1] = movers
+// After a drift the kick marks the particles whose cell changed ("movers") by
+// setting bit 31 of their new key and counts them per tile of RS_TILE slots
+// (and per group of tiles).  The others ("stayers") keep their key, so in
+// storage order they are still sorted by (key, previous slot).  The stable
+// sort by new key with ties in previous order is the merge of the stayers with
+// the movers by (key, previous slot), and every particle's place in it follows
+// from its mesh row (key / N) alone:
+//   place = (stayers in earlier rows) + (movers in earlier rows)
+//         + (stayers of its row before it) + (movers of its row before it),
+// and a row holds a few tens of particles.  So the re-sort is: a stable
+// partition that also counts stayers and movers per row; a scan of the row
+// counts (which also gives the new row starts); a scatter of the movers into
+// per-row buckets; and the placement of every mover and every stayer, each
+// counting the entries of its own row that precede it (a mover among its
+// bucket and its row's stayers, a stayer among its row's bucket) and moving
+// its records there.  No sort pass over the movers and no search over the
+// whole sequence; the order is fixed by comparisons, so the result is the
+// same as the full stable sort (integer atomics only count and claim bucket
+// slots, whose order within a bucket does not enter the result).
+// Packed groups of simulations: member blockIdx.y, pointers ms bytes apart.
+
+__device__ __forceinline__ bool kv_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
+// row of a key (z*N + y), by a shift when N is a power of two
+__device__ __forceinline__ uint32_t key_row(uint32_t key, uint32_t n_mesh, int log2n) {
+  return log2n >= 0 ? key >> log2n : key / n_mesh;
+}
+
+// Movers before every tile: an exclusive scan of the drift's per-tile mover
+// counts (tcount[0..T)) into tcount[T..2T), by one block per simulation.
+constexpr int TS_THREADS = 1024;
+static __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(uint32_t* tcount, uint32_t ntiles, size_t ms) {
+  __shared__ uint32_t wsum[TS_THREADS / 32];
+  if (ms) tcount = moff(tcount, size_t(blockIdx.y) * ms);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t per = (ntiles + TS_THREADS - 1) / TS_THREADS;
+  const uint32_t t0 = threadIdx.x * per, t1 = min(t0 + per, ntiles);
+  uint32_t sum = 0;
+  for (uint32_t t = t0; t < t1; ++t) sum += tcount[t];
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t off = 0;
+  for (int w = 0; w < warp; ++w) off += wsum[w];
+  uint32_t run = off + inc - sum;
+  for (uint32_t t = t0; t < t1; ++t) {
+    const uint32_t c = tcount[t];
+    tcount[ntiles + t] = run;
+    run += c;
+  }
+}
+
+// Stable partition, one block per tile of RS_TILE slots; the movers of the
+// earlier tiles come from the tile scan.  It writes its stayers to (s_keys, s_vals) and its
+// movers, flag cleared, to (m_keys, m_vals) (values: previous slots), adds
+// its stayers and movers to the per-row counts rcnt[0][row] and rcnt[1][row]
+// (cleared before; one atomic per run of equal rows in a warp for the
+// stayers), and the last tile stores counts[0] = stayers, counts[1] = movers
 // and adds one re-sort and the movers to stats (nullable).
 static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
     const uint32_t* __restrict__ keys, int64_t n, const uint32_t* __restrict__ tcount,
     uint32_t* __restrict__ s_keys, uint32_t* __restrict__ s_vals, uint32_t* __restrict__ m_keys,
-    uint32_t* __restrict__ m_vals, uint32_t* __restrict__ counts, uint32_t* __restrict__ hist, int passes,
-    int digit_bits, int key_bits, uint32_t* __restrict__ sort_epoch, unsigned long long* __restrict__ stats) {
-  __shared__ uint32_t sh_hist[3 << RS_MAX_BITS];
-  __shared__ uint32_t wm[RS_WARPS], wsum[RS_WARPS];
+    uint32_t* __restrict__ m_vals, uint32_t* __restrict__ counts, uint32_t* __restrict__ rcnt, uint32_t n_mesh,
+    int log2n, unsigned long long* __restrict__ stats, size_t ms) {
+  __shared__ uint32_t wm[RS_WARPS];
+  if (ms) {  // member blockIdx.y of a packed group
+    const size_t o = size_t(blockIdx.y) * ms;
+    keys = moff(keys, o), tcount = moff(tcount, o), s_keys = moff(s_keys, o), s_vals = moff(s_vals, o);
+    m_keys = moff(m_keys, o), m_vals = moff(m_vals, o), counts = moff(counts, o), rcnt = moff(rcnt, o);
+    stats = moff(stats, o);
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int radix = 1 << digit_bits;
+  const uint32_t nrows = n_mesh * n_mesh;
   const uint32_t ntiles = uint32_t((n + RS_TILE - 1) >> RS_TILE_SHIFT);
   const uint32_t tile = blockIdx.x;
-  for (int d = threadIdx.x; d < passes * radix; d += RS_THREADS) sh_hist[d] = 0u;
-  if (tile == 0 && threadIdx.x == 0) *sort_epoch = (*sort_epoch + uint32_t(passes)) % 65530u + 1u;
   const int64_t tile_base = int64_t(tile) * RS_TILE;
   const uint32_t lt = lanemask_lt();
-  // movers before this tile: the earlier groups' counts, then the earlier tiles of this group
-  const uint32_t grp = tile >> RS_GROUP_SHIFT, first = grp << RS_GROUP_SHIFT;
-  uint32_t e = 0;
-  for (uint32_t g = threadIdx.x; g < grp; g += RS_THREADS) e += __ldg(tcount + ntiles + g);
-  for (uint32_t t = first + threadIdx.x; t < tile; t += RS_THREADS) e += __ldg(tcount + t);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  if (lane == 0) wsum[warp] = e;
+  const uint32_t excl = __ldg(tcount + ntiles + tile);  // movers before this tile
   // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32
   uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
     key[r] = i < n ? __ldg(keys + i) : 0u;
-    const uint32_t b = __ballot_sync(0xffffffffu, (key[r] & KEY_MOVER) != 0);
+    const bool mover = i < n && (key[r] & KEY_MOVER);
+    const uint32_t b = __ballot_sync(0xffffffffu, mover);
     rank[r] = mcount + __popc(b & lt);  // movers before this slot in the warp
     mcount += __popc(b);
+    // per-row counts: stayers by runs of equal rows in the warp, movers one by one
+    const uint32_t row = key_row(key[r] & ~KEY_MOVER, n_mesh, log2n);
+    const bool stayer = i < n && !mover;
+    const uint32_t peers = __match_any_sync(0xffffffffu, stayer ? row : 0xffffffffu) & __ballot_sync(0xffffffffu, stayer);
+    if (stayer && row < nrows && (peers & lt) == 0) atomicAdd(rcnt + row, uint32_t(__popc(peers)));
+    if (mover && row < nrows) atomicAdd(rcnt + nrows + row, 1u);
   }
   if (lane == 0) wm[warp] = mcount;
   __syncthreads();
-  uint32_t excl = 0, total = 0;
+  uint32_t total = 0;
 #pragma unroll
-  for (int w = 0; w < RS_WARPS; ++w) {
-    excl += wsum[w];
-    total += wm[w];
-  }
+  for (int w = 0; w < RS_WARPS; ++w) total += wm[w];
   if (tile == ntiles - 1 && threadIdx.x == 0) {
     counts[0] = uint32_t(n) - (excl + total);
     counts[1] = excl + total;
@@ -413,15 +472,9 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
     if (i < n) {
       const uint32_t before = mbase + rank[r];  // movers before slot i
       if (key[r] & KEY_MOVER) {
-        const uint32_t k = key[r] & ~KEY_MOVER;
         if (before < uint32_t(n)) {  // always (the counts bound the movers)
-          m_keys[before] = k;
+          m_keys[before] = key[r] & ~KEY_MOVER;
           m_vals[before] = uint32_t(i);
-        }
-        for (int p = 0; p < passes; ++p) {
-          const int shift = p * digit_bits;
-          const int bits = min(digit_bits, key_bits - shift);
-          atomicAdd(&sh_hist[p * radix + ((k >> shift) & ((1u << bits) - 1u))], 1u);
         }
       } else if (uint32_t(i) >= before) {
         s_keys[uint32_t(i) - before] = key[r];
@@ -429,181 +482,260 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
       }
     }
   }
-  __syncthreads();
-  for (int d = threadIdx.x; d < passes * radix; d += RS_THREADS)
-    if (sh_hist[d]) atomicAdd(hist + (d / radix) * (1 << RS_MAX_BITS) + (d % radix), sh_hist[d]);
 }
 
-__device__ __forceinline__ bool kv_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
-  return ka < kb || (ka == kb && va < vb);
-}
+// Exclusive scans of the per-row stayer and mover counts over the N^2 rows,
+// in tiles of RT_TILE rows: k_row_totals sums each tile, k_row_scan adds the
+// earlier tiles' totals and scans its own, writing srow (stayers before row
+// r), mrow (movers before row r) and the new row starts row_start = srow +
+// mrow, with the closing entries at r = N^2.
+constexpr int RT_THREADS = 1024, RT_ITEMS = 4, RT_TILE = RT_THREADS * RT_ITEMS;
 
-// number of stayers among the first d outputs of the merge (merge path)
-__device__ __forceinline__ uint32_t merge_split(const uint32_t* sk, const uint32_t* sv, uint32_t ns,
-                                                const uint32_t* mk, const uint32_t* mv, uint32_t nm, uint32_t d) {
-  uint32_t lo = d > nm ? d - nm : 0u, hi = d < ns ? d : ns;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    const uint32_t j = d - 1 - mid;  // the mover compared with stayer mid
-    if (kv_less(sk[mid], sv[mid], mk[j], mv[j]))
-      lo = mid + 1;
-    else
-      hi = mid;
+static __global__ void __launch_bounds__(RT_THREADS) k_row_totals(const uint32_t* __restrict__ rcnt, uint32_t nrows,
+                                                                  uint32_t* __restrict__ btot, size_t ms) {
+  __shared__ uint32_t sh[2][32];
+  if (ms) {
+    const size_t o = size_t(blockIdx.y) * ms;
+    rcnt = moff(rcnt, o), btot = moff(btot, o);
   }
-  return lo;
-}
-
-constexpr int MG_TILE = RS_TILE;  // outputs per block
-inline size_t merge_smem_bytes() { return size_t(MG_TILE) * 6 * sizeof(uint32_t); }
-
-// Both ends of the block's output range on the merge path, found by the two
-// halves of the block at once with a 128-way search: each round probes 128
-// evenly spaced candidates, so about three rounds (one dependent global load
-// each) narrow two million candidates to one.  Returns the number of stayers
-// before output d0 (split[0]) and d1 (split[1]).
-__device__ __forceinline__ void merge_split_block(const uint32_t* sk, const uint32_t* sv, uint32_t ns,
-                                                  const uint32_t* mk, const uint32_t* mv, uint32_t nm, uint32_t d0,
-                                                  uint32_t d1, uint32_t* lo_s, uint32_t* hi_s) {
-  const int grp = threadIdx.x >> 7, t = threadIdx.x & 127;
-  const uint32_t d = grp ? d1 : d0;
-  if (t == 0) {
-    lo_s[grp] = d > nm ? d - nm : 0u;
-    hi_s[grp] = d < ns ? d : ns;
-    lo_s[2 + grp] = 0u;
-    hi_s[2 + grp] = 0xffffffffu;
+  const uint32_t r0 = blockIdx.x * RT_TILE;
+  uint32_t a = 0, b = 0;
+#pragma unroll
+  for (int k = 0; k < RT_ITEMS; ++k) {
+    const uint32_t r = r0 + threadIdx.x + k * RT_THREADS;
+    if (r < nrows) {
+      a += __ldg(rcnt + r);
+      b += __ldg(rcnt + nrows + r);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    sh[0][warp] = a;
+    sh[1][warp] = b;
   }
   __syncthreads();
-  for (;;) {
-    const uint32_t lo = lo_s[grp], hi = hi_s[grp];
-    if (!__syncthreads_or(lo < hi)) break;
-    // candidate a in [lo, hi): are there more than a stayers before d?  (stayer a precedes mover d-1-a)
-    if (lo < hi) {
-      const uint32_t a = lo + uint32_t((uint64_t(hi - lo) * uint32_t(t)) >> 7);
-      const uint32_t j = d - 1 - a;
-      if (kv_less(sk[a], sv[a], mk[j], mv[j]))
-        atomicMax(lo_s + 2 + grp, a + 1);
+  if (threadIdx.x < 2) {
+    uint32_t t = 0;
+    for (int w = 0; w < RT_THREADS / 32; ++w) t += sh[threadIdx.x][w];
+    btot[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+static __global__ void __launch_bounds__(RT_THREADS) k_row_scan(const uint32_t* __restrict__ rcnt, uint32_t nrows,
+                                                                const uint32_t* __restrict__ btot,
+                                                                uint32_t* __restrict__ srow, uint32_t* __restrict__ mrow,
+                                                                uint32_t* __restrict__ row_start, size_t ms) {
+  __shared__ uint32_t sh[2][32];
+  __shared__ uint32_t base[2];
+  if (ms) {
+    const size_t o = size_t(blockIdx.y) * ms;
+    rcnt = moff(rcnt, o), btot = moff(btot, o), srow = moff(srow, o), mrow = moff(mrow, o);
+    row_start = moff(row_start, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nb = gridDim.x;
+  // totals of the earlier tiles
+  uint32_t pa = 0, pb = 0;
+  for (uint32_t t = threadIdx.x; t < blockIdx.x; t += RT_THREADS) {
+    pa += __ldg(btot + t);
+    pb += __ldg(btot + nb + t);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pa += __shfl_xor_sync(0xffffffffu, pa, o);
+    pb += __shfl_xor_sync(0xffffffffu, pb, o);
+  }
+  if (lane == 0) {
+    sh[0][warp] = pa;
+    sh[1][warp] = pb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    uint32_t t = 0;
+    for (int w = 0; w < RT_THREADS / 32; ++w) t += sh[threadIdx.x][w];
+    base[threadIdx.x] = t;
+  }
+  __syncthreads();
+  // this thread's RT_ITEMS consecutive rows, then a block scan of the thread sums
+  const uint32_t r0 = blockIdx.x * RT_TILE + threadIdx.x * RT_ITEMS;
+  uint32_t ca[RT_ITEMS], cb[RT_ITEMS], sa = 0, sb = 0;
+#pragma unroll
+  for (int k = 0; k < RT_ITEMS; ++k) {
+    const uint32_t r = r0 + k;
+    ca[k] = r < nrows ? __ldg(rcnt + r) : 0u;
+    cb[k] = r < nrows ? __ldg(rcnt + nrows + r) : 0u;
+    sa += ca[k];
+    sb += cb[k];
+  }
+  uint32_t ia = sa, ib = sb;  // inclusive warp scan
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += ua;
+      ib += ub;
+    }
+  }
+  __syncthreads();  // sh is reused
+  if (lane == 31) {
+    sh[0][warp] = ia;
+    sh[1][warp] = ib;
+  }
+  __syncthreads();
+  uint32_t wa = 0, wb = 0;
+  for (int w = 0; w < warp; ++w) {
+    wa += sh[0][w];
+    wb += sh[1][w];
+  }
+  uint32_t xa = base[0] + wa + ia - sa, xb = base[1] + wb + ib - sb;
+#pragma unroll
+  for (int k = 0; k < RT_ITEMS; ++k) {
+    const uint32_t r = r0 + k;
+    if (r < nrows) {
+      srow[r] = xa;
+      mrow[r] = xb;
+      row_start[r] = xa + xb;
+    }
+    xa += ca[k];
+    xb += cb[k];
+  }
+  if (blockIdx.x == nb - 1 && threadIdx.x == RT_THREADS - 1) {
+    srow[nrows] = xa;
+    mrow[nrows] = xb;
+    row_start[nrows] = xa + xb;
+  }
+}
+
+// movers into per-row buckets: bucket r holds the entries [mrow[r], mrow[r+1])
+// of (bk, bv), in an order the placement does not depend on
+static __global__ void __launch_bounds__(RS_THREADS) k_bucket_movers(
+    const uint32_t* __restrict__ mk, const uint32_t* __restrict__ mv, const uint32_t* __restrict__ counts,
+    const uint32_t* __restrict__ mrow, uint32_t* __restrict__ fill, uint32_t* __restrict__ bk,
+    uint32_t* __restrict__ bv, uint32_t n_mesh, int log2n, size_t ms) {
+  if (ms) {
+    const size_t o = size_t(blockIdx.y) * ms;
+    mk = moff(mk, o), mv = moff(mv, o), counts = moff(counts, o), mrow = moff(mrow, o), fill = moff(fill, o);
+    bk = moff(bk, o), bv = moff(bv, o);
+  }
+  const uint32_t nm = counts[1], nrows = n_mesh * n_mesh;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nm; j += gridDim.x * blockDim.x) {
+    const uint32_t k = mk[j];
+    const uint32_t r = key_row(k, n_mesh, log2n);
+    if (r >= nrows) continue;  // (only a corrupt key)
+    const uint32_t at = mrow[r] + atomicAdd(fill + r, 1u);
+    bk[at] = k;
+    bv[at] = mv[j];
+  }
+}
+
+// The placement, one warp per mesh row: the row's stayers (sorted, the
+// entries [srow[r], srow[r+1]) of (sk, sv)) and its movers (the bucket
+// [mrow[r], mrow[r+1]) of (bk, bv), in any order) go to the outputs
+// row_start[r] .. row_start[r+1] - 1 in the order of (key, previous slot): a
+// stayer moves up by the bucket entries before it, a mover lands after the
+// stayers before it (a binary search over the row's stayers) and the bucket
+// entries before it.  The keys go to keys_out and the records, gathered from
+// their previous slots, to (pos_out, mom_out).  A row holds a few tens of
+// particles, and only the movers of its own row are compared.
+constexpr int PR_WARPS = 8;
+template <typename V4>
+__global__ void __launch_bounds__(PR_WARPS * 32) k_place_rows(
+    const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ bk,
+    const uint32_t* __restrict__ bv, const uint32_t* __restrict__ srow, const uint32_t* __restrict__ mrow,
+    const uint32_t* __restrict__ row_start, uint32_t nrows, uint32_t* __restrict__ keys_out,
+    const V4* __restrict__ pos_in, const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out,
+    size_t ms) {
+  if (ms) {
+    const size_t o = size_t(blockIdx.y) * ms;
+    sk = moff(sk, o), sv = moff(sv, o), bk = moff(bk, o), bv = moff(bv, o), srow = moff(srow, o);
+    mrow = moff(mrow, o), row_start = moff(row_start, o), keys_out = moff(keys_out, o), pos_in = moff(pos_in, o);
+    mom_in = moff(mom_in, o), pos_out = moff(pos_out, o), mom_out = moff(mom_out, o);
+  }
+  const int lane = threadIdx.x & 31;
+  const uint32_t r = blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
+  if (r >= nrows) return;
+  const uint32_t s0 = __ldg(srow + r), s1 = __ldg(srow + r + 1);
+  const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
+  const uint32_t out0 = __ldg(row_start + r);
+  // stayers: shifted by the movers of the row before them
+  for (uint32_t t = lane; s0 + t < s1; t += 32) {
+    const uint32_t k = __ldg(sk + s0 + t), v = __ldg(sv + s0 + t);
+    uint32_t c = 0;
+    for (uint32_t f = m0; f < m1; ++f) c += kv_less(__ldg(bk + f), __ldg(bv + f), k, v) ? 1u : 0u;
+    const uint32_t i = out0 + t + c;
+    keys_out[i] = k;
+    pos_out[i] = pos_in[v];
+    mom_out[i] = mom_in[v];
+  }
+  // movers: after the stayers and the movers of the row before them
+  for (uint32_t u = m0 + lane; u < m1; u += 32) {
+    const uint32_t k = __ldg(bk + u), v = __ldg(bv + u);
+    uint32_t c = 0;
+    for (uint32_t f = m0; f < m1; ++f) c += kv_less(__ldg(bk + f), __ldg(bv + f), k, v) ? 1u : 0u;
+    uint32_t lo = s0, hi = s1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (kv_less(__ldg(sk + mid), __ldg(sv + mid), k, v))
+        lo = mid + 1;
       else
-        atomicMin(hi_s + 2 + grp, a);
+        hi = mid;
     }
-    __syncthreads();
-    if (t == 0 && lo < hi) {
-      if (lo_s[2 + grp] > lo) lo_s[grp] = lo_s[2 + grp];
-      if (hi_s[2 + grp] < hi) hi_s[grp] = hi_s[2 + grp];
-      lo_s[2 + grp] = 0u;
-      hi_s[2 + grp] = 0xffffffffu;
-    }
-    __syncthreads();
+    const uint32_t i = out0 + (lo - s0) + c;
+    keys_out[i] = k;
+    pos_out[i] = pos_in[v];
+    mom_out[i] = mom_in[v];
   }
 }
 
-// merge of the stayers with the sorted movers, by (key, previous slot); writes
-// the sorted keys, the previous slot of every sorted index (src: the records
-// stay where the drift wrote them, and the deposit and the next kick read
-// them through src) and the row starts (row_start[r] = first slot whose key
-// is in row r or above; row_start[N^2] = n)
-static __global__ void __launch_bounds__(RS_THREADS) k_merge(
-    const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ mk,
-    const uint32_t* __restrict__ mv, const uint32_t* __restrict__ counts, int64_t n, uint32_t* __restrict__ keys_out,
-    uint32_t* __restrict__ src_out, uint32_t n_mesh, uint32_t* __restrict__ row_start) {
-  extern __shared__ uint32_t msm[];
-  uint32_t* a_k = msm;               // stayers of this tile
-  uint32_t* a_v = a_k + MG_TILE;
-  uint32_t* b_k = a_v + MG_TILE;     // movers of this tile
-  uint32_t* b_v = b_k + MG_TILE;
-  uint32_t* o_k = b_v + MG_TILE;     // merged
-  uint32_t* o_v = o_k + MG_TILE;
-  __shared__ uint32_t lo_s[4], hi_s[4];
-  __shared__ uint32_t prev_key;
-  const uint32_t ns = counts[0], nm = counts[1];
-  const uint32_t d0 = blockIdx.x * uint32_t(MG_TILE);
-  const uint32_t d1 = int64_t(d0) + MG_TILE < n ? d0 + uint32_t(MG_TILE) : uint32_t(n);
-  merge_split_block(sk, sv, ns, mk, mv, nm, d0, d1, lo_s, hi_s);
-  const uint32_t a0 = lo_s[0], a1 = lo_s[1];
-  const uint32_t b0 = d0 - a0, b1 = d1 - a1;
-  const uint32_t na = a1 - a0, nb = b1 - b0;
-  const uint32_t tn = d1 - d0;
-  if (nb == 0) {
-    // no mover falls in this tile (the common case): the stayers pass through
-    for (uint32_t q = threadIdx.x; q < tn; q += RS_THREADS) {
-      const uint32_t k = __ldg(sk + a0 + q);
-      keys_out[d0 + q] = k;
-      src_out[d0 + q] = __ldg(sv + a0 + q);
-      o_k[q] = k;
-    }
+// the three parts of the re-sort: the partition, the rows (scan and
+// buckets) and the placement
+template <typename V4>
+inline cudaError_t launch_resort_place(int part, const uint32_t* keys, int64_t n, const uint32_t* tcount, uint32_t* sk,
+                                       uint32_t* sv, uint32_t* mk, uint32_t* mv, uint32_t* bk, uint32_t* bv,
+                                       uint32_t* counts, uint32_t* rcnt, uint32_t* btot, uint32_t* srow, uint32_t* mrow,
+                                       uint32_t* row_start, Mesh m, unsigned long long* stats, uint32_t* keys_out,
+                                       const V4* pos_in, const V4* mom_in, V4* pos_out, V4* mom_out, int sms,
+                                       cudaStream_t s, int nm, size_t ms) {
+  const size_t o = nm > 1 ? ms : 0;
+  const uint32_t N = uint32_t(m.n), nrows = N * N;
+  if (part == 0) {
+    const unsigned ntiles = unsigned((n + RS_TILE - 1) / RS_TILE);
+    k_tile_scan<<<dim3(1, unsigned(nm)), TS_THREADS, 0, s>>>(const_cast<uint32_t*>(tcount), ntiles, o);
+    k_mover_partition<<<dim3(ntiles, unsigned(nm)), RS_THREADS, 0, s>>>(keys, n, tcount, sk, sv, mk, mv, counts, rcnt,
+                                                                       N, m.log2n, stats, o);
+  } else if (part == 1) {
+    const unsigned nb = (nrows + RT_TILE - 1) / RT_TILE;
+    k_row_totals<<<dim3(nb, unsigned(nm)), RT_THREADS, 0, s>>>(rcnt, nrows, btot, o);
+    k_row_scan<<<dim3(nb, unsigned(nm)), RT_THREADS, 0, s>>>(rcnt, nrows, btot, srow, mrow, row_start, o);
+    // the bucket scatter runs over the device's mover count: a grid of resident blocks shared by the members
+    int64_t cap = int64_t(16) * sms / nm;
+    if (cap < 1) cap = 1;
+    const int64_t need = (n + RS_THREADS - 1) / RS_THREADS;
+    const unsigned mg = unsigned(need < cap ? need : cap);
+    k_bucket_movers<<<dim3(mg, unsigned(nm)), RS_THREADS, 0, s>>>(mk, mv, counts, mrow, rcnt + 2 * nrows, bk, bv, N,
+                                                                  m.log2n, o);
   } else {
-    for (uint32_t t = threadIdx.x; t < na; t += RS_THREADS) {
-      a_k[t] = sk[a0 + t];
-      a_v[t] = sv[a0 + t];
-    }
-    for (uint32_t t = threadIdx.x; t < nb; t += RS_THREADS) {
-      b_k[t] = mk[b0 + t];
-      b_v[t] = mv[b0 + t];
-    }
-    __syncthreads();
-    // each thread merges RS_ITEMS consecutive outputs of the tile
-    const uint32_t q0 = min(uint32_t(threadIdx.x) * RS_ITEMS, tn), q1 = min(q0 + RS_ITEMS, tn);
-    if (q0 < q1) {
-      uint32_t ia = merge_split(a_k, a_v, na, b_k, b_v, nb, q0);
-      uint32_t ib = q0 - ia;
-      for (uint32_t q = q0; q < q1; ++q) {
-        const bool take_a = ib >= nb || (ia < na && kv_less(a_k[ia], a_v[ia], b_k[ib], b_v[ib]));
-        if (take_a) {
-          o_k[q] = a_k[ia];
-          o_v[q] = a_v[ia];
-          ++ia;
-        } else {
-          o_k[q] = b_k[ib];
-          o_v[q] = b_v[ib];
-          ++ib;
-        }
-      }
-    }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < tn; q += RS_THREADS) {
-      keys_out[d0 + q] = o_k[q];
-      src_out[d0 + q] = o_v[q];
-    }
+    k_place_rows<V4><<<dim3((nrows + PR_WARPS - 1) / PR_WARPS, unsigned(nm)), PR_WARPS * 32, 0, s>>>(
+        sk, sv, bk, bv, srow, mrow, row_start, nrows, keys_out, pos_in, mom_in, pos_out, mom_out, o);
   }
-  if (threadIdx.x == 0 && d0 > 0) {
-    // the key at output d0-1: the larger of the last stayer and the last mover before this tile
-    uint32_t k = 0, v = 0;
-    bool have = false;
-    if (a0 > 0) {
-      k = sk[a0 - 1];
-      v = sv[a0 - 1];
-      have = true;
-    }
-    if (b0 > 0 && (!have || kv_less(k, v, mk[b0 - 1], mv[b0 - 1]))) k = mk[b0 - 1];
-    prev_key = k;
-  }
-  __syncthreads();
-  // rows (row of output i-1, row of output i] start at i (rows clamped to N^2, as in k_row_start)
-  const int64_t nrows = int64_t(n_mesh) * n_mesh;
-  for (uint32_t q = threadIdx.x; q <= tn; q += RS_THREADS) {
-    const uint32_t i = d0 + q;
-    if (q == tn && i != uint32_t(n)) break;  // output n (the closing row starts) belongs to the last block
-    const int64_t prev = i == 0 ? -1 : min(int64_t((q ? o_k[q - 1] : prev_key) / n_mesh), nrows);
-    const int64_t cur = i == uint32_t(n) ? nrows : min(int64_t(o_k[q] / n_mesh), nrows);
-    for (int64_t r = prev + 1; r <= cur; ++r) row_start[r] = i;
-  }
+  return cudaGetLastError();
 }
 
-inline cudaError_t launch_merge_impl(const uint32_t* sk, const uint32_t* sv, const uint32_t* mk, const uint32_t* mv,
-                                     const uint32_t* counts, int64_t n, uint32_t* keys_out, uint32_t* src_out,
-                                     uint32_t n_mesh, uint32_t* row_start, cudaStream_t s) {
-  static bool done[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(merge_smem_bytes()));
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) done[dev] = true;
-  }
-  const unsigned blocks = unsigned((n + MG_TILE - 1) / MG_TILE);
-  k_merge<<<blocks, RS_THREADS, merge_smem_bytes(), s>>>(sk, sv, mk, mv, counts, n, keys_out, src_out, n_mesh,
-                                                          row_start);
-  return cudaGetLastError();
+template <typename R>
+cudaError_t launch_resort(int part, const uint32_t* keys, int64_t n, const uint32_t* tcount, uint32_t* sk,
+                          uint32_t* sv, uint32_t* mk, uint32_t* mv, uint32_t* bk, uint32_t* bv, uint32_t* counts,
+                          uint32_t* rcnt, uint32_t* btot, uint32_t* srow, uint32_t* mrow, uint32_t* row_start, Mesh m,
+                          unsigned long long* stats, uint32_t* keys_out, const void* pos_in, const void* mom_in,
+                          void* pos_out, void* mom_out, int sms, cudaStream_t s, int nm, size_t ms) {
+  using V4 = typename VT<R>::v4;
+  return launch_resort_place<V4>(part, keys, n, tcount, sk, sv, mk, mv, bk, bv, counts, rcnt, btot, srow, mrow,
+                                 row_start, m, stats, keys_out, (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
+                                 (V4*)mom_out, sms, s, nm, ms);
 }
 
 template <typename R>
@@ -611,8 +743,15 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
                              int bits, const uint32_t* digit_total, uint64_t* status, uint32_t* tile_counter,
                              const uint32_t* epoch, int pass, int ntiles, uint32_t* keys_out, uint32_t* vals_out,
                              const void* pos_in, const void* mom_in, void* pos_out, void* mom_out, uint32_t* err,
-                             cudaStream_t s, const uint32_t* n_dev) {
+                             cudaStream_t s, const uint32_t* n_dev, int nm, size_t ms, int spin_limit) {
+  if (spin_limit < 1) spin_limit = RS_SPIN_LIMIT;
   using V4 = typename VT<R>::v4;
+  if (nm > 1 && (last || !n_dev)) return cudaErrorInvalidValue;  // packed groups: mover passes only
+  const size_t o = nm > 1 ? ms : 0;
+  // persistent blocks (they claim tiles until none is left): at most RS_PASS_BLOCKS in all
+  int per = RS_PASS_BLOCKS / nm;
+  if (per < 1) per = 1;
+  const dim3 grid = dim3(unsigned(ntiles < per ? ntiles : per), unsigned(nm), 1u);
   const size_t smem = radix_smem_bytes(bits);
   // shared-memory limits are raised once per device (for the largest digit), outside any capture
   static bool done[64];
@@ -627,14 +766,14 @@ cudaError_t launch_sort_pass(bool last, const uint32_t* keys_in, const uint32_t*
     if (dev >= 0 && dev < 64) done[dev] = true;
   }
   if (last) {
-    k_sort_pass<true, V4><<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
-                                                           tile_counter, epoch, pass, keys_out, vals_out,
-                                                           (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
-                                                           (V4*)mom_out, err, n_dev);
+    k_sort_pass<true, V4><<<grid, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
+                                                         tile_counter, epoch, pass, keys_out, vals_out,
+                                                         (const V4*)pos_in, (const V4*)mom_in, (V4*)pos_out,
+                                                         (V4*)mom_out, err, n_dev, o, spin_limit);
   } else {
-    k_sort_pass<false, V4><<<ntiles, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
-                                                            tile_counter, epoch, pass, keys_out, vals_out, nullptr,
-                                                            nullptr, nullptr, nullptr, err, n_dev);
+    k_sort_pass<false, V4><<<grid, RS_THREADS, smem, s>>>(keys_in, vals_in, n, shift, bits, digit_total, status,
+                                                          tile_counter, epoch, pass, keys_out, vals_out, nullptr,
+                                                          nullptr, nullptr, nullptr, err, n_dev, o, spin_limit);
   }
   return cudaGetLastError();
 }

@@ -30,7 +30,7 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error",
            "pm_batch_arena_bytes", "pm_batch_create", "pm_batch_destroy", "pm_batch_member", "pm_batch_run",
            "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_run_adaptive",
-           "pm_sort_stats"]
+           "pm_sort_stats", "pm_batch_info", "pm_debug_sort_timeout"]
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_set_density": (C.c_int, [vp, dp]),
         "pm_get_order": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
         "pm_sort_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "pm_debug_sort_timeout": (C.c_int, [vp, C.c_int32]),
         "pm_profile_begin": (C.c_int, [vp, C.c_int32]),
         "pm_profile_end": (C.c_int, [vp, dp, C.POINTER(C.c_int64)]),
         "pm_deposit_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, C.c_double, vp, vp, vp]),
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_batch_member": (vp, [vp, C.c_int32]),
         "pm_batch_run": (C.c_int, [vp, C.c_int32, dp, dp]),
         "pm_batch_last_error": (C.c_char_p, [vp]),
+        "pm_batch_info": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "pm_get_tuning": (C.c_int, [vp, C.POINTER(pm_tuning)]),
         "pm_set_tuning": (C.c_int, [vp, C.POINTER(pm_tuning)]),
         "pm_autotune": (C.c_int, [vp, C.c_int32, C.POINTER(pm_tuning)]),
@@ -326,6 +328,11 @@ class Sim:
             cache[key] = t.as_dict()
         return t.as_dict()
 
+    def debug_sort_timeout(self, spin_limit=64):
+        """Status of a radix pass whose look-back waits on a tile that never
+        publishes (a test of the bounded device waits; PM_ERR_TIMEOUT)."""
+        return int(lib().pm_debug_sort_timeout(self.handle, int(spin_limit)))
+
     def sort_stats(self):
         """(incremental re-sorts, particles they moved) since creation."""
         r, m = C.c_int64(0), C.c_int64(0)
@@ -391,6 +398,14 @@ class Batch:
         st = lib().pm_batch_run(self.handle, int(nsteps), _dptr(a0), _dptr(a1))
         if st != PM_OK:
             raise PMError(st, lib().pm_batch_last_error(self.handle).decode())
+
+    def info(self):
+        """(classes, members the last run stepped by packed launches)."""
+        c, p = C.c_int32(0), C.c_int32(0)
+        st = lib().pm_batch_info(self.handle, C.byref(c), C.byref(p))
+        if st != PM_OK:
+            raise PMError(st, lib().pm_batch_last_error(self.handle).decode())
+        return int(c.value), int(p.value)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -82,3 +82,75 @@ def test_batch_member_matches_oracle(pm):
     assert np.abs(d).max() < 1e-9
     assert np.sqrt(np.mean((pb - po) ** 2) / np.mean(po ** 2)) < 1e-9
     batch.close()
+
+
+# a batch whose members share configurations (size, precision, kernel, force
+# mode) but not box, mass or seed: the members of each class are stepped by
+# one launch per kernel and one batched transform per class
+PACKED = [  # (n_side, n_mesh, box, m22, seed, precision, mode)
+    (16, 32, 1.0, 2.5, 10, "fp32", "hybrid"),
+    (32, 64, 1.7, 10.0, 11, "fp32", "hybrid"),
+    (16, 32, 3.1, 1.0, 12, "fp32", "hybrid"),
+    (32, 64, 2.9, 5.0, 13, "fp32", "hybrid"),
+    (16, 32, 1.3, 2.5, 14, "fp32", "hybrid"),
+    (16, 32, 2.2, 5.0, 15, "fp32", "lagrangian"),
+    (16, 32, 1.5, 1.0, 16, "fp32", "lagrangian"),
+]
+
+
+def _packed_vs_single(pm, nsteps, a1):
+    a0 = 1 / 101.0
+    batch = pm.Batch([_cfg(pm, m) for m in PACKED])
+    for mem, m in zip(batch.members, PACKED):
+        mem.set_particles(*_ics(m, a0))
+    batch.run(nsteps, a0, a1)
+    assert batch.info() == (3, len(PACKED))  # three classes, every member stepped packed
+    out = []
+    for i, m in enumerate(PACKED):
+        xb, pb = batch.members[i].get_particles()
+        eb = batch.members[i].energy(a1[i])
+        cb, ib = batch.members[i].get_order()
+        kb, pkb, _ = batch.members[i].power_spectrum()
+        single = pm.Sim(_cfg(pm, m))
+        single.set_particles(*_ics(m, a0))
+        single.run(nsteps, a0, a1[i])
+        xs, ps = single.get_particles()
+        es = single.energy(a1[i])
+        _, pks, _ = single.power_spectrum()
+        single.close()
+        # the storage order is the stable order of the cells (ties by previous order)
+        assert np.all(np.diff(cb.astype(np.int64)) >= 0)
+        assert sorted(ib.tolist()) == list(range(len(ib)))
+        d = xb - xs
+        d -= m[2] * np.round(d / m[2])
+        out.append((m, np.abs(d).max() / (m[2] / m[1]), np.abs(pb - ps).max() / np.abs(ps).max(),
+                    np.abs(eb[:3] - es[:3]).max() / np.abs(es[:3]).max(), np.abs(pkb / pks - 1).max()))
+    batch.close()
+    return out
+
+
+A1 = np.array([1 / 60.0, 1 / 50.0, 1 / 70.0, 1 / 55.0, 1 / 40.0, 1 / 65.0, 1 / 45.0])
+
+
+def test_packed_batch_members_match_single_runs_over_two_steps(pm):
+    """Members stepped in packed launches against the same simulations run
+    alone, over one captured pair of steps: the re-sort, deposit, stencil and
+    kick are the same kernels, the batched transforms may round differently
+    from the single ones, so the states agree to fp32 rounding (1e-5 of a
+    cell, 1e-5 relative in momenta and energies)."""
+    a1 = (1 / 101.0) * (A1 * 101.0) ** 0.05  # two short steps
+    for m, dx, dp, de, dpk in _packed_vs_single(pm, 2, a1):
+        assert dx < 1e-5, (m, dx)
+        assert dp < 1e-5, (m, dp)
+        assert de < 1e-5, (m, de)
+
+
+def test_packed_batch_members_match_single_runs_over_nine_steps(pm):
+    """Nine steps: with the quantum force on meshes of eight cells per particle
+    a rounding difference can flip a discrete choice (a cell, the extended-
+    precision branch of a near-empty node), so single particles may part by a
+    fraction of a cell; P(k) and the energies stay within 1e-3."""
+    for m, dx, dp, de, dpk in _packed_vs_single(pm, 9, A1):
+        assert dx < 1e-2, (m, dx)
+        assert de < 1e-3, (m, de)
+        assert dpk < 1e-3, (m, dpk)
