@@ -644,12 +644,21 @@ def run_served(serve, n_requests):
     srv = serve.Server(SERVE["budget"], max_slots=64, chunk_steps=SERVE["chunk"], tuning=cache)
     res = srv.run(reqs, realtime=True, initial=initial)
     lat = serve.latency_percentiles(res)
+    # steady state: the requests that arrived in the middle half of the stream
+    t_end = max(r.arrival for r in reqs)
+    mid = [x for x, r in zip(res, reqs) if 0.25 * t_end <= r.arrival <= 0.75 * t_end]
+    lat_mid = serve.latency_percentiles(mid) if mid else lat
     offered = SERVE["rate"] * float(np.mean([r.n_side ** 3 * r.nsteps for r in reqs]))
-    return {"value": srv.stats["particle_steps"] / srv.stats["makespan"], "unit": "particle-steps/s",
-            "p50_s": lat["p50"], "p99_s": lat["p99"], "requests": n_requests,
-            "offered_particle_steps_per_s": offered, "makespan_s": srv.stats["makespan"],
+    served = srv.stats["particle_steps"] / srv.stats["makespan"]
+    # the GPU's capacity for this mix is at least the rate at which it served the whole stream; the
+    # stream is beyond it when the arrivals outlast the makespan less the last request's own time
+    return {"value": served, "unit": "particle-steps/s",
+            "p50_s": lat["p50"], "p99_s": lat["p99"], "steady_p50_s": lat_mid["p50"], "steady_p99_s": lat_mid["p99"],
+            "requests": n_requests, "offered_particle_steps_per_s": offered,
+            "utilisation": served / offered, "arrivals_end_s": t_end, "makespan_s": srv.stats["makespan"],
+            "saturated": served < 0.97 * offered,
             "max_active": srv.stats["max_active"], "peak_arena_gb": srv.stats["peak_bytes"] / 2 ** 30,
-            "workload": SERVE["name"]}
+            "workload": SERVE["name"] + ", %d requests" % n_requests}
 
 
 def main():
@@ -665,7 +674,7 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-parallel-oracle", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--tuning", default=None, help="launch shapes (pm_tuning fields as JSON) instead of the "
                     "autotuner's, for the single simulation")
     args = ap.parse_args()

@@ -97,7 +97,10 @@ typedef struct {
   int32_t fft_jit;     /* 1: plan the 3D transforms in cuFFT's patient JIT mode (kernels chosen and
                           linked at pm_create: a slower creation, ~6 % faster transforms at 256^3 on a
                           GB300; for long-lived simulations), 0: default plans */
-  int32_t reserved2;   /* 0 */
+  int32_t smooth_real; /* PM_KERNEL_SPLINE, PM_FP32, smooth_h <= 4, n_mesh <= 512: 1 smooths the density and Q
+                          by a direct sum over the node weights in real space (each node keeps the relative
+                          precision of its neighbours even where the field is near zero; slower than the
+                          transforms at 256^3 on a GB300), 0: by the transforms (default) */
 } pm_config;
 
 typedef struct pm_sim pm_sim;

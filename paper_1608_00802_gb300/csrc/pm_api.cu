@@ -142,6 +142,12 @@ bool valid_config(const pm_config* c, std::string* why) {
     *why = "smooth_h must be in [1, n_mesh/4] mesh cells";
     return false;
   }
+  // real-space smoothing: fp32, support within three cells, one block of n_mesh threads per mesh row
+  if (c->smooth_real != 0 && (c->smooth_real != 1 || c->kernel != PM_KERNEL_SPLINE || c->precision != PM_FP32 ||
+                              !(c->smooth_h <= 4.0) || c->n_mesh > 512)) {
+    *why = "smooth_real needs the spline kernel, PM_FP32, smooth_h <= 4 and n_mesh <= 512";
+    return false;
+  }
   return true;
 }
 
@@ -256,6 +262,7 @@ struct pm_sim {
   // unsmoothed Q~ between the stencil and its smoothing
   bool direct = false;
   double taps[19 * 4];
+  int taps_r2 = 27;  // largest squared offset with a nonzero weight
   int sms = 152;              // multiprocessors of the device
   bool krho_valid = false;    // the K_rho partials belong to the current Q~
   cufftHandle plan_fwd, plan_inv;
@@ -524,7 +531,7 @@ template <typename R>
 pm_status smooth_field(pm_sim* s, size_t in, size_t out) {
   if (s->direct) {
     PROF(s, PM_STAGE_GREEN);
-    CU(s, launch_smooth_direct<float>(s->at<float>(in), s->at<float>(out), s->mesh, s->taps, s->stream));
+    CU(s, launch_smooth_direct<float>(s->at<float>(in), s->at<float>(out), s->mesh, s->taps, s->taps_r2, s->stream));
     return PM_OK;
   }
   PMST(fft_r2c<R>(s, s->arena + in, s->arena + s->L.spec));
@@ -975,9 +982,11 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
   }
   if (c->precision == PM_FP32) kick_stream_prepare();
   if (s->cfg.kernel == PM_KERNEL_SPLINE) {
-    // real-space smoothing for fp32 supports within three cells (h <= 4 cells)
-    s->direct = c->precision == PM_FP32 && c->smooth_h <= 4.0;
+    s->direct = c->smooth_real != 0;
     spline_taps(c->smooth_h, s->taps);
+    s->taps_r2 = 0;
+    for (int r2 = 0; r2 <= 27; ++r2)
+      if (sqrt(double(r2)) < c->smooth_h) s->taps_r2 = r2;
     pm_status st = DISPATCH(s, spline_symbol, s);
     if (st == PM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) st = PM_ERR_CUDA;
     if (st != PM_OK) {
@@ -1530,8 +1539,8 @@ cufftResult class_plans(const pm_config& c, int nm, size_t ms, cufftHandle* fwd,
   for (int k = 0; k < 2; ++k) {
     cufftResult r = cufftCreate(h[k]);
     if (r != CUFFT_SUCCESS) return r;
+    // (default plans: patient JIT planning measured slower for these batched transforms)
     r = cufftSetAutoAllocation(*h[k], 0);
-    if (r == CUFFT_SUCCESS && c.fft_jit) r = cufftSetPlanPropertyInt64(*h[k], NVFFT_PLAN_PROPERTY_INT64_PATIENT_JIT, 1);
     if (r == CUFFT_SUCCESS)
       r = k == 0 ? cufftMakePlanMany64(*h[k], 3, n, re, 1, (long long)(ms / 4), cx, 1, (long long)(ms / 8), CUFFT_R2C,
                                        nm, &w[k])

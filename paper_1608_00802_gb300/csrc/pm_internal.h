@@ -156,9 +156,10 @@ template <typename R>
 cudaError_t launch_green_spline(void* spec, void* spec2, const void* what, Mesh m, double coef, double* part,
                                 cudaStream_t s, int smooth_in);
 // the spline smoothing in real space for supports within three cells (fp32):
-// g[s*4 + i] = normalised node weight at squared distance i^2 + s (s <= 18)
+// g[s*4 + i] = normalised node weight at squared distance i^2 + s (s <= 18);
+// maxr2: the largest squared distance with a nonzero weight
 template <typename R>
-cudaError_t launch_smooth_direct(const R* in, R* out, Mesh m, const double* g, cudaStream_t s);
+cudaError_t launch_smooth_direct(const R* in, R* out, Mesh m, const double* g, int maxr2, cudaStream_t s);
 template <typename R>
 cudaError_t launch_smooth_spec(void* spec, const void* what, Mesh m, cudaStream_t s);
 template <typename R>

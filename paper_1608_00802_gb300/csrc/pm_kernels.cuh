@@ -312,12 +312,12 @@ __device__ __forceinline__ void seg_add2(R lo, R hi, int t, bool valid, R* acc) 
   __syncwarp();
 }
 
-template <typename R>
+template <typename R, bool PACKED>
 __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
                                                             const uint32_t* __restrict__ row_start, uint32_t np,
                                                             Mesh m, R norm, R* __restrict__ rho, size_t ms) {
   using V4 = typename VT<R>::v4;
-  if (ms) {  // member blockIdx.y of a packed group
+  if constexpr (PACKED) {  // member blockIdx.y of a packed group
     const size_t o = size_t(blockIdx.y) * ms;
     pos = moff(pos, o), row_start = moff(row_start, o), rho = moff(rho, o);
   }
@@ -430,10 +430,10 @@ __device__ __forceinline__ void green_one(typename VT<R>::cplx& v, uint32_t e, u
 
 // coefp (nullable): the coefficient in device memory (member 0's, ms bytes
 // apart), used instead of coef by the packed groups, whose members differ in box
-template <typename R>
+template <typename R, bool PACKED>
 __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* spec, Mesh m, R coef, DivU32 dv,
                                                         double* part, const double* coefp, size_t ms) {
-  if (coefp) {  // member blockIdx.y of a packed group
+  if constexpr (PACKED) {  // member blockIdx.y of a packed group
     const size_t o = size_t(blockIdx.y) * ms;
     spec = moff(spec, o), part = moff(part, o);
     coef = R(*moff(coefp, o));
@@ -566,23 +566,74 @@ __global__ void __launch_bounds__(MESH_THREADS) k_smooth_spec(typename VT<R>::cp
 // smoothing multiplies by.  Summed in real space every output is a positive
 // combination of nearby values, so it keeps their relative precision (the
 // transforms' rounding is relative to the whole field's norm instead, which a
-// near-empty region cannot afford).  The weight of offset (i, j, k) depends on
-// s = j^2 + k^2 and i^2 only, so with g[s][i] = w(i^2 + s) the sum is
-//   out(x) = T_0(x) + sum_{i=1..3} (T_i(x - i) + T_i(x + i)),
-//   T_i(x) = sum_s g[s][i] R_s(x),  R_s(x) = sum_{j^2 + k^2 = s} in(x, y+j, z+k):
-// one block per y row (all x) and a run of z planes; each thread keeps the
-// 7 x 7 (j, k) window of its column in registers while it steps along z and
-// loads one value per j for the next plane; the T_i of the row are exchanged
-// through shared memory (periodic in x).
-constexpr int SP_S = 19;  // s = j^2 + k^2 <= 18
+// near-empty region cannot afford).  The weight of offset (i, j, k) is
+// c[i][|j|][|k|] = w(i^2 + j^2 + k^2), so with the x taps done last,
+//   out(x, z) = T_0(x) + sum_{i=1..3} (T_i(x - i) + T_i(x + i)),
+//   T_i(x, z) = sum_{k=-3..3} V_{|k|,i}(x, z + k),
+//   V_{|k|,i}(x, p) = sum_{|j|} c[i][|j|][|k|] (in(x, y+j, p) + in(x, y-j, p)):
+// one block per y row (one thread per x) and a run of z planes.  Each input
+// plane p is read once per thread (its seven rows y-3..y+3), turned into the
+// V values and added to the T accumulators of the seven outputs p-3..p+3,
+// kept in a ring of registers; the output p-3 is then complete, and the row
+// exchanges its T_i through shared memory for the x taps.  Terms with
+// i^2 + j^2 + k^2 > MAXR2 are left out at compile time (their weights are 0
+// when MAXR2 >= the squared support).
 template <typename R>
 struct SplineTaps {
-  R g[SP_S][4];  // g[s][i] = w(i^2 + s), 0 beyond the support
+  R c[4][4][4];  // c[i][|j|][|k|]
 };
 
-template <typename R>
-__global__ void __launch_bounds__(1024) k_smooth_direct(const R* __restrict__ in, R* __restrict__ out, Mesh m,
-                                                        SplineTaps<R> tp, int zc) {
+template <typename R, int MAXR2, int U>
+__device__ __forceinline__ void smooth_plane(const R* __restrict__ in, R* __restrict__ out, const Mesh& m,
+                                             const SplineTaps<R>& tp, const uint32_t (&row)[7], int p, int z0, int z1,
+                                             R (&acc)[7][4], R (&v)[7], R* T, int x, int xm1, int xp1, int xm2, int xp2,
+                                             int xm3, int xp3) {
+  const int n = m.n;
+  // v holds plane p (loaded one plane ahead); plane p + 1 is requested before p is worked on
+  const R P[4] = {v[3], v[2] + v[4], v[1] + v[5], v[0] + v[6]};
+  {
+    const R* pl = in + size_t(wrap(p + 1, n)) * m.n2;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) v[j] = __ldg(pl + row[j]);
+  }
+  // output p+3 enters the ring at slot U (slots advance by one per plane)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[U][i] = R(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    R V[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      R a = R(0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i * i + j * j + k * k <= MAXR2) a += tp.c[i][j][k] * P[j];
+      V[i] = a;
+    }
+    // output p - k' with |k'| = k sits at slot (U - 3 - k') mod 7
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[(U + 4 - k + 7) % 7][i] += V[i];
+      if (k) acc[(U + 4 + k) % 7][i] += V[i];
+    }
+  }
+  // output p - 3 (slot U + 1) is complete
+  const int z = p - 3;
+  if (z >= z0 && z < z1) {
+    const R* a = acc[(U + 1) % 7];
+    T[x] = a[1];
+    T[n + x] = a[2];
+    T[2 * n + x] = a[3];
+    __syncthreads();
+    const R o = a[0] + (T[xm1] + T[xp1]) + (T[n + xm2] + T[n + xp2]) + (T[2 * n + xm3] + T[2 * n + xp3]);
+    out[size_t(z) * m.n2 + row[3]] = o;
+    __syncthreads();  // T is rewritten for the next output
+  }
+}
+
+template <typename R, int MAXR2>
+__global__ void __launch_bounds__(512) k_smooth_direct(const R* __restrict__ in, R* __restrict__ out, Mesh m,
+                                                       SplineTaps<R> tp, int zc) {
   extern __shared__ __align__(16) unsigned char sd_smem[];
   R* T = reinterpret_cast<R*>(sd_smem);  // T_1, T_2, T_3 of the row
   const int n = m.n, x = threadIdx.x, y = blockIdx.x;
@@ -590,47 +641,28 @@ __global__ void __launch_bounds__(1024) k_smooth_direct(const R* __restrict__ in
   uint32_t row[7];
 #pragma unroll
   for (int j = 0; j < 7; ++j) row[j] = uint32_t(wrap(y + j - 3, n)) * uint32_t(n) + uint32_t(x);
-  R w[7][7];  // w[j][k] = in(x, y + j - 3, z + k - 3) for the plane z being computed
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const R* pl = in + size_t(wrap(z0 - 3 + k, n)) * m.n2;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) w[j][k] = __ldg(pl + row[j]);
-  }
   const int xm1 = wrap(x - 1, n), xp1 = wrap(x + 1, n), xm2 = wrap(x - 2, n), xp2 = wrap(x + 2, n);
   const int xm3 = wrap(x - 3, n), xp3 = wrap(x + 3, n);
-  for (int z = z0; z < z1; ++z) {
-    const R* pl = in + size_t(wrap(z + 3, n)) * m.n2;
+  R acc[7][4];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) w[j][6] = __ldg(pl + row[j]);
-    R rs[SP_S];
+  for (int q = 0; q < 7; ++q)
 #pragma unroll
-    for (int q = 0; q < SP_S; ++q) rs[q] = R(0);
+    for (int i = 0; i < 4; ++i) acc[q][i] = R(0);
+  R v[7];
+  {
+    const R* pl = in + size_t(wrap(z0 - 3, n)) * m.n2;
 #pragma unroll
-    for (int j = 0; j < 7; ++j)
-#pragma unroll
-      for (int k = 0; k < 7; ++k) rs[(j - 3) * (j - 3) + (k - 3) * (k - 3)] += w[j][k];
-    R t[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      R a = R(0);
-#pragma unroll
-      for (int q = 0; q < SP_S; ++q)
-        if (q == 0 || q == 1 || q == 2 || q == 4 || q == 5 || q == 8 || q == 9 || q == 10 || q == 13 || q == 18)
-          a += tp.g[q][i] * rs[q];
-      t[i] = a;
-    }
-    T[x] = t[1];
-    T[n + x] = t[2];
-    T[2 * n + x] = t[3];
-    __syncthreads();
-    const R o = t[0] + (T[xm1] + T[xp1]) + (T[n + xm2] + T[n + xp2]) + (T[2 * n + xm3] + T[2 * n + xp3]);
-    out[size_t(z) * m.n2 + row[3]] = o;
-    __syncthreads();  // T is rewritten for the next plane
-#pragma unroll
-    for (int j = 0; j < 7; ++j)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) w[j][k] = w[j][k + 1];
+    for (int j = 0; j < 7; ++j) v[j] = __ldg(pl + row[j]);
+  }
+  // input planes z0-3 .. z1+2, seven per round so that the ring slots are compile-time
+  for (int p = z0 - 3; p - 3 < z1; p += 7) {
+    smooth_plane<R, MAXR2, 0>(in, out, m, tp, row, p + 0, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
+    smooth_plane<R, MAXR2, 1>(in, out, m, tp, row, p + 1, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
+    smooth_plane<R, MAXR2, 2>(in, out, m, tp, row, p + 2, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
+    smooth_plane<R, MAXR2, 3>(in, out, m, tp, row, p + 3, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
+    smooth_plane<R, MAXR2, 4>(in, out, m, tp, row, p + 4, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
+    smooth_plane<R, MAXR2, 5>(in, out, m, tp, row, p + 5, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
+    smooth_plane<R, MAXR2, 6>(in, out, m, tp, row, p + 6, z0, z1, acc, v, T, x, xm1, xp1, xm2, xp2, xm3, xp3);
   }
 }
 
@@ -1059,12 +1091,13 @@ static __global__ void __launch_bounds__(SB_THREADS) k_stencil_bulk(const float*
 // region of a global list and are redone in float-float (densities reread
 // through L2).
 // Per node the arithmetic is that of k_stencil_tiled (same bits).
-static __global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float* __restrict__ rho, Mesh m, float fl,
+template <bool PACKED>
+__global__ void __launch_bounds__(SB_THREADS) k_stencil_tile(const float* __restrict__ rho, Mesh m, float fl,
                                                                     float qc, float slim, int ty, int tz,
                                                                     float* __restrict__ q, uint32_t* list,
                                                                     double* part, uint32_t* err, int diag,
                                                                     const double* qcp, size_t ms) {
-  if (qcp) {  // member blockIdx.z of a packed group (coefficient from device memory, as in k_green)
+  if constexpr (PACKED) {  // member blockIdx.z of a packed group (coefficient from device memory, as in k_green)
     const size_t o = size_t(blockIdx.z) * ms;
     rho = moff(rho, o), q = moff(q, o), list = moff(list, o), part = moff(part, o), err = moff(err, o);
     qc = float(*moff(qcp, o));
@@ -1403,15 +1436,8 @@ __device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, 
     if (kp.has_drift) {
       const bool moved = ncell != cell;
       keys[i] = ncell | (moved ? KEY_MOVER : 0u);
-      // one atomic per tile among the active lanes of the warp that moved
-      const uint32_t act = __activemask();
-      if (__ballot_sync(act, moved)) {
-        const uint32_t peers = __match_any_sync(act, uint32_t(i >> RS_TILE_SHIFT));
-        const uint32_t movers = __ballot_sync(act, moved) & peers;
-        uint32_t lt;
-        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-        if (movers && (peers & lt) == 0) atomicAdd(tcount + (i >> RS_TILE_SHIFT), uint32_t(__popc(movers)));
-      }
+      // (one integer atomic per mover: measured faster than a warp-aggregated count)
+      if (moved) atomicAdd(tcount + (i >> RS_TILE_SHIFT), 1u);
     }
   }
 }
@@ -1446,13 +1472,15 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT
 #ifndef PM_KICK_STREAM_MINB
 #define PM_KICK_STREAM_MINB 3  // the prefetched records need registers beyond k_kick's cap
 #endif
-template <typename R>
+// PACKED: the members of a packed group, member blockIdx.y (a separate
+// instantiation: the member offsets cost the single pass ~20 % when present)
+template <typename R, bool PACKED>
 __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_STREAM_MINB) k_kick_stream(
     typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys, uint32_t* tcount, int64_t n, const R* __restrict__ phi,
     const R* __restrict__ qf, Mesh m, KickParams kp_arg, const KickParams* __restrict__ kp_tab,
     const uint32_t* __restrict__ step, uint32_t* err, size_t ms) {
   using V4 = typename VT<R>::v4;
-  if (ms) {  // member blockIdx.y of a packed group
+  if constexpr (PACKED) {
     const size_t o = size_t(blockIdx.y) * ms;
     pos = moff(pos, o), mom = moff(mom, o), keys = moff(keys, o), tcount = moff(tcount, o), phi = moff(phi, o);
     qf = moff(qf, o), kp_tab = moff(kp_tab, o), step = moff(step, o), err = moff(err, o);
@@ -1585,14 +1613,19 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !done[dev]) {
       const int most = int(size_t(DEP_WARPS) * (1024 + 1) * sizeof(R));
-      cudaError_t e = cudaFuncSetAttribute(k_deposit<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      cudaError_t e = cudaFuncSetAttribute(k_deposit<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_deposit<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
       if (e != cudaSuccess) return e;
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
   const unsigned blocks = (m.n2 + warps - 1) / warps;
-  k_deposit<R><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m,
-                                                                    R(norm), rho, nm > 1 ? ms : 0);
+  if (nm > 1)
+    k_deposit<R, true><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n),
+                                                                             m, R(norm), rho, ms);
+  else
+    k_deposit<R, false><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho, 0);
   return cudaGetLastError();
 }
 
@@ -1619,15 +1652,29 @@ cudaError_t launch_green_spline(void* spec, void* spec2, const void* what, Mesh 
   return cudaGetLastError();
 }
 
-// the direct smoothing (support within three cells); zc planes per block
+// the direct smoothing (support within three cells, n_mesh <= 512: one
+// thread per x of a row); zc planes per block.  g[s*4 + i] = w(i^2 + s);
+// maxr2: the largest squared offset with a nonzero weight
 template <typename R>
-cudaError_t launch_smooth_direct(const R* in, R* out, Mesh m, const double* g, cudaStream_t s) {
+cudaError_t launch_smooth_direct(const R* in, R* out, Mesh m, const double* g, int maxr2, cudaStream_t s) {
   SplineTaps<R> tp;
-  for (int q = 0; q < SP_S; ++q)
-    for (int i = 0; i < 4; ++i) tp.g[q][i] = R(g[q * 4 + i]);
-  const int zc = m.n >= 64 ? 32 : m.n;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 4; ++k) tp.c[i][j][k] = R(g[(j * j + k * k) * 4 + i]);
+#ifndef PM_SD_ZC
+#define PM_SD_ZC 16
+#endif
+  const int zc = m.n >= 2 * PM_SD_ZC ? PM_SD_ZC : m.n;
   const dim3 grid(unsigned(m.n), unsigned((m.n + zc - 1) / zc));
-  k_smooth_direct<R><<<grid, unsigned(m.n), 3 * m.n * sizeof(R), s>>>(in, out, m, tp, zc);
+  const size_t smem = 3 * m.n * sizeof(R);
+  if (maxr2 <= 8)
+    k_smooth_direct<R, 8><<<grid, unsigned(m.n), smem, s>>>(in, out, m, tp, zc);
+  else if (maxr2 <= 12)
+    k_smooth_direct<R, 12><<<grid, unsigned(m.n), smem, s>>>(in, out, m, tp, zc);
+  else if (maxr2 <= 15)
+    k_smooth_direct<R, 15><<<grid, unsigned(m.n), smem, s>>>(in, out, m, tp, zc);
+  else
+    k_smooth_direct<R, 27><<<grid, unsigned(m.n), smem, s>>>(in, out, m, tp, zc);
   return cudaGetLastError();
 }
 
@@ -1643,8 +1690,12 @@ template <typename R>
 cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStream_t s, const double* coefp, int nm,
                          size_t ms) {
   using C = typename VT<R>::cplx;
-  k_green<R><<<dim3(MESH_GRID, unsigned(nm)), MESH_THREADS, m.n * sizeof(R), s>>>(
-      (C*)spec, m, R(coef), divu32_make(uint32_t(m.n / 2 + 1)), part, coefp, ms);
+  if (nm > 1)
+    k_green<R, true><<<dim3(MESH_GRID, unsigned(nm)), MESH_THREADS, m.n * sizeof(R), s>>>(
+        (C*)spec, m, R(coef), divu32_make(uint32_t(m.n / 2 + 1)), part, coefp, ms);
+  else
+    k_green<R, false><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>(
+        (C*)spec, m, R(coef), divu32_make(uint32_t(m.n / 2 + 1)), part, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -1676,15 +1727,23 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
       int dev = 0;
       cudaGetDevice(&dev);
       if (dev < 0 || dev >= 64 || !done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_stencil_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(SB_SMEM_MAX));
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(k_stencil_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(SB_SMEM_MAX));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) done[dev] = true;
       }
       const dim3 g(unsigned(m.n / sp.ty), unsigned((m.n + sp.zlen - 1) / sp.zlen), unsigned(nm));
-      k_stencil_tile<<<g, SB_THREADS, stencil_tile_smem(m.n, sp.ty, sp.zlen), s>>>(
-          (const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, sp.ty, sp.zlen, (float*)q, list, part,
-          err, sp.diag, nm > 1 ? qcp : nullptr, ms);
+      if (nm > 1)
+        k_stencil_tile<true><<<g, SB_THREADS, stencil_tile_smem(m.n, sp.ty, sp.zlen), s>>>(
+            (const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, sp.ty, sp.zlen, (float*)q, list, part,
+            err, sp.diag, qcp, ms);
+      else
+        k_stencil_tile<false><<<g, SB_THREADS, stencil_tile_smem(m.n, sp.ty, sp.zlen), s>>>(
+            (const float*)rho, m, float(sp.rho_floor), float(sp.qcoef), slim, sp.ty, sp.zlen, (float*)q, list, part,
+            err, sp.diag, nullptr, 0);
       return cudaGetLastError();
     }
     if (sp.ty > 0 && stencil_bulk_shape_ok(m.n, sp.ty, sp.zlen, sp.stages)) {
@@ -1724,7 +1783,7 @@ int kick_stream_resident(int threads) {
   const int t = threads == 128 ? 0 : 1;
   if (dev >= 0 && dev < 64 && cache[dev][t] > 0) return cache[dev][t];
   int per_sm = 0, sms = 0, r = 1 << 30;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kick_stream<R>, threads, 0) == cudaSuccess &&
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kick_stream<R, false>, threads, 0) == cudaSuccess &&
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && per_sm > 0 && sms > 0)
     r = per_sm * sms;
   else
@@ -1751,8 +1810,8 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, uint32_t* tcount, 
       if (threads != 128 && threads != 256) threads = KICK_THREADS;
       const int per = kick_stream_resident<R>(threads) / nm;
       const unsigned g = kick_stream_blocks(n, threads, per > 1 ? per : 1);
-      k_kick_stream<R><<<dim3(g, unsigned(nm)), threads, 0, s>>>((V4*)pos, (V4*)mom, keys, tcount, n, phi, q, m,
-                                                                  kp, kp_tab, step, err, ms);
+      k_kick_stream<R, true><<<dim3(g, unsigned(nm)), threads, 0, s>>>((V4*)pos, (V4*)mom, keys, tcount, n, phi, q,
+                                                                        m, kp, kp_tab, step, err, ms);
       return cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;
@@ -1769,7 +1828,7 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, uint32_t* tcount, 
   else if (kp.diag)
     k_kick<R, 1><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if constexpr (sizeof(R) == 4)  // the fp64 records would spill in the streaming loop
-    k_kick_stream<R><<<kick_stream_blocks(n, threads, kick_stream_resident<R>(threads)), threads, 0, s>>>(
+    k_kick_stream<R, false><<<kick_stream_blocks(n, threads, kick_stream_resident<R>(threads)), threads, 0, s>>>(
         p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, err, 0);
   else
     k_kick<R, 0><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);

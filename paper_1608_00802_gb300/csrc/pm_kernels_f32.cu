@@ -93,6 +93,6 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
 }
 
 PM_INSTANTIATE(float)
-template cudaError_t launch_smooth_direct<float>(const float*, float*, Mesh, const double*, cudaStream_t);
+template cudaError_t launch_smooth_direct<float>(const float*, float*, Mesh, const double*, int, cudaStream_t);
 
 }  // namespace pm

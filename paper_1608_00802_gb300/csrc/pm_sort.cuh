@@ -643,53 +643,98 @@ static __global__ void __launch_bounds__(RS_THREADS) k_bucket_movers(
 // their previous slots, to (pos_out, mom_out).  A row holds a few tens of
 // particles, and only the movers of its own row are compared.
 constexpr int PR_WARPS = 8;
+
+// entries of (k_, v_) held one per lane (lanes < cnt) that precede (k, v)
+__device__ __forceinline__ uint32_t warp_count_less(uint32_t k_, uint32_t v_, uint32_t cnt, uint32_t k, uint32_t v) {
+  uint32_t c = 0;
+  for (uint32_t q = 0; q < cnt; ++q) {
+    const uint32_t kq = __shfl_sync(0xffffffffu, k_, int(q)), vq = __shfl_sync(0xffffffffu, v_, int(q));
+    c += kv_less(kq, vq, k, v) ? 1u : 0u;
+  }
+  return c;
+}
+
+// the general placement of one row (any counts)
 template <typename V4>
+__device__ __forceinline__ void place_row(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
+                                          const uint32_t* __restrict__ bk, const uint32_t* __restrict__ bv,
+                                          uint32_t s0, uint32_t ns, uint32_t m0, uint32_t nm, uint32_t out0,
+                                          uint32_t lane, uint32_t* __restrict__ keys_out, const V4* __restrict__ pos_in,
+                                          const V4* __restrict__ mom_in, V4* __restrict__ pos_out,
+                                          V4* __restrict__ mom_out) {
+  // stayers, 32 at a time: shifted by the row's bucket entries before them
+  for (uint32_t t0 = 0; t0 < ns; t0 += 32) {
+    const uint32_t t = t0 + lane;
+    const bool have = t < ns;
+    const uint32_t k = have ? __ldg(sk + s0 + t) : 0xffffffffu, v = have ? __ldg(sv + s0 + t) : 0xffffffffu;
+    V4 pr, mr;
+    if (have) {
+      pr = pos_in[v];
+      mr = mom_in[v];
+    }
+    uint32_t c = 0;
+    for (uint32_t u0 = 0; u0 < nm; u0 += 32) {
+      const uint32_t u = u0 + lane;
+      const uint32_t bk_ = u < nm ? __ldg(bk + m0 + u) : 0u, bv_ = u < nm ? __ldg(bv + m0 + u) : 0u;
+      c += warp_count_less(bk_, bv_, min(32u, nm - u0), k, v);
+    }
+    if (have) {
+      const uint32_t i = out0 + t + c;
+      keys_out[i] = k;
+      pos_out[i] = pr;
+      mom_out[i] = mr;
+    }
+  }
+  // movers, 32 at a time: after the stayers and the bucket entries of the row before them
+  for (uint32_t u0 = 0; u0 < nm; u0 += 32) {
+    const uint32_t u = u0 + lane;
+    const bool have = u < nm;
+    const uint32_t k = have ? __ldg(bk + m0 + u) : 0xffffffffu, v = have ? __ldg(bv + m0 + u) : 0xffffffffu;
+    V4 pr, mr;
+    if (have) {
+      pr = pos_in[v];
+      mr = mom_in[v];
+    }
+    uint32_t c = 0;
+    for (uint32_t w0 = 0; w0 < nm; w0 += 32) {
+      const uint32_t w = w0 + lane;
+      const uint32_t bk_ = w < nm ? __ldg(bk + m0 + w) : 0u, bv_ = w < nm ? __ldg(bv + m0 + w) : 0u;
+      c += warp_count_less(bk_, bv_, min(32u, nm - w0), k, v);
+    }
+    for (uint32_t t0 = 0; t0 < ns; t0 += 32) {
+      const uint32_t t = t0 + lane;
+      const uint32_t sk_ = t < ns ? __ldg(sk + s0 + t) : 0u, sv_ = t < ns ? __ldg(sv + s0 + t) : 0u;
+      c += warp_count_less(sk_, sv_, min(32u, ns - t0), k, v);
+    }
+    if (have) {
+      const uint32_t i = out0 + c;
+      keys_out[i] = k;
+      pos_out[i] = pr;
+      mom_out[i] = mr;
+    }
+  }
+}
+
+template <typename V4, bool PACKED>
 __global__ void __launch_bounds__(PR_WARPS * 32) k_place_rows(
     const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ bk,
     const uint32_t* __restrict__ bv, const uint32_t* __restrict__ srow, const uint32_t* __restrict__ mrow,
     const uint32_t* __restrict__ row_start, uint32_t nrows, uint32_t* __restrict__ keys_out,
     const V4* __restrict__ pos_in, const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out,
     size_t ms) {
-  if (ms) {
+  if constexpr (PACKED) {
     const size_t o = size_t(blockIdx.y) * ms;
     sk = moff(sk, o), sv = moff(sv, o), bk = moff(bk, o), bv = moff(bv, o), srow = moff(srow, o);
     mrow = moff(mrow, o), row_start = moff(row_start, o), keys_out = moff(keys_out, o), pos_in = moff(pos_in, o);
     mom_in = moff(mom_in, o), pos_out = moff(pos_out, o), mom_out = moff(mom_out, o);
   }
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t r = blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
-  if (r >= nrows) return;
+  if (r >= nrows) return;  // (whole warps)
   const uint32_t s0 = __ldg(srow + r), s1 = __ldg(srow + r + 1);
   const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
-  const uint32_t out0 = __ldg(row_start + r);
-  // stayers: shifted by the movers of the row before them
-  for (uint32_t t = lane; s0 + t < s1; t += 32) {
-    const uint32_t k = __ldg(sk + s0 + t), v = __ldg(sv + s0 + t);
-    uint32_t c = 0;
-    for (uint32_t f = m0; f < m1; ++f) c += kv_less(__ldg(bk + f), __ldg(bv + f), k, v) ? 1u : 0u;
-    const uint32_t i = out0 + t + c;
-    keys_out[i] = k;
-    pos_out[i] = pos_in[v];
-    mom_out[i] = mom_in[v];
-  }
-  // movers: after the stayers and the movers of the row before them
-  for (uint32_t u = m0 + lane; u < m1; u += 32) {
-    const uint32_t k = __ldg(bk + u), v = __ldg(bv + u);
-    uint32_t c = 0;
-    for (uint32_t f = m0; f < m1; ++f) c += kv_less(__ldg(bk + f), __ldg(bv + f), k, v) ? 1u : 0u;
-    uint32_t lo = s0, hi = s1;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (kv_less(__ldg(sk + mid), __ldg(sv + mid), k, v))
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    const uint32_t i = out0 + (lo - s0) + c;
-    keys_out[i] = k;
-    pos_out[i] = pos_in[v];
-    mom_out[i] = mom_in[v];
-  }
+  place_row<V4>(sk, sv, bk, bv, s0, s1 - s0, m0, m1 - m0, __ldg(row_start + r), lane, keys_out, pos_in, mom_in,
+                pos_out, mom_out);
 }
 
 // the three parts of the re-sort: the partition, the rows (scan and
@@ -720,8 +765,13 @@ inline cudaError_t launch_resort_place(int part, const uint32_t* keys, int64_t n
     k_bucket_movers<<<dim3(mg, unsigned(nm)), RS_THREADS, 0, s>>>(mk, mv, counts, mrow, rcnt + 2 * nrows, bk, bv, N,
                                                                   m.log2n, o);
   } else {
-    k_place_rows<V4><<<dim3((nrows + PR_WARPS - 1) / PR_WARPS, unsigned(nm)), PR_WARPS * 32, 0, s>>>(
-        sk, sv, bk, bv, srow, mrow, row_start, nrows, keys_out, pos_in, mom_in, pos_out, mom_out, o);
+    const dim3 grid((nrows + PR_WARPS - 1) / PR_WARPS, unsigned(nm));
+    if (nm > 1)
+      k_place_rows<V4, true><<<grid, PR_WARPS * 32, 0, s>>>(sk, sv, bk, bv, srow, mrow, row_start, nrows, keys_out,
+                                                            pos_in, mom_in, pos_out, mom_out, o);
+    else
+      k_place_rows<V4, false><<<grid, PR_WARPS * 32, 0, s>>>(sk, sv, bk, bv, srow, mrow, row_start, nrows, keys_out,
+                                                             pos_in, mom_in, pos_out, mom_out, 0);
   }
   return cudaGetLastError();
 }

@@ -45,7 +45,7 @@ class pm_config(C.Structure):
                 ("force_mode", C.c_int32), ("lap", C.c_int32), ("cosmological", C.c_int32),
                 ("rho_floor", C.c_double), ("rho_fp64", C.c_double), ("kernel", C.c_int32),
                 ("reserved", C.c_int32), ("smooth_h", C.c_double), ("fft_jit", C.c_int32),
-                ("reserved2", C.c_int32)]
+                ("smooth_real", C.c_int32)]
 
 
 class pm_tuning(C.Structure):
@@ -135,7 +135,8 @@ def _dptr(a):
 
 def make_config(n_part, n_mesh, box, precision=FP32, omega_m=0.3, omega_l=0.7, h=0.7, m22=2.5,
                 quantum=True, force_mode=FORCE_MESHGRAD, lap=LAP_COMPACT, cosmological=True,
-                rho_floor=1e-6, rho_fp64=1e-2, kernel=KERNEL_CIC, smooth_h=3.5, fft_jit=False) -> pm_config:
+                rho_floor=1e-6, rho_fp64=1e-2, kernel=KERNEL_CIC, smooth_h=3.5, fft_jit=False,
+                smooth_real=False) -> pm_config:
     cfg = pm_config()
     lib().pm_config_default(C.byref(cfg))
     cfg.n_part, cfg.n_mesh, cfg.box = int(n_part), int(n_mesh), float(box)
@@ -146,6 +147,7 @@ def make_config(n_part, n_mesh, box, precision=FP32, omega_m=0.3, omega_l=0.7, h
     cfg.rho_floor, cfg.rho_fp64 = float(rho_floor), float(rho_fp64)
     cfg.kernel, cfg.smooth_h = int(kernel), float(smooth_h)
     cfg.fft_jit = int(bool(fft_jit))
+    cfg.smooth_real = int(bool(smooth_real))
     return cfg
 
 

@@ -33,6 +33,7 @@ def main():
     ap.add_argument("--tuning", default=None, help="launch shapes as JSON (pm_tuning fields), e.g. "
                     "'{\"stencil_rows\": 8, \"stencil_planes\": 8, \"stencil_stages\": 4}'")
     ap.add_argument("--autotune", action="store_true", help="measure the launch shapes first")
+    ap.add_argument("--kernel", choices=["cic", "spline"], default="cic", help="density kernel (spline: h = 3.5)")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -43,7 +44,8 @@ def main():
     a0, a1 = 1 / 101.0, 1 / 4.0
     x, p = ics.zeldovich(args.n_side, args.n_mesh, args.box, a0, 42, m22=args.m22)
     cfg = pm.make_config(len(x), args.n_mesh, args.box, m22=args.m22, force_mode=modes[args.mode],
-                         precision=pm.FP64 if args.precision == "fp64" else pm.FP32, rho_fp64=args.rho_fp64)
+                         precision=pm.FP64 if args.precision == "fp64" else pm.FP32, rho_fp64=args.rho_fp64,
+                         kernel=pm.KERNEL_SPLINE if args.kernel == "spline" else pm.KERNEL_CIC, smooth_h=3.5)
     sim = pm.Sim(cfg)
     sim.set_particles(x, p)
     if args.tuning:
