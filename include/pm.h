@@ -216,6 +216,12 @@ typedef struct {
                               sweep along z through a ring of that many planes (ignored when rows = 0) */
   int32_t kick_threads;    /* threads (particles) per interpolate+kick+drift block: 128 or 256 */
   int32_t deposit_warps;   /* mesh rows (one warp each) per deposit block: 1..8 */
+  int32_t green_fused;     /* PM_FP32 cloud-in-cell on a power-of-two mesh of 16..512 only: 1 transforms the
+                              planes of constant z with batched 2D transforms and does the z transforms, the
+                              Green multiplication and the inverse z transforms in one kernel between them
+                              (the spectrum crosses device memory once instead of three times; the default
+                              where it applies); 0 uses the 3D transforms and a separate Green pass.  The
+                              potential agrees to fp32 rounding either way */
 } pm_tuning;
 
 /* Current shapes. */

@@ -21,6 +21,8 @@ using namespace pm;
 namespace {
 
 thread_local std::string g_create_error;
+// set while a batch creates a member that its class steps packed (with the class's own transforms)
+thread_local bool g_batch_member = false;
 
 // ---------------------------------------------------------------- units
 // hbar/m in (Mpc/h)^2 H0: (hbar c) c / (m c^2), with one code unit of
@@ -89,7 +91,7 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
   size_t pos[2], mom[2], keys[4], vals[3], tcount, rcnt, btot, srow, mrow, tile_cnt, row_start, rho, phi, q, spec, what,
-      spec2, work, staging, hist, status, st_list, st_count, part, part_aux, red, err, ktab, total;
+      spec2, work, staging, hist, status, st_list, st_count, part, part_aux, red, err, ktab, green, total;
   int key_bits, passes, digit_bits, ntiles;
 };
 
@@ -206,12 +208,15 @@ Layout make_layout(const pm_config& c, size_t work_bytes) {
   L.part = take(npart * 8);
   L.st_list = take(c.precision == PM_FP32 ? stencil_list_entries(int(N)) * 4 : 4);
   L.st_count = take(size_t(stencil_max_blocks(int(N))) * 4);
-  const size_t aux = std::max<size_t>(MESH_GRID, size_t(stencil_max_blocks(int(N))));
+  size_t aux = std::max<size_t>(MESH_GRID, size_t(stencil_max_blocks(int(N))));
+  if (spec_z_supported(int(N))) aux = std::max<size_t>(aux, size_t(spec_z_tiles(int(N))));
   L.part_aux = take(2 * aux * 8);
   L.red = take(3 * PK_MAX_BINS * 8 + 64);
   L.err = take(256);
   // per-step kick weights of pm_run and of a batch run
   L.ktab = take(size_t(std::max(PM_RUN_GRAPH_MAX_STEPS, PM_BATCH_MAX_STEPS)) * sizeof(KickParams));
+  // the z transform's twiddles and the Green's sin^2 table (fp32 cloud-in-cell, power-of-two meshes)
+  L.green = take(c.precision == PM_FP32 && !spline && spec_z_supported(int(N)) ? N * 12 : 0);
   L.total = off;
   return L;
 }
@@ -266,6 +271,11 @@ struct pm_sim {
   int sms = 152;              // multiprocessors of the device
   bool krho_valid = false;    // the K_rho partials belong to the current Q~
   cufftHandle plan_fwd, plan_inv;
+  // fp32 cloud-in-cell, power-of-two mesh: batched 2D transforms of the z planes, between which
+  // one kernel does the z transforms and the Green multiplication
+  cufftHandle plan2_fwd = 0, plan2_inv = 0;
+  bool have_plan2 = false;
+  int wg_count = MESH_GRID;  // W_g partials the last force evaluation wrote
   bool have_particles, sorted, fields_valid;
   std::string err;
   // profiler: event pairs around launches while enabled
@@ -359,7 +369,10 @@ struct ProfScope {
 // `part_aux` (one MESH_GRID-long row each) until the next evaluation.
 double* wg_part(pm_sim* s) { return s->at<double>(s->L.part_aux); }
 size_t aux_len(const pm_sim* s) {
-  return std::max<size_t>(MESH_GRID, size_t(stencil_max_blocks(s->cfg.n_mesh)));
+  const int N = s->cfg.n_mesh;
+  size_t aux = std::max<size_t>(MESH_GRID, size_t(stencil_max_blocks(N)));
+  if (spec_z_supported(N)) aux = std::max<size_t>(aux, size_t(spec_z_tiles(N)));
+  return aux;
 }
 double* kr_part(pm_sim* s) { return wg_part(s) + aux_len(s); }
 int kr_blocks(const pm_sim* s) {
@@ -547,6 +560,60 @@ double green_coef(const pm_sim* s) {
   return -1.5 * s->cfg.omega_m * s->dx * s->dx / (4.0 * N * N * N);
 }
 
+// the Green multiplication inside the z transform, between batched 2D transforms
+bool green_fused(const pm_sim* s) { return s->tune.green_fused && s->have_plan2; }
+
+// The batched 2D transforms of the N z planes (forward: the real density to
+// the (ky, kx) half planes; inverse: back to the real potential), sharing the
+// work area of the 3D plans, and the z kernel's tables.  Sync.
+cufftResult spec_plan_setup(pm_sim* s, std::string* why) {
+  if (s->have_plan2) return CUFFT_SUCCESS;
+  const int N = s->cfg.n_mesh;
+  if (s->fp64() || spline(s) || !spec_z_supported(N)) {
+    *why = "not an fp32 cloud-in-cell simulation on a power-of-two mesh of 16..512";
+    return CUFFT_NOT_SUPPORTED;
+  }
+  const Layout& L = s->L;
+  cudaError_t ce = launch_spec_tables(s->at<float2>(L.green), s->at<float>(L.green + size_t(N) * 8), N, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) {
+    *why = std::string("tables: ") + cudaGetErrorString(ce);
+    return CUFFT_SETUP_FAILED;
+  }
+  cufftHandle h[2] = {0, 0};
+  const char* step = "cufftCreate";
+  cufftResult r = CUFFT_SUCCESS;
+  const long long nh = N / 2 + 1;
+  for (int k = 0; k < 2 && r == CUFFT_SUCCESS; ++k) {
+    long long n[2] = {N, N}, re[2] = {N, N}, cx[2] = {N, nh};
+    size_t w = 0;
+    step = "cufftCreate";
+    r = cufftCreate(&h[k]);
+    if (r == CUFFT_SUCCESS) r = cufftSetAutoAllocation(h[k], 0);
+    if (r == CUFFT_SUCCESS) {
+      step = "cufftMakePlanMany64";
+      r = k == 0 ? cufftMakePlanMany64(h[k], 2, n, re, 1, (long long)N * N, cx, 1, (long long)N * nh, CUFFT_R2C, N, &w)
+                 : cufftMakePlanMany64(h[k], 2, n, cx, 1, (long long)N * nh, re, 1, (long long)N * N, CUFFT_C2R, N, &w);
+    }
+    if (r == CUFFT_SUCCESS && w > L.staging - L.work) {  // the 3D plans' area
+      step = "work area";
+      r = CUFFT_NO_WORKSPACE;
+    }
+    if (r == CUFFT_SUCCESS) r = cufftSetWorkArea(h[k], s->arena + L.work);
+    if (r == CUFFT_SUCCESS) r = cufftSetStream(h[k], s->stream);
+  }
+  if (r != CUFFT_SUCCESS) {
+    *why = step;
+    for (cufftHandle x : h)
+      if (x) cufftDestroy(x);
+    return r;
+  }
+  s->plan2_fwd = h[0];
+  s->plan2_inv = h[1];
+  s->have_plan2 = true;
+  return CUFFT_SUCCESS;
+}
+
 // Q~ from the density, smoothed with the spline kernel (the transpose of the
 // density's smoothing); diag: with the K_rho partials.  In real space the
 // stencil writes the raw Q~ to `rho` and the smoothing moves it to `q`.
@@ -575,6 +642,26 @@ pm_status krho_stage(pm_sim* s) {
 template <typename R>
 pm_status mesh_from_density(pm_sim* s) {
   const Layout& L = s->L;
+  if (green_fused(s)) {  // 2D transforms of the planes; z transforms and Green in one pass between them
+    const int N = s->cfg.n_mesh;
+    {
+      PROF(s, PM_STAGE_FFT_R2C);
+      CF(s, cufftExecR2C(s->plan2_fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
+    }
+    {
+      PROF(s, PM_STAGE_GREEN);
+      CU(s, launch_spec_z(s->arena + L.spec, s->at<float2>(L.green), s->at<float>(L.green + size_t(N) * 8), s->mesh,
+                          green_coef(s), wg_part(s), s->stream));
+    }
+    s->wg_count = spec_z_tiles(N);
+    {
+      PROF(s, PM_STAGE_FFT_C2R);
+      CF(s, cufftExecC2R(s->plan2_inv, (cufftComplex*)(s->arena + L.spec), s->at<cufftReal>(L.phi)));
+    }
+    PMST(quantum_stage<R>(s));
+    s->fields_valid = true;
+    return PM_OK;
+  }
   PMST(fft_r2c<R>(s, s->arena + density_field(s), s->arena + L.spec));
   {
     PROF(s, PM_STAGE_GREEN);
@@ -584,6 +671,7 @@ pm_status mesh_from_density(pm_sim* s) {
     else
       CU(s, launch_green<R>(s->arena + L.spec, s->mesh, green_coef(s), wg_part(s), s->stream));
   }
+  s->wg_count = MESH_GRID;
   PMST(fft_c2r<R>(s, s->arena + L.spec, s->arena + L.phi));
   PMST(quantum_stage<R>(s));
   s->fields_valid = true;
@@ -603,6 +691,7 @@ pm_status spline_fields(pm_sim* s) {
     CU(s, launch_green_spline<R>(s->arena + L.spec, s->direct ? nullptr : s->arena + L.spec2, s->arena + L.what,
                                  s->mesh, green_coef(s), wg_part(s), s->stream, 1));
   }
+  s->wg_count = MESH_GRID;
   if (s->direct)
     PMST(smooth_field<R>(s, L.rho, L.spec2));
   else
@@ -764,6 +853,7 @@ void to_public(const Tuning& t, pm_tuning* o) {
   o->stencil_stages = t.st_stages;
   o->kick_threads = t.kick_threads;
   o->deposit_warps = t.dep_warps;
+  o->green_fused = t.green_fused;
 }
 
 // drops the captured steps (they hold the launch shapes)
@@ -981,6 +1071,13 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     }
   }
   if (c->precision == PM_FP32) kick_stream_prepare();
+  // fp32 cloud-in-cell on power-of-two meshes: the Green multiplication inside the z transform
+  // (members of a packed batch class use the class's own transforms).  Where cuFFT refuses the 2D
+  // plans, the 3D transforms and the separate pass stay.
+  if (c->precision == PM_FP32 && c->kernel == PM_KERNEL_CIC && spec_z_supported(N) && !g_batch_member) {
+    std::string ignored;
+    if (spec_plan_setup(s, &ignored) == CUFFT_SUCCESS) s->tune.green_fused = 1;
+  }
   if (s->cfg.kernel == PM_KERNEL_SPLINE) {
     s->direct = c->smooth_real != 0;
     spline_taps(c->smooth_h, s->taps);
@@ -1017,6 +1114,10 @@ pm_status pm_destroy(pm_sim* s) {
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   cufftDestroy(s->plan_fwd);
   cufftDestroy(s->plan_inv);
+  if (s->have_plan2) {
+    cufftDestroy(s->plan2_fwd);
+    cufftDestroy(s->plan2_inv);
+  }
   delete s;
   return PM_OK;
 }
@@ -1203,6 +1304,10 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
     s->stream = s->cap;
     CF(s, cufftSetStream(s->plan_fwd, s->cap));
     CF(s, cufftSetStream(s->plan_inv, s->cap));
+    if (s->have_plan2) {
+      CF(s, cufftSetStream(s->plan2_fwd, s->cap));
+      CF(s, cufftSetStream(s->plan2_inv, s->cap));
+    }
     // graphs for the present state and for the other record buffer (the state
     // after an odd number of steps); capturing executes nothing, so the host
     // state is flipped for the second capture and restored
@@ -1246,6 +1351,10 @@ pm_status pm_run(pm_sim* s, int32_t nsteps, double a_start, double a_end) {
     s->stream = user;
     cufftSetStream(s->plan_fwd, user);
     cufftSetStream(s->plan_inv, user);
+    if (s->have_plan2) {
+      cufftSetStream(s->plan2_fwd, user);
+      cufftSetStream(s->plan2_inv, user);
+    }
     if (st != PM_OK) return st;
     if (ec != cudaSuccess) return fail(s, PM_ERR_CUDA, "captured steps: %s", cudaGetErrorString(ec));
     // the replays leave the state as it was before them (two sorts per graph),
@@ -1281,7 +1390,7 @@ pm_status pm_energy(pm_sim* s, double a, double out[6]) {
   const int nkb = kick_blocks(s->n(), s->tune.kick_threads);
   double* red = s->red();
   CU(s, launch_reduce(s->part(), nkb, 4, red, s->stream));
-  CU(s, launch_reduce(wg_part(s), MESH_GRID, 1, red + 4, s->stream));
+  CU(s, launch_reduce(wg_part(s), s->wg_count, 1, red + 4, s->stream));
   if (s->cfg.quantum) CU(s, launch_reduce(kr_part(s), kr_blocks(s), 1, red + 5, s->stream));
   double h[6];
   CU(s, cudaMemcpyAsync(h, red, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -1396,7 +1505,17 @@ pm_status pm_set_tuning(pm_sim* s, const pm_tuning* t) {
   if (!stencil_shape_ok(n, t->stencil_rows, t->stencil_planes, t->stencil_stages))
     return fail(s, PM_ERR_INVALID_ARG, "stencil shape (%d rows, %d planes, %d stages) is not valid for N = %d",
                 t->stencil_rows, t->stencil_planes, t->stencil_stages, n);
+  if (t->green_fused != 0 && t->green_fused != 1) return fail(s, PM_ERR_INVALID_ARG, "green_fused must be 0 or 1");
+  if (t->green_fused && (s->fp64() || spline(s) || !spec_z_supported(s->cfg.n_mesh)))
+    return fail(s, PM_ERR_INVALID_ARG, "green_fused needs PM_FP32, the cloud-in-cell kernel and a power-of-two mesh");
   drop_graphs(s);
+  if (t->green_fused) {
+    std::string why;
+    const cufftResult r = spec_plan_setup(s, &why);
+    if (r != CUFFT_SUCCESS)
+      return fail(s, PM_ERR_CUFFT, "batched 2D transforms: %s failed (%d)", why.c_str(), int(r));
+  }
+  s->tune.green_fused = t->green_fused;
   s->tune.st_ty = t->stencil_rows;
   s->tune.st_zlen = t->stencil_rows ? t->stencil_planes : 0;
   s->tune.st_stages = t->stencil_rows ? t->stencil_stages : 0;
@@ -1714,6 +1833,7 @@ pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cuda
     m->sorted = true;
     m->fields_valid = true;
     m->krho_valid = false;
+    m->wg_count = MESH_GRID;
   }
   return PM_OK;
 }
@@ -1762,6 +1882,9 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(PM_ERR_CUDA, "event or stream creation failed");
   b->sims.assign(n, nullptr);
+  std::vector<char> packed_member(n, 0);
+  for (const BatchClass& BC : L.classes)
+    for (int m : BC.members) packed_member[m] = BC.packed;
   for (int i = 0; i < n; ++i) {
     cudaStream_t st2;
     cudaEvent_t ev;
@@ -1772,7 +1895,9 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
       return cleanup(PM_ERR_CUDA, "event creation failed");
     b->join.push_back(ev);
     pm_sim* s = nullptr;
+    g_batch_member = packed_member[i] != 0;
     pm_status r = pm_create(&cfgs[i], b->arena + L.off[i], L.bytes[i], st2, &s);
+    g_batch_member = false;
     if (r != PM_OK) return cleanup(r, "member " + std::to_string(i) + ": " + g_create_error);
     b->sims[i] = s;
   }

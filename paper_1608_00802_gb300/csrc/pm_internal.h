@@ -63,6 +63,7 @@ struct Tuning {
   int st_ty, st_zlen, st_stages;  // fp32 compact stencil tiles (see StencilParams)
   int kick_threads;               // 128 or 256
   int dep_warps;                  // mesh rows (one warp each) per deposit block, 1..8
+  int green_fused;                // fp32 cloud-in-cell: the Green multiplication inside the z transform
 };
 constexpr int KICK_MIN_THREADS = 128;
 
@@ -75,6 +76,17 @@ template <typename T>
 __host__ __device__ __forceinline__ T* moff(T* p, size_t off) {
   return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + off) : p;
 }
+
+// The Green multiplication between batched 2D transforms (fp32 cloud-in-cell,
+// N a power of two in [16, 512]): one kernel transforms the half spectrum's
+// columns along z, multiplies by the Green's function and transforms back;
+// tiles of 16 columns, one W_g partial per tile.
+bool spec_z_supported(int n);
+int spec_z_tiles(int n);
+// exp(-2 pi i t / N) for t < N (rounded from fp64) and sin^2(pi t / N) as k_green computes it
+cudaError_t launch_spec_tables(float2* tw, float* s2, int n, cudaStream_t s);
+cudaError_t launch_spec_z(void* spec, const float2* tw, const float* s2, Mesh m, double coef, double* part,
+                          cudaStream_t s, const double* coefp = nullptr, int nm = 1, size_t ms = 0);
 
 // error bits of the device error word
 enum : uint32_t { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };

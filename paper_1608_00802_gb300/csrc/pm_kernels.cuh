@@ -466,6 +466,187 @@ __global__ void __launch_bounds__(MESH_THREADS) k_green(typename VT<R>::cplx* sp
   block_sum_store<1>(acc, part, gridDim.x);
 }
 
+// ---------------------------------------------------------------- Green's function inside the z transform
+// With the x and y transforms done plane by plane (batched 2D cuFFT), the z
+// transform, the Green multiplication and the inverse z transform of one
+// column of the half spectrum need nothing but that column: one kernel does
+// all three in shared memory, so the spectrum crosses HBM once (read + write)
+// between the two 2D transforms instead of three times (3D forward's last
+// pass, k_green, 3D inverse's first pass).
+//
+// A z column of N = P Q points is transformed in two steps (the four-step
+// factorisation, n = j + P m, k = k1 + Q k2):
+//   X[k1 + Q k2] = sum_j W_P^{j k2} W_N^{j k1} sum_m x[j + P m] W_Q^{m k1},
+// so thread j does a Q-point DFT over m and the twiddle W_N^{j k1}, and, after
+// one exchange through shared memory, thread k1 a P-point DFT over j.  The
+// inverse runs the same steps backwards with conjugate twiddles; the thread
+// that ends the forward transform holds X[k1 + Q k2] for every k2, so it
+// multiplies by G and starts the inverse without an exchange.  A block owns 16
+// adjacent columns of the flattened (ky, kx) plane (128 contiguous bytes per z
+// row: every global access is a full segment).
+
+// exp(2 pi i t / 32) for t < 32: the twiddles of the in-register DFTs
+__device__ constexpr float kCos32[32] = {
+    1.0f,          0.980785251f,  0.923879504f,  0.831469595f,  0.707106769f,  0.555570245f,  0.382683426f,
+    0.195090324f,  0.0f,          -0.195090324f, -0.382683426f, -0.555570245f, -0.707106769f, -0.831469595f,
+    -0.923879504f, -0.980785251f, -1.0f,         -0.980785251f, -0.923879504f, -0.831469595f, -0.707106769f,
+    -0.555570245f, -0.382683426f, -0.195090324f, 0.0f,          0.195090324f,  0.382683426f,  0.555570245f,
+    0.707106769f,  0.831469595f,  0.923879504f,  0.980785251f};
+__device__ constexpr float kSin32[32] = {
+    0.0f,          0.195090324f,  0.382683426f,  0.555570245f,  0.707106769f,  0.831469595f,  0.923879504f,
+    0.980785251f,  1.0f,          0.980785251f,  0.923879504f,  0.831469595f,  0.707106769f,  0.555570245f,
+    0.382683426f,  0.195090324f,  0.0f,          -0.195090324f, -0.382683426f, -0.555570245f, -0.707106769f,
+    -0.831469595f, -0.923879504f, -0.980785251f, -1.0f,         -0.980785251f, -0.923879504f, -0.831469595f,
+    -0.707106769f, -0.555570245f, -0.382683426f, -0.195090324f};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+// a * exp(-+2 pi i t / 32) (forward: minus), t < 16 known at compile time after unrolling
+template <bool INV>
+__device__ __forceinline__ float2 twiddle32(float2 a, int t) {
+  if (t == 0) return a;
+  if (t == 8) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);  // times +i / -i
+  constexpr float h = 0.707106769f;                                           // cos(pi / 4)
+  if (t == 4) return INV ? make_float2(h * (a.x - a.y), h * (a.x + a.y)) : make_float2(h * (a.x + a.y), h * (a.y - a.x));
+  if (t == 12)
+    return INV ? make_float2(-h * (a.x + a.y), h * (a.x - a.y)) : make_float2(h * (a.y - a.x), -h * (a.x + a.y));
+  return cmul(a, make_float2(kCos32[t], INV ? kSin32[t] : -kSin32[t]));
+}
+
+// In-register DFT of M <= 32 points, radix-2 decimation in frequency: natural
+// order in, bit-reversed order out (a[bitrev(k)] = X[k]); INV: exp(+2 pi i nk/M).
+template <int M, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&a)[M]) {
+#pragma unroll
+  for (int len = M; len >= 2; len >>= 1) {
+    const int half = len >> 1;
+#pragma unroll
+    for (int b = 0; b < M; b += len) {
+#pragma unroll
+      for (int j = 0; j < half; ++j) {
+        const float2 u = a[b + j], v = a[b + j + half];
+        a[b + j] = make_float2(u.x + v.x, u.y + v.y);
+        a[b + j + half] = twiddle32<INV>(make_float2(u.x - v.x, u.y - v.y), j * (32 / len));
+      }
+    }
+  }
+}
+
+template <int M>
+__host__ __device__ constexpr int bitrev(int k) {
+  int r = 0;
+  for (int b = 1; b < M; b <<= 1) {
+    r <<= 1;
+    if (k & b) r |= 1;
+  }
+  return r;
+}
+
+constexpr int SPZ_COLS = 16;  // z columns per block (16 complex = 128 bytes per z row)
+#ifndef PM_SPZ_MINB
+#define PM_SPZ_MINB 4  // resident blocks of up to 256 threads the z kernel is compiled for
+#endif
+
+// exp(-2 pi i t / N) from fp64 sincospi, and k_green's sin^2(pi t / N)
+static __global__ void k_spec_tables(float2* tw, float* s2, int n) {
+  const float inv_n = 1.0f / float(n);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    double sv, cv;
+    sincospi(2.0 * double(t) / double(n), &sv, &cv);
+    tw[t] = make_float2(float(cv), float(-sv));
+    s2[t] = sinpi_sq(float(t) * inv_n);
+  }
+}
+
+// z transform, phi^ = G rho^ (with k_green's arithmetic and Parseval partial
+// of W_g), inverse z transform, over 16 columns of the flattened (ky, kx)
+// half plane per block; N = P Q, P >= Q, 16 P threads.  coefp (packed
+// groups): the coefficient in device memory, member blockIdx.y, ms bytes apart.
+template <int P, int Q, bool PACKED>
+__global__ void __launch_bounds__(SPZ_COLS * P, SPZ_COLS * P <= 256 ? PM_SPZ_MINB : 1) k_spec_z(float2* __restrict__ spec, const float2* __restrict__ twg,
+                                                         const float* __restrict__ s2g, float coef, double* part,
+                                                         const double* coefp, size_t ms) {
+  constexpr int N = P * Q, T = SPZ_COLS * P;
+  constexpr uint32_t NH = N / 2 + 1, PLANE = uint32_t(N) * NH;
+  if constexpr (PACKED) {
+    const size_t o = size_t(blockIdx.y) * ms;
+    spec = moff(spec, o), part = moff(part, o);
+    coef = float(*moff(coefp, o));
+  }
+  extern __shared__ __align__(16) unsigned char spz_smem[];
+  float2* tile = reinterpret_cast<float2*>(spz_smem);  // [z][16 columns]
+  float2* tw = tile + N * SPZ_COLS;
+  float* s2 = reinterpret_cast<float*>(tw + N);
+  const int tid = threadIdx.x;
+  const uint32_t col0 = blockIdx.x * SPZ_COLS;
+  for (int i = tid; i < N * 8; i += T) {
+    const int r = i >> 3, q = i & 7;
+    reinterpret_cast<float4*>(tile + r * SPZ_COLS)[q] =
+        __ldg(reinterpret_cast<const float4*>(spec + size_t(r) * PLANE + col0) + q);
+  }
+  for (int i = tid; i < N; i += T) {
+    tw[i] = twg[i];
+    s2[i] = s2g[i];
+  }
+  __syncthreads();
+  const int c = tid & (SPZ_COLS - 1), jt = tid / SPZ_COLS;
+  {  // forward, first step: thread j, Q-point DFT over m, twiddle W_N^{j k1}
+    float2 a[Q];
+#pragma unroll
+    for (int mm = 0; mm < Q; ++mm) a[mm] = tile[(jt + P * mm) * SPZ_COLS + c];
+    dft_reg<Q, false>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1)
+      tile[(jt + P * k1) * SPZ_COLS + c] = cmul(a[bitrev<Q>(k1)], tw[(jt * k1) & (N - 1)]);
+  }
+  __syncthreads();
+  float wsum = 0.0f;
+  if (jt < Q) {  // thread k1: P-point DFT over j, Green, inverse P-point DFT, conjugate twiddle
+    const int k1 = jt;
+    float2 b[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) b[j] = tile[(j + P * k1) * SPZ_COLS + c];
+    dft_reg<P, false>(b);
+    const uint32_t col = col0 + uint32_t(c), ky = col / NH, kx = col - ky * NH;
+    const float sx = s2[kx], sy = s2[ky];
+    const float w = (kx == 0 || kx == N / 2) ? 1.0f : 2.0f;
+    float2 d[P];
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) {
+      const int kz = k1 + Q * k2;
+      float2 v = b[bitrev<P>(k2)];
+      const float syz = sy + s2[kz];
+      const float sum = syz + sx;
+      const float g = (ky == 0 && kz == 0 && kx == 0) ? 0.0f : coef * __frcp_rn(sum);
+      wsum += w * g * (v.x * v.x + v.y * v.y);
+      d[k2] = make_float2(v.x * g, v.y * g);
+    }
+    dft_reg<P, true>(d);
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      const float2 t = tw[(j * k1) & (N - 1)];
+      tile[(j + P * k1) * SPZ_COLS + c] = cmul(d[bitrev<P>(j)], make_float2(t.x, -t.y));
+    }
+  }
+  __syncthreads();
+  {  // inverse, second step: thread j, inverse Q-point DFT over k1
+    float2 e[Q];
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) e[k1] = tile[(jt + P * k1) * SPZ_COLS + c];
+    dft_reg<Q, true>(e);
+#pragma unroll
+    for (int mm = 0; mm < Q; ++mm) tile[(jt + P * mm) * SPZ_COLS + c] = e[bitrev<Q>(mm)];
+  }
+  __syncthreads();
+  for (int i = tid; i < N * 8; i += T) {
+    const int r = i >> 3, q = i & 7;
+    reinterpret_cast<float4*>(spec + size_t(r) * PLANE + col0)[q] = reinterpret_cast<const float4*>(tile + r * SPZ_COLS)[q];
+  }
+  float acc[1] = {wsum};
+  block_sum_store<1>(acc, part, gridDim.x);
+}
+
 // ---------------------------------------------------------------- cubic spline kernel
 // The cubic spline W(r, h) of Sec. II.A on the mesh: its weights W(|x_n|, h) dx^3
 // at the node offsets (periodic minimum image; with h = hc dx they are
@@ -1696,6 +1877,20 @@ cudaError_t launch_green(void* spec, Mesh m, double coef, double* part, cudaStre
   else
     k_green<R, false><<<MESH_GRID, MESH_THREADS, m.n * sizeof(R), s>>>(
         (C*)spec, m, R(coef), divu32_make(uint32_t(m.n / 2 + 1)), part, nullptr, 0);
+  return cudaGetLastError();
+}
+
+template <int P, int Q>
+cudaError_t launch_spec_z_pq(float2* spec, const float2* tw, const float* s2, double coef, double* part,
+                             cudaStream_t s, const double* coefp, int nm, size_t ms) {
+  constexpr int N = P * Q;
+  const size_t smem = size_t(N) * (SPZ_COLS * sizeof(float2) + sizeof(float2) + sizeof(float));
+  const unsigned tiles = unsigned(N * (N / 2 + 1) / SPZ_COLS);
+  if (nm > 1)
+    k_spec_z<P, Q, true><<<dim3(tiles, unsigned(nm)), SPZ_COLS * P, smem, s>>>(spec, tw, s2, float(coef), part, coefp,
+                                                                             ms);
+  else
+    k_spec_z<P, Q, false><<<tiles, SPZ_COLS * P, smem, s>>>(spec, tw, s2, float(coef), part, nullptr, 0);
   return cudaGetLastError();
 }
 

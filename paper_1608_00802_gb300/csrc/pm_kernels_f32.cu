@@ -58,6 +58,7 @@ Tuning default_tuning(int n) {
   Tuning t;
   t.kick_threads = KICK_THREADS;
   t.dep_warps = 8;
+  t.green_fused = 0;
   // one-shot tiles of 4 rows x 4 planes where they fit (the multiple-of-4 meshes up to 1024)
   if (stencil_tile_shape_ok(n, 4, 4)) {
     t.st_ty = 4;
@@ -94,5 +95,43 @@ cudaError_t launch_reduce(const double* part, int nblocks, int nvals, double* ou
 
 PM_INSTANTIATE(float)
 template cudaError_t launch_smooth_direct<float>(const float*, float*, Mesh, const double*, int, cudaStream_t);
+
+
+// ---------------------------------------------------------------- Green's function inside the z transform
+bool spec_z_supported(int n) { return n >= 16 && n <= 512 && (n & (n - 1)) == 0; }
+int spec_z_tiles(int n) { return n * (n / 2 + 1) / SPZ_COLS; }
+
+cudaError_t launch_spec_tables(float2* tw, float* s2, int n, cudaStream_t s) {
+  if (!spec_z_supported(n)) return cudaErrorInvalidValue;
+  // the 512-point blocks take 70 KB of shared memory (set once, outside any stream capture)
+  static bool done[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !done[dev]) {
+    const int most = 512 * int(SPZ_COLS * sizeof(float2) + sizeof(float2) + sizeof(float));
+    e = cudaFuncSetAttribute(k_spec_z<32, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_spec_z<32, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+  }
+  k_spec_tables<<<(n + 255) / 256, 256, 0, s>>>(tw, s2, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_z(void* spec, const float2* tw, const float* s2, Mesh m, double coef, double* part,
+                          cudaStream_t s, const double* coefp, int nm, size_t ms) {
+  float2* sp = static_cast<float2*>(spec);
+  switch (m.n) {
+    case 16: return launch_spec_z_pq<4, 4>(sp, tw, s2, coef, part, s, coefp, nm, ms);
+    case 32: return launch_spec_z_pq<8, 4>(sp, tw, s2, coef, part, s, coefp, nm, ms);
+    case 64: return launch_spec_z_pq<8, 8>(sp, tw, s2, coef, part, s, coefp, nm, ms);
+    case 128: return launch_spec_z_pq<16, 8>(sp, tw, s2, coef, part, s, coefp, nm, ms);
+    case 256: return launch_spec_z_pq<16, 16>(sp, tw, s2, coef, part, s, coefp, nm, ms);
+    case 512: return launch_spec_z_pq<32, 16>(sp, tw, s2, coef, part, s, coefp, nm, ms);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 }  // namespace pm

@@ -50,7 +50,7 @@ class pm_config(C.Structure):
 
 class pm_tuning(C.Structure):
     _fields_ = [("stencil_rows", C.c_int32), ("stencil_planes", C.c_int32), ("stencil_stages", C.c_int32),
-                ("kick_threads", C.c_int32), ("deposit_warps", C.c_int32)]
+                ("kick_threads", C.c_int32), ("deposit_warps", C.c_int32), ("green_fused", C.c_int32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -313,7 +313,10 @@ class Sim:
         return t.as_dict()
 
     def set_tuning(self, shapes):
-        t = pm_tuning.from_dict(shapes)
+        """Sets the launch shapes; keys missing from `shapes` keep their values."""
+        cur = self.get_tuning()
+        cur.update(shapes)
+        t = pm_tuning.from_dict(cur)
         self._check(lib().pm_set_tuning(self.handle, C.byref(t)))
 
     def autotune(self, reps=5, cache=None):
