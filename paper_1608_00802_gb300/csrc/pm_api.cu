@@ -21,8 +21,6 @@ using namespace pm;
 namespace {
 
 thread_local std::string g_create_error;
-// set while a batch creates a member that its class steps packed (with the class's own transforms)
-thread_local bool g_batch_member = false;
 
 // ---------------------------------------------------------------- units
 // hbar/m in (Mpc/h)^2 H0: (hbar c) c / (m c^2), with one code unit of
@@ -918,7 +916,7 @@ pm_status autotune(pm_sim* s, int reps) {
         }
     s->tune = best;
   }
-  // deposit: rows (warps) per block
+  // deposit: warps per tile of mesh rows
   {
     double tbest = -1.0;
     for (int w : {2, 4, 8}) {
@@ -1071,10 +1069,11 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
     }
   }
   if (c->precision == PM_FP32) kick_stream_prepare();
-  // fp32 cloud-in-cell on power-of-two meshes: the Green multiplication inside the z transform
-  // (members of a packed batch class use the class's own transforms).  Where cuFFT refuses the 2D
-  // plans, the 3D transforms and the separate pass stay.
-  if (c->precision == PM_FP32 && c->kernel == PM_KERNEL_CIC && spec_z_supported(N) && !g_batch_member) {
+  // fp32 cloud-in-cell on power-of-two meshes from 128^3: the Green multiplication inside the z
+  // transform (smaller meshes keep the 3D transforms, which a packed batch class batches over its
+  // members; pm_set_tuning turns it on there).  Where cuFFT refuses the 2D plans, the 3D transforms
+  // and the separate pass stay.
+  if (c->precision == PM_FP32 && c->kernel == PM_KERNEL_CIC && spec_z_supported(N) && N >= GREEN_FUSE_MIN_MESH) {
     std::string ignored;
     if (spec_plan_setup(s, &ignored) == CUFFT_SUCCESS) s->tune.green_fused = 1;
   }
@@ -1772,9 +1771,10 @@ bool same_state(const pm_batch::Class& C, const std::vector<pm_sim*>& sims) {
         s->keys_marked != a->keys_marked || (s->keys - s->at<uint32_t>(0)) != (a->keys - a->at<uint32_t>(0)) ||
         s->tune.st_ty != a->tune.st_ty || s->tune.st_zlen != a->tune.st_zlen ||
         s->tune.st_stages != a->tune.st_stages || s->tune.kick_threads != a->tune.kick_threads ||
-        s->tune.dep_warps != a->tune.dep_warps)
+        s->tune.dep_warps != a->tune.dep_warps || green_fused(s) != green_fused(a))
       return false;
   }
+  if (!green_fused(a) && !C.fwd) return false;  // the class's batched 3D transforms were not planned
   const StencilParams sp = stencil_params(a, false);
   return !a->cfg.quantum || (a->tune.st_ty > 0 && a->tune.st_stages == 0 && stencil_shape_ok(a->cfg.n_mesh, sp.ty, sp.zlen, 0));
 }
@@ -1816,11 +1816,31 @@ pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cuda
   // deposit, potential, quantum pressure
   PCU(launch_deposit<float>(s->arena + L.pos[nxt], s->at<uint32_t>(L.row_start), n, s->mesh, s->norm,
                             s->at<float>(L.rho), st, s->tune.dep_warps, nm, ms));
-  CF(s, cufftSetStream(C.fwd, st));
-  CF(s, cufftSetStream(C.inv, st));
-  CF(s, cufftExecR2C(C.fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
-  PCU(launch_green<float>(s->arena + L.spec, s->mesh, green_coef(s), wg_part(s), st, s->coefs(), nm, ms));
-  CF(s, cufftExecC2R(C.inv, (cufftComplex*)(s->arena + L.spec), s->at<cufftReal>(L.phi)));
+  const bool fused = green_fused(s);
+  if (fused) {  // each member's own 2D transforms (the same as alone), the z kernel over the whole class
+    for (int i : C.members) {
+      pm_sim* m = sims[i];
+      CF(s, cufftSetStream(m->plan2_fwd, st));
+      const cufftResult r = cufftExecR2C(m->plan2_fwd, m->at<cufftReal>(L.rho), (cufftComplex*)(m->arena + L.spec));
+      CF(s, cufftSetStream(m->plan2_fwd, m->stream));
+      CF(s, r);
+    }
+    PCU(launch_spec_z(s->arena + L.spec, s->at<float2>(L.green), s->at<float>(L.green + size_t(N) * 8), s->mesh,
+                      green_coef(s), wg_part(s), st, s->coefs(), nm, ms));
+    for (int i : C.members) {
+      pm_sim* m = sims[i];
+      CF(s, cufftSetStream(m->plan2_inv, st));
+      const cufftResult r = cufftExecC2R(m->plan2_inv, (cufftComplex*)(m->arena + L.spec), m->at<cufftReal>(L.phi));
+      CF(s, cufftSetStream(m->plan2_inv, m->stream));
+      CF(s, r);
+    }
+  } else {
+    CF(s, cufftSetStream(C.fwd, st));
+    CF(s, cufftSetStream(C.inv, st));
+    CF(s, cufftExecR2C(C.fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
+    PCU(launch_green<float>(s->arena + L.spec, s->mesh, green_coef(s), wg_part(s), st, s->coefs(), nm, ms));
+    CF(s, cufftExecC2R(C.inv, (cufftComplex*)(s->arena + L.spec), s->at<cufftReal>(L.phi)));
+  }
   if (s->cfg.quantum)
     PCU(launch_stencil<float>(s->at<float>(L.rho), s->mesh, stencil_params(s, false), s->at<float>(L.q), kr_part(s),
                               s->at<uint32_t>(L.st_list), s->at<uint32_t>(L.st_count), s->errword(), st,
@@ -1833,7 +1853,7 @@ pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cuda
     m->sorted = true;
     m->fields_valid = true;
     m->krho_valid = false;
-    m->wg_count = MESH_GRID;
+    m->wg_count = fused ? spec_z_tiles(N) : MESH_GRID;
   }
   return PM_OK;
 }
@@ -1882,9 +1902,6 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(PM_ERR_CUDA, "event or stream creation failed");
   b->sims.assign(n, nullptr);
-  std::vector<char> packed_member(n, 0);
-  for (const BatchClass& BC : L.classes)
-    for (int m : BC.members) packed_member[m] = BC.packed;
   for (int i = 0; i < n; ++i) {
     cudaStream_t st2;
     cudaEvent_t ev;
@@ -1895,9 +1912,7 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
       return cleanup(PM_ERR_CUDA, "event creation failed");
     b->join.push_back(ev);
     pm_sim* s = nullptr;
-    g_batch_member = packed_member[i] != 0;
     pm_status r = pm_create(&cfgs[i], b->arena + L.off[i], L.bytes[i], st2, &s);
-    g_batch_member = false;
     if (r != PM_OK) return cleanup(r, "member " + std::to_string(i) + ": " + g_create_error);
     b->sims[i] = s;
   }
@@ -1911,7 +1926,7 @@ pm_status pm_batch_create(const pm_config* cfgs, int32_t n, void* dev_arena, siz
       b->classes.push_back(C);
       return cleanup(PM_ERR_CUDA, "class stream creation failed");
     }
-    if (C.packed) {
+    if (C.packed && !green_fused(b->sims[C.members[0]])) {  // fused members transform with their own 2D plans
       size_t w = 0;
       const pm_config& c = cfgs[C.members[0]];
       if (class_plans(c, int(C.members.size()), C.stride, &C.fwd, &C.inv, &w) != CUFFT_SUCCESS || w > BC.work ||

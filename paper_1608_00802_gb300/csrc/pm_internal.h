@@ -62,9 +62,11 @@ struct StencilParams {
 struct Tuning {
   int st_ty, st_zlen, st_stages;  // fp32 compact stencil tiles (see StencilParams)
   int kick_threads;               // 128 or 256
-  int dep_warps;                  // mesh rows (one warp each) per deposit block, 1..8
+  int dep_warps;                  // warps per deposit block (one block per tile of mesh rows), 1..8
   int green_fused;                // fp32 cloud-in-cell: the Green multiplication inside the z transform
 };
+// smallest mesh whose simulations take the Green multiplication inside the z transform by default
+constexpr int GREEN_FUSE_MIN_MESH = 128;
 constexpr int KICK_MIN_THREADS = 128;
 
 // Packed groups of simulations: member m of a group of equal configurations

@@ -266,53 +266,67 @@ __global__ void k_init_particles(const double* __restrict__ x, const double* __r
 
 // ---------------------------------------------------------------- cloud-in-cell deposit
 // rho_n = norm * sum_i W(x_n - q_i): Eq. (rhodis) with the cloud-in-cell
-// tent, no floating-point atomics.  One warp owns one mesh row (z, y) and
-// keeps it in shared memory (N + 1 slots, slot N = node 0 seen from cell
-// N-1).  For each of the four source rows (z - dz, y - dy) it loads that
-// row's particles 32 at a time (they are contiguous after the sort) and adds
-// the x-weights f_x (to node c + 1) and 1 - f_x (to node c), times the y and z
-// weights, through a segmented warp scan: lanes with the same target node are
-// adjacent, the scan sums each run in a fixed tree order and the run's last
-// lane adds it to the node.  The order of all additions is fixed by the
-// particle order, so the result is reproducible.
+// tent, no floating-point atomics.  A warp owns a column of TZ mesh rows
+// (z0 .. z0 + TZ - 1, y) and keeps them in shared memory (N + 1 slots per
+// row, slot N = node 0 seen from cell N-1).  A particle of source row
+// (z', y') adds to the rows (z' + dz, y' + dy), dz, dy in {0, 1}, so the
+// warp reads the 2 (TZ + 1) source rows (z0 - 1 .. z0 + TZ - 1, y - 1 .. y)
+// (each particle about 2 + 2/TZ times instead of 4 with one row per warp) and
+// adds both of a source row's destination rows' x-weights (f_x to node c + 1,
+// 1 - f_x to node c, times the y and z weights) through one segmented warp
+// scan: lanes with the same cell are adjacent after the sort, the scan sums
+// each run in a fixed tree order and the run's last lane adds the sums to the
+// nodes.  The warp alone writes its rows, in a fixed order of source rows and
+// of particles within them, so the result is reproducible.
 constexpr int DEP_WARPS = 8;
 
-// Both halves of a batch's x-weights in one segmented scan: the particles of
-// a lane's cell t (sorted, so cells form runs of lanes) sum their f_x shares
-// (for node t+1) and 1 - f_x shares (for node t); the last lane of each run
-// adds them, first every run's f_x sum, then every run's 1 - f_x sum (the
-// same order, and the same bits, as two separate scans).  Lanes with `valid`
-// false carry unique targets past the row.
-// The scan stops after the steps the longest run needs (a batch of distinct
-// cells, the common case on a mesh of several cells per particle, takes none);
-// the steps it skips would add nothing, so the sums are the same bits.
+// One batch of 32 records: the segmented sums of the x-weights of the two
+// destination rows (acc + dst[d]; dst[d] < 0: the row is outside the column),
+// hi (f_x, to node t + 1) first, then lo (1 - f_x, to node t).  Lanes with
+// `valid` false carry unique targets past the row.  The scan stops after the
+// steps the longest run needs (a batch of distinct cells, the common case on
+// a mesh of several cells per particle, takes none); the skipped steps would
+// add nothing, so the sums are the same bits.
 template <typename R>
-__device__ __forceinline__ void seg_add2(R lo, R hi, int t, bool valid, R* acc) {
+__device__ __forceinline__ void seg_add_rows(R (&lo)[2], R (&hi)[2], int t, bool valid, R* acc, const int (&dst)[2]) {
   const int lane = threadIdx.x & 31;
   const int tp = __shfl_up_sync(0xffffffffu, t, 1);
   const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || tp != t);
-  // length of the run that starts at this lane (0 elsewhere), and the longest
-  const uint32_t above = heads & ~((2u << lane) - 1u);
-  const int len = ((heads >> lane) & 1u) ? (above ? __ffs(above) - 1 : 32) - lane : 0;
-  const int longest = int(__reduce_max_sync(0xffffffffu, uint32_t(len)));
-  for (int off = 1; off < longest; off <<= 1) {
-    const R ulo = __shfl_up_sync(0xffffffffu, lo, off);
-    const R uhi = __shfl_up_sync(0xffffffffu, hi, off);
-    // lane - off is in this lane's run iff no run starts in (lane - off, lane]
-    const uint32_t span = lane >= off ? ((2u << lane) - 1u) & ~((2u << (lane - off)) - 1u) : 0u;
-    if (lane >= off && !(heads & span)) {
-      lo += ulo;
-      hi += uhi;
+  if (heads != 0xffffffffu) {  // some cell holds several particles of the batch
+    // length of the run that starts at this lane (0 elsewhere), and the longest
+    const uint32_t above = heads & ~((2u << lane) - 1u);
+    const int len = ((heads >> lane) & 1u) ? (above ? __ffs(above) - 1 : 32) - lane : 0;
+    const int longest = int(__reduce_max_sync(0xffffffffu, uint32_t(len)));
+    for (int off = 1; off < longest; off <<= 1) {
+      R ulo[2], uhi[2];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        ulo[d] = __shfl_up_sync(0xffffffffu, lo[d], off);
+        uhi[d] = __shfl_up_sync(0xffffffffu, hi[d], off);
+      }
+      // lane - off is in this lane's run iff no run starts in (lane - off, lane]
+      const uint32_t span = lane >= off ? ((2u << lane) - 1u) & ~((2u << (lane - off)) - 1u) : 0u;
+      if (lane >= off && !(heads & span)) {
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          lo[d] += ulo[d];
+          hi[d] += uhi[d];
+        }
+      }
     }
   }
-  const bool last = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (valid && last) acc[t + 1] += hi;
+  const bool add = valid && (lane == 31 || ((heads >> (lane + 1)) & 1u));
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+    if (dst[d] >= 0 && add) acc[dst[d] + t + 1] += hi[d];
   __syncwarp();
-  if (valid && last) acc[t] += lo;
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+    if (dst[d] >= 0 && add) acc[dst[d] + t] += lo[d];
   __syncwarp();
 }
 
-template <typename R, bool PACKED>
+template <typename R, int TZ, bool PACKED>
 __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
                                                             const uint32_t* __restrict__ row_start, uint32_t np,
                                                             Mesh m, R norm, R* __restrict__ rho, size_t ms) {
@@ -322,47 +336,82 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
     pos = moff(pos, o), row_start = moff(row_start, o), rho = moff(rho, o);
   }
   extern __shared__ __align__(16) unsigned char dep_smem[];
-  const int n = m.n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t orow = blockIdx.x * (blockDim.x >> 5) + warp;  // z*N + y
-  if (orow >= m.n2) return;
-  R* acc = reinterpret_cast<R*>(dep_smem) + warp * (n + 1);
-  for (int i = lane; i <= n; i += 32) acc[i] = R(0);
+  const int n = m.n, stride = n + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int tiles_y = (n + nw - 1) / nw;
+  const int y = int(blockIdx.x % unsigned(tiles_y)) * nw + warp, z0 = int(blockIdx.x / unsigned(tiles_y)) * TZ;
+  if (y >= n) return;
+  const int tz = min(TZ, n - z0);
+  R* acc = reinterpret_cast<R*>(dep_smem) + warp * TZ * stride;  // [TZ][N + 1], this warp's
+  for (int i = lane; i < TZ * stride; i += 32) acc[i] = R(0);
   __syncwarp();
-  const int y = int(orow % uint32_t(n)), z = int(orow / uint32_t(n));
+  // the 2 (tz + 1) source rows k = 2 sz + (1 - dy): plane z0 - 1 + sz (to local rows sz - 1 with
+  // dz = 0 and sz with dz = 1), row y - dy; their bounds loaded at once, one per lane
+  const int nrows = 2 * (tz + 1);
+  uint32_t bk = 0, ek = 0;
+  if (lane < nrows) {
+    const uint32_t srow =
+        uint32_t(wrap(z0 - 1 + (lane >> 1), n)) * uint32_t(n) + uint32_t(wrap(y - 1 + (lane & 1), n));
+    bk = __ldg(row_start + srow);
+    ek = min(__ldg(row_start + srow + 1), np);
+  }
+  // batches of 32 records in row order, the next batch's records loaded while the current one is added
+  auto next_row = [&](int& kk, uint32_t& jj, uint32_t& ee) {
+    do {
+      ++kk;
+      jj = __shfl_sync(0xffffffffu, bk, kk & 31);
+      ee = __shfl_sync(0xffffffffu, ek, kk & 31);
+    } while (kk < nrows && jj >= ee);
+  };
+  int k = -1;
+  uint32_t j0 = 0, e = 0;
+  next_row(k, j0, e);
+  V4 rec = {};
+  if (k < nrows && j0 + lane < e) rec = ldg(pos + j0 + lane);
+  while (k < nrows) {
+    int k2 = k;
+    uint32_t j2 = j0 + 32, e2 = e;
+    if (j2 >= e) next_row(k2, j2, e2);
+    V4 rec2 = {};
+    if (k2 < nrows && j2 + lane < e2) rec2 = ldg(pos + j2 + lane);
+    const int sz = k >> 1, dy = 1 - (k & 1);
+    const int dst[2] = {sz >= 1 ? (sz - 1) * stride : -1, sz < tz ? sz * stride : -1};
+    const uint32_t base_cell =
+        (uint32_t(wrap(z0 - 1 + sz, n)) * uint32_t(n) + uint32_t(wrap(y - dy, n))) * uint32_t(n);
+    bool valid = j0 + lane < e;
+    R lo[2] = {R(0), R(0)}, hi[2] = {R(0), R(0)};
+    int c = n + 1 + lane;  // invalid lanes: unique targets past the row
+    if (valid) {
+      const uint32_t cx = rec_cell(rec) - base_cell;
+      // a record outside this row (only after a sort whose look-back timed
+      // out, which the error word reports) is skipped, not written out of bounds
+      valid = cx < uint32_t(n);
+      c = valid ? int(cx) : c;
+      const R wy = dy ? rec.z : R(1) - rec.z;
 #pragma unroll
-  for (int dz = 0; dz < 2; ++dz) {
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy) {
-      const uint32_t srow = uint32_t(wrap(z - dz, n)) * uint32_t(n) + uint32_t(wrap(y - dy, n));
-      const uint32_t base_cell = srow * uint32_t(n);
-      const uint32_t b = __ldg(row_start + srow);
-      const uint32_t e = min(__ldg(row_start + srow + 1), np);
-      for (uint32_t j0 = b; j0 < e; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        bool valid = j < e;
-        R lo = R(0), hi = R(0);
-        int c = n + 1 + lane;  // invalid lanes: unique targets past the row
-        if (valid) {
-          const V4 r = ldg(pos + j);
-          const uint32_t cx = rec_cell(r) - base_cell;
-          // a record outside this row (only after a sort whose look-back timed
-          // out, which the error word reports) is skipped, not written out of bounds
-          valid = cx < uint32_t(n);
-          c = valid ? int(cx) : c;
-          const R wyz = (dy ? r.z : R(1) - r.z) * (dz ? r.w : R(1) - r.w);
-          hi = r.y * wyz;
-          lo = (R(1) - r.y) * wyz;
-        }
-        // f_x to the node above (slot N = node 0), 1 - f_x to the node of the cell
-        seg_add2(lo, hi, c, valid, acc);
+      for (int d = 0; d < 2; ++d) {
+        const R wyz = wy * (d ? rec.w : R(1) - rec.w);
+        hi[d] = rec.y * wyz;
+        lo[d] = (R(1) - rec.y) * wyz;
       }
     }
+    seg_add_rows(lo, hi, c, valid, acc, dst);
+    k = k2, j0 = j2, e = e2, rec = rec2;
   }
-  if (lane == 0) acc[0] += acc[n];
-  __syncwarp();
-  R* out = rho + size_t(orow) * n;
-  for (int i = lane; i < n; i += 32) out[i] = acc[i] * norm;
+  for (int lz = 0; lz < tz; ++lz) {
+    R* a = acc + lz * stride;
+    if (lane == 0) a[0] += a[n];
+    __syncwarp();
+    R* out = rho + (size_t(z0 + lz) * n + size_t(y)) * n;
+    if constexpr (sizeof(R) == 4) {
+      if ((n & 3) == 0) {  // 16-byte stores
+        for (int i = 4 * lane; i < n; i += 128)
+          *reinterpret_cast<float4*>(out + i) = make_float4(a[i] * norm, a[i + 1] * norm, a[i + 2] * norm, a[i + 3] * norm);
+        continue;
+      }
+    }
+    for (int i = lane; i < n; i += 32) out[i] = a[i] * norm;
+  }
 }
 
 // ---------------------------------------------------------------- Green's function
@@ -1781,33 +1830,55 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
   return cudaGetLastError();
 }
 
+// rows along z of a deposit column: the most of 4, 2, 1 whose rows fit 8.5 KB of shared memory per warp
+template <typename R>
+inline int deposit_tz(int n) {
+  for (int tz = 4; tz > 1; tz >>= 1)
+    if (size_t(tz) * (n + 1) * sizeof(R) <= size_t(8704)) return tz;
+  return 1;
+}
+
+template <typename R, int TZ>
+cudaError_t launch_deposit_tz(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
+                              cudaStream_t s, int warps, int nm, size_t ms) {
+  using V4 = typename VT<R>::v4;
+  const size_t smem = size_t(warps) * TZ * (m.n + 1) * sizeof(R);
+  const unsigned blocks = unsigned((m.n + warps - 1) / warps) * unsigned((m.n + TZ - 1) / TZ);
+  if (nm > 1)
+    k_deposit<R, TZ, true><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start,
+                                                                                 uint32_t(n), m, R(norm), rho, ms);
+  else
+    k_deposit<R, TZ, false><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho,
+                                                             0);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
                            cudaStream_t s, int warps, int nm, size_t ms) {
-  using V4 = typename VT<R>::v4;
   if (warps < 1 || warps > DEP_WARPS) warps = DEP_WARPS;
-  const size_t smem = size_t(warps) * (m.n + 1) * sizeof(R);
-  if (smem > 48 * 1024) {
-    // once per device, for the largest mesh, so that no attribute call falls inside a stream capture
+  const int tz = deposit_tz<R>(m.n);
+  if (size_t(warps) * tz * (m.n + 1) * sizeof(R) > 48 * 1024) {
+    // once per device, for every tile shape, so that no attribute call falls inside a stream capture
     static bool done[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !done[dev]) {
-      const int most = int(size_t(DEP_WARPS) * (1024 + 1) * sizeof(R));
-      cudaError_t e = cudaFuncSetAttribute(k_deposit<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_deposit<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      const int most = 68 * 1024;
+      cudaError_t e = cudaSuccess;
+      void* fns[6] = {(void*)k_deposit<R, 4, false>, (void*)k_deposit<R, 4, true>, (void*)k_deposit<R, 2, false>,
+                      (void*)k_deposit<R, 2, true>,  (void*)k_deposit<R, 1, false>, (void*)k_deposit<R, 1, true>};
+      for (void* f : fns)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
       if (e != cudaSuccess) return e;
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  const unsigned blocks = (m.n2 + warps - 1) / warps;
-  if (nm > 1)
-    k_deposit<R, true><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n),
-                                                                             m, R(norm), rho, ms);
-  else
-    k_deposit<R, false><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho, 0);
-  return cudaGetLastError();
+  switch (tz) {
+    case 4: return launch_deposit_tz<R, 4>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+    case 2: return launch_deposit_tz<R, 2>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+    default: return launch_deposit_tz<R, 1>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+  }
 }
 
 template <typename R>

@@ -38,8 +38,10 @@ def _sim(pm, n_side, n_mesh, box=1.0, seed=42, fused=None, **kw):
 
 
 def test_fused_by_default_where_it_applies(pm):
-    cases = [((8, 16), {}, 1), ((32, 64), {}, 1), ((24, 48), {}, 0), ((8, 8), {}, 0),
-             ((16, 32), {"precision": pm.FP64}, 0), ((16, 32), {"kernel": pm.KERNEL_SPLINE}, 0)]
+    """On by default for fp32 cloud-in-cell power-of-two meshes from 128^3 up;
+    smaller ones keep the 3D transforms (and take it through pm_set_tuning)."""
+    cases = [((32, 128), {}, 1), ((8, 16), {}, 0), ((32, 64), {}, 0), ((24, 48), {}, 0), ((8, 8), {}, 0),
+             ((16, 128), {"precision": pm.FP64}, 0), ((16, 128), {"kernel": pm.KERNEL_SPLINE}, 0)]
     for (n_side, n_mesh), kw, want in cases:
         sim, _, _ = _sim(pm, n_side, n_mesh, **kw)
         assert sim.get_tuning()["green_fused"] == want, (n_side, n_mesh, kw)
@@ -109,7 +111,7 @@ def test_fused_potential_of_plane_waves_in_closed_form(pm, n_mesh):
         ref += -1.5 * 0.3 * dx * dx / 4.0 * amp * c / s
     cfg = pm.make_config(8, N, box, force_mode=pm.FORCE_HYBRID)
     sim = pm.Sim(cfg)
-    assert sim.get_tuning()["green_fused"] == 1
+    sim.set_tuning({"green_fused": 1})
     x0 = np.random.default_rng(1).random((8, 3)) * box
     sim.set_particles(x0, np.zeros((8, 3)))
     sim.set_density(rho)
@@ -156,3 +158,34 @@ def test_fused_runs_follow_the_separate_pass(pm, quantum, nsteps):
     assert np.abs(d).max() < 1e-4 / 128
     assert np.abs(out[0][1] - out[1][1]).max() < 1e-5 * np.abs(out[1][1]).max()
     np.testing.assert_allclose(out[0][2][:3], out[1][2][:3], rtol=1e-5, atol=1e-12)
+
+
+def test_packed_batch_class_with_the_fusion_equals_single_runs(pm):
+    """Three members of one configuration class on 128^3 (different boxes,
+    masses and seeds) stepped by packed launches: each member's own 2D
+    transforms and one z kernel over the class, so every member ends on the
+    bits of the same simulation run alone."""
+    members = [(32, 128, 1.0, 2.5, 20), (32, 128, 2.0, 10.0, 21), (32, 128, 3.0, 1.0, 22)]
+    a0 = 1 / 101.0
+    a1 = np.array([1 / 90.0, 1 / 85.0, 1 / 95.0])
+    cfgs = [pm.make_config(n ** 3, N, box, m22=m22, force_mode=pm.FORCE_HYBRID) for n, N, box, m22, _ in members]
+    batch = pm.Batch(cfgs)
+    ics_ = [ics.zeldovich(n, N, box, a0, seed, m22=m22, amplitude=2.0) for n, N, box, m22, seed in members]
+    for mem, (x, p) in zip(batch.members, ics_):
+        mem.set_particles(x, p)
+    batch.run(4, a0, a1)
+    assert batch.info() == (1, 3)
+    for i, cfg in enumerate(cfgs):
+        assert batch.members[i].get_tuning()["green_fused"] == 1
+        xb, pb = batch.members[i].get_particles()
+        eb = batch.members[i].energy(a1[i])
+        single = pm.Sim(cfg)
+        single.set_particles(*ics_[i])
+        single.run(4, a0, a1[i])
+        xs, ps = single.get_particles()
+        es = single.energy(a1[i])
+        single.close()
+        np.testing.assert_array_equal(xb, xs)
+        np.testing.assert_array_equal(pb, ps)
+        np.testing.assert_allclose(eb, es, rtol=1e-12)
+    batch.close()
