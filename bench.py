@@ -301,7 +301,7 @@ def run_reference(args):
 # ---------------------------------------------------------------- GPU arm
 KERNEL_NAMES = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
                 "sort_pass": "k_row_scan+k_bucket_movers", "sort_histogram": "k_sort_histogram",
-                "row_start": "k_row_start", "sort_partition": "k_mover_partition", "sort_merge": "k_place_rows"}
+                "row_start": "k_row_start", "sort_partition": "k_mover_partition", "sort_merge": "k_place"}
 
 
 def measure(pm, sim, w, K, W, stream, rsz=4, spline=False, tuning=None, peak=None, workload_key=None):

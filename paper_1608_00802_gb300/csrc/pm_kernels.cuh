@@ -326,6 +326,13 @@ __device__ __forceinline__ void seg_add_rows(R (&lo)[2], R (&hi)[2], int t, bool
   __syncwarp();
 }
 
+// slots of a deposit row: N + 1 rounded up to 16 bytes
+template <typename R>
+__host__ __device__ inline int deposit_stride_of(int n) {
+  const int q = 16 / int(sizeof(R));
+  return (n + 1 + q - 1) / q * q;
+}
+
 template <typename R, int TZ, bool PACKED>
 __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
                                                             const uint32_t* __restrict__ row_start, uint32_t np,
@@ -336,14 +343,16 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
     pos = moff(pos, o), row_start = moff(row_start, o), rho = moff(rho, o);
   }
   extern __shared__ __align__(16) unsigned char dep_smem[];
-  const int n = m.n, stride = n + 1;
+  // rows of N + 1 slots padded to a multiple of 16 bytes (vector zeroing and write-out)
+  const int n = m.n, stride = deposit_stride_of<R>(n);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int tiles_y = (n + nw - 1) / nw;
   const int y = int(blockIdx.x % unsigned(tiles_y)) * nw + warp, z0 = int(blockIdx.x / unsigned(tiles_y)) * TZ;
   if (y >= n) return;
   const int tz = min(TZ, n - z0);
   R* acc = reinterpret_cast<R*>(dep_smem) + warp * TZ * stride;  // [TZ][N + 1], this warp's
-  for (int i = lane; i < TZ * stride; i += 32) acc[i] = R(0);
+  for (int i = lane; i < TZ * stride * int(sizeof(R)) / 16; i += 32)
+    reinterpret_cast<float4*>(acc)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   __syncwarp();
   // the 2 (tz + 1) source rows k = 2 sz + (1 - dy): plane z0 - 1 + sz (to local rows sz - 1 with
   // dz = 0 and sz with dz = 1), row y - dy; their bounds loaded at once, one per lane
@@ -404,9 +413,11 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
     __syncwarp();
     R* out = rho + (size_t(z0 + lz) * n + size_t(y)) * n;
     if constexpr (sizeof(R) == 4) {
-      if ((n & 3) == 0) {  // 16-byte stores
-        for (int i = 4 * lane; i < n; i += 128)
-          *reinterpret_cast<float4*>(out + i) = make_float4(a[i] * norm, a[i + 1] * norm, a[i + 2] * norm, a[i + 3] * norm);
+      if ((n & 3) == 0) {  // 16-byte loads and stores
+        for (int i = 4 * lane; i < n; i += 128) {
+          const float4 v = *reinterpret_cast<const float4*>(a + i);
+          *reinterpret_cast<float4*>(out + i) = make_float4(v.x * norm, v.y * norm, v.z * norm, v.w * norm);
+        }
         continue;
       }
     }
@@ -1834,7 +1845,7 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
 template <typename R>
 inline int deposit_tz(int n) {
   for (int tz = 4; tz > 1; tz >>= 1)
-    if (size_t(tz) * (n + 1) * sizeof(R) <= size_t(8704)) return tz;
+    if (size_t(tz) * deposit_stride_of<R>(n) * sizeof(R) <= size_t(8704)) return tz;
   return 1;
 }
 
@@ -1842,7 +1853,7 @@ template <typename R, int TZ>
 cudaError_t launch_deposit_tz(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
                               cudaStream_t s, int warps, int nm, size_t ms) {
   using V4 = typename VT<R>::v4;
-  const size_t smem = size_t(warps) * TZ * (m.n + 1) * sizeof(R);
+  const size_t smem = size_t(warps) * TZ * deposit_stride_of<R>(m.n) * sizeof(R);
   const unsigned blocks = unsigned((m.n + warps - 1) / warps) * unsigned((m.n + TZ - 1) / TZ);
   if (nm > 1)
     k_deposit<R, TZ, true><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start,
@@ -1858,7 +1869,7 @@ cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n
                            cudaStream_t s, int warps, int nm, size_t ms) {
   if (warps < 1 || warps > DEP_WARPS) warps = DEP_WARPS;
   const int tz = deposit_tz<R>(m.n);
-  if (size_t(warps) * tz * (m.n + 1) * sizeof(R) > 48 * 1024) {
+  if (size_t(warps) * tz * deposit_stride_of<R>(m.n) * sizeof(R) > 48 * 1024) {
     // once per device, for every tile shape, so that no attribute call falls inside a stream capture
     static bool done[64];
     int dev = 0;

@@ -633,108 +633,67 @@ static __global__ void __launch_bounds__(RS_THREADS) k_bucket_movers(
   }
 }
 
-// The placement, one warp per mesh row: the row's stayers (sorted, the
-// entries [srow[r], srow[r+1]) of (sk, sv)) and its movers (the bucket
-// [mrow[r], mrow[r+1]) of (bk, bv), in any order) go to the outputs
-// row_start[r] .. row_start[r+1] - 1 in the order of (key, previous slot): a
-// stayer moves up by the bucket entries before it, a mover lands after the
-// stayers before it (a binary search over the row's stayers) and the bucket
-// entries before it.  The keys go to keys_out and the records, gathered from
-// their previous slots, to (pos_out, mom_out).  A row holds a few tens of
-// particles, and only the movers of its own row are compared.
-constexpr int PR_WARPS = 8;
-
-// entries of (k_, v_) held one per lane (lanes < cnt) that precede (k, v)
-__device__ __forceinline__ uint32_t warp_count_less(uint32_t k_, uint32_t v_, uint32_t cnt, uint32_t k, uint32_t v) {
-  uint32_t c = 0;
-  for (uint32_t q = 0; q < cnt; ++q) {
-    const uint32_t kq = __shfl_sync(0xffffffffu, k_, int(q)), vq = __shfl_sync(0xffffffffu, v_, int(q));
-    c += kv_less(kq, vq, k, v) ? 1u : 0u;
-  }
-  return c;
-}
-
-// the general placement of one row (any counts)
-template <typename V4>
-__device__ __forceinline__ void place_row(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv,
-                                          const uint32_t* __restrict__ bk, const uint32_t* __restrict__ bv,
-                                          uint32_t s0, uint32_t ns, uint32_t m0, uint32_t nm, uint32_t out0,
-                                          uint32_t lane, uint32_t* __restrict__ keys_out, const V4* __restrict__ pos_in,
-                                          const V4* __restrict__ mom_in, V4* __restrict__ pos_out,
-                                          V4* __restrict__ mom_out) {
-  // stayers, 32 at a time: shifted by the row's bucket entries before them
-  for (uint32_t t0 = 0; t0 < ns; t0 += 32) {
-    const uint32_t t = t0 + lane;
-    const bool have = t < ns;
-    const uint32_t k = have ? __ldg(sk + s0 + t) : 0xffffffffu, v = have ? __ldg(sv + s0 + t) : 0xffffffffu;
-    V4 pr, mr;
-    if (have) {
-      pr = pos_in[v];
-      mr = mom_in[v];
-    }
-    uint32_t c = 0;
-    for (uint32_t u0 = 0; u0 < nm; u0 += 32) {
-      const uint32_t u = u0 + lane;
-      const uint32_t bk_ = u < nm ? __ldg(bk + m0 + u) : 0u, bv_ = u < nm ? __ldg(bv + m0 + u) : 0u;
-      c += warp_count_less(bk_, bv_, min(32u, nm - u0), k, v);
-    }
-    if (have) {
-      const uint32_t i = out0 + t + c;
-      keys_out[i] = k;
-      pos_out[i] = pr;
-      mom_out[i] = mr;
-    }
-  }
-  // movers, 32 at a time: after the stayers and the bucket entries of the row before them
-  for (uint32_t u0 = 0; u0 < nm; u0 += 32) {
-    const uint32_t u = u0 + lane;
-    const bool have = u < nm;
-    const uint32_t k = have ? __ldg(bk + m0 + u) : 0xffffffffu, v = have ? __ldg(bv + m0 + u) : 0xffffffffu;
-    V4 pr, mr;
-    if (have) {
-      pr = pos_in[v];
-      mr = mom_in[v];
-    }
-    uint32_t c = 0;
-    for (uint32_t w0 = 0; w0 < nm; w0 += 32) {
-      const uint32_t w = w0 + lane;
-      const uint32_t bk_ = w < nm ? __ldg(bk + m0 + w) : 0u, bv_ = w < nm ? __ldg(bv + m0 + w) : 0u;
-      c += warp_count_less(bk_, bv_, min(32u, nm - w0), k, v);
-    }
-    for (uint32_t t0 = 0; t0 < ns; t0 += 32) {
-      const uint32_t t = t0 + lane;
-      const uint32_t sk_ = t < ns ? __ldg(sk + s0 + t) : 0u, sv_ = t < ns ? __ldg(sv + s0 + t) : 0u;
-      c += warp_count_less(sk_, sv_, min(32u, ns - t0), k, v);
-    }
-    if (have) {
-      const uint32_t i = out0 + c;
-      keys_out[i] = k;
-      pos_out[i] = pr;
-      mom_out[i] = mr;
-    }
-  }
-}
+// The placement, one thread per output record over all of them: thread i <
+// ns (the stayers' count) takes stayer i (the sorted (sk, sv) of the
+// partition), thread ns + u the mover in bucket entry u.  Every record goes
+// to the place of its (key, previous slot) in its row: a stayer of row r moves
+// up by the movers of the rows before it (mrow[r]) and by the bucket entries
+// of its own row that sort before it, a mover lands at row_start[r] plus the
+// row's stayers before it (a binary search) and the bucket entries before it.
+// Consecutive stayers keep consecutive places except at the few rows that
+// take movers, so the keys, the slots, the gathered records and the written
+// records all stream through memory in order.  The keys go to keys_out and the
+// records, gathered from their previous slots, to (pos_out, mom_out).
+constexpr int PF_THREADS = 256;
 
 template <typename V4, bool PACKED>
-__global__ void __launch_bounds__(PR_WARPS * 32) k_place_rows(
+__global__ void __launch_bounds__(PF_THREADS) k_place(
     const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, const uint32_t* __restrict__ bk,
     const uint32_t* __restrict__ bv, const uint32_t* __restrict__ srow, const uint32_t* __restrict__ mrow,
-    const uint32_t* __restrict__ row_start, uint32_t nrows, uint32_t* __restrict__ keys_out,
-    const V4* __restrict__ pos_in, const V4* __restrict__ mom_in, V4* __restrict__ pos_out, V4* __restrict__ mom_out,
-    size_t ms) {
+    const uint32_t* __restrict__ row_start, const uint32_t* __restrict__ counts, uint32_t n, uint32_t n_mesh,
+    int log2n, uint32_t* __restrict__ keys_out, const V4* __restrict__ pos_in, const V4* __restrict__ mom_in,
+    V4* __restrict__ pos_out, V4* __restrict__ mom_out, size_t ms) {
   if constexpr (PACKED) {
     const size_t o = size_t(blockIdx.y) * ms;
     sk = moff(sk, o), sv = moff(sv, o), bk = moff(bk, o), bv = moff(bv, o), srow = moff(srow, o);
-    mrow = moff(mrow, o), row_start = moff(row_start, o), keys_out = moff(keys_out, o), pos_in = moff(pos_in, o);
-    mom_in = moff(mom_in, o), pos_out = moff(pos_out, o), mom_out = moff(mom_out, o);
+    mrow = moff(mrow, o), row_start = moff(row_start, o), counts = moff(counts, o), keys_out = moff(keys_out, o);
+    pos_in = moff(pos_in, o), mom_in = moff(mom_in, o), pos_out = moff(pos_out, o), mom_out = moff(mom_out, o);
   }
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t r = blockIdx.x * PR_WARPS + (threadIdx.x >> 5);
-  if (r >= nrows) return;  // (whole warps)
-  const uint32_t s0 = __ldg(srow + r), s1 = __ldg(srow + r + 1);
-  const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
-  place_row<V4>(sk, sv, bk, bv, s0, s1 - s0, m0, m1 - m0, __ldg(row_start + r), lane, keys_out, pos_in, mom_in,
-                pos_out, mom_out);
+  const uint32_t ns = counts[0], nrows = n_mesh * n_mesh;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t k, v, out;
+    if (i < ns) {
+      k = __ldg(sk + i), v = __ldg(sv + i);
+      const uint32_t r = key_row(k, n_mesh, log2n);
+      if (r >= nrows) continue;  // (only a corrupt key)
+      const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
+      uint32_t c = 0;
+      for (uint32_t u = m0; u < m1; ++u) c += kv_less(__ldg(bk + u), __ldg(bv + u), k, v) ? 1u : 0u;
+      out = i + m0 + c;
+    } else {
+      const uint32_t u = i - ns;
+      k = __ldg(bk + u), v = __ldg(bv + u);
+      const uint32_t r = key_row(k, n_mesh, log2n);
+      if (r >= nrows) continue;
+      const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
+      uint32_t c = 0;
+      for (uint32_t w = m0; w < m1; ++w) c += kv_less(__ldg(bk + w), __ldg(bv + w), k, v) ? 1u : 0u;
+      const uint32_t s0 = __ldg(srow + r);
+      uint32_t lo = s0, hi = __ldg(srow + r + 1);
+      while (lo < hi) {  // the row's stayers before it
+        const uint32_t mid = (lo + hi) >> 1;
+        if (kv_less(__ldg(sk + mid), __ldg(sv + mid), k, v))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      out = __ldg(row_start + r) + c + (lo - s0);
+    }
+    if (out >= n) continue;  // (only after corrupt counts)
+    keys_out[out] = k;
+    pos_out[out] = pos_in[v];
+    mom_out[out] = mom_in[v];
+  }
 }
 
 // the three parts of the re-sort: the partition, the rows (scan and
@@ -765,13 +724,17 @@ inline cudaError_t launch_resort_place(int part, const uint32_t* keys, int64_t n
     k_bucket_movers<<<dim3(mg, unsigned(nm)), RS_THREADS, 0, s>>>(mk, mv, counts, mrow, rcnt + 2 * nrows, bk, bv, N,
                                                                   m.log2n, o);
   } else {
-    const dim3 grid((nrows + PR_WARPS - 1) / PR_WARPS, unsigned(nm));
+    // a grid of resident blocks shared by the members, striding over the records
+    int64_t cap = int64_t(8) * sms / nm;
+    if (cap < 1) cap = 1;
+    const int64_t need = (n + PF_THREADS - 1) / PF_THREADS;
+    const dim3 grid(unsigned(need < cap ? need : cap), unsigned(nm));
     if (nm > 1)
-      k_place_rows<V4, true><<<grid, PR_WARPS * 32, 0, s>>>(sk, sv, bk, bv, srow, mrow, row_start, nrows, keys_out,
-                                                            pos_in, mom_in, pos_out, mom_out, o);
+      k_place<V4, true><<<grid, PF_THREADS, 0, s>>>(sk, sv, bk, bv, srow, mrow, row_start, counts, uint32_t(n), N,
+                                                    m.log2n, keys_out, pos_in, mom_in, pos_out, mom_out, o);
     else
-      k_place_rows<V4, false><<<grid, PR_WARPS * 32, 0, s>>>(sk, sv, bk, bv, srow, mrow, row_start, nrows, keys_out,
-                                                             pos_in, mom_in, pos_out, mom_out, 0);
+      k_place<V4, false><<<grid, PF_THREADS, 0, s>>>(sk, sv, bk, bv, srow, mrow, row_start, counts, uint32_t(n), N,
+                                                     m.log2n, keys_out, pos_in, mom_in, pos_out, mom_out, 0);
   }
   return cudaGetLastError();
 }
