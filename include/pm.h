@@ -94,7 +94,8 @@ typedef struct {
   int32_t reserved;    /* 0 */
   double smooth_h;     /* PM_KERNEL_SPLINE: smoothing length h in mesh cells, 1 .. n_mesh/4
                           (the paper's cosmological runs: 3.5) */
-  int32_t fft_jit;     /* 1: plan the 3D transforms in cuFFT's patient JIT mode (kernels chosen and
+  int32_t fft_jit;     /* 1: plan the transforms (3D, and the batched 2D ones of green_fused) in cuFFT's
+                          patient JIT mode (kernels chosen and
                           linked at pm_create: a slower creation, ~6 % faster transforms at 256^3 on a
                           GB300; for long-lived simulations), 0: default plans */
   int32_t smooth_real; /* PM_KERNEL_SPLINE, PM_FP32, smooth_h <= 4, n_mesh <= 512: 1 smooths the density and Q

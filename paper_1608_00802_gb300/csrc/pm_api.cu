@@ -588,6 +588,8 @@ cufftResult spec_plan_setup(pm_sim* s, std::string* why) {
     step = "cufftCreate";
     r = cufftCreate(&h[k]);
     if (r == CUFFT_SUCCESS) r = cufftSetAutoAllocation(h[k], 0);
+    if (r == CUFFT_SUCCESS && s->cfg.fft_jit)
+      r = cufftSetPlanPropertyInt64(h[k], NVFFT_PLAN_PROPERTY_INT64_PATIENT_JIT, 1);
     if (r == CUFFT_SUCCESS) {
       step = "cufftMakePlanMany64";
       r = k == 0 ? cufftMakePlanMany64(h[k], 2, n, re, 1, (long long)N * N, cx, 1, (long long)N * nh, CUFFT_R2C, N, &w)

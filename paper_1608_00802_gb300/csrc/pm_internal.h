@@ -147,7 +147,7 @@ cudaError_t launch_resort(int part, const uint32_t* keys, int64_t n, const uint3
                           uint32_t* btot, uint32_t* srow, uint32_t* mrow, uint32_t* row_start, Mesh m,
                           unsigned long long* stats, uint32_t* keys_out, const void* pos_in, const void* mom_in,
                           void* pos_out, void* mom_out, int sms, cudaStream_t s, int nm = 1, size_t ms = 0);
-inline size_t row_scan_tiles(int n_mesh) { return (size_t(n_mesh) * n_mesh + 4095) / 4096; }
+inline size_t row_scan_tiles(int n_mesh) { return (size_t(n_mesh) * n_mesh + 1023) / 1024; }  // tiles of 1024 rows
 cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s, int nm = 1, size_t ms = 0);
 // row starts of sorted keys
 cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);

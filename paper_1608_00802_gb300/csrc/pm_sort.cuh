@@ -489,7 +489,8 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
 // earlier tiles' totals and scans its own, writing srow (stayers before row
 // r), mrow (movers before row r) and the new row starts row_start = srow +
 // mrow, with the closing entries at r = N^2.
-constexpr int RT_THREADS = 1024, RT_ITEMS = 4, RT_TILE = RT_THREADS * RT_ITEMS;
+constexpr int RT_THREADS = 256, RT_ITEMS = 4, RT_TILE = RT_THREADS * RT_ITEMS;
+static_assert(RT_TILE == 1024, "row_scan_tiles counts tiles of 1024 rows");
 
 static __global__ void __launch_bounds__(RT_THREADS) k_row_totals(const uint32_t* __restrict__ rcnt, uint32_t nrows,
                                                                   uint32_t* __restrict__ btot, size_t ms) {
