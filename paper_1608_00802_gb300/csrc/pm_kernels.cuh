@@ -1677,8 +1677,12 @@ __device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, 
     if (kp.has_drift) {
       const bool moved = ncell != cell;
       keys[i] = ncell | (moved ? KEY_MOVER : 0u);
-      // (one integer atomic per mover: measured faster than a warp-aggregated count)
-      if (moved) atomicAdd(tcount + (i >> RS_TILE_SHIFT), 1u);
+      // one atomic per warp with movers (the warp's 32 consecutive slots lie in one tile): when every
+      // particle moves, per-particle atomics on the tile's counter serialise
+      const uint32_t active = __activemask();
+      const uint32_t movers = __ballot_sync(active, moved);
+      if (movers && (threadIdx.x & 31) == uint32_t(__ffs(movers) - 1))
+        atomicAdd(tcount + (i >> RS_TILE_SHIFT), uint32_t(__popc(movers)));
     }
   }
 }
