@@ -593,8 +593,9 @@ def run_batched(pm, ics, K, W, stream):
             for n, nm, box, m22, _ in members]
     batch = pm.Batch(cfgs, stream=stream)
     cache = pm.TuningCache()  # one autotuner run per member size, shared by the others (untimed)
-    for mem, (n, nm, box, m22, seed) in zip(batch.members, members):
-        mem.set_particles(*ics.zeldovich(n, nm, box, a[0], seed, m22=m22))
+    init = [ics.zeldovich(n, nm, box, a[0], seed, m22=m22) for n, nm, box, m22, seed in members]
+    for mem, x0 in zip(batch.members, init):
+        mem.set_particles(*x0)
         key = pm.tuning_key(mem.cfg)
         if key not in cache:
             t = mem.autotune(reps=5)
@@ -603,6 +604,20 @@ def run_batched(pm, ics, K, W, stream):
                 t = dict(t, stencil_rows=4, stencil_planes=4, stencil_stages=0)
             cache[key] = t
         mem.set_tuning(cache[key])
+    # the same simulations one after the other, each with its own captured steps (host-timed around
+    # a device synchronisation: the members run on their own streams)
+    alone_s = 0.0
+    for mem, x0 in zip(batch.members, init):
+        mem.set_particles(*x0)
+        if W > 0:
+            mem.run(W, a[0], a[W])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mem.run(K, a[W], a[W + K])
+        torch.cuda.synchronize()
+        alone_s += time.perf_counter() - t0
+    for mem, x0 in zip(batch.members, init):
+        mem.set_particles(*x0)
     with torch.cuda.stream(stream):
         if W > 0:
             batch.run(W, a[0], a[W])
@@ -619,6 +634,9 @@ def run_batched(pm, ics, K, W, stream):
     return {"value": units / (t / 1e3), "unit": "particle-steps/s", "steps": K, "ms_per_step": t / K,
             "workload": BATCH["name"], "particles": sum(n ** 3 for n, *_ in members),
             "classes": classes, "packed_members": packed,
+            "alone": {"value": units / alone_s, "ms_per_step": 1e3 * alone_s / K,
+                      "note": "the same 48 simulations stepped one after the other (pm_run each)"},
+            "speedup_vs_alone": alone_s / (t / 1e3),
             "launch_shapes": {k: v for k, v in cache.items()}}
 
 

@@ -376,6 +376,11 @@ __device__ __forceinline__ uint32_t key_row(uint32_t key, uint32_t n_mesh, int l
   return log2n >= 0 ? key >> log2n : key / n_mesh;
 }
 
+constexpr int RT_THREADS = 256, RT_ITEMS = 4, RT_TILE = RT_THREADS * RT_ITEMS;
+static_assert(RT_TILE == 1024, "row_scan_tiles counts tiles of 1024 rows");
+// the partition sums the earlier tiles' mover counts itself up to this many tiles (else k_tile_scan)
+constexpr uint32_t PART_OWN_SCAN_TILES = 2048;
+
 // Movers before every tile: an exclusive scan of the drift's per-tile mover
 // counts (tcount[0..T)) into tcount[T..2T), by one block per simulation.
 constexpr int TS_THREADS = 1024;
@@ -415,8 +420,8 @@ static __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(uint32_t* tcoun
 static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
     const uint32_t* __restrict__ keys, int64_t n, const uint32_t* __restrict__ tcount,
     uint32_t* __restrict__ s_keys, uint32_t* __restrict__ s_vals, uint32_t* __restrict__ m_keys,
-    uint32_t* __restrict__ m_vals, uint32_t* __restrict__ counts, uint32_t* __restrict__ rcnt, uint32_t n_mesh,
-    int log2n, unsigned long long* __restrict__ stats, size_t ms) {
+    uint32_t* __restrict__ m_vals, uint32_t* __restrict__ counts, uint32_t* __restrict__ rcnt,
+    uint32_t n_mesh, int log2n, unsigned long long* __restrict__ stats, int own_scan, size_t ms) {
   __shared__ uint32_t wm[RS_WARPS];
   if (ms) {  // member blockIdx.y of a packed group
     const size_t o = size_t(blockIdx.y) * ms;
@@ -430,7 +435,22 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
   const uint32_t tile = blockIdx.x;
   const int64_t tile_base = int64_t(tile) * RS_TILE;
   const uint32_t lt = lanemask_lt();
-  const uint32_t excl = __ldg(tcount + ntiles + tile);  // movers before this tile
+  // movers before this tile: the tile scan's, or (few tiles) summed here from the drift's counts
+  uint32_t excl;
+  if (own_scan) {
+    uint32_t sum = 0;
+    for (uint32_t t = threadIdx.x; t < tile; t += RS_THREADS) sum += tcount[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) wm[warp] = sum;
+    __syncthreads();
+    excl = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) excl += wm[w];
+    __syncthreads();  // wm is reused below
+  } else {
+    excl = __ldg(tcount + ntiles + tile);
+  }
   // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32
   uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
 #pragma unroll
@@ -489,8 +509,6 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
 // earlier tiles' totals and scans its own, writing srow (stayers before row
 // r), mrow (movers before row r) and the new row starts row_start = srow +
 // mrow, with the closing entries at r = N^2.
-constexpr int RT_THREADS = 256, RT_ITEMS = 4, RT_TILE = RT_THREADS * RT_ITEMS;
-static_assert(RT_TILE == 1024, "row_scan_tiles counts tiles of 1024 rows");
 
 static __global__ void __launch_bounds__(RT_THREADS) k_row_totals(const uint32_t* __restrict__ rcnt, uint32_t nrows,
                                                                   uint32_t* __restrict__ btot, size_t ms) {
@@ -710,9 +728,11 @@ inline cudaError_t launch_resort_place(int part, const uint32_t* keys, int64_t n
   const uint32_t N = uint32_t(m.n), nrows = N * N;
   if (part == 0) {
     const unsigned ntiles = unsigned((n + RS_TILE - 1) / RS_TILE);
-    k_tile_scan<<<dim3(1, unsigned(nm)), TS_THREADS, 0, s>>>(const_cast<uint32_t*>(tcount), ntiles, o);
+    // up to PART_OWN_SCAN_TILES tiles each block sums the counts of the tiles before it
+    const int own = ntiles <= PART_OWN_SCAN_TILES;
+    if (!own) k_tile_scan<<<dim3(1, unsigned(nm)), TS_THREADS, 0, s>>>(const_cast<uint32_t*>(tcount), ntiles, o);
     k_mover_partition<<<dim3(ntiles, unsigned(nm)), RS_THREADS, 0, s>>>(keys, n, tcount, sk, sv, mk, mv, counts, rcnt,
-                                                                       N, m.log2n, stats, o);
+                                                                       N, m.log2n, stats, own, o);
   } else if (part == 1) {
     const unsigned nb = (nrows + RT_TILE - 1) / RT_TILE;
     k_row_totals<<<dim3(nb, unsigned(nm)), RT_THREADS, 0, s>>>(rcnt, nrows, btot, o);
