@@ -299,7 +299,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-KERNEL_NAMES = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_green",
+KERNEL_NAMES = {"kick": "k_kick_stream", "deposit": "k_deposit", "stencil": "k_stencil", "green": "k_spec_z",
                 "sort_pass": "k_row_scan+k_bucket_movers", "sort_histogram": "k_sort_histogram",
                 "row_start": "k_row_start", "sort_partition": "k_mover_partition", "sort_merge": "k_place"}
 
