@@ -262,6 +262,31 @@ pm_status pm_debug_sort_timeout(pm_sim* sim, int32_t spin_limit);
  * the particles they moved to another cell, summed on the device.  Sync. */
 pm_status pm_sort_stats(pm_sim* sim, int64_t* resorts, int64_t* movers);
 
+/* ---- checkpoint and resume -------------------------------------------------
+ * A checkpoint holds what the steps continue from: the particle records in
+ * storage order (cell, offsets, momenta, id), the sorted cell keys and their
+ * flags, the re-sort statistics and the launch shapes.  The momenta a run
+ * leaves are synchronised with the positions (every pm_run / pm_step ends with
+ * its closing half kick), so a checkpoint taken between calls and loaded into a
+ * simulation of the same n_part, n_mesh, precision and kernel (a new one, or
+ * the same) continues on the same bits as the uninterrupted run: the mesh fields
+ * are recomputed from the records when next needed.  The scale factor is the
+ * caller's (it passes a to every call).  Layout: a 256-byte header (magic,
+ * version, sizes, flags, shapes, statistics), then the position records, the
+ * momentum records (16 bytes each in PM_FP32, 32 in PM_FP64) and the keys
+ * (4 bytes each), host byte order. */
+size_t pm_checkpoint_bytes(const pm_sim* sim);
+
+/* Writes the checkpoint to `host` (>= pm_checkpoint_bytes bytes).  PM_ERR_STATE
+ * without particles, PM_ERR_INVALID_ARG for a short buffer.  Sync. */
+pm_status pm_save(pm_sim* sim, void* host, size_t bytes);
+
+/* Replaces the simulation's particles, keys, statistics and launch shapes by a
+ * checkpoint's.  PM_ERR_INVALID_ARG if the buffer is short or its header does
+ * not match this simulation (magic, version, n_part, n_mesh, precision,
+ * kernel); the simulation is unchanged then.  Sync. */
+pm_status pm_load(pm_sim* sim, const void* host, size_t bytes);
+
 /* Starts recording a CUDA-event pair around every launch of this handle, for
  * up to `capacity` launches (events are created here, before any timed work).
  * Async. */

@@ -1583,6 +1583,89 @@ pm_status pm_sort_stats(pm_sim* s, int64_t* resorts, int64_t* movers) {
   return PM_OK;
 }
 
+// ---------------------------------------------------------------- checkpoint
+namespace {
+constexpr uint32_t CKPT_MAGIC = 0x4b43504du;  // "MPCK"
+constexpr uint32_t CKPT_VERSION = 1;
+constexpr size_t CKPT_HEADER = 256;
+struct CkptHeader {
+  uint32_t magic, version;
+  int64_t n_part;
+  int32_t n_mesh, precision, kernel, flags;  // flags: 1 sorted, 2 keys marked
+  pm_tuning tuning;
+  uint64_t resorts, moved;
+};
+static_assert(sizeof(CkptHeader) <= CKPT_HEADER, "checkpoint header fits its 256 bytes");
+size_t rec_bytes(const pm_sim* s) { return s->fp64() ? 32 : 16; }
+}  // namespace
+
+size_t pm_checkpoint_bytes(const pm_sim* s) {
+  if (!s) return 0;
+  return CKPT_HEADER + size_t(s->n()) * (2 * rec_bytes(s) + 4);
+}
+
+pm_status pm_save(pm_sim* s, void* host, size_t bytes) {
+  pm_status st = check(s);
+  if (st != PM_OK) return st;
+  if (!host || bytes < pm_checkpoint_bytes(s))
+    return fail(s, PM_ERR_INVALID_ARG, "checkpoint buffer needs %zu bytes", pm_checkpoint_bytes(s));
+  CkptHeader h;
+  memset(&h, 0, sizeof h);
+  h.magic = CKPT_MAGIC;
+  h.version = CKPT_VERSION;
+  h.n_part = s->n();
+  h.n_mesh = s->cfg.n_mesh;
+  h.precision = s->cfg.precision;
+  h.kernel = s->cfg.kernel;
+  h.flags = (s->sorted ? 1 : 0) | (s->keys_marked ? 2 : 0);
+  to_public(s->tune, &h.tuning);
+  unsigned long long stats[2];
+  char* out = static_cast<char*>(host);
+  const size_t rb = size_t(s->n()) * rec_bytes(s);
+  CU(s, cudaMemcpyAsync(stats, s->sort_stats(), sizeof stats, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaMemcpyAsync(out + CKPT_HEADER, s->pos(), rb, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaMemcpyAsync(out + CKPT_HEADER + rb, s->mom(), rb, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaMemcpyAsync(out + CKPT_HEADER + 2 * rb, s->keys, size_t(s->n()) * 4, cudaMemcpyDeviceToHost, s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  h.resorts = stats[0];
+  h.moved = stats[1];
+  memset(out, 0, CKPT_HEADER);
+  memcpy(out, &h, sizeof h);
+  return PM_OK;
+}
+
+pm_status pm_load(pm_sim* s, const void* host, size_t bytes) {
+  if (!s) return PM_ERR_INVALID_ARG;
+  if (!host || bytes < CKPT_HEADER) return fail(s, PM_ERR_INVALID_ARG, "checkpoint buffer too short");
+  CkptHeader h;
+  memcpy(&h, host, sizeof h);
+  if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION)
+    return fail(s, PM_ERR_INVALID_ARG, "not a checkpoint of this library version");
+  if (h.n_part != s->n() || h.n_mesh != s->cfg.n_mesh || h.precision != s->cfg.precision ||
+      h.kernel != s->cfg.kernel)
+    return fail(s, PM_ERR_INVALID_ARG, "checkpoint of another configuration (n_part, n_mesh, precision or kernel)");
+  if (bytes < pm_checkpoint_bytes(s)) return fail(s, PM_ERR_INVALID_ARG, "checkpoint buffer too short");
+  pm_status st = pm_set_tuning(s, &h.tuning);  // validates the shapes and drops captured steps
+  if (st != PM_OK) return st;
+  const char* in = static_cast<const char*>(host);
+  const size_t rb = size_t(s->n()) * rec_bytes(s);
+  const unsigned long long stats[2] = {h.resorts, h.moved};
+  CU(s, cudaMemcpyAsync(s->pos(), in + CKPT_HEADER, rb, cudaMemcpyHostToDevice, s->stream));
+  CU(s, cudaMemcpyAsync(s->mom(), in + CKPT_HEADER + rb, rb, cudaMemcpyHostToDevice, s->stream));
+  CU(s, cudaMemcpyAsync(s->keys, in + CKPT_HEADER + 2 * rb, size_t(s->n()) * 4, cudaMemcpyHostToDevice, s->stream));
+  CU(s, cudaMemcpyAsync(s->sort_stats(), stats, sizeof stats, cudaMemcpyHostToDevice, s->stream));
+  // sorted records: the deposit reads the row starts of the keys (integer, so the same as the re-sort's)
+  if (h.flags & 1)
+    CU(s, launch_row_start(s->keys, s->n(), uint32_t(s->cfg.n_mesh), s->at<uint32_t>(s->L.row_start), s->stream));
+  CU(s, cudaStreamSynchronize(s->stream));
+  s->have_particles = true;
+  s->sorted = (h.flags & 1) != 0;
+  s->keys_marked = (h.flags & 2) != 0;
+  s->fields_valid = false;
+  s->krho_valid = false;
+  return PM_OK;
+}
+
 pm_status pm_profile_begin(pm_sim* s, int32_t capacity) {
   if (!s) return PM_ERR_INVALID_ARG;
   if (capacity < 1) return fail(s, PM_ERR_INVALID_ARG, "capacity must be >= 1");

@@ -30,7 +30,7 @@ EXPORTS = ["pm_config_default", "pm_hbar_over_m", "pm_arena_bytes", "pm_create",
            "pm_profile_begin", "pm_profile_end", "pm_deposit_noalloc", "pm_last_error",
            "pm_batch_arena_bytes", "pm_batch_create", "pm_batch_destroy", "pm_batch_member", "pm_batch_run",
            "pm_batch_last_error", "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_run_adaptive",
-           "pm_sort_stats", "pm_batch_info", "pm_debug_sort_timeout"]
+           "pm_sort_stats", "pm_batch_info", "pm_debug_sort_timeout", "pm_checkpoint_bytes", "pm_save", "pm_load"]
 NOALLOC_MAX_PARTICLES = 65536
 NOALLOC_MAX_MESH = 128
 STAGES = ["sort_histogram", "sort_pass", "row_start", "deposit", "fft_r2c", "green", "fft_c2r", "stencil",
@@ -97,6 +97,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "pm_get_order": (C.c_int, [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
         "pm_sort_stats": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "pm_debug_sort_timeout": (C.c_int, [vp, C.c_int32]),
+        "pm_checkpoint_bytes": (C.c_size_t, [vp]),
+        "pm_save": (C.c_int, [vp, vp, C.c_size_t]),
+        "pm_load": (C.c_int, [vp, vp, C.c_size_t]),
         "pm_profile_begin": (C.c_int, [vp, C.c_int32]),
         "pm_profile_end": (C.c_int, [vp, dp, C.POINTER(C.c_int64)]),
         "pm_deposit_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, C.c_double, vp, vp, vp]),
@@ -343,6 +346,18 @@ class Sim:
         r, m = C.c_int64(0), C.c_int64(0)
         self._check(lib().pm_sort_stats(self.handle, C.byref(r), C.byref(m)))
         return int(r.value), int(m.value)
+
+    def save(self):
+        """The checkpoint (numpy uint8 array) this simulation continues from:
+        records in storage order, keys, statistics, launch shapes."""
+        buf = np.empty(int(lib().pm_checkpoint_bytes(self.handle)), dtype=np.uint8)
+        self._check(lib().pm_save(self.handle, buf.ctypes.data_as(C.c_void_p), buf.nbytes))
+        return buf
+
+    def load(self, buf):
+        """Continues from a checkpoint of `save` (same n_part, n_mesh, precision, kernel)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(lib().pm_load(self.handle, buf.ctypes.data_as(C.c_void_p), buf.nbytes))
 
     def profile_begin(self, capacity):
         self._check(lib().pm_profile_begin(self.handle, int(capacity)))
