@@ -640,15 +640,17 @@ __global__ void __launch_bounds__(SPZ_COLS * P, SPZ_COLS * P <= 256 ? PM_SPZ_MIN
   float* s2 = reinterpret_cast<float*>(tw + N);
   const int tid = threadIdx.x;
   const uint32_t col0 = blockIdx.x * SPZ_COLS;
+  // the tile by asynchronous 16-byte copies: every copy of a thread in flight at once
   for (int i = tid; i < N * 8; i += T) {
     const int r = i >> 3, q = i & 7;
-    reinterpret_cast<float4*>(tile + r * SPZ_COLS)[q] =
-        __ldg(reinterpret_cast<const float4*>(spec + size_t(r) * PLANE + col0) + q);
+    cp_async16(reinterpret_cast<float4*>(tile + r * SPZ_COLS) + q,
+               reinterpret_cast<const float4*>(spec + size_t(r) * PLANE + col0) + q);
   }
   for (int i = tid; i < N; i += T) {
     tw[i] = twg[i];
     s2[i] = s2g[i];
   }
+  cp_async_wait_all();
   __syncthreads();
   const int c = tid & (SPZ_COLS - 1), jt = tid / SPZ_COLS;
   {  // forward, first step: thread j, Q-point DFT over m, twiddle W_N^{j k1}
