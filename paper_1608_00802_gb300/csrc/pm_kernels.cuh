@@ -1594,7 +1594,10 @@ __device__ __forceinline__ KickR<R> kick_r(const KickParams& kp) {
 // The records are updated in place; with a drift the new key goes to
 // keys[i] and a particle that changed cell counts in the mover count of its
 // tile of RS_TILE slots (tcount).
-template <typename R, int MODE>
+// FM: the force form fixed at compile time (KICK_FM_HYBRID_Q: gravity by central differences, the
+// quantum force on, by the kernel gradient) or taken from kp at run time (KICK_FM_ANY)
+constexpr int KICK_FM_ANY = 0, KICK_FM_HYBRID_Q = 1;
+template <typename R, int MODE, int FM = KICK_FM_ANY>
 __device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, typename VT<R>::v4 mo,
                                               typename VT<R>::v4* pos, typename VT<R>::v4* mom,
                                               uint32_t* keys, uint32_t* tcount,
@@ -1614,12 +1617,15 @@ __device__ __forceinline__ void kick_particle(int64_t i, typename VT<R>::v4 ps, 
   const R wx[2] = {R(1) - ps.y, ps.y}, wy[2] = {R(1) - ps.z, ps.z}, wz[2] = {R(1) - ps.w, ps.w};
   const R inv_dx = kp.inv_dx;
   R gp[3], gq[3] = {R(0), R(0), R(0)};
-  if (kp.grav_kernel)
+  const bool grav_kernel = FM == KICK_FM_HYBRID_Q ? false : kp.grav_kernel;
+  const bool quantum = FM == KICK_FM_HYBRID_Q ? true : kp.quantum;
+  const bool q_kernel = FM == KICK_FM_HYBRID_Q ? true : kp.q_kernel;
+  if (grav_kernel)
     grad_kernel(phi, s, wx, wy, wz, inv_dx, gp);
   else
     grad_central(phi, s, wx, wy, wz, inv_dx, gp);
-  if (kp.quantum) {
-    if (kp.q_kernel)
+  if (quantum) {
+    if (q_kernel)
       grad_kernel(qf, s, wx, wy, wz, inv_dx, gq);
     else
       grad_central(qf, s, wx, wy, wz, inv_dx, gq);
@@ -1721,8 +1727,12 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_MINB) k_kick(typename VT
 #endif
 // PACKED: the members of a packed group, member blockIdx.y (a separate
 // instantiation: the member offsets cost the single pass ~20 % when present)
-template <typename R, bool PACKED>
-__global__ void __launch_bounds__(KICK_THREADS, PM_KICK_STREAM_MINB) k_kick_stream(
+#ifndef PM_KICK_STREAM_HQ_MINB
+#define PM_KICK_STREAM_HQ_MINB 4  // the HYBRID single pass fits 64 registers without spills
+#endif
+template <typename R, bool PACKED, int FM>
+__global__ void __launch_bounds__(KICK_THREADS, (FM == KICK_FM_HYBRID_Q && !PACKED) ? PM_KICK_STREAM_HQ_MINB
+                                                                                     : PM_KICK_STREAM_MINB) k_kick_stream(
     typename VT<R>::v4* pos, typename VT<R>::v4* mom, uint32_t* keys, uint32_t* tcount, int64_t n, const R* __restrict__ phi,
     const R* __restrict__ qf, Mesh m, KickParams kp_arg, const KickParams* __restrict__ kp_tab,
     const uint32_t* __restrict__ step, uint32_t* err, size_t ms) {
@@ -1746,7 +1756,7 @@ __global__ void __launch_bounds__(KICK_THREADS, PM_KICK_STREAM_MINB) k_kick_stre
       nps = pos[j];
       nmo = mom[j];
     }
-    kick_particle<R, 0>(i, ps, mo, pos, mom, keys, tcount, phi, qf, m, kp, nullptr, err, dg);
+    kick_particle<R, 0, FM>(i, ps, mo, pos, mom, keys, tcount, phi, qf, m, kp, nullptr, err, dg);
     if (j >= nn) break;
     i = j;
     ps = nps;
@@ -2059,20 +2069,25 @@ cudaError_t launch_stencil(const R* rho, Mesh m, StencilParams sp, R* q, double*
 // once per device and block size (pm_create asks first, outside any capture);
 // if the query fails, one particle per thread
 template <typename R>
-int kick_stream_resident(int threads) {
-  static int cache[64][2];
+int kick_stream_resident(int threads, int fm = KICK_FM_ANY) {
+  static int cache[64][2][2];
   int dev = 0;
   cudaGetDevice(&dev);
-  const int t = threads == 128 ? 0 : 1;
-  if (dev >= 0 && dev < 64 && cache[dev][t] > 0) return cache[dev][t];
+  const int t = threads == 128 ? 0 : 1, f = fm == KICK_FM_HYBRID_Q ? 1 : 0;
+  if (dev >= 0 && dev < 64 && cache[dev][t][f] > 0) return cache[dev][t][f];
   int per_sm = 0, sms = 0, r = 1 << 30;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kick_stream<R, false>, threads, 0) == cudaSuccess &&
+  const void* fn = f ? (const void*)k_kick_stream<R, false, KICK_FM_HYBRID_Q> : (const void*)k_kick_stream<R, false, KICK_FM_ANY>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) == cudaSuccess &&
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && per_sm > 0 && sms > 0)
     r = per_sm * sms;
   else
     cudaGetLastError();
-  if (dev >= 0 && dev < 64) cache[dev][t] = r;
+  if (dev >= 0 && dev < 64) cache[dev][t][f] = r;
   return r;
+}
+// the compile-time force form of a kick's parameters (the common HYBRID run with the quantum force)
+inline int kick_fm(const KickParams& kp) {
+  return (!kp.grav_kernel && kp.quantum && kp.q_kernel) ? KICK_FM_HYBRID_Q : KICK_FM_ANY;
 }
 inline unsigned kick_stream_blocks(int64_t n, int threads, int resident) {
   const int64_t need = (n + threads - 1) / threads;
@@ -2093,8 +2108,12 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, uint32_t* tcount, 
       if (threads != 128 && threads != 256) threads = KICK_THREADS;
       const int per = kick_stream_resident<R>(threads) / nm;
       const unsigned g = kick_stream_blocks(n, threads, per > 1 ? per : 1);
-      k_kick_stream<R, true><<<dim3(g, unsigned(nm)), threads, 0, s>>>((V4*)pos, (V4*)mom, keys, tcount, n, phi, q,
-                                                                        m, kp, kp_tab, step, err, ms);
+      if (kick_fm(kp) == KICK_FM_HYBRID_Q)
+        k_kick_stream<R, true, KICK_FM_HYBRID_Q><<<dim3(g, unsigned(nm)), threads, 0, s>>>(
+            (V4*)pos, (V4*)mom, keys, tcount, n, phi, q, m, kp, kp_tab, step, err, ms);
+      else
+        k_kick_stream<R, true, KICK_FM_ANY><<<dim3(g, unsigned(nm)), threads, 0, s>>>(
+            (V4*)pos, (V4*)mom, keys, tcount, n, phi, q, m, kp, kp_tab, step, err, ms);
       return cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;
@@ -2110,9 +2129,16 @@ cudaError_t launch_kick(void* pos, void* mom, uint32_t* keys, uint32_t* tcount, 
     k_kick<R, 2><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   else if (kp.diag)
     k_kick<R, 1><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
-  else if constexpr (sizeof(R) == 4)  // the fp64 records would spill in the streaming loop
-    k_kick_stream<R, false><<<kick_stream_blocks(n, threads, kick_stream_resident<R>(threads)), threads, 0, s>>>(
-        p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, err, 0);
+  else if constexpr (sizeof(R) == 4) {  // the fp64 records would spill in the streaming loop
+    const int fm = kick_fm(kp);
+    const unsigned gs = kick_stream_blocks(n, threads, kick_stream_resident<R>(threads, fm));
+    if (fm == KICK_FM_HYBRID_Q)
+      k_kick_stream<R, false, KICK_FM_HYBRID_Q><<<gs, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab,
+                                                                       step, err, 0);
+    else
+      k_kick_stream<R, false, KICK_FM_ANY><<<gs, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step,
+                                                                  err, 0);
+  }
   else
     k_kick<R, 0><<<g, threads, 0, s>>>(p, mo, keys, tcount, n, phi, q, m, kp, kp_tab, step, part, acc, err);
   return cudaGetLastError();

@@ -34,8 +34,10 @@ cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, u
 size_t stencil_list_entries(int n) { return stencil_list_len(n); }
 
 void kick_stream_prepare() {
-  kick_stream_resident<float>(128);
-  kick_stream_resident<float>(256);
+  for (int fm : {KICK_FM_ANY, KICK_FM_HYBRID_Q}) {
+    kick_stream_resident<float>(128, fm);
+    kick_stream_resident<float>(256, fm);
+  }
 }
 
 int stencil_launch_blocks(int n, int ty, int zlen) {
