@@ -265,181 +265,6 @@ __global__ void k_init_particles(const double* __restrict__ x, const double* __r
 }
 
 // ---------------------------------------------------------------- cloud-in-cell deposit
-// rho_n = norm * sum_i W(x_n - q_i): Eq. (rhodis) with the cloud-in-cell
-// tent, no floating-point atomics.  A warp owns a column of TZ mesh rows
-// (z0 .. z0 + TZ - 1, y) and keeps them in shared memory (N + 1 slots per
-// row, slot N = node 0 seen from cell N-1).  A particle of source row
-// (z', y') adds to the rows (z' + dz, y' + dy), dz, dy in {0, 1}, so the
-// warp reads the 2 (TZ + 1) source rows (z0 - 1 .. z0 + TZ - 1, y - 1 .. y)
-// (each particle about 2 + 2/TZ times instead of 4 with one row per warp) and
-// adds both of a source row's destination rows' x-weights (f_x to node c + 1,
-// 1 - f_x to node c, times the y and z weights) through one segmented warp
-// scan: lanes with the same cell are adjacent after the sort, the scan sums
-// each run in a fixed tree order and the run's last lane adds the sums to the
-// nodes.  The warp alone writes its rows, in a fixed order of source rows and
-// of particles within them, so the result is reproducible.
-constexpr int DEP_WARPS = 8;
-
-// One batch of 32 records: the segmented sums of the x-weights of the two
-// destination rows (acc + dst[d]; dst[d] < 0: the row is outside the column),
-// hi (f_x, to node t + 1) first, then lo (1 - f_x, to node t).  Lanes with
-// `valid` false carry unique targets past the row.  The scan stops after the
-// steps the longest run needs (a batch of distinct cells, the common case on
-// a mesh of several cells per particle, takes none); the skipped steps would
-// add nothing, so the sums are the same bits.
-template <typename R>
-__device__ __forceinline__ void seg_add_rows(R (&lo)[2], R (&hi)[2], int t, bool valid, R* acc, const int (&dst)[2]) {
-  const int lane = threadIdx.x & 31;
-  const int tp = __shfl_up_sync(0xffffffffu, t, 1);
-  const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || tp != t);
-  if (heads != 0xffffffffu) {  // some cell holds several particles of the batch
-    // length of the run that starts at this lane (0 elsewhere), and the longest
-    const uint32_t above = heads & ~((2u << lane) - 1u);
-    const int len = ((heads >> lane) & 1u) ? (above ? __ffs(above) - 1 : 32) - lane : 0;
-    const int longest = int(__reduce_max_sync(0xffffffffu, uint32_t(len)));
-    for (int off = 1; off < longest; off <<= 1) {
-      R ulo[2], uhi[2];
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        ulo[d] = __shfl_up_sync(0xffffffffu, lo[d], off);
-        uhi[d] = __shfl_up_sync(0xffffffffu, hi[d], off);
-      }
-      // lane - off is in this lane's run iff no run starts in (lane - off, lane]
-      const uint32_t span = lane >= off ? ((2u << lane) - 1u) & ~((2u << (lane - off)) - 1u) : 0u;
-      if (lane >= off && !(heads & span)) {
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          lo[d] += ulo[d];
-          hi[d] += uhi[d];
-        }
-      }
-    }
-  }
-  const bool add = valid && (lane == 31 || ((heads >> (lane + 1)) & 1u));
-#pragma unroll
-  for (int d = 0; d < 2; ++d)
-    if (dst[d] >= 0 && add) acc[dst[d] + t + 1] += hi[d];
-  __syncwarp();
-#pragma unroll
-  for (int d = 0; d < 2; ++d)
-    if (dst[d] >= 0 && add) acc[dst[d] + t] += lo[d];
-  __syncwarp();
-}
-
-// slots of a deposit row: N + 1 rounded up to 16 bytes
-template <typename R>
-__host__ __device__ inline int deposit_stride_of(int n) {
-  const int q = 16 / int(sizeof(R));
-  return (n + 1 + q - 1) / q * q;
-}
-
-template <typename R, int TZ, bool PACKED>
-__global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
-                                                            const uint32_t* __restrict__ row_start, uint32_t np,
-                                                            Mesh m, R norm, R* __restrict__ rho, size_t ms) {
-  using V4 = typename VT<R>::v4;
-  if constexpr (PACKED) {  // member blockIdx.y of a packed group
-    const size_t o = size_t(blockIdx.y) * ms;
-    pos = moff(pos, o), row_start = moff(row_start, o), rho = moff(rho, o);
-  }
-  extern __shared__ __align__(16) unsigned char dep_smem[];
-  // rows of N + 1 slots padded to a multiple of 16 bytes (vector zeroing and write-out)
-  const int n = m.n, stride = deposit_stride_of<R>(n);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int tiles_y = (n + nw - 1) / nw;
-  const int y = int(blockIdx.x % unsigned(tiles_y)) * nw + warp, z0 = int(blockIdx.x / unsigned(tiles_y)) * TZ;
-  if (y >= n) return;
-  const int tz = min(TZ, n - z0);
-  R* acc = reinterpret_cast<R*>(dep_smem) + warp * TZ * stride;  // [TZ][N + 1], this warp's
-  for (int i = lane; i < TZ * stride * int(sizeof(R)) / 16; i += 32)
-    reinterpret_cast<float4*>(acc)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  __syncwarp();
-  // the 2 (tz + 1) source rows k = 2 sz + (1 - dy): plane z0 - 1 + sz (to local rows sz - 1 with
-  // dz = 0 and sz with dz = 1), row y - dy; their bounds loaded at once, one per lane
-  const int nrows = 2 * (tz + 1);
-  uint32_t bk = 0, ek = 0;
-  if (lane < nrows) {
-    const uint32_t srow =
-        uint32_t(wrap(z0 - 1 + (lane >> 1), n)) * uint32_t(n) + uint32_t(wrap(y - 1 + (lane & 1), n));
-    bk = __ldg(row_start + srow);
-    ek = min(__ldg(row_start + srow + 1), np);
-  }
-  // batches of 32 records in row order, the next batch's records loaded while the current one is added
-  auto next_row = [&](int& kk, uint32_t& jj, uint32_t& ee) {
-    do {
-      ++kk;
-      jj = __shfl_sync(0xffffffffu, bk, kk & 31);
-      ee = __shfl_sync(0xffffffffu, ek, kk & 31);
-    } while (kk < nrows && jj >= ee);
-  };
-  int k = -1;
-  uint32_t j0 = 0, e = 0;
-  next_row(k, j0, e);
-  V4 rec = {};
-  if (k < nrows && j0 + lane < e) rec = ldg(pos + j0 + lane);
-  while (k < nrows) {
-    int k2 = k;
-    uint32_t j2 = j0 + 32, e2 = e;
-    if (j2 >= e) next_row(k2, j2, e2);
-    V4 rec2 = {};
-    if (k2 < nrows && j2 + lane < e2) rec2 = ldg(pos + j2 + lane);
-    const int sz = k >> 1, dy = 1 - (k & 1);
-    const int dst[2] = {sz >= 1 ? (sz - 1) * stride : -1, sz < tz ? sz * stride : -1};
-    const uint32_t base_cell =
-        (uint32_t(wrap(z0 - 1 + sz, n)) * uint32_t(n) + uint32_t(wrap(y - dy, n))) * uint32_t(n);
-    bool valid = j0 + lane < e;
-    R lo[2] = {R(0), R(0)}, hi[2] = {R(0), R(0)};
-    int c = n + 1 + lane;  // invalid lanes: unique targets past the row
-    if (valid) {
-      const uint32_t cx = rec_cell(rec) - base_cell;
-      // a record outside this row (only after a sort whose look-back timed
-      // out, which the error word reports) is skipped, not written out of bounds
-      valid = cx < uint32_t(n);
-      c = valid ? int(cx) : c;
-      const R wy = dy ? rec.z : R(1) - rec.z;
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const R wyz = wy * (d ? rec.w : R(1) - rec.w);
-        hi[d] = rec.y * wyz;
-        lo[d] = (R(1) - rec.y) * wyz;
-      }
-    }
-    seg_add_rows(lo, hi, c, valid, acc, dst);
-    k = k2, j0 = j2, e = e2, rec = rec2;
-  }
-  for (int lz = 0; lz < tz; ++lz) {
-    R* a = acc + lz * stride;
-    if (lane == 0) a[0] += a[n];
-    __syncwarp();
-    R* out = rho + (size_t(z0 + lz) * n + size_t(y)) * n;
-    if constexpr (sizeof(R) == 4) {
-      if ((n & 3) == 0) {  // 16-byte loads and stores
-        for (int i = 4 * lane; i < n; i += 128) {
-          const float4 v = *reinterpret_cast<const float4*>(a + i);
-          *reinterpret_cast<float4*>(out + i) = make_float4(v.x * norm, v.y * norm, v.z * norm, v.w * norm);
-        }
-        continue;
-      }
-    }
-    for (int i = lane; i < n; i += 32) out[i] = a[i] * norm;
-  }
-}
-
-// ---------------------------------------------------------------- Green's function
-__device__ __forceinline__ float sinpi_sq(float t) {
-  float s = sinpif(t);
-  return s * s;
-}
-__device__ __forceinline__ double sinpi_sq(double t) {
-  double s = sinpi(t);
-  return s * s;
-}
-
-// phi^_k = coef * rho^_k / sum_d sin^2(pi j_d / N), coef = -(3/2) Om dx^2 / (4 N^3):
-// the exact periodic inverse of the compact seven-point Laplacian with the
-// inverse-FFT normalisation folded in; k = 0 set to zero.  Also accumulates
-// sum_n rho_n phi_n = sum_k w_k G_k |rho^_k|^2 (Parseval over the half spectrum,
-// w = 1 on the x = 0 and x = N/2 planes, 2 elsewhere) for W_g.
 // e / d for every 32-bit e, by the multiply-high method for invariant divisors
 // (Granlund & Montgomery 1994): mul = 2^32 (2^l - d) / d + 1, l = ceil(log2 d)
 struct DivU32 {
@@ -460,6 +285,199 @@ __device__ __forceinline__ uint32_t divu32(uint32_t e, DivU32 dv) {
   return (t + ((e - t) >> 1)) >> (dv.l - 1);
 }
 
+// rho_n = norm * sum_i W(x_n - q_i): Eq. (rhodis) with the cloud-in-cell
+// tent, no floating-point atomics.  A warp owns a tile of TY x TZ mesh rows
+// (rows y0 .. y0 + TY - 1 of the planes z0 .. z0 + TZ - 1) and keeps them in
+// shared memory (N + 1 slots per row, slot N = node 0 seen from cell N - 1).
+// A particle of source row (z', y') adds to the rows (z' + dz, y' + dy),
+// dz, dy in {0, 1}, so the warp reads the source rows y0 - 1 .. y0 + TY - 1
+// of the planes z0 - 1 .. z0 + TZ - 1: each particle (TY + 1)(TZ + 1)/(TY TZ)
+// times (1.875 for 2 x 4, against 2.5 for a column of four rows of one y).
+// The source rows of one plane follow each other in the sorted order (a
+// "chain"; the periodic seam at y = 0 splits it), so the warp takes a chain
+// in full batches of 32 records that run across row boundaries.  In a batch:
+//  - equal cells (adjacent after the sort) are summed first by a segmented
+//    warp scan in a fixed tree order, and only the run's last lane adds;
+//  - the f_x weight of cell t goes to node t + 1, which is the 1 - f_x node
+//    of cell t + 1, so the f_x adds and the 1 - f_x adds are separated by
+//    __syncwarp;
+//  - source rows y' and y' + 1 share the destination row y' + 1, so the adds
+//    run in two phases: dy = 0 (each source row to its own row), then dy = 1
+//    (to the next row); within a phase no two source rows meet.
+// The warp alone writes its rows, in a fixed order of chains, batches and
+// phases, so the result is reproducible.
+constexpr int DEP_WARPS = 8;
+
+// slots of a deposit row: N + 1 rounded up to 16 bytes
+template <typename R>
+__host__ __device__ inline int deposit_stride_of(int n) {
+  const int q = 16 / int(sizeof(R));
+  return (n + 1 + q - 1) / q * q;
+}
+
+template <typename R, int TY, int TZ, bool PACKED>
+__global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>::v4* __restrict__ pos,
+                                                            const uint32_t* __restrict__ row_start, uint32_t np,
+                                                            Mesh m, DivU32 dvn, R norm, R* __restrict__ rho,
+                                                            size_t ms) {
+  using V4 = typename VT<R>::v4;
+  static_assert((TY + 1) * (TZ + 1) <= 32, "one source row per lane");
+  if constexpr (PACKED) {  // member blockIdx.y of a packed group
+    const size_t o = size_t(blockIdx.y) * ms;
+    pos = moff(pos, o), row_start = moff(row_start, o), rho = moff(rho, o);
+  }
+  extern __shared__ __align__(16) unsigned char dep_smem[];
+  const int n = m.n, stride = deposit_stride_of<R>(n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int span_y = nw * TY, tiles_y = (n + span_y - 1) / span_y;
+  const int y0 = int(blockIdx.x % unsigned(tiles_y)) * span_y + warp * TY, z0 = int(blockIdx.x / unsigned(tiles_y)) * TZ;
+  if (y0 >= n) return;
+  const int ty = min(TY, n - y0), tz = min(TZ, n - z0);
+  R* acc = reinterpret_cast<R*>(dep_smem) + warp * (TY * TZ * stride);  // [TZ][TY][N + 1], this warp's
+  for (int i = lane; i < TY * TZ * stride * int(sizeof(R)) / 16; i += 32)
+    reinterpret_cast<float4*>(acc)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  __syncwarp();
+  // the (tz + 1)(ty + 1) source rows, one per lane: plane slot sz (plane z0 - 1 + sz), row slot ly
+  // (row y0 - 1 + ly).  A lane whose row does not follow the previous lane's in memory heads a chain,
+  // which runs up to the next head.
+  const int nr = (tz + 1) * (ty + 1);
+  const int sz_l = lane / (ty + 1), ly_l = lane - sz_l * (ty + 1);
+  bool head = false;
+  uint32_t b = 0, e = 0, base = 0;
+  if (lane < nr) {
+    const int yr = wrap(y0 - 1 + ly_l, n);
+    const uint32_t srow = uint32_t(wrap(z0 - 1 + sz_l, n)) * uint32_t(n) + uint32_t(yr);
+    b = __ldg(row_start + srow);
+    e = min(__ldg(row_start + srow + 1), np);
+    head = ly_l == 0 || yr != wrap(y0 - 2 + ly_l, n) + 1;
+    base = srow * uint32_t(n);
+  }
+  const uint32_t heads = __ballot_sync(0xffffffffu, head);
+  const uint32_t later = heads & ~((2u << lane) - 1u);
+  const int last = (later ? __ffs(later) - 1 : nr) - 1;                  // the chain's last row (head lanes)
+  const uint32_t ce = __shfl_sync(0xffffffffu, e, last < 0 ? 0 : last);  // the chain's end
+  const int crows = last - lane + 1;                                     // rows in the chain
+  uint32_t todo = __ballot_sync(0xffffffffu, head && b < ce);            // nonempty chains, in order
+  if (todo) {
+    int k = __ffs(todo) - 1;
+    todo &= todo - 1;
+    uint32_t j = __shfl_sync(0xffffffffu, b, k), en = __shfl_sync(0xffffffffu, ce, k);
+    V4 rec = {};
+    if (j + lane < en) rec = ldg(pos + j + lane);
+    // batches of 32 records, the next batch's records loaded while the current one is added
+    for (;;) {
+      int k2 = k;
+      uint32_t j2 = j + 32, e2 = en, todo2 = todo;
+      bool more = true;
+      if (j2 >= en) {
+        if (todo2) {
+          k2 = __ffs(todo2) - 1;
+          todo2 &= todo2 - 1;
+          j2 = __shfl_sync(0xffffffffu, b, k2), e2 = __shfl_sync(0xffffffffu, ce, k2);
+        } else {
+          more = false;
+        }
+      }
+      V4 rec2 = {};
+      if (more && j2 + lane < e2) rec2 = ldg(pos + j2 + lane);
+      const int sz = __shfl_sync(0xffffffffu, sz_l, k), ly0 = __shfl_sync(0xffffffffu, ly_l, k);
+      const int nrc = __shfl_sync(0xffffffffu, crows, k);
+      const uint32_t cbase = __shfl_sync(0xffffffffu, base, k);
+      bool valid = j + lane < en;
+      uint32_t key = 0x80000000u + uint32_t(lane);  // invalid lanes: unique keys
+      int x = 0, ly = 0;
+      R v[2][2][2];  // [dy][dz][0: 1 - f_x to node x, 1: f_x to node x + 1]
+      if (valid) {
+        const uint32_t rel = rec_cell(rec) - cbase;
+        const uint32_t off = divu32(rel, dvn);
+        // a record outside the chain's rows (only after a sort whose look-back
+        // timed out, which the error word reports) is skipped, not written out of bounds
+        valid = off < uint32_t(nrc);
+        if (valid) key = rel, ly = ly0 + int(off), x = int(rel - off * uint32_t(n));
+      }
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const R wz = dz ? rec.w : R(1) - rec.w;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const R w = (dy ? rec.z : R(1) - rec.z) * wz;
+          v[dy][dz][1] = rec.y * w;
+          v[dy][dz][0] = (R(1) - rec.y) * w;
+        }
+      }
+      const uint32_t kp = __shfl_up_sync(0xffffffffu, key, 1);
+      const uint32_t runs = __ballot_sync(0xffffffffu, lane == 0 || kp != key);
+      if (runs != 0xffffffffu) {  // some cell holds several particles of the batch
+        // length of the run that starts at this lane (0 elsewhere), and the longest; the scan stops
+        // after the steps the longest run needs (the skipped steps would add nothing)
+        const uint32_t above = runs & ~((2u << lane) - 1u);
+        const int len = ((runs >> lane) & 1u) ? (above ? __ffs(above) - 1 : 32) - lane : 0;
+        const int longest = int(__reduce_max_sync(0xffffffffu, uint32_t(len)));
+        for (int off = 1; off < longest; off <<= 1) {
+          R u[2][2][2];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) (&u[0][0][0])[a] = __shfl_up_sync(0xffffffffu, (&v[0][0][0])[a], off);
+          // lane - off is in this lane's run iff no run starts in (lane - off, lane]
+          const uint32_t span = lane >= off ? ((2u << lane) - 1u) & ~((2u << (lane - off)) - 1u) : 0u;
+          if (lane >= off && !(runs & span)) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a) (&v[0][0][0])[a] += (&u[0][0][0])[a];
+          }
+        }
+      }
+      const bool add = valid && (lane == 31 || ((runs >> (lane + 1)) & 1u));
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const int ry = ly - 1 + dy;  // destination row of this phase
+        const bool okr = add && unsigned(ry) < unsigned(ty);
+        const bool ok0 = okr && sz >= 1, ok1 = okr && sz < tz;  // planes sz - 1 (dz = 0) and sz (dz = 1)
+        const int a0 = ((sz - 1) * TY + ry) * stride + x, a1 = a0 + TY * stride;
+        if (ok0) acc[a0 + 1] += v[dy][0][1];
+        if (ok1) acc[a1 + 1] += v[dy][1][1];
+        __syncwarp();
+        if (ok0) acc[a0] += v[dy][0][0];
+        if (ok1) acc[a1] += v[dy][1][0];
+        __syncwarp();
+      }
+      if (!more) break;
+      k = k2, j = j2, en = e2, todo = todo2, rec = rec2;
+    }
+  }
+  for (int lz = 0; lz < tz; ++lz) {
+    for (int ry = 0; ry < ty; ++ry) {
+      R* a = acc + (lz * TY + ry) * stride;
+      if (lane == 0) a[0] += a[n];
+      __syncwarp();
+      R* out = rho + (size_t(z0 + lz) * n + size_t(y0 + ry)) * n;
+      if constexpr (sizeof(R) == 4) {
+        if ((n & 3) == 0) {  // 16-byte loads and stores
+          for (int i = 4 * lane; i < n; i += 128) {
+            const float4 q = *reinterpret_cast<const float4*>(a + i);
+            *reinterpret_cast<float4*>(out + i) = make_float4(q.x * norm, q.y * norm, q.z * norm, q.w * norm);
+          }
+          continue;
+        }
+      }
+      for (int i = lane; i < n; i += 32) out[i] = a[i] * norm;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Green's function
+__device__ __forceinline__ float sinpi_sq(float t) {
+  float s = sinpif(t);
+  return s * s;
+}
+__device__ __forceinline__ double sinpi_sq(double t) {
+  double s = sinpi(t);
+  return s * s;
+}
+
+// phi^_k = coef * rho^_k / sum_d sin^2(pi j_d / N), coef = -(3/2) Om dx^2 / (4 N^3):
+// the exact periodic inverse of the compact seven-point Laplacian with the
+// inverse-FFT normalisation folded in; k = 0 set to zero.  Also accumulates
+// sum_n rho_n phi_n = sum_k w_k G_k |rho^_k|^2 (Parseval over the half spectrum,
+// w = 1 on the x = 0 and x = N/2 planes, 2 elsewhere) for W_g.
 // phi^ = -(3/2) Omega_m rho^ / kappa^2 in place over the half spectrum, with
 // kappa^2 = (4/dx^2) sum_d sin^2(k_d dx/2) the exact symbol of the seven-point
 // Laplacian (the comoving Poisson equation of Sec. II), and the Parseval
@@ -1857,26 +1875,38 @@ cudaError_t launch_init_particles(const double* x, const double* p, int64_t n, M
   return cudaGetLastError();
 }
 
-// rows along z of a deposit column: the most of 4, 2, 1 whose rows fit 8.5 KB of shared memory per warp
+// deposit tile of TY x TZ rows per warp: the largest of 2 x 4, 2 x 2, 1 x 2, 1 x 1 whose rows fit
+// PM_DEPOSIT_WARP_BYTES of shared memory per 4-byte accumulator (4.25 KB: 2 x 2 rows of a 256^3
+// fp32 mesh; measured there: 43 us against 53 us for 2 x 4 rows, whose 8.3 KB per warp leave
+// too few resident warps)
+#ifndef PM_DEPOSIT_WARP_BYTES
+#define PM_DEPOSIT_WARP_BYTES 4352
+#endif
 template <typename R>
-inline int deposit_tz(int n) {
-  for (int tz = 4; tz > 1; tz >>= 1)
-    if (size_t(tz) * deposit_stride_of<R>(n) * sizeof(R) <= size_t(8704)) return tz;
-  return 1;
+inline int deposit_shape(int n, int& ty, int& tz) {
+  static const int shapes[4][2] = {{2, 4}, {2, 2}, {1, 2}, {1, 1}};
+  const size_t row = size_t(deposit_stride_of<R>(n)) * sizeof(R);
+  const size_t most = size_t(PM_DEPOSIT_WARP_BYTES) * sizeof(R) / 4;
+  int s = 0;
+  while (s < 3 && size_t(shapes[s][0] * shapes[s][1]) * row > most) ++s;
+  ty = shapes[s][0], tz = shapes[s][1];
+  return s;
 }
 
-template <typename R, int TZ>
-cudaError_t launch_deposit_tz(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
-                              cudaStream_t s, int warps, int nm, size_t ms) {
+template <typename R, int TY, int TZ>
+cudaError_t launch_deposit_tile(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
+                                cudaStream_t s, int warps, int nm, size_t ms) {
   using V4 = typename VT<R>::v4;
-  const size_t smem = size_t(warps) * TZ * deposit_stride_of<R>(m.n) * sizeof(R);
-  const unsigned blocks = unsigned((m.n + warps - 1) / warps) * unsigned((m.n + TZ - 1) / TZ);
+  const size_t smem = size_t(warps) * TY * TZ * deposit_stride_of<R>(m.n) * sizeof(R);
+  const unsigned tiles_y = unsigned((m.n + warps * TY - 1) / (warps * TY));
+  const unsigned blocks = tiles_y * unsigned((m.n + TZ - 1) / TZ);
+  const DivU32 dv = divu32_make(uint32_t(m.n));
   if (nm > 1)
-    k_deposit<R, TZ, true><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>((const V4*)pos, row_start,
-                                                                                 uint32_t(n), m, R(norm), rho, ms);
+    k_deposit<R, TY, TZ, true><<<dim3(blocks, unsigned(nm)), warps * 32, smem, s>>>(
+        (const V4*)pos, row_start, uint32_t(n), m, dv, R(norm), rho, ms);
   else
-    k_deposit<R, TZ, false><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, R(norm), rho,
-                                                             0);
+    k_deposit<R, TY, TZ, false><<<blocks, warps * 32, smem, s>>>((const V4*)pos, row_start, uint32_t(n), m, dv,
+                                                                 R(norm), rho, 0);
   return cudaGetLastError();
 }
 
@@ -1884,27 +1914,31 @@ template <typename R>
 cudaError_t launch_deposit(const void* pos, const uint32_t* row_start, int64_t n, Mesh m, double norm, R* rho,
                            cudaStream_t s, int warps, int nm, size_t ms) {
   if (warps < 1 || warps > DEP_WARPS) warps = DEP_WARPS;
-  const int tz = deposit_tz<R>(m.n);
-  if (size_t(warps) * tz * deposit_stride_of<R>(m.n) * sizeof(R) > 48 * 1024) {
+  int ty = 1, tz = 1;
+  const int shape = deposit_shape<R>(m.n, ty, tz);
+  if (size_t(warps) * ty * tz * deposit_stride_of<R>(m.n) * sizeof(R) > 48 * 1024) {
     // once per device, for every tile shape, so that no attribute call falls inside a stream capture
     static bool done[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !done[dev]) {
-      const int most = 68 * 1024;
+      const int most = int(DEP_WARPS * PM_DEPOSIT_WARP_BYTES * sizeof(R) / 4);
       cudaError_t e = cudaSuccess;
-      void* fns[6] = {(void*)k_deposit<R, 4, false>, (void*)k_deposit<R, 4, true>, (void*)k_deposit<R, 2, false>,
-                      (void*)k_deposit<R, 2, true>,  (void*)k_deposit<R, 1, false>, (void*)k_deposit<R, 1, true>};
+      void* fns[8] = {(void*)k_deposit<R, 2, 4, false>, (void*)k_deposit<R, 2, 4, true>,
+                      (void*)k_deposit<R, 2, 2, false>, (void*)k_deposit<R, 2, 2, true>,
+                      (void*)k_deposit<R, 1, 2, false>, (void*)k_deposit<R, 1, 2, true>,
+                      (void*)k_deposit<R, 1, 1, false>, (void*)k_deposit<R, 1, 1, true>};
       for (void* f : fns)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
       if (e != cudaSuccess) return e;
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  switch (tz) {
-    case 4: return launch_deposit_tz<R, 4>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
-    case 2: return launch_deposit_tz<R, 2>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
-    default: return launch_deposit_tz<R, 1>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+  switch (shape) {
+    case 0: return launch_deposit_tile<R, 2, 4>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+    case 1: return launch_deposit_tile<R, 2, 2>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+    case 2: return launch_deposit_tile<R, 1, 2>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
+    default: return launch_deposit_tile<R, 1, 1>(pos, row_start, n, m, norm, rho, s, warps, nm, ms);
   }
 }
 

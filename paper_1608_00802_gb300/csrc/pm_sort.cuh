@@ -435,6 +435,14 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
   const uint32_t tile = blockIdx.x;
   const int64_t tile_base = int64_t(tile) * RS_TILE;
   const uint32_t lt = lanemask_lt();
+  // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32; all its keys
+  // are requested before anything waits on them
+  uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
+    key[r] = i < n ? __ldg(keys + i) : 0u;
+  }
   // movers before this tile: the tile scan's, or (few tiles) summed here from the drift's counts
   uint32_t excl;
   if (own_scan) {
@@ -451,12 +459,9 @@ static __global__ void __launch_bounds__(RS_THREADS) k_mover_partition(
   } else {
     excl = __ldg(tcount + ntiles + tile);
   }
-  // warp w owns slots [w*RS_ITEMS*32, (w+1)*RS_ITEMS*32) of the tile, in rounds of 32
-  uint32_t key[RS_ITEMS], rank[RS_ITEMS], mcount = 0;
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int64_t i = tile_base + warp * (RS_ITEMS * 32) + r * 32 + lane;
-    key[r] = i < n ? __ldg(keys + i) : 0u;
     const bool mover = i < n && (key[r] & KEY_MOVER);
     const uint32_t b = __ballot_sync(0xffffffffu, mover);
     rank[r] = mcount + __popc(b & lt);  // movers before this slot in the warp
