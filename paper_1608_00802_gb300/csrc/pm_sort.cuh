@@ -685,23 +685,22 @@ __global__ void __launch_bounds__(PF_THREADS) k_place(
   }
   const uint32_t ns = counts[0], nrows = n_mesh * n_mesh;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t k, v, out;
-    if (i < ns) {
-      k = __ldg(sk + i), v = __ldg(sv + i);
-      const uint32_t r = key_row(k, n_mesh, log2n);
-      if (r >= nrows) continue;  // (only a corrupt key)
-      const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
-      uint32_t c = 0;
-      for (uint32_t u = m0; u < m1; ++u) c += kv_less(__ldg(bk + u), __ldg(bv + u), k, v) ? 1u : 0u;
+    const bool stayer = i < ns;
+    const uint32_t k = stayer ? __ldg(sk + i) : __ldg(bk + (i - ns));
+    const uint32_t v = stayer ? __ldg(sv + i) : __ldg(bv + (i - ns));
+    // the record is requested as soon as its slot is known: its load overlaps the
+    // place computation instead of following it
+    if (v >= n) continue;  // (only after corrupt counts)
+    const V4 pr = pos_in[v], mr = mom_in[v];
+    const uint32_t r = key_row(k, n_mesh, log2n);
+    if (r >= nrows) continue;  // (only a corrupt key)
+    const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
+    uint32_t c = 0;
+    for (uint32_t u = m0; u < m1; ++u) c += kv_less(__ldg(bk + u), __ldg(bv + u), k, v) ? 1u : 0u;
+    uint32_t out;
+    if (stayer) {
       out = i + m0 + c;
     } else {
-      const uint32_t u = i - ns;
-      k = __ldg(bk + u), v = __ldg(bv + u);
-      const uint32_t r = key_row(k, n_mesh, log2n);
-      if (r >= nrows) continue;
-      const uint32_t m0 = __ldg(mrow + r), m1 = __ldg(mrow + r + 1);
-      uint32_t c = 0;
-      for (uint32_t w = m0; w < m1; ++w) c += kv_less(__ldg(bk + w), __ldg(bv + w), k, v) ? 1u : 0u;
       const uint32_t s0 = __ldg(srow + r);
       uint32_t lo = s0, hi = __ldg(srow + r + 1);
       while (lo < hi) {  // the row's stayers before it
@@ -715,8 +714,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_place(
     }
     if (out >= n) continue;  // (only after corrupt counts)
     keys_out[out] = k;
-    pos_out[out] = pos_in[v];
-    mom_out[out] = mom_in[v];
+    pos_out[out] = pr;
+    mom_out[out] = mr;
   }
 }
 
