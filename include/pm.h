@@ -221,8 +221,11 @@ typedef struct {
                               planes of constant z with batched 2D transforms and does the z transforms, the
                               Green multiplication and the inverse z transforms in one kernel between them
                               (the spectrum crosses device memory once instead of three times; the default
-                              where it applies); 0 uses the 3D transforms and a separate Green pass.  The
-                              potential agrees to fp32 rounding either way */
+                              where it applies); 2 (256^3 meshes only, their default) does the same with
+                              the x and y transforms of each plane in one kernel per direction (a cluster of
+                              CTAs per plane) instead of the batched 2D cuFFT plans; 0 uses the 3D
+                              transforms and a separate Green pass.  The potential agrees to fp32 rounding
+                              in every mode */
 } pm_tuning;
 
 /* Current shapes. */

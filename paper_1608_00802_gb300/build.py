@@ -1,7 +1,8 @@
 """Builds libpm.so (the C-ABI library) in-tree for sm_103a with nvcc.
 
-Three translation units compile in parallel (host API, fp32 kernels, fp64
-kernels) and link against cuFFT.  Usage: ``python -m paper_1608_00802_gb300.build``.
+The translation units compile in parallel (host API, fp32 kernels, fp64
+kernels, the allocation-free deposit, the fused x-y transforms) and link
+against cuFFT.  Usage: ``python -m paper_1608_00802_gb300.build``.
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpm.so")
-SOURCES = ["pm_api.cu", "pm_kernels_f32.cu", "pm_kernels_f64.cu", "pm_noalloc.cu"]
+SOURCES = ["pm_api.cu", "pm_kernels_f32.cu", "pm_kernels_f64.cu", "pm_noalloc.cu", "pm_xyfft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

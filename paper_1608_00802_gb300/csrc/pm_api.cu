@@ -646,7 +646,10 @@ pm_status mesh_from_density(pm_sim* s) {
     const int N = s->cfg.n_mesh;
     {
       PROF(s, PM_STAGE_FFT_R2C);
-      CF(s, cufftExecR2C(s->plan2_fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
+      if (s->tune.green_fused == 2)
+        CU(s, launch_xy_r2c(s->at<float>(L.rho), s->arena + L.spec, s->at<float2>(L.green), N, s->stream));
+      else
+        CF(s, cufftExecR2C(s->plan2_fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));
     }
     {
       PROF(s, PM_STAGE_GREEN);
@@ -656,7 +659,10 @@ pm_status mesh_from_density(pm_sim* s) {
     s->wg_count = spec_z_tiles(N);
     {
       PROF(s, PM_STAGE_FFT_C2R);
-      CF(s, cufftExecC2R(s->plan2_inv, (cufftComplex*)(s->arena + L.spec), s->at<cufftReal>(L.phi)));
+      if (s->tune.green_fused == 2)
+        CU(s, launch_xy_c2r(s->arena + L.spec, s->at<float>(L.phi), s->at<float2>(L.green), N, s->stream));
+      else
+        CF(s, cufftExecC2R(s->plan2_inv, (cufftComplex*)(s->arena + L.spec), s->at<cufftReal>(L.phi)));
     }
     PMST(quantum_stage<R>(s));
     s->fields_valid = true;
@@ -1077,7 +1083,7 @@ pm_status pm_create(const pm_config* c, void* dev_arena, size_t bytes, void* str
   // and the separate pass stay.
   if (c->precision == PM_FP32 && c->kernel == PM_KERNEL_CIC && spec_z_supported(N) && N >= GREEN_FUSE_MIN_MESH) {
     std::string ignored;
-    if (spec_plan_setup(s, &ignored) == CUFFT_SUCCESS) s->tune.green_fused = 1;
+    if (spec_plan_setup(s, &ignored) == CUFFT_SUCCESS) s->tune.green_fused = xy_fft_supported(N) ? 2 : 1;
   }
   if (s->cfg.kernel == PM_KERNEL_SPLINE) {
     s->direct = c->smooth_real != 0;
@@ -1506,9 +1512,11 @@ pm_status pm_set_tuning(pm_sim* s, const pm_tuning* t) {
   if (!stencil_shape_ok(n, t->stencil_rows, t->stencil_planes, t->stencil_stages))
     return fail(s, PM_ERR_INVALID_ARG, "stencil shape (%d rows, %d planes, %d stages) is not valid for N = %d",
                 t->stencil_rows, t->stencil_planes, t->stencil_stages, n);
-  if (t->green_fused != 0 && t->green_fused != 1) return fail(s, PM_ERR_INVALID_ARG, "green_fused must be 0 or 1");
+  if (t->green_fused < 0 || t->green_fused > 2) return fail(s, PM_ERR_INVALID_ARG, "green_fused must be 0, 1 or 2");
   if (t->green_fused && (s->fp64() || spline(s) || !spec_z_supported(s->cfg.n_mesh)))
     return fail(s, PM_ERR_INVALID_ARG, "green_fused needs PM_FP32, the cloud-in-cell kernel and a power-of-two mesh");
+  if (t->green_fused == 2 && !xy_fft_supported(s->cfg.n_mesh))
+    return fail(s, PM_ERR_INVALID_ARG, "green_fused = 2 (the fused x-y transform kernels) needs a 256^3 mesh");
   drop_graphs(s);
   if (t->green_fused) {
     std::string why;
@@ -1856,7 +1864,8 @@ bool same_state(const pm_batch::Class& C, const std::vector<pm_sim*>& sims) {
         s->keys_marked != a->keys_marked || (s->keys - s->at<uint32_t>(0)) != (a->keys - a->at<uint32_t>(0)) ||
         s->tune.st_ty != a->tune.st_ty || s->tune.st_zlen != a->tune.st_zlen ||
         s->tune.st_stages != a->tune.st_stages || s->tune.kick_threads != a->tune.kick_threads ||
-        s->tune.dep_warps != a->tune.dep_warps || green_fused(s) != green_fused(a))
+        s->tune.dep_warps != a->tune.dep_warps || green_fused(s) != green_fused(a) ||
+        s->tune.green_fused != a->tune.green_fused)
       return false;
   }
   if (!green_fused(a) && !C.fwd) return false;  // the class's batched 3D transforms were not planned
@@ -1902,7 +1911,10 @@ pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cuda
   PCU(launch_deposit<float>(s->arena + L.pos[nxt], s->at<uint32_t>(L.row_start), n, s->mesh, s->norm,
                             s->at<float>(L.rho), st, s->tune.dep_warps, nm, ms));
   const bool fused = green_fused(s);
-  if (fused) {  // each member's own 2D transforms (the same as alone), the z kernel over the whole class
+  const bool own_xy = fused && s->tune.green_fused == 2;
+  if (own_xy)  // the x-y transforms of every member's planes in one launch
+    PCU(launch_xy_r2c(s->at<float>(L.rho), s->arena + L.spec, s->at<float2>(L.green), N, st, nm, ms));
+  if (fused && !own_xy) {  // each member's own 2D transforms (the same as alone)
     for (int i : C.members) {
       pm_sim* m = sims[i];
       CF(s, cufftSetStream(m->plan2_fwd, st));
@@ -1910,8 +1922,13 @@ pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cuda
       CF(s, cufftSetStream(m->plan2_fwd, m->stream));
       CF(s, r);
     }
+  }
+  if (fused) {  // the z kernel over the whole class
     PCU(launch_spec_z(s->arena + L.spec, s->at<float2>(L.green), s->at<float>(L.green + size_t(N) * 8), s->mesh,
                       green_coef(s), wg_part(s), st, s->coefs(), nm, ms));
+  }
+  if (own_xy) PCU(launch_xy_c2r(s->arena + L.spec, s->at<float>(L.phi), s->at<float2>(L.green), N, st, nm, ms));
+  if (fused && !own_xy) {
     for (int i : C.members) {
       pm_sim* m = sims[i];
       CF(s, cufftSetStream(m->plan2_inv, st));
@@ -1919,7 +1936,8 @@ pm_status packed_step(pm_batch::Class& C, const std::vector<pm_sim*>& sims, cuda
       CF(s, cufftSetStream(m->plan2_inv, m->stream));
       CF(s, r);
     }
-  } else {
+  }
+  if (!fused) {
     CF(s, cufftSetStream(C.fwd, st));
     CF(s, cufftSetStream(C.inv, st));
     CF(s, cufftExecR2C(C.fwd, s->at<cufftReal>(L.rho), (cufftComplex*)(s->arena + L.spec)));

@@ -149,6 +149,13 @@ cudaError_t launch_resort(int part, const uint32_t* keys, int64_t n, const uint3
                           void* pos_out, void* mom_out, int sms, cudaStream_t s, int nm = 1, size_t ms = 0);
 inline size_t row_scan_tiles(int n_mesh) { return (size_t(n_mesh) * n_mesh + 1023) / 1024; }  // tiles of 1024 rows
 cudaError_t launch_step_inc(uint32_t* step, cudaStream_t s, int nm = 1, size_t ms = 0);
+// the x-y transforms of the z-planes of a 256^3 fp32 mesh, one kernel per direction (unnormalised,
+// the layouts of the batched 2D R2C / C2R); tw: exp(-2 pi i t / 256), t < 256
+bool xy_fft_supported(int n_mesh);
+cudaError_t launch_xy_r2c(const float* rho, void* spec, const void* tw, int n_mesh, cudaStream_t s, int nm = 1,
+                          size_t ms = 0);
+cudaError_t launch_xy_c2r(const void* spec, float* phi, const void* tw, int n_mesh, cudaStream_t s, int nm = 1,
+                          size_t ms = 0);
 // row starts of sorted keys
 cudaError_t launch_row_start(const uint32_t* keys, int64_t n, uint32_t n_mesh, uint32_t* row_start, cudaStream_t s);
 // (nm, ms: a packed group of nm members, ms bytes apart; coefp/qcp: member
