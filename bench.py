@@ -339,19 +339,23 @@ def measure(pm, sim, w, K, W, stream, rsz=4, spline=False, tuning=None, peak=Non
         avg = ms / cnt
         per_stage[name] = {"ms_per_step": ms / K, "launches": cnt, "avg_launch_ms": avg,
                            "bytes_per_launch": b, "GBps": (b / (avg / 1e3) / 1e9) if b else None}
-    ours = {k: v for k, v in per_stage.items() if k not in pm.CUFFT_STAGES and v["GBps"] is not None}
+    # the transform stages are cuFFT's, except with the fused x-y kernels of 256^3 meshes (green_fused = 2)
+    own_xy = sim.get_tuning().get("green_fused") == 2
+    lib_stages = () if own_xy else pm.CUFFT_STAGES
+    names = dict(KERNEL_NAMES, **({"fft_r2c": "k_xy_r2c", "fft_c2r": "k_xy_c2r"} if own_xy else {}))
+    ours = {k: v for k, v in per_stage.items() if k not in lib_stages and v["GBps"] is not None}
     dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
     d = per_stage[dom]
-    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES.get(dom, dom), "achieved": d["GBps"], "peak": peak,
+    roofline = {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": d["GBps"], "peak": peak,
                 "unit": "GB/s", "frac": d["GBps"] / peak if d["GBps"] else None,
-                "traffic": ncu_traffic(KERNEL_NAMES.get(dom, dom), workload_key) if workload_key else None,
+                "traffic": ncu_traffic(names.get(dom, dom), workload_key) if workload_key else None,
                 "algorithmic_bytes_per_launch": d["bytes_per_launch"]}
     step_bytes = step_bytes_fft = fft_ms = 0.0
     for name, (ms, cnt) in stages.items():
         b = algorithmic_bytes(name, n, nm, rsz, movers=movers, spline=spline)
         if cnt and b:
             step_bytes += b * cnt / K
-            if name in pm.CUFFT_STAGES:
+            if name in lib_stages:
                 step_bytes_fft += b * cnt / K
                 fft_ms += ms / K
     t_step = t_ms / K
@@ -359,10 +363,11 @@ def measure(pm, sim, w, K, W, stream, rsz=4, spline=False, tuning=None, peak=Non
                      "frac": step_bytes / (t_step / 1e3) / 1e9 / peak,
                      "frac_excl_cufft": ((step_bytes - step_bytes_fft) / (max(t_step - fft_ms, 1e-9) / 1e3) / 1e9
                                          / peak),
-                     "note": "cuFFT time taken from the profiled pass; peak as in roofline"}
+                     "note": ("no library kernels on the path (the transforms are the fused x-y kernels)" if own_xy
+                              else "cuFFT time taken from the profiled pass; peak as in roofline")}
     # our kernels per timed region: the profiled pass launches the same kernels one by one; the replayed
     # graph adds one step-counter kernel per step
-    launches = sum(v["launches"] for k, v in per_stage.items() if k not in pm.CUFFT_STAGES) + K
+    launches = sum(v["launches"] for k, v in per_stage.items() if k not in lib_stages) + K
     return {"value": n * K / (t_ms / 1e3), "t_ms": t_ms, "ms_per_step": t_step, "stages": per_stage,
             "roofline": roofline, "step_roofline": step_roofline, "launches": launches,
             "movers_per_step": movers, "clocks": clk.summary(), "launch_shapes": tuning}
