@@ -3,7 +3,8 @@
 // the inverse transform of the potential after it), in place of the batched
 // 2D cuFFT plans, which read and write every plane twice.
 //
-// A cluster of eight CTAs owns one plane (four with PM_XY_CLUSTER=4).  Forward (real rows -> half spectrum):
+// A cluster of eight CTAs owns one plane (four with PM_XY_CLUSTER=4).
+// Forward (real rows -> half spectrum):
 //  - CTA q transforms its 32 rows y = 32 q .. 32 q + 31 along x.  A 256-point
 //    real transform is a 128-point complex one of z[m] = x[2m] + i x[2m+1]
 //    (four-step, 128 = 8 x 16: thread j of a row does the 16-point DFT over
@@ -12,8 +13,8 @@
 //      X[k] = E[k] + W^k O[k],  E = (Z[k] + Z*[128-k]) / 2,
 //      O = -i (Z[k] - Z*[128-k]) / 2,  W = exp(-2 pi i / 256);
 //    X[0] and X[128] are real and travel packed as X[0] + i X[128].
-//  - Every CTA writes its rows' values into the shared memory of the CTA
-//    that owns their column (columns 16 q' .. 16 q' + 15 belong to CTA q').
+//  - After a cluster barrier, CTA q reads its columns (16 q .. 16 q + 15) of
+//    every row from the shared memory of the CTA that owns the row.
 //  - CTA q transforms its 16 columns along y (four-step, 256 = 16 x 16, as
 //    in the z kernel) and writes them to the half spectrum [z][ky][kx].  The
 //    packed column holds the transforms A + i B of two real sequences, so
@@ -76,7 +77,7 @@ __global__ void __cluster_dims__(XY_CL, 1, 1) __launch_bounds__(XY_THREADS, XY_M
   float2* tw = T + XY_TSZ;
   cg::cluster_group cl = cg::this_cluster();
   const int q = int(cl.block_rank()), z = int(blockIdx.x) / XY_CL, tid = threadIdx.x;
-  // the CTA's 64 rows by 16-byte asynchronous copies, XY_SROW complex values apart
+  // the CTA's XY_ROWS rows by 16-byte asynchronous copies, XY_SROW complex values apart
   {
     float* R = reinterpret_cast<float*>(T);
     const float* src = rho + (size_t(z) * XY_N + size_t(XY_ROWS) * q) * XY_N;
