@@ -9,6 +9,7 @@
 // None of these kernels use floating-point atomics on the step's data, so a
 // step is bitwise reproducible for a fixed launch configuration.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -426,19 +427,30 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
         }
       }
       const bool add = valid && (lane == 31 || ((runs >> (lane + 1)) & 1u));
+      // planes sz - 1 (dz = 0) and sz (dz = 1); the edge plane slots of the tile have one of the two,
+      // and the chain's slot is the same for the whole warp, so the adds branch on it instead of
+      // issuing the missing half predicated off
+      auto adds = [&](auto h0, auto h1) {
+        constexpr bool H0 = decltype(h0)::value, H1 = decltype(h1)::value;
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const int ry = ly - 1 + dy;  // destination row of this phase
-        const bool okr = add && unsigned(ry) < unsigned(ty);
-        const bool ok0 = okr && sz >= 1, ok1 = okr && sz < tz;  // planes sz - 1 (dz = 0) and sz (dz = 1)
-        const int a0 = ((sz - 1) * TY + ry) * stride + x, a1 = a0 + TY * stride;
-        if (ok0) acc[a0 + 1] += v[dy][0][1];
-        if (ok1) acc[a1 + 1] += v[dy][1][1];
-        __syncwarp();
-        if (ok0) acc[a0] += v[dy][0][0];
-        if (ok1) acc[a1] += v[dy][1][0];
-        __syncwarp();
-      }
+        for (int dy = 0; dy < 2; ++dy) {
+          const int ry = ly - 1 + dy;  // destination row of this phase
+          const bool okr = add && unsigned(ry) < unsigned(ty);
+          const int a0 = ((sz - 1) * TY + ry) * stride + x, a1 = a0 + TY * stride;
+          if (H0 && okr) acc[a0 + 1] += v[dy][0][1];
+          if (H1 && okr) acc[a1 + 1] += v[dy][1][1];
+          __syncwarp();
+          if (H0 && okr) acc[a0] += v[dy][0][0];
+          if (H1 && okr) acc[a1] += v[dy][1][0];
+          __syncwarp();
+        }
+      };
+      if (sz >= 1 && sz < tz)
+        adds(std::true_type{}, std::true_type{});
+      else if (sz >= 1)
+        adds(std::true_type{}, std::false_type{});
+      else
+        adds(std::false_type{}, std::true_type{});
       if (!more) break;
       k = k2, j = j2, en = e2, todo = todo2, rec = rec2;
     }
