@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(const typename VT<R>
         for (int dy = 0; dy < 2; ++dy) {
           const int ry = ly - 1 + dy;  // destination row of this phase
           const bool okr = add && unsigned(ry) < unsigned(ty);
+          if (!__any_sync(0xffffffffu, okr)) continue;  // a batch within the chain's first or last row
           const int a0 = ((sz - 1) * TY + ry) * stride + x, a1 = a0 + TY * stride;
           if (H0 && okr) acc[a0 + 1] += v[dy][0][1];
           if (H1 && okr) acc[a1 + 1] += v[dy][1][1];
