@@ -367,7 +367,10 @@ def measure(pm, sim, w, K, W, stream, rsz=4, spline=False, tuning=None, peak=Non
                               else "cuFFT time taken from the profiled pass; peak as in roofline")}
     # our kernels per timed region: the profiled pass launches the same kernels one by one; the replayed
     # graph adds one step-counter kernel per step
-    launches = sum(v["launches"] for k, v in per_stage.items() if k not in lib_stages) + K
+    # (the "sort_pass" record covers three kernels: row totals, row scan, bucket scatter; the partition
+    # adds a tile scan beyond 2048 tiles of 2048 particles)
+    per_record = {"sort_pass": 3, "sort_partition": 1 + int((n + 2047) // 2048 > 2048)}
+    launches = sum(v["launches"] * per_record.get(k, 1) for k, v in per_stage.items() if k not in lib_stages) + K
     return {"value": n * K / (t_ms / 1e3), "t_ms": t_ms, "ms_per_step": t_step, "stages": per_stage,
             "roofline": roofline, "step_roofline": step_roofline, "launches": launches,
             "movers_per_step": movers, "clocks": clk.summary(), "launch_shapes": tuning}
