@@ -216,7 +216,7 @@ typedef struct {
   int32_t stencil_stages;  /* 0 = one-shot tile (the block loads its whole input at once); 4..8 = a
                               sweep along z through a ring of that many planes (ignored when rows = 0) */
   int32_t kick_threads;    /* threads (particles) per interpolate+kick+drift block: 128 or 256 */
-  int32_t deposit_warps;   /* warps per deposit block (one block per tile of up to 4 x 8 mesh rows): 1..8 */
+  int32_t deposit_warps;   /* warps per deposit block (each warp owns a tile of up to 2 x 4 mesh rows): 1..8 */
   int32_t green_fused;     /* PM_FP32 cloud-in-cell on a power-of-two mesh of 16..512 only: 1 transforms the
                               planes of constant z with batched 2D transforms and does the z transforms, the
                               Green multiplication and the inverse z transforms in one kernel between them
